@@ -1,0 +1,148 @@
+/*
+ * sign.h — C ABI of the GB300 filtered Newton-Schulz sign solver.
+ *
+ * Computes S = sign(A) for a square sparse matrix A with the filtered
+ * Newton-Schulz iteration (NSF) of Wu et al., "Two iterative algorithms for
+ * the matrix sign function based on the adaptive filtering technology",
+ * arXiv 2210.03356, Alg. 3.2.1:
+ *
+ *   X_1 = A (optionally A / ||A||_1);  e_1 = ||I - X_1^2||
+ *   while e_k > tol:
+ *       Xbar_{k+1} = 1/2 X_k (3I - X_k^2)            (two sparse products)
+ *       X_{k+1}    = Xbar_{k+1} - F_{k+1}            (drop entries below tau_k)
+ *       e_{k+1}    = ||I - X_{k+1}^2||
+ *
+ * The bound on ||F_k|| is c4*tol while e_k >= switch_resid and
+ * 3/4 e_k^2 / (3x + x^3), x = ||X_k||, afterwards (Eq. 1.18; Sec. 3.2 and
+ * Sec. 4 for the two phases). Norms are Frobenius divided by sqrt(n).
+ *
+ * Every step runs in CUDA kernels on the current device; there is no CPU
+ * fallback. Matrices are CSR with
+ *   rowptr int64[n+1] (rowptr[0] = 0, non-decreasing),
+ *   col    int32[nnz] (0 <= col < n, strictly ascending inside a row),
+ *   val    double[nnz] (finite).
+ *
+ * Conventions
+ *   - Every function returns a sign_status; no C++ exception crosses the ABI.
+ *     On failure sign_last_error() describes the last error of the calling
+ *     thread (valid until that thread's next call).
+ *   - sign_create copies its inputs; the caller keeps ownership of its arrays.
+ *   - The CUDA stream passed to sign_create is borrowed, not owned. All work of
+ *     a handle is ordered on it; sign_solve and sign_get_csr return after the
+ *     stream has finished the work they queued.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *   - Device memory is allocated stream-ordered (cudaMallocAsync) on the
+ *     handle's stream and released by sign_destroy or the end of a solve.
+ */
+#ifndef GB300_SIGN_H
+#define GB300_SIGN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sign_ctx *sign_t; /* opaque, owned by the library */
+
+typedef enum {
+  SIGN_OK = 0,        /* converged: ||X^2 - I||_F/sqrt(n) <= tol            */
+  SIGN_EINVAL = 1,    /* invalid argument or malformed CSR                   */
+  SIGN_ENOMEM = 2,    /* device allocation failed                            */
+  SIGN_ENOTCONV = 3,  /* max_iter updates done without reaching tol          */
+  SIGN_EDIVERGED = 4, /* residual non-finite or above div_limit (Sec. 2:
+                         convergence needs ||I - X_1^2|| < 1)                 */
+  SIGN_ECUDA = 5,     /* a CUDA runtime call failed                          */
+  SIGN_ETIMEOUT = 6,  /* reserved: a bounded device wait gave up             */
+  SIGN_ESTATE = 7     /* call out of order (e.g. sign_get_csr before solve)  */
+} sign_status;
+
+typedef enum {
+  SIGN_FILTER_NONE = 0,  /* plain Newton-Schulz: nothing dropped             */
+  SIGN_FILTER_EXACT = 1, /* drop the largest set of smallest magnitudes whose
+                            Frobenius norm fits the budget; equal magnitudes
+                            are dropped or kept together                     */
+  SIGN_FILTER_BOUND = 2  /* drop |x| < b / sqrt(nnz(Xbar)) (never exceeds b) */
+} sign_filter;
+
+typedef enum {
+  SIGN_PREC_FP64 = 0,  /* FP64 values and fused multiply-adds throughout     */
+  SIGN_PREC_MIXED = 1  /* FP32 values and accumulation until the residual is
+                          below fp32_until, then FP64; norms, budgets and
+                          thresholds are FP64 in both stages                 */
+} sign_prec;
+
+typedef struct {
+  double tol;          /* stop when ||X^2 - I||_F/sqrt(n) <= tol; 1e-8       */
+  int filter;          /* sign_filter; SIGN_FILTER_EXACT                     */
+  double c4;           /* fixed budget factor (Sec. 3.2); 1e-4               */
+  double switch_resid; /* fixed -> Eq. (1.18) budget below this; 1e-6        */
+  int max_iter;        /* maximum Newton-Schulz updates; 100                 */
+  int prec;            /* sign_prec; SIGN_PREC_FP64                          */
+  double fp32_until;   /* FP32 stage ends below this residual; 1e-4          */
+  double dense_frac;   /* reserved for the dense path; 0.25                  */
+  int scale_1norm;     /* 1: X_1 = A/||A||_1 (default); 0: X_1 = A (paper)   */
+  double div_limit;    /* residual above this = diverged; 1e6                */
+} sign_opts;
+
+/* Per-iteration record, filled by sign_solve when non-NULL. The arrays are
+ * caller-owned with `cap` slots each (any may be NULL). Record k describes
+ * the check of iterate X_k (k = 0 is X_1 of the paper) and, when an update
+ * followed it, the filter that formed the next iterate. In the mixed mode
+ * the iterate at the switch has two records (FP32 check, then FP64 check). */
+typedef struct {
+  int iters;          /* out: Newton-Schulz updates performed                */
+  int status;         /* out: sign_status of this matrix                     */
+  double resid;       /* out: final ||X^2 - I||_F / sqrt(n)                  */
+  int64_t nnz_final;  /* out: nnz of the result                              */
+  int cap;            /* in: slots in each array below                       */
+  int count;          /* out: records written                                */
+  int64_t *nnz_x;     /* nnz of X_k                                          */
+  int64_t *nnz_t;     /* nnz of T = X_k X_k                                  */
+  double *resid_k;    /* ||T - I||_F / sqrt(n)                               */
+  double *xnorm_k;    /* ||X_k||_F / sqrt(n)                                 */
+  double *beta_k;     /* RMS budget for the next filter (0 if none)          */
+  double *tau_k;      /* element threshold of the next filter                */
+  double *fnorm_k;    /* ||F||_F dropped by the next filter                  */
+  int64_t *nnz_bar;   /* nnz of Xbar before the next filter                  */
+  int *prec_k;        /* 32 or 64                                            */
+} sign_info;
+
+/* Fills *o with the defaults listed in sign_opts. */
+void sign_default_opts(sign_opts *o);
+
+/* Creates a handle holding a copy of A (n x n, CSR as above).
+ * on_device = 1: the three arrays are device pointers; 0: host pointers.
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ * The CSR is validated on the device; malformed input gives SIGN_EINVAL. */
+sign_status sign_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col,
+                        const double *val, int on_device, void *cuda_stream, sign_t *out);
+
+/* Runs the solve (Alg. 3.2.1). Returns the matrix's status (SIGN_OK,
+ * SIGN_ENOTCONV or SIGN_EDIVERGED leave a result to read) or an error. */
+sign_status sign_solve(sign_t h, const sign_opts *o, sign_info *info);
+
+/* Solves `count` independent matrices together: their rows are processed in
+ * the same kernel launches, each matrix with its own residual, budget,
+ * threshold, stage and stopping test, so every result is the one a lone
+ * sign_solve gives. All work goes to hs[0]'s stream. infos may be NULL or an
+ * array of `count`. Returns SIGN_OK if the batch ran (per-matrix outcomes are
+ * in infos[i].status) or an error that applies to the whole call. */
+sign_status sign_solve_batch(sign_t *hs, int count, const sign_opts *o, sign_info *infos);
+
+/* Copies the result out. Call first with row_ptr = col = val = NULL to get
+ * *nnz_out; then with buffers of n+1, nnz and nnz elements (device pointers if
+ * on_device = 1). Columns are ascending inside each row. */
+sign_status sign_get_csr(sign_t h, int64_t *nnz_out, int64_t *row_ptr, int32_t *col, double *val,
+                         int on_device);
+
+/* Releases the handle and its device memory (NULL is ignored). */
+void sign_destroy(sign_t h);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *sign_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,191 @@
+"""GB300-native filtered Newton-Schulz sign solver (arXiv 2210.03356, Alg. 3.2.1).
+
+Python binding of the C ABI in include/sign.h. The functions here only move
+arguments across the ABI; every step of a solve runs in the CUDA library
+``libsign_gb300.so`` (built in-tree by ``build.build()``).
+
+    import paper_2210_03356_gb300 as sg
+    res = sg.solve(csr, tol=1e-8, filter="exact")        # host numpy CSR in
+    res.rowptr, res.col, res.val, res.iters, res.trace    # host numpy CSR out
+
+Inputs are objects with ``n``, ``rowptr`` (int64), ``col`` (int32) and ``val``
+(float64): numpy arrays (copied host to device) or CUDA torch tensors (copied
+device to device).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _native as N
+from ._native import (SIGN_EDIVERGED, SIGN_EINVAL, SIGN_ENOTCONV, SIGN_OK, SignError,
+                      default_opts, last_error, load)
+
+__all__ = ["solve", "solve_batch", "Handle", "Result", "default_opts", "load", "last_error",
+           "SignError", "SIGN_OK", "SIGN_EINVAL", "SIGN_ENOTCONV", "SIGN_EDIVERGED"]
+
+_TRACE = [("nnz_x", np.int64), ("nnz_t", np.int64), ("resid_k", np.float64),
+          ("xnorm_k", np.float64), ("beta_k", np.float64), ("tau_k", np.float64),
+          ("fnorm_k", np.float64), ("nnz_bar", np.int64), ("prec_k", np.int32)]
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _ptr(x):
+    if _is_torch_cuda(x) or hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(C.c_void_p)
+
+
+def current_stream():
+    """The torch current CUDA stream handle, or None (legacy default stream)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return None
+
+
+@dataclass
+class Result:
+    status: int
+    iters: int
+    resid: float
+    rowptr: object
+    col: object
+    val: object
+    trace: dict = field(default_factory=dict)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+
+class _Info:
+    """A sign_info with numpy-owned trace arrays."""
+
+    def __init__(self, cap: int):
+        self.arrays = {k: np.zeros(max(cap, 1), dtype=t) for k, t in _TRACE}
+        self.s = N.sign_info()
+        self.s.cap = cap
+        for k, t in _TRACE:
+            setattr(self.s, k, self.arrays[k].ctypes.data_as(C.POINTER(np.ctypeslib.as_ctypes_type(t))))
+
+    def trace(self, s=None) -> dict:
+        c = (s if s is not None else self.s).count
+        return {k: v[:c].copy() for k, v in self.arrays.items()}
+
+
+class Handle:
+    """One matrix on the device (sign_create / sign_destroy)."""
+
+    def __init__(self, a, stream=None):
+        L = load()
+        self.n = int(a.n)
+        on_dev = _is_torch_cuda(a.val)
+        if not on_dev:
+            self._keep = (np.ascontiguousarray(a.rowptr, dtype=np.int64),
+                          np.ascontiguousarray(a.col, dtype=np.int32),
+                          np.ascontiguousarray(a.val, dtype=np.float64))
+        else:
+            self._keep = (a.rowptr.contiguous(), a.col.contiguous(), a.val.contiguous())
+        rp, col, val = self._keep
+        nnz = int(rp[-1])
+        self.stream = stream if stream is not None else current_stream()
+        h = N.sign_t()
+        st = L.sign_create(self.n, nnz, _ptr(rp), _ptr(col), _ptr(val), int(on_dev), self.stream,
+                           C.byref(h))
+        if st != SIGN_OK:
+            raise SignError(st, "sign_create")
+        self.h = h
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sign_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def result(self, device=False):
+        """sign_get_csr: host numpy arrays, or CUDA torch tensors if device=True."""
+        L = load()
+        nnz = C.c_int64()
+        st = L.sign_get_csr(self.h, C.byref(nnz), None, None, None, 0)
+        if st != SIGN_OK:
+            raise SignError(st, "sign_get_csr")
+        if device:
+            import torch
+            rp = torch.empty(self.n + 1, dtype=torch.int64, device="cuda")
+            col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device="cuda")
+            val = torch.empty(max(nnz.value, 1), dtype=torch.float64, device="cuda")
+            st = L.sign_get_csr(self.h, C.byref(nnz), _ptr(rp), _ptr(col), _ptr(val), 1)
+            col, val = col[:nnz.value], val[:nnz.value]
+        else:
+            rp = np.empty(self.n + 1, dtype=np.int64)
+            col = np.empty(max(nnz.value, 1), dtype=np.int32)
+            val = np.empty(max(nnz.value, 1), dtype=np.float64)
+            st = L.sign_get_csr(self.h, C.byref(nnz), _ptr(rp), _ptr(col), _ptr(val), 0)
+            col, val = col[:nnz.value], val[:nnz.value]
+        if st != SIGN_OK:
+            raise SignError(st, "sign_get_csr")
+        return rp, col, val
+
+
+def _opts(opts, kw):
+    if opts is None:
+        return default_opts(**kw)
+    for k, v in kw.items():
+        setattr(opts, k, v)
+    return opts
+
+
+def solve(a, opts=None, trace_cap: int = 256, device_out: bool = False, stream=None,
+          **kw) -> Result:
+    """sign_create + sign_solve + sign_get_csr for one matrix."""
+    o = _opts(opts, kw)
+    with Handle(a, stream) as h:
+        info = _Info(trace_cap)
+        st = load().sign_solve(h.h, C.byref(o), C.byref(info.s))
+        if st not in (SIGN_OK, SIGN_ENOTCONV, SIGN_EDIVERGED):
+            raise SignError(st, "sign_solve")
+        rp, col, val = h.result(device=device_out)
+        return Result(info.s.status, info.s.iters, info.s.resid, rp, col, val, info.trace())
+
+
+def solve_batch(mats, opts=None, trace_cap: int = 256, device_out: bool = False, stream=None,
+                **kw) -> list[Result]:
+    """sign_solve_batch: all matrices in the same kernel launches, one result each."""
+    o = _opts(opts, kw)
+    hs = [Handle(a, stream) for a in mats]
+    try:
+        arr = (N.sign_t * len(hs))(*[h.h for h in hs])
+        infos = [_Info(trace_cap) for _ in hs]
+        iarr = (N.sign_info * len(hs))(*[i.s for i in infos])
+        st = load().sign_solve_batch(arr, len(hs), C.byref(o), iarr)
+        if st != SIGN_OK:
+            raise SignError(st, "sign_solve_batch")
+        out = []
+        for h, i, s in zip(hs, infos, iarr):  # iarr holds the filled copies of the structs
+            rp, col, val = h.result(device=device_out)
+            out.append(Result(s.status, s.iters, s.resid, rp, col, val, i.trace(s)))
+        return out
+    finally:
+        for h in hs:
+            h.close()

@@ -1,0 +1,95 @@
+"""ctypes binding of include/sign.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library; if the library is missing
+this module raises instead of computing anything itself.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsign_gb300.so")
+
+SIGN_OK, SIGN_EINVAL, SIGN_ENOMEM, SIGN_ENOTCONV, SIGN_EDIVERGED, SIGN_ECUDA, SIGN_ETIMEOUT, \
+    SIGN_ESTATE = range(8)
+SIGN_FILTER_NONE, SIGN_FILTER_EXACT, SIGN_FILTER_BOUND = 0, 1, 2
+SIGN_PREC_FP64, SIGN_PREC_MIXED = 0, 1
+STATUS_NAMES = ["SIGN_OK", "SIGN_EINVAL", "SIGN_ENOMEM", "SIGN_ENOTCONV", "SIGN_EDIVERGED",
+                "SIGN_ECUDA", "SIGN_ETIMEOUT", "SIGN_ESTATE"]
+
+
+class sign_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("filter", C.c_int), ("c4", C.c_double),
+                ("switch_resid", C.c_double), ("max_iter", C.c_int), ("prec", C.c_int),
+                ("fp32_until", C.c_double), ("dense_frac", C.c_double), ("scale_1norm", C.c_int),
+                ("div_limit", C.c_double)]
+
+
+class sign_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int), ("resid", C.c_double),
+                ("nnz_final", C.c_int64), ("cap", C.c_int), ("count", C.c_int),
+                ("nnz_x", C.POINTER(C.c_int64)), ("nnz_t", C.POINTER(C.c_int64)),
+                ("resid_k", C.POINTER(C.c_double)), ("xnorm_k", C.POINTER(C.c_double)),
+                ("beta_k", C.POINTER(C.c_double)), ("tau_k", C.POINTER(C.c_double)),
+                ("fnorm_k", C.POINTER(C.c_double)), ("nnz_bar", C.POINTER(C.c_int64)),
+                ("prec_k", C.POINTER(C.c_int))]
+
+
+sign_t = C.c_void_p
+_P64, _P32, _PD = C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_double)
+
+# name -> (restype, argtypes); every function declared in include/sign.h
+SIGNATURES = {
+    "sign_default_opts": (None, [C.POINTER(sign_opts)]),
+    "sign_create": (C.c_int, [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                              C.c_void_p, C.POINTER(sign_t)]),
+    "sign_solve": (C.c_int, [sign_t, C.POINTER(sign_opts), C.POINTER(sign_info)]),
+    "sign_solve_batch": (C.c_int, [C.POINTER(sign_t), C.c_int, C.POINTER(sign_opts),
+                                   C.POINTER(sign_info)]),
+    "sign_get_csr": (C.c_int, [sign_t, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_int]),
+    "sign_destroy": (None, [sign_t]),
+    "sign_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return load().sign_last_error().decode()
+
+
+class SignError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 8 else status}: "
+                         f"{last_error()}")
+
+
+def default_opts(**kw) -> sign_opts:
+    o = sign_opts()
+    load().sign_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "filter" and isinstance(v, str):
+            v = {"none": 0, "exact": 1, "bound": 2}[v]
+        if k == "prec" and isinstance(v, str):
+            v = {"fp64": 0, "mixed": 1}[v]
+        setattr(o, k, v)
+    return o

@@ -1,0 +1,67 @@
+// Internal helpers shared by the CUDA translation units of the sign solver.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <stdexcept>
+#include <string>
+
+namespace sgn {
+
+// Error raised inside the library; converted to a sign_status at the ABI.
+struct Error : std::runtime_error {
+  int status;
+  Error(int s, const std::string &m) : std::runtime_error(m), status(s) {}
+};
+
+#define SGN_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      throw ::sgn::Error(e_ == cudaErrorMemoryAllocation ? 2 : 5,                           \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));               \
+  } while (0)
+
+#define SGN_LAUNCH_CHECK() SGN_CUDA(cudaGetLastError())
+
+// Shared-memory row accumulators: rows whose column range fits WARP_W slots
+// are handled by one warp; wider rows by one CTA in chunks of CTA_W slots.
+constexpr int WARP_W = 1024;
+constexpr int WARPS_PER_CTA = 4;
+constexpr int CTA_THREADS = 256;
+template <typename T> struct CtaW;
+template <> struct CtaW<double> { static constexpr int value = 12288; };
+template <> struct CtaW<float> { static constexpr int value = 20480; };
+// symbolic pass of wide rows: one bitmap covering up to SYM_BITS columns
+constexpr int SYM_BITS = 1 << 18;
+constexpr int K_BATCH = 256;  // k entries whose B-row ranges are located at once
+
+// Grow-only device buffer, allocated stream-ordered.
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    cap = 0;
+  }
+  void *ensure(size_t bytes, cudaStream_t st) {
+    if (bytes <= cap && p) return p;
+    release();
+    s = st;
+    size_t want = bytes + bytes / 4 + 256;
+    SGN_CUDA(cudaMallocAsync(&p, want, st));
+    cap = want;
+    return p;
+  }
+  template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+}  // namespace sgn

@@ -1,0 +1,119 @@
+// Host-side launchers of the sign solver's CUDA kernels. Every pointer is a
+// device pointer; every launcher enqueues on `s` and returns immediately.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sgn {
+
+// ---------------------------------------------------------------- csr utils
+// flag |= 1 if the CSR is malformed (rowptr not monotone or not ending at
+// nnz, column out of range or not strictly ascending, value not finite).
+void launch_validate(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col,
+                     const double *val, int *flag, cudaStream_t s);
+
+// out[0] = 0, out[i+1] = sum_{r<=i} cnt[r] for i < n. tmp holds
+// scan_tmp_elems(n) int64 values.
+int64_t scan_tmp_elems(int64_t n);
+void launch_scan(int64_t n, const int64_t *cnt, int64_t *out, int64_t *tmp, cudaStream_t s);
+
+// One block of a block-diagonal assembly: rows [row0, row0+nrows) of a source
+// CSR whose column indices are shifted by col_shift on the way.
+struct AsmBlock {
+  const int64_t *rp;
+  const int32_t *col;
+  const void *val;
+  int64_t row0, nrows, col_shift;
+  int val_f32;  // source values are float
+};
+// Writes dst rowptr (n_dst+1) from the blocks, laid out one after another.
+// blocks/boff are device arrays: boff[b] is the first destination row of
+// block b (boff[nblocks] = n_dst). lens is an int64[n_dst] scratch.
+void launch_assemble_rows(int nblocks, const AsmBlock *blocks, const int64_t *boff, int64_t n_dst,
+                          int64_t *lens, int64_t *dst_rp, int64_t *scan_tmp, cudaStream_t s);
+void launch_assemble_vals(int nblocks, const AsmBlock *blocks, const int64_t *boff, int64_t n_dst,
+                          const int64_t *dst_rp, int32_t *dst_col, void *dst_val, int dst_f32,
+                          cudaStream_t s);
+
+// seg[r] = matrix of row r, from moff (nb+1 row offsets).
+void launch_fill_seg(int nb, const int64_t *moff, int64_t n, int32_t *seg, cudaStream_t s);
+
+// Reproducible ||A||_1 per matrix (see kernels_csr.cu) and X_1 = A / ||A||_1.
+// work: 2*n + 4*nb uint64 scratch. norm: double[nb].
+void launch_onenorm(int nb, const int64_t *moff, const int32_t *seg, int64_t n, const int64_t *rp,
+                    const int32_t *col, const double *val, unsigned long long *work, double *norm,
+                    cudaStream_t s);
+void launch_scale(int64_t n, const int32_t *seg, const int64_t *rp, double *val,
+                  const double *norm, cudaStream_t s);
+
+// out[m] = rp[moff[m]] for m = 0..nb (entry offsets of the matrices).
+void launch_gather_offsets(int nb, const int64_t *moff, const int64_t *rp, int64_t *out,
+                           cudaStream_t s);
+
+// out[m*ncomp + c] = sum over rows r of matrix m of part[r*ncomp + c], in a
+// fixed order (deterministic).
+void launch_seg_reduce(int nb, const int64_t *moff, const double *part, int ncomp, double *out,
+                       cudaStream_t s);
+
+// ---------------------------------------------------------------- spgemm
+enum ProductMode { MODE_SQUARE = 0, MODE_UPDATE = 1 };
+
+// Per row i of C = A B (rows of inactive matrices are empty): the column
+// range [lo, lo+len) of the row (including A's own row in MODE_UPDATE),
+// sets cnt[i] = 0 for empty rows and appends non-empty rows to the warp list
+// (len <= WARP_W) or the CTA list. counters[0], counters[1] are the list
+// lengths (zeroed by the caller).
+void launch_bounds(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
+                   const int32_t *bcol, const int32_t *seg, const int *active, int mode,
+                   int32_t *lo, int32_t *len, int64_t *cnt, int32_t *wlist, int32_t *clist,
+                   int *counters, cudaStream_t s);
+// Exact nnz of every listed row (symbolic product).
+void launch_symbolic(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
+                     const int32_t *bcol, int mode, const int32_t *lo, const int32_t *len,
+                     const int32_t *wlist, const int32_t *clist, const int *counters,
+                     int64_t *cnt, cudaStream_t s);
+// Numeric product into the pattern of crp. MODE_SQUARE: C = A A, and
+// part[2i] = sum_j (C_ij - delta_ij)^2, part[2i+1] = sum_k a_ik^2.
+// MODE_UPDATE: C = 1.5 A - 0.5 A B.
+template <typename T>
+void launch_numeric(int64_t n, const int64_t *arp, const int32_t *acol, const T *aval,
+                    const int64_t *brp, const int32_t *bcol, const T *bval, int mode,
+                    const int32_t *lo, const int32_t *len, const int32_t *wlist,
+                    const int32_t *clist, const int *counters, const int64_t *crp, int32_t *ccol,
+                    T *cval, double *part, cudaStream_t s);
+
+// ---------------------------------------------------------------- filter
+// Per-matrix scalars after the check of the current iterates.
+struct MatScalars {
+  double r;      // ||T - I||_F / sqrt(n)
+  double x;      // ||X||_F / sqrt(n)
+  double beta;   // RMS budget (Eq. 1.18 or c4 * tol_stage)
+  double b;      // absolute Frobenius budget sqrt(n) * beta
+  double tau;    // element threshold of the filter
+  double fnorm;  // ||F||_F dropped
+  int64_t nnz_x, nnz_t, nnz_bar, nnz_hat;
+};
+// From sums[2m] = sum (T-I)^2, sums[2m+1] = sum X^2: r, x, beta, b.
+void launch_matrix_scalars(int nb, const int64_t *moff, const double *sums, double c4,
+                           double tol_stage, double switch_resid, MatScalars *ms, cudaStream_t s);
+
+// Threshold selection (EXACT) for every active matrix; writes ms[m].tau.
+// Scratch sizes: see select_scratch_bytes.
+size_t select_scratch_bytes(int nb, int64_t nnz);
+void launch_select_exact(int nb, const int64_t *eoff, const int *active, int64_t nnz,
+                         const void *val, int val_f32, MatScalars *ms, void *scratch,
+                         cudaStream_t s);
+// BOUND: tau = b / sqrt(nnz_bar) per matrix.
+void launch_select_bound(int nb, const int *active, MatScalars *ms, cudaStream_t s);
+
+// Keeps |x| >= tau_m and x != 0 (filter != NONE), counts kept entries per
+// row and the dropped sum of squares per row.
+void launch_filter_count(int64_t n, const int32_t *seg, const int *active, const int64_t *rp,
+                         const void *val, int val_f32, const MatScalars *ms, int64_t *cnt,
+                         double *dropped, cudaStream_t s);
+void launch_filter_write(int64_t n, const int32_t *seg, const int *active, const int64_t *rp,
+                         const int32_t *col, const void *val, int val_f32, const MatScalars *ms,
+                         const int64_t *orp, int32_t *ocol, void *oval, cudaStream_t s);
+
+}  // namespace sgn

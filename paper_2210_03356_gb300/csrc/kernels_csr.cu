@@ -1,0 +1,379 @@
+// CSR utilities of the sign solver: validation, the reproducible 1-norm and
+// scaling of step a1, prefix scans, block-diagonal assembly of batches and
+// deterministic per-matrix reductions.
+#include <cfloat>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sgn {
+
+namespace {
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+template <typename F>
+__device__ __forceinline__ void for_each_row_warp(int64_t n, F f) {
+  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nwarps) f(r);
+}
+
+int grid_for(int64_t items, int per_block, int cap = 152 * 16) {
+  int64_t g = (items + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return int(g);
+}
+
+// ------------------------------------------------------------ validation
+__global__ void k_validate(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col,
+                           const double *val, int *flag) {
+  int lane = lane_id();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (rp[0] != 0 || rp[n] != nnz) atomicOr(flag, 1);
+  }
+  for_each_row_warp(n, [&](int64_t r) {
+    int64_t b = rp[r], e = rp[r + 1];
+    if (e < b || b < 0 || e > nnz) {
+      if (lane == 0) atomicOr(flag, 1);
+      return;
+    }
+    bool bad = false;
+    for (int64_t p = b + lane; p < e; p += 32) {
+      int32_t c = col[p];
+      if (c < 0 || c >= n) bad = true;
+      if (p > b && col[p - 1] >= c) bad = true;
+      if (!isfinite(val[p])) bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
+  });
+}
+
+// ------------------------------------------------------------ scan
+constexpr int SCAN_T = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_T * SCAN_ITEMS;
+
+// Exclusive scan of v over the block (1024 threads); *total gets the sum.
+__device__ int64_t block_excl_scan(int64_t v, int64_t *sm, int64_t *total) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sm[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t t = sm[lane];
+    int64_t u = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, u, o);
+      if (lane >= o) u += y;
+    }
+    sm[lane] = u - t;
+    if (lane == 31) sm[32] = u;
+  }
+  __syncthreads();
+  int64_t r = sm[warp] + x - v;
+  if (total) *total = sm[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(int64_t n, const int64_t *cnt,
+                                                        int64_t *tmp) {
+  __shared__ int64_t sm[33];
+  int64_t base = int64_t(blockIdx.x) * SCAN_TILE + int64_t(threadIdx.x) * SCAN_ITEMS;
+  int64_t v = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i)
+    if (base + i < n) v += cnt[base + i];
+  int64_t total;
+  block_excl_scan(v, sm, &total);
+  if (threadIdx.x == 0) tmp[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_blocks(int64_t nblocks, int64_t *tmp) {
+  __shared__ int64_t sm[33];
+  int64_t carry = 0;
+  for (int64_t b0 = 0; b0 < nblocks; b0 += SCAN_T) {
+    int64_t i = b0 + threadIdx.x;
+    int64_t v = i < nblocks ? tmp[i] : 0;
+    int64_t total;
+    int64_t ex = block_excl_scan(v, sm, &total);
+    if (i < nblocks) tmp[i] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_final(int64_t n, const int64_t *cnt,
+                                                       const int64_t *tmp, int64_t *out) {
+  __shared__ int64_t sm[33];
+  int64_t base = int64_t(blockIdx.x) * SCAN_TILE + int64_t(threadIdx.x) * SCAN_ITEMS;
+  int64_t v[SCAN_ITEMS];
+  int64_t s = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    v[i] = base + i < n ? cnt[base + i] : 0;
+    s += v[i];
+  }
+  int64_t ex = block_excl_scan(s, sm, nullptr) + tmp[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    ex += v[i];
+    if (base + i < n) out[base + i + 1] = ex;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+}
+
+// ------------------------------------------------------------ assembly
+__device__ __forceinline__ int find_block(const int64_t *off, int nb, int64_t r) {
+  int lo = 0, hi = nb;  // off[lo] <= r < off[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (off[mid] <= r)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_asm_lens(int nblocks, const AsmBlock *blocks, const int64_t *boff, int64_t n,
+                           int64_t *lens) {
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += int64_t(gridDim.x) * blockDim.x) {
+    int b = find_block(boff, nblocks, r);
+    const AsmBlock &B = blocks[b];
+    int64_t sr = B.row0 + (r - boff[b]);
+    lens[r] = B.rp[sr + 1] - B.rp[sr];
+  }
+}
+
+__global__ void k_asm_vals(int nblocks, const AsmBlock *blocks, const int64_t *boff, int64_t n,
+                           const int64_t *drp, int32_t *dcol, void *dval, int dst_f32) {
+  int lane = lane_id();
+  for_each_row_warp(n, [&](int64_t r) {
+    int b = find_block(boff, nblocks, r);
+    const AsmBlock B = blocks[b];
+    int64_t sr = B.row0 + (r - boff[b]);
+    int64_t sb = B.rp[sr], se = B.rp[sr + 1], d = drp[r];
+    for (int64_t p = sb + lane; p < se; p += 32) {
+      dcol[d + (p - sb)] = int32_t(B.col[p] + B.col_shift);
+      double v = B.val_f32 ? double(static_cast<const float *>(B.val)[p])
+                           : static_cast<const double *>(B.val)[p];
+      if (dst_f32)
+        static_cast<float *>(dval)[d + (p - sb)] = __double2float_rn(v);
+      else
+        static_cast<double *>(dval)[d + (p - sb)] = v;
+    }
+  });
+}
+
+__global__ void k_fill_seg(int nb, const int64_t *moff, int64_t n, int32_t *seg) {
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += int64_t(gridDim.x) * blockDim.x)
+    seg[r] = find_block(moff, nb, r);
+}
+
+// ------------------------------------------------------------ 1-norm (step a1)
+// ||A||_1 = max_j sum_i |a_ij|, made independent of summation order: with
+// M = max |a_ij| < 2^e every |a_ij| is put on the grid 2^(e-62) by one
+// round-to-nearest-even conversion of the exact product |a| * 2^(62-e); the
+// column sums are exact 128-bit integers (two 64-bit atomics with carry), and
+// the largest one, hi * 2^64 + lo, comes back as
+// ((double)hi * 2^64 + (double)lo) * 2^(e-62).
+
+__device__ __forceinline__ void add128(unsigned long long *lohi, unsigned long long q) {
+  unsigned long long old = atomicAdd(&lohi[0], q);
+  if (old + q < old) atomicAdd(&lohi[1], 1ULL);
+}
+
+__global__ void k_absmax(int64_t n, const int32_t *seg, const int64_t *rp, const double *val,
+                         unsigned long long *mmax) {
+  int lane = lane_id();
+  for_each_row_warp(n, [&](int64_t r) {
+    double m = 0.0;
+    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) m = fmax(m, fabs(val[p]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && m > 0.0)
+      atomicMax(&mmax[seg[r]], (unsigned long long)__double_as_longlong(m));
+  });
+}
+
+__global__ void k_colsum(int64_t n, const int32_t *seg, const int64_t *rp, const int32_t *col,
+                         const double *val, const unsigned long long *mmax,
+                         unsigned long long *colsum) {
+  int lane = lane_id();
+  for_each_row_warp(n, [&](int64_t r) {
+    double M = __longlong_as_double((long long)mmax[seg[r]]);
+    if (M == 0.0) return;
+    int e;
+    frexp(M, &e);
+    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) {
+      unsigned long long q = __double2ull_rn(ldexp(fabs(val[p]), 62 - e));
+      if (q) add128(&colsum[2 * int64_t(col[p])], q);
+    }
+  });
+}
+
+__global__ void k_colmax_hi(int64_t n, const int32_t *seg, const unsigned long long *colsum,
+                            unsigned long long *maxhi) {
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n;
+       j += int64_t(gridDim.x) * blockDim.x)
+    if (colsum[2 * j] | colsum[2 * j + 1]) atomicMax(&maxhi[seg[j]], colsum[2 * j + 1]);
+}
+
+__global__ void k_colmax_lo(int64_t n, const int32_t *seg, const unsigned long long *colsum,
+                            const unsigned long long *maxhi, unsigned long long *maxlo) {
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n;
+       j += int64_t(gridDim.x) * blockDim.x)
+    if (colsum[2 * j + 1] == maxhi[seg[j]]) atomicMax(&maxlo[seg[j]], colsum[2 * j]);
+}
+
+__global__ void k_norm_final(int nb, const unsigned long long *mmax,
+                             const unsigned long long *maxhi, const unsigned long long *maxlo,
+                             double *norm) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nb) return;
+  double M = __longlong_as_double((long long)mmax[m]);
+  if (M == 0.0) {
+    norm[m] = 0.0;
+    return;
+  }
+  int e;
+  frexp(M, &e);
+  double d = __dadd_rn(__dmul_rn(__ull2double_rn(maxhi[m]), 18446744073709551616.0),
+                       __ull2double_rn(maxlo[m]));
+  norm[m] = ldexp(d, e - 62);
+}
+
+__global__ void k_scale(int64_t n, const int32_t *seg, const int64_t *rp, double *val,
+                        const double *norm) {
+  int lane = lane_id();
+  for_each_row_warp(n, [&](int64_t r) {
+    double s = norm[seg[r]];
+    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) val[p] = __ddiv_rn(val[p], s);
+  });
+}
+
+__global__ void k_gather_offsets(int nb, const int64_t *moff, const int64_t *rp, int64_t *out) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m <= nb) out[m] = rp[moff[m]];
+}
+
+// ------------------------------------------------------------ reductions
+constexpr int RED_T = 256;
+__global__ void __launch_bounds__(RED_T) k_seg_reduce(const int64_t *moff, const double *part,
+                                                      int ncomp, double *out) {
+  __shared__ double sm[RED_T];
+  int m = blockIdx.x;
+  int64_t b = moff[m], e = moff[m + 1];
+  for (int c = 0; c < ncomp; ++c) {
+    double acc = 0.0;
+    for (int64_t r = b + threadIdx.x; r < e; r += RED_T) acc += part[r * ncomp + c];
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = RED_T / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[int64_t(m) * ncomp + c] = sm[0];
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+void launch_validate(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col,
+                     const double *val, int *flag, cudaStream_t s) {
+  k_validate<<<grid_for(n, 8), 256, 0, s>>>(n, nnz, rp, col, val, flag);
+  SGN_LAUNCH_CHECK();
+}
+
+int64_t scan_tmp_elems(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+void launch_scan(int64_t n, const int64_t *cnt, int64_t *out, int64_t *tmp, cudaStream_t s) {
+  int64_t nblocks = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (nblocks == 0) {
+    SGN_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+    return;
+  }
+  k_scan_reduce<<<unsigned(nblocks), SCAN_T, 0, s>>>(n, cnt, tmp);
+  SGN_LAUNCH_CHECK();
+  k_scan_blocks<<<1, SCAN_T, 0, s>>>(nblocks, tmp);
+  SGN_LAUNCH_CHECK();
+  k_scan_final<<<unsigned(nblocks), SCAN_T, 0, s>>>(n, cnt, tmp, out);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_assemble_rows(int nblocks, const AsmBlock *blocks, const int64_t *boff, int64_t n_dst,
+                          int64_t *lens, int64_t *dst_rp, int64_t *scan_tmp, cudaStream_t s) {
+  if (n_dst > 0) {
+    k_asm_lens<<<grid_for(n_dst, 256), 256, 0, s>>>(nblocks, blocks, boff, n_dst, lens);
+    SGN_LAUNCH_CHECK();
+  }
+  launch_scan(n_dst, lens, dst_rp, scan_tmp, s);
+}
+
+void launch_assemble_vals(int nblocks, const AsmBlock *blocks, const int64_t *boff, int64_t n_dst,
+                          const int64_t *dst_rp, int32_t *dst_col, void *dst_val, int dst_f32,
+                          cudaStream_t s) {
+  if (n_dst == 0) return;
+  k_asm_vals<<<grid_for(n_dst, 8), 256, 0, s>>>(nblocks, blocks, boff, n_dst, dst_rp, dst_col,
+                                                 dst_val, dst_f32);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_fill_seg(int nb, const int64_t *moff, int64_t n, int32_t *seg, cudaStream_t s) {
+  if (n == 0) return;
+  k_fill_seg<<<grid_for(n, 256), 256, 0, s>>>(nb, moff, n, seg);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_onenorm(int nb, const int64_t *moff, const int32_t *seg, int64_t n, const int64_t *rp,
+                    const int32_t *col, const double *val, unsigned long long *work, double *norm,
+                    cudaStream_t s) {
+  (void)moff;
+  unsigned long long *colsum = work;            // 2n
+  unsigned long long *mmax = work + 2 * n;      // nb
+  unsigned long long *maxhi = mmax + nb;        // nb
+  unsigned long long *maxlo = maxhi + nb;       // nb
+  SGN_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned long long) * size_t(2 * n + 3 * nb), s));
+  k_absmax<<<grid_for(n, 8), 256, 0, s>>>(n, seg, rp, val, mmax);
+  SGN_LAUNCH_CHECK();
+  k_colsum<<<grid_for(n, 8), 256, 0, s>>>(n, seg, rp, col, val, mmax, colsum);
+  SGN_LAUNCH_CHECK();
+  k_colmax_hi<<<grid_for(n, 256), 256, 0, s>>>(n, seg, colsum, maxhi);
+  SGN_LAUNCH_CHECK();
+  k_colmax_lo<<<grid_for(n, 256), 256, 0, s>>>(n, seg, colsum, maxhi, maxlo);
+  SGN_LAUNCH_CHECK();
+  k_norm_final<<<(nb + 127) / 128, 128, 0, s>>>(nb, mmax, maxhi, maxlo, norm);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_scale(int64_t n, const int32_t *seg, const int64_t *rp, double *val,
+                  const double *norm, cudaStream_t s) {
+  k_scale<<<grid_for(n, 8), 256, 0, s>>>(n, seg, rp, val, norm);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_gather_offsets(int nb, const int64_t *moff, const int64_t *rp, int64_t *out,
+                           cudaStream_t s) {
+  k_gather_offsets<<<(nb + 1 + 127) / 128, 128, 0, s>>>(nb, moff, rp, out);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_seg_reduce(int nb, const int64_t *moff, const double *part, int ncomp, double *out,
+                       cudaStream_t s) {
+  if (nb == 0) return;
+  k_seg_reduce<<<nb, RED_T, 0, s>>>(moff, part, ncomp, out);
+  SGN_LAUNCH_CHECK();
+}
+
+}  // namespace sgn

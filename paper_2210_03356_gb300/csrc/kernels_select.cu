@@ -1,0 +1,420 @@
+// Budget, element threshold and filter of the NSF step (steps a4-a6).
+//
+// Budget (Eq. 1.18 with the fixed phase of Sec. 3.2 / Sec. 4): the RMS budget
+// is c4 * tol_stage while r >= switch_resid, else 3/4 r^2 / (3x + x^3), with
+// r = ||T - I||_F / sqrt(n) and x = ||X||_F / sqrt(n) of the current iterate;
+// the filter's absolute Frobenius bound is b = sqrt(n) * beta.
+//
+// EXACT threshold: tau is the smallest magnitude v such that the squares of
+// all entries with |x| <= v sum to more than b^2 (every |x| < tau is
+// dropped, every |x| >= tau kept, so equal magnitudes share their fate); if
+// all entries with |x| <= b fit, tau is the smallest magnitude above b
+// (+inf if there is none). It is found by a radix select on the IEEE bit
+// pattern of |x| (positive doubles order like unsigned integers): a
+// histogram of the top 16 bits over a 1024-bucket window below b, then six
+// 8-bit digits over the candidates of the crossing bucket. The squares are
+// summed as exact 128-bit integers q = round((x/b)^2 * 2^62), b^2 = 2^62, so
+// the decision does not depend on the order of the additions.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sgn {
+
+namespace {
+
+constexpr int NB0 = 1024;        // level-0 buckets
+constexpr int NDIG = 256;        // digit buckets
+constexpr unsigned long long ONE62 = 1ULL << 62;
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__global__ void k_matrix_scalars(int nb, const int64_t *moff, const double *sums, double c4,
+                                 double tol_stage, double switch_resid, MatScalars *ms) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nb) return;
+  double sn = __dsqrt_rn(double(moff[m + 1] - moff[m]));
+  double r = __ddiv_rn(__dsqrt_rn(sums[2 * m]), sn);
+  double x = __ddiv_rn(__dsqrt_rn(sums[2 * m + 1]), sn);
+  double beta;
+  if (r >= switch_resid)
+    beta = __dmul_rn(c4, tol_stage);
+  else
+    beta = __ddiv_rn(__dmul_rn(__dmul_rn(0.75, r), r),
+                     __dadd_rn(__dmul_rn(3.0, x), __dmul_rn(__dmul_rn(x, x), x)));
+  ms[m].r = r;
+  ms[m].x = x;
+  ms[m].beta = beta;
+  ms[m].b = __dmul_rn(sn, beta);
+}
+
+__global__ void k_select_bound(int nb, const int *active, MatScalars *ms) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nb || !active[m]) return;
+  int64_t c = ms[m].nnz_bar;
+  ms[m].tau = c > 0 ? __ddiv_rn(ms[m].b, __dsqrt_rn(double(c))) : __longlong_as_double(0x7ff0000000000000LL);
+}
+
+// ------------------------------------------------------------ EXACT select
+struct SelState {
+  unsigned long long prefix;  // key bits known so far
+  unsigned long long below_lo, below_hi;  // 128-bit sum of q strictly below the prefix range
+  unsigned long long cand_cnt, cand_off, cursor;
+  int found;  // 1: a crossing exists; 0: everything <= b fits
+  int pad;
+};
+
+struct SelScratch {
+  unsigned long long *hist0;    // nb * NB0 * 3  (count, lo, hi)
+  unsigned long long *hdig;     // nb * NDIG * 3
+  unsigned long long *minabove; // nb
+  SelState *st;                 // nb
+  unsigned long long *cand;     // nnz
+  unsigned long long *cand_off; // nb + 1
+};
+
+__host__ __device__ inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+SelScratch carve(void *base, int nb, int64_t nnz) {
+  char *p = static_cast<char *>(base);
+  SelScratch s;
+  s.hist0 = reinterpret_cast<unsigned long long *>(p);
+  p += align_up(size_t(nb) * NB0 * 3 * 8);
+  s.hdig = reinterpret_cast<unsigned long long *>(p);
+  p += align_up(size_t(nb) * NDIG * 3 * 8);
+  s.minabove = reinterpret_cast<unsigned long long *>(p);
+  p += align_up(size_t(nb) * 8);
+  s.st = reinterpret_cast<SelState *>(p);
+  p += align_up(size_t(nb) * sizeof(SelState));
+  s.cand_off = reinterpret_cast<unsigned long long *>(p);
+  p += align_up(size_t(nb + 1) * 8);
+  s.cand = reinterpret_cast<unsigned long long *>(p);
+  (void)nnz;
+  return s;
+}
+
+__device__ __forceinline__ int find_seg(const int64_t *off, int nb, int64_t p) {
+  int lo = 0, hi = nb;  // off[lo] <= p < off[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (off[mid] <= p)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ unsigned long long key_of(const void *val, int f32, int64_t p) {
+  double x = f32 ? double(static_cast<const float *>(val)[p]) : static_cast<const double *>(val)[p];
+  return (unsigned long long)__double_as_longlong(fabs(x));
+}
+
+// q = round((x / b)^2 * 2^62), x <= b; 0 when b == 0.
+__device__ __forceinline__ unsigned long long qval(unsigned long long key, double b) {
+  if (b == 0.0) return 0ULL;
+  double r = __ddiv_rn(__longlong_as_double((long long)key), b);
+  return __double2ull_rn(__dmul_rn(__dmul_rn(r, r), 4611686018427387904.0));
+}
+
+__device__ __forceinline__ void add128(unsigned long long *lohi, unsigned long long q) {
+  unsigned long long old = atomicAdd(&lohi[0], q);
+  if (old + q < old) atomicAdd(&lohi[1], 1ULL);
+}
+
+__device__ __forceinline__ int bucket0(unsigned long long key, unsigned long long bkey) {
+  long long base = (long long)(bkey >> 48) - (NB0 - 1);
+  long long t = (long long)(key >> 48);
+  if (base < 0) base = 0;
+  return t <= base ? 0 : int(t - base);
+}
+
+__global__ void k_sel_hist0(int nb, const int64_t *eoff, const int *active, int64_t nnz,
+                            const void *val, int f32, const MatScalars *ms, SelScratch sc) {
+  for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < nnz;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    int m = find_seg(eoff, nb, p);
+    if (!active[m]) continue;
+    double b = ms[m].b;
+    unsigned long long bkey = (unsigned long long)__double_as_longlong(b);
+    unsigned long long key = key_of(val, f32, p);
+    if (key > bkey) {
+      atomicMin(&sc.minabove[m], key);
+      continue;
+    }
+    unsigned long long *h = sc.hist0 + (size_t(m) * NB0 + bucket0(key, bkey)) * 3;
+    atomicAdd(&h[0], 1ULL);
+    unsigned long long q = qval(key, b);
+    if (q) add128(h + 1, q);
+  }
+}
+
+__device__ __forceinline__ void u128_add(unsigned long long &lo, unsigned long long &hi,
+                                         unsigned long long alo, unsigned long long ahi) {
+  unsigned long long o = lo;
+  lo += alo;
+  hi += ahi + (lo < o ? 1ULL : 0ULL);
+}
+
+// (hi, lo) > 2^62 ?
+__device__ __forceinline__ bool exceeds(unsigned long long lo, unsigned long long hi) {
+  return hi != 0ULL || lo > ONE62;
+}
+
+__global__ void k_sel_find0(int nb, const int *active, const MatScalars *ms, SelScratch sc) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nb) return;
+  SelState st = {};
+  if (active[m]) {
+    unsigned long long bkey = (unsigned long long)__double_as_longlong(ms[m].b);
+    long long base = (long long)(bkey >> 48) - (NB0 - 1);
+    if (base < 0) base = 0;
+    unsigned long long lo = 0, hi = 0;
+    const unsigned long long *h = sc.hist0 + size_t(m) * NB0 * 3;
+    for (int c = 0; c < NB0; ++c) {
+      unsigned long long nlo = lo, nhi = hi;
+      u128_add(nlo, nhi, h[3 * c + 1], h[3 * c + 2]);
+      if (exceeds(nlo, nhi)) {
+        st.found = 1;
+        st.prefix = (unsigned long long)(base + c) << 48;
+        st.below_lo = lo;
+        st.below_hi = hi;
+        st.cand_cnt = h[3 * c];
+        break;
+      }
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  sc.st[m] = st;
+}
+
+__global__ void k_sel_candoff(int nb, SelScratch sc) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  unsigned long long off = 0;
+  for (int m = 0; m < nb; ++m) {
+    sc.cand_off[m] = off;
+    sc.st[m].cand_off = off;
+    off += sc.st[m].cand_cnt;
+  }
+  sc.cand_off[nb] = off;
+}
+
+__global__ void k_sel_extract(int nb, const int64_t *eoff, const int *active, int64_t nnz,
+                              const void *val, int f32, const MatScalars *ms, SelScratch sc) {
+  for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < nnz;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    int m = find_seg(eoff, nb, p);
+    if (!active[m] || !sc.st[m].found) continue;
+    unsigned long long bkey = (unsigned long long)__double_as_longlong(ms[m].b);
+    unsigned long long key = key_of(val, f32, p);
+    if (key > bkey || (key >> 48) != (sc.st[m].prefix >> 48)) continue;
+    unsigned long long slot = atomicAdd(&sc.st[m].cursor, 1ULL);
+    sc.cand[sc.st[m].cand_off + slot] = key;
+  }
+}
+
+__global__ void k_sel_hist_digit(int nb, const MatScalars *ms, SelScratch sc, int shift) {
+  unsigned long long total = sc.cand_off[nb];
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nb;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (sc.cand_off[mid] <= i)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    int m = lo;
+    unsigned long long key = sc.cand[i];
+    unsigned long long pre = sc.st[m].prefix;
+    if ((key >> (shift + 8)) != (pre >> (shift + 8))) continue;
+    int d = int((key >> shift) & 255ULL);
+    unsigned long long *h = sc.hdig + (size_t(m) * NDIG + d) * 3;
+    atomicAdd(&h[0], 1ULL);
+    unsigned long long q = qval(key, ms[m].b);
+    if (q) add128(h + 1, q);
+  }
+}
+
+__global__ void k_sel_find_digit(int nb, SelScratch sc, int shift) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nb) return;
+  SelState &st = sc.st[m];
+  if (!st.found) return;
+  const unsigned long long *h = sc.hdig + size_t(m) * NDIG * 3;
+  unsigned long long lo = st.below_lo, hi = st.below_hi;
+  for (int d = 0; d < NDIG; ++d) {
+    unsigned long long nlo = lo, nhi = hi;
+    u128_add(nlo, nhi, h[3 * d + 1], h[3 * d + 2]);
+    if (exceeds(nlo, nhi) && h[3 * d] > 0) {
+      st.prefix |= (unsigned long long)d << shift;
+      st.below_lo = lo;
+      st.below_hi = hi;
+      return;
+    }
+    lo = nlo;
+    hi = nhi;
+  }
+}
+
+__global__ void k_sel_final(int nb, const int *active, SelScratch sc, MatScalars *ms) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nb || !active[m]) return;
+  if (sc.st[m].found) {
+    ms[m].tau = __longlong_as_double((long long)sc.st[m].prefix);
+  } else {
+    unsigned long long k = sc.minabove[m];
+    ms[m].tau = k == ~0ULL ? __longlong_as_double(0x7ff0000000000000LL)
+                           : __longlong_as_double((long long)k);
+  }
+}
+
+// ------------------------------------------------------------ filter
+__global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
+                               const int64_t *rp, const void *val, int f32,
+                               const MatScalars *ms, int64_t *cnt, double *dropped) {
+  int lane = lane_id();
+  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nwarps) {
+    int m = seg[r];
+    double tau = ms[m].tau;
+    int c = 0;
+    double d2 = 0.0;
+    if (active[m]) {
+      for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) {
+        double x = f32 ? double(static_cast<const float *>(val)[p])
+                       : static_cast<const double *>(val)[p];
+        double ax = fabs(x);
+        if (ax >= tau && x != 0.0)
+          ++c;
+        else
+          d2 += x * x;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    }
+    if (lane == 0) {
+      cnt[r] = c;
+      dropped[r] = d2;
+    }
+  }
+}
+
+__global__ void k_filter_write(int64_t n, const int32_t *seg, const int *active,
+                               const int64_t *rp, const int32_t *col, const void *val, int f32,
+                               const MatScalars *ms, const int64_t *orp, int32_t *ocol,
+                               void *oval) {
+  int lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nwarps) {
+    int m = seg[r];
+    if (!active[m]) continue;
+    double tau = ms[m].tau;
+    int64_t out = orp[r];
+    int64_t b = rp[r], e = rp[r + 1];
+    for (int64_t p0 = b; p0 < e; p0 += 32) {
+      int64_t p = p0 + lane;
+      bool keep = false;
+      double x = 0.0;
+      if (p < e) {
+        x = f32 ? double(static_cast<const float *>(val)[p]) : static_cast<const double *>(val)[p];
+        keep = fabs(x) >= tau && x != 0.0;
+      }
+      unsigned m32 = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        int64_t pos = out + __popc(m32 & lt);
+        ocol[pos] = col[p];
+        if (f32)
+          static_cast<float *>(oval)[pos] = static_cast<const float *>(val)[p];
+        else
+          static_cast<double *>(oval)[pos] = x;
+      }
+      out += __popc(m32);
+    }
+  }
+}
+
+int grid_for(int64_t items, int per_block, int cap = 152 * 16) {
+  int64_t g = (items + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return int(g);
+}
+
+}  // namespace
+
+void launch_matrix_scalars(int nb, const int64_t *moff, const double *sums, double c4,
+                           double tol_stage, double switch_resid, MatScalars *ms, cudaStream_t s) {
+  k_matrix_scalars<<<(nb + 127) / 128, 128, 0, s>>>(nb, moff, sums, c4, tol_stage, switch_resid,
+                                                    ms);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_select_bound(int nb, const int *active, MatScalars *ms, cudaStream_t s) {
+  k_select_bound<<<(nb + 127) / 128, 128, 0, s>>>(nb, active, ms);
+  SGN_LAUNCH_CHECK();
+}
+
+size_t select_scratch_bytes(int nb, int64_t nnz) {
+  return align_up(size_t(nb) * NB0 * 3 * 8) + align_up(size_t(nb) * NDIG * 3 * 8) +
+         align_up(size_t(nb) * 8) + align_up(size_t(nb) * sizeof(SelState)) +
+         align_up(size_t(nb + 1) * 8) + align_up(size_t(nnz > 0 ? nnz : 1) * 8);
+}
+
+void launch_select_exact(int nb, const int64_t *eoff, const int *active, int64_t nnz,
+                         const void *val, int val_f32, MatScalars *ms, void *scratch,
+                         cudaStream_t s) {
+  SelScratch sc = carve(scratch, nb, nnz);
+  SGN_CUDA(cudaMemsetAsync(sc.hist0, 0, size_t(nb) * NB0 * 3 * 8, s));
+  SGN_CUDA(cudaMemsetAsync(sc.minabove, 0xff, size_t(nb) * 8, s));
+  int g = grid_for(nnz, 256);
+  if (nnz > 0) {
+    k_sel_hist0<<<g, 256, 0, s>>>(nb, eoff, active, nnz, val, val_f32, ms, sc);
+    SGN_LAUNCH_CHECK();
+  }
+  k_sel_find0<<<(nb + 127) / 128, 128, 0, s>>>(nb, active, ms, sc);
+  SGN_LAUNCH_CHECK();
+  k_sel_candoff<<<1, 32, 0, s>>>(nb, sc);
+  SGN_LAUNCH_CHECK();
+  if (nnz > 0) {
+    k_sel_extract<<<g, 256, 0, s>>>(nb, eoff, active, nnz, val, val_f32, ms, sc);
+    SGN_LAUNCH_CHECK();
+  }
+  for (int level = 0; level < 6; ++level) {
+    int shift = 40 - 8 * level;
+    SGN_CUDA(cudaMemsetAsync(sc.hdig, 0, size_t(nb) * NDIG * 3 * 8, s));
+    k_sel_hist_digit<<<grid_for(nnz, 256, 152 * 4), 256, 0, s>>>(nb, ms, sc, shift);
+    SGN_LAUNCH_CHECK();
+    k_sel_find_digit<<<(nb + 127) / 128, 128, 0, s>>>(nb, sc, shift);
+    SGN_LAUNCH_CHECK();
+  }
+  k_sel_final<<<(nb + 127) / 128, 128, 0, s>>>(nb, active, sc, ms);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_filter_count(int64_t n, const int32_t *seg, const int *active, const int64_t *rp,
+                         const void *val, int val_f32, const MatScalars *ms, int64_t *cnt,
+                         double *dropped, cudaStream_t s) {
+  if (n == 0) return;
+  k_filter_count<<<grid_for(n, 8), 256, 0, s>>>(n, seg, active, rp, val, val_f32, ms, cnt,
+                                                 dropped);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_filter_write(int64_t n, const int32_t *seg, const int *active, const int64_t *rp,
+                         const int32_t *col, const void *val, int val_f32, const MatScalars *ms,
+                         const int64_t *orp, int32_t *ocol, void *oval, cudaStream_t s) {
+  if (n == 0) return;
+  k_filter_write<<<grid_for(n, 8), 256, 0, s>>>(n, seg, active, rp, col, val, val_f32, ms, orp,
+                                                 ocol, oval);
+  SGN_LAUNCH_CHECK();
+}
+
+}  // namespace sgn

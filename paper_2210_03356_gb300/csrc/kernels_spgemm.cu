@@ -1,0 +1,565 @@
+// Row-wise sparse products of the Newton-Schulz step (steps a2 and a3):
+//   MODE_SQUARE:  T = X X, plus per-row partial sums for ||T - I||_F and ||X||_F
+//   MODE_UPDATE:  Xbar = 1.5 X - 0.5 X T   (= 1/2 X (3I - X^2), Alg. 3.2.1 step 3)
+//
+// Row i of C = A B is accumulated in shared memory over its column range
+// [lo_i, lo_i + len_i) (union of the ranges of the rows B_k, k in A_i), indexed
+// by column - lo_i, so the output comes out in ascending column order without
+// hashing or sorting. Rows with len <= WARP_W go to one warp each; wider rows
+// to one CTA each, in chunks of CTA_W columns.
+//
+// Accumulation order: the k of A_i are visited in ascending order, one at a
+// time; within one k the lanes (threads) stride over the entries of B_k,
+// whose columns are distinct, so no two lanes touch the same slot, and a
+// barrier separates consecutive k. Every slot therefore receives its
+// products in ascending k with one fused multiply-add each, starting from
+// +0: the result is the same bit for bit on every run and launch shape.
+#include <climits>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sgn {
+
+namespace {
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// 1.5 x - 0.5 p with each product and the difference rounded once.
+__device__ __forceinline__ double ns_combine(double x, double p) {
+  return __dsub_rn(__dmul_rn(1.5, x), __dmul_rn(0.5, p));
+}
+__device__ __forceinline__ float ns_combine(float x, float p) {
+  return __fsub_rn(__fmul_rn(1.5f, x), __fmul_rn(0.5f, p));
+}
+
+__device__ __forceinline__ int64_t lower_bound(const int32_t *a, int64_t lo, int64_t hi,
+                                               int64_t v) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < v)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// counters: [0] warp-list length, [1] CTA-list length, [2],[3] symbolic
+// queue heads, [4],[5] numeric queue heads.
+__global__ void k_bounds(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
+                         const int32_t *bcol, const int32_t *seg, const int *active, int mode,
+                         int32_t *lo, int32_t *len, int64_t *cnt, int32_t *wlist, int32_t *clist,
+                         int *counters) {
+  int lane = lane_id();
+  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nwarps) {
+    if (!active[seg[r]]) {
+      if (lane == 0) {
+        cnt[r] = 0;
+        len[r] = 0;
+        lo[r] = 0;
+      }
+      continue;
+    }
+    int32_t mn = INT_MAX, mx = -1;
+    for (int64_t p = arp[r] + lane; p < arp[r + 1]; p += 32) {
+      int32_t k = acol[p];
+      int64_t b0 = brp[k], b1 = brp[k + 1];
+      if (b1 > b0) {
+        mn = min(mn, bcol[b0]);
+        mx = max(mx, bcol[b1 - 1]);
+      }
+      if (mode == MODE_UPDATE) {
+        mn = min(mn, k);
+        mx = max(mx, k);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+      if (mx < 0) {
+        cnt[r] = 0;
+        len[r] = 0;
+        lo[r] = 0;
+      } else {
+        int32_t L = mx - mn + 1;
+        lo[r] = mn;
+        len[r] = L;
+        if (L <= WARP_W)
+          wlist[atomicAdd(&counters[0], 1)] = int32_t(r);
+        else
+          clist[atomicAdd(&counters[1], 1)] = int32_t(r);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- symbolic
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32)
+    k_sym_warp(const int64_t *arp, const int32_t *acol, const int64_t *brp, const int32_t *bcol,
+               int mode, const int32_t *lo, const int32_t *len, const int32_t *wlist,
+               int *counters, int64_t *cnt) {
+  __shared__ unsigned char flags[WARPS_PER_CTA][WARP_W];
+  int lane = lane_id(), w = threadIdx.x >> 5;
+  unsigned char *f = flags[w];
+  for (;;) {
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(&counters[2], 1);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    if (idx >= counters[0]) break;
+    int32_t r = wlist[idx];
+    int L = len[r];
+    int32_t c0 = lo[r];
+    for (int s = lane; s < L; s += 32) f[s] = 0;
+    __syncwarp();
+    int64_t a0 = arp[r], a1 = arp[r + 1];
+    if (a1 - a0 >= 16) {
+      for (int64_t p = a0 + lane; p < a1; p += 32) {
+        int32_t k = acol[p];
+        for (int64_t q = brp[k]; q < brp[k + 1]; ++q) f[bcol[q] - c0] = 1;
+      }
+    } else {
+      for (int64_t p = a0; p < a1; ++p) {
+        int32_t k = acol[p];
+        for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) f[bcol[q] - c0] = 1;
+      }
+    }
+    if (mode == MODE_UPDATE)
+      for (int64_t p = a0 + lane; p < a1; p += 32) f[acol[p] - c0] = 1;
+    __syncwarp();
+    int c = 0;
+    for (int s = lane; s < L; s += 32) c += f[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[r] = c;
+    __syncwarp();
+  }
+}
+
+constexpr int SYM_WORDS = SYM_BITS / 32;
+
+__global__ void __launch_bounds__(CTA_THREADS)
+    k_sym_cta(const int64_t *arp, const int32_t *acol, const int64_t *brp, const int32_t *bcol,
+              int mode, const int32_t *lo, const int32_t *len, const int32_t *clist,
+              int *counters, int64_t *cnt) {
+  extern __shared__ unsigned int bits[];  // SYM_WORDS
+  __shared__ int s_idx;
+  __shared__ int s_red[CTA_THREADS / 32];
+  int lane = lane_id(), w = threadIdx.x >> 5, nw = CTA_THREADS / 32;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(&counters[3], 1);
+    __syncthreads();
+    int idx = s_idx;
+    __syncthreads();
+    if (idx >= counters[1]) break;
+    int32_t r = clist[idx];
+    int64_t L = len[r];
+    int64_t base = lo[r];
+    int64_t a0 = arp[r], a1 = arp[r + 1];
+    bool multi = L > SYM_BITS;
+    int64_t total = 0;
+    for (int64_t c0 = base; c0 < base + L; c0 += SYM_BITS) {
+      int64_t W = min(int64_t(SYM_BITS), base + L - c0);
+      int nwords = int((W + 31) / 32);
+      for (int s = threadIdx.x; s < nwords; s += CTA_THREADS) bits[s] = 0u;
+      __syncthreads();
+      for (int64_t p = a0 + w; p < a1; p += nw) {
+        int32_t k = acol[p];
+        int64_t s = brp[k], e = brp[k + 1];
+        if (multi) {
+          s = lower_bound(bcol, s, e, c0);
+          e = lower_bound(bcol, s, e, c0 + W);
+        }
+        for (int64_t q = s + lane; q < e; q += 32) {
+          int64_t j = bcol[q] - c0;
+          atomicOr(&bits[j >> 5], 1u << (j & 31));
+        }
+      }
+      if (mode == MODE_UPDATE)
+        for (int64_t p = a0 + threadIdx.x; p < a1; p += CTA_THREADS) {
+          int64_t j = int64_t(acol[p]) - c0;
+          if (j >= 0 && j < W) atomicOr(&bits[j >> 5], 1u << (j & 31));
+        }
+      __syncthreads();
+      int c = 0;
+      for (int s = threadIdx.x; s < nwords; s += CTA_THREADS) c += __popc(bits[s]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+      if (lane == 0) s_red[w] = c;
+      __syncthreads();
+      for (int i = 0; i < nw; ++i) total += s_red[i];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) cnt[r] = total;
+  }
+}
+
+// ---------------------------------------------------------------- numeric
+template <typename T, int MODE>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32)
+    k_num_warp(const int64_t *arp, const int32_t *acol, const T *aval, const int64_t *brp,
+               const int32_t *bcol, const T *bval, const int32_t *lo, const int32_t *len,
+               const int32_t *wlist, int *counters, const int64_t *crp, int32_t *ccol, T *cval,
+               double *part) {
+  __shared__ T acc_all[WARPS_PER_CTA][WARP_W];
+  __shared__ unsigned char flags[WARPS_PER_CTA][WARP_W];
+  int lane = lane_id(), w = threadIdx.x >> 5;
+  T *acc = acc_all[w];
+  unsigned char *f = flags[w];
+  const unsigned lt = (1u << lane) - 1u;
+  for (;;) {
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(&counters[4], 1);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    if (idx >= counters[0]) break;
+    int32_t r = wlist[idx];
+    int L = len[r];
+    int32_t c0 = lo[r];
+    for (int s = lane; s < L; s += 32) {
+      acc[s] = T(0);
+      f[s] = 0;
+    }
+    __syncwarp();
+    int64_t a0 = arp[r], a1 = arp[r + 1];
+    for (int64_t p = a0; p < a1; ++p) {  // ascending k
+      int32_t k = acol[p];
+      T a = aval[p];
+      int64_t q1 = brp[k + 1];
+      for (int64_t q = brp[k] + lane; q < q1; q += 32) {
+        int j = bcol[q] - c0;
+        acc[j] = fma_rn(a, bval[q], acc[j]);
+        f[j] = 1;
+      }
+      __syncwarp();
+    }
+    if (MODE == MODE_UPDATE) {
+      for (int64_t p = a0 + lane; p < a1; p += 32) {
+        int j = acol[p] - c0;
+        acc[j] = ns_combine(aval[p], acc[j]);
+        f[j] = 3;
+      }
+      __syncwarp();
+    }
+    int64_t out = crp[r];
+    double rs = 0.0;
+    bool diag = false;
+    for (int s0 = 0; s0 < L; s0 += 32) {
+      int s = s0 + lane;
+      int fl = s < L ? f[s] : 0;
+      unsigned m = __ballot_sync(0xffffffffu, fl != 0);
+      if (fl) {
+        int64_t pos = out + __popc(m & lt);
+        int32_t cj = c0 + s;
+        T v = acc[s];
+        if (MODE == MODE_UPDATE && !(fl & 2)) v = ns_combine(T(0), v);
+        ccol[pos] = cj;
+        cval[pos] = v;
+        if (MODE == MODE_SQUARE) {
+          double d = double(v);
+          if (cj == r) {
+            d = d - 1.0;
+            diag = true;
+          }
+          rs += d * d;
+        }
+      }
+      out += __popc(m);
+    }
+    if (MODE == MODE_SQUARE) {
+      double xs = 0.0;
+      for (int64_t p = a0 + lane; p < a1; p += 32) {
+        double x = double(aval[p]);
+        xs += x * x;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        rs += __shfl_xor_sync(0xffffffffu, rs, o);
+        xs += __shfl_xor_sync(0xffffffffu, xs, o);
+      }
+      bool any_diag = __any_sync(0xffffffffu, diag);
+      if (lane == 0) {
+        part[2 * int64_t(r)] = any_diag ? rs : rs + 1.0;
+        part[2 * int64_t(r) + 1] = xs;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T>
+constexpr size_t num_cta_smem() {
+  return size_t(CtaW<T>::value) * (sizeof(T) + 1) + 2 * K_BATCH * sizeof(int64_t);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(CTA_THREADS)
+    k_num_cta(const int64_t *arp, const int32_t *acol, const T *aval, const int64_t *brp,
+              const int32_t *bcol, const T *bval, const int32_t *lo, const int32_t *len,
+              const int32_t *clist, int *counters, const int64_t *crp, int32_t *ccol, T *cval,
+              double *part) {
+  constexpr int CW = CtaW<T>::value;
+  constexpr int NW = CTA_THREADS / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int64_t *ks = reinterpret_cast<int64_t *>(smem_raw);
+  int64_t *ke = ks + K_BATCH;
+  T *acc = reinterpret_cast<T *>(ke + K_BATCH);
+  unsigned char *f = reinterpret_cast<unsigned char *>(acc + CW);
+  __shared__ int s_idx;
+  __shared__ int s_cnt[NW];
+  __shared__ double s_red[2][NW];
+  int lane = lane_id(), w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(&counters[5], 1);
+    __syncthreads();
+    int idx = s_idx;
+    __syncthreads();
+    if (idx >= counters[1]) break;
+    int32_t r = clist[idx];
+    int64_t L = len[r];
+    int64_t base = lo[r];
+    int64_t a0 = arp[r], a1 = arp[r + 1];
+    int64_t nA = a1 - a0;
+    bool multi = L > CW;
+    int64_t out = crp[r];
+    double rs = 0.0;
+    bool diag = false;
+    for (int64_t c0 = base; c0 < base + L; c0 += CW) {
+      int W = int(min(int64_t(CW), base + L - c0));
+      for (int s = threadIdx.x; s < W; s += CTA_THREADS) {
+        acc[s] = T(0);
+        f[s] = 0;
+      }
+      __syncthreads();
+      for (int64_t kb = 0; kb < nA; kb += K_BATCH) {
+        int nk = int(min(int64_t(K_BATCH), nA - kb));
+        if (threadIdx.x < nk) {
+          int32_t k = acol[a0 + kb + threadIdx.x];
+          int64_t s = brp[k], e = brp[k + 1];
+          if (multi) {
+            s = lower_bound(bcol, s, e, c0);
+            e = lower_bound(bcol, s, e, c0 + W);
+          }
+          ks[threadIdx.x] = s;
+          ke[threadIdx.x] = e;
+        }
+        __syncthreads();
+        for (int t = 0; t < nk; ++t) {  // ascending k
+          T a = aval[a0 + kb + t];
+          int64_t e = ke[t];
+          for (int64_t q = ks[t] + threadIdx.x; q < e; q += CTA_THREADS) {
+            int j = int(bcol[q] - c0);
+            acc[j] = fma_rn(a, bval[q], acc[j]);
+            f[j] = 1;
+          }
+          __syncthreads();
+        }
+      }
+      if (MODE == MODE_UPDATE) {
+        for (int64_t p = a0 + threadIdx.x; p < a1; p += CTA_THREADS) {
+          int64_t j = int64_t(acol[p]) - c0;
+          if (j >= 0 && j < W) {
+            acc[j] = ns_combine(aval[p], acc[j]);
+            f[j] = 3;
+          }
+        }
+        __syncthreads();
+      }
+      // ordered emission: round g covers words g*NW .. g*NW+NW-1, warp w one word
+      for (int s0 = 0; s0 < W; s0 += 32 * NW) {
+        int s = s0 + w * 32 + lane;
+        int fl = s < W ? f[s] : 0;
+        unsigned m = __ballot_sync(0xffffffffu, fl != 0);
+        if (lane == 0) s_cnt[w] = __popc(m);
+        __syncthreads();
+        int64_t wbase = out;
+        int64_t round_total = 0;
+        for (int i = 0; i < NW; ++i) {
+          if (i < w) wbase += s_cnt[i];
+          round_total += s_cnt[i];
+        }
+        if (fl) {
+          int64_t pos = wbase + __popc(m & lt);
+          int64_t cj = c0 + s;
+          T v = acc[s];
+          if (MODE == MODE_UPDATE && !(fl & 2)) v = ns_combine(T(0), v);
+          ccol[pos] = int32_t(cj);
+          cval[pos] = v;
+          if (MODE == MODE_SQUARE) {
+            double d = double(v);
+            if (cj == r) {
+              d = d - 1.0;
+              diag = true;
+            }
+            rs += d * d;
+          }
+        }
+        out += round_total;
+        __syncthreads();
+      }
+    }
+    if (MODE == MODE_SQUARE) {
+      double xs = 0.0;
+      for (int64_t p = a0 + threadIdx.x; p < a1; p += CTA_THREADS) {
+        double x = double(aval[p]);
+        xs += x * x;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        rs += __shfl_xor_sync(0xffffffffu, rs, o);
+        xs += __shfl_xor_sync(0xffffffffu, xs, o);
+      }
+      int any_diag = __syncthreads_or(diag ? 1 : 0);
+      if (lane == 0) {
+        s_red[0][w] = rs;
+        s_red[1][w] = xs;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < NW; ++i) {
+          a += s_red[0][i];
+          b += s_red[1][i];
+        }
+        part[2 * int64_t(r)] = any_diag ? a : a + 1.0;
+        part[2 * int64_t(r) + 1] = b;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Rows of T = X X with an empty pattern still contribute to the norms:
+// (0 - 1)^2 = 1 for the missing diagonal, and sum_k a_ik^2 for ||X||.
+template <typename T>
+__global__ void k_part_empty(int64_t n, const int64_t *arp, const T *aval, const int32_t *len,
+                             double *part) {
+  int lane = lane_id();
+  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nwarps) {
+    if (len[r] != 0) continue;
+    double xs = 0.0;
+    for (int64_t p = arp[r] + lane; p < arp[r + 1]; p += 32) {
+      double x = double(aval[p]);
+      xs += x * x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, o);
+    if (lane == 0) {
+      part[2 * r] = 1.0;
+      part[2 * r + 1] = xs;
+    }
+  }
+}
+
+int g_sms = 0;
+int sm_count() {
+  if (!g_sms) {
+    int dev = 0;
+    SGN_CUDA(cudaGetDevice(&dev));
+    SGN_CUDA(cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return g_sms;
+}
+
+int grid_cap(int64_t items, int per_block, int per_sm) {
+  int64_t g = (items + per_block - 1) / per_block;
+  int64_t cap = int64_t(sm_count()) * per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return int(g);
+}
+
+}  // namespace
+
+void launch_bounds(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
+                   const int32_t *bcol, const int32_t *seg, const int *active, int mode,
+                   int32_t *lo, int32_t *len, int64_t *cnt, int32_t *wlist, int32_t *clist,
+                   int *counters, cudaStream_t s) {
+  if (n == 0) return;
+  k_bounds<<<grid_cap(n, 8, 16), 256, 0, s>>>(n, arp, acol, brp, bcol, seg, active, mode, lo,
+                                               len, cnt, wlist, clist, counters);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_symbolic(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
+                     const int32_t *bcol, int mode, const int32_t *lo, const int32_t *len,
+                     const int32_t *wlist, const int32_t *clist, const int *counters,
+                     int64_t *cnt, cudaStream_t s) {
+  if (n == 0) return;
+  int *ctr = const_cast<int *>(counters);
+  k_sym_warp<<<grid_cap(n, WARPS_PER_CTA, 12), WARPS_PER_CTA * 32, 0, s>>>(
+      arp, acol, brp, bcol, mode, lo, len, wlist, ctr, cnt);
+  SGN_LAUNCH_CHECK();
+  static bool attr = false;
+  size_t sm = size_t(SYM_WORDS) * 4;
+  if (!attr) {
+    SGN_CUDA(cudaFuncSetAttribute(k_sym_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+    attr = true;
+  }
+  k_sym_cta<<<grid_cap(n, 1, 4), CTA_THREADS, sm, s>>>(arp, acol, brp, bcol, mode, lo, len, clist,
+                                                       ctr, cnt);
+  SGN_LAUNCH_CHECK();
+}
+
+template <typename T, int MODE>
+static void num_launch(int64_t n, const int64_t *arp, const int32_t *acol, const T *aval,
+                       const int64_t *brp, const int32_t *bcol, const T *bval, const int32_t *lo,
+                       const int32_t *len, const int32_t *wlist, const int32_t *clist, int *ctr,
+                       const int64_t *crp, int32_t *ccol, T *cval, double *part, cudaStream_t s) {
+  k_num_warp<T, MODE><<<grid_cap(n, WARPS_PER_CTA, 6), WARPS_PER_CTA * 32, 0, s>>>(
+      arp, acol, aval, brp, bcol, bval, lo, len, wlist, ctr, crp, ccol, cval, part);
+  SGN_LAUNCH_CHECK();
+  static bool attr = false;
+  constexpr size_t sm = num_cta_smem<T>();
+  if (!attr) {
+    SGN_CUDA(cudaFuncSetAttribute(k_num_cta<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(sm)));
+    attr = true;
+  }
+  k_num_cta<T, MODE><<<grid_cap(n, 1, 2), CTA_THREADS, sm, s>>>(
+      arp, acol, aval, brp, bcol, bval, lo, len, clist, ctr, crp, ccol, cval, part);
+  SGN_LAUNCH_CHECK();
+}
+
+template <typename T>
+void launch_numeric(int64_t n, const int64_t *arp, const int32_t *acol, const T *aval,
+                    const int64_t *brp, const int32_t *bcol, const T *bval, int mode,
+                    const int32_t *lo, const int32_t *len, const int32_t *wlist,
+                    const int32_t *clist, const int *counters, const int64_t *crp, int32_t *ccol,
+                    T *cval, double *part, cudaStream_t s) {
+  if (n == 0) return;
+  int *ctr = const_cast<int *>(counters);
+  if (mode == MODE_SQUARE) {
+    k_part_empty<T><<<grid_cap(n, 8, 16), 256, 0, s>>>(n, arp, aval, len, part);
+    SGN_LAUNCH_CHECK();
+  }
+  if (mode == MODE_SQUARE)
+    num_launch<T, MODE_SQUARE>(n, arp, acol, aval, brp, bcol, bval, lo, len, wlist, clist, ctr,
+                               crp, ccol, cval, part, s);
+  else
+    num_launch<T, MODE_UPDATE>(n, arp, acol, aval, brp, bcol, bval, lo, len, wlist, clist, ctr,
+                               crp, ccol, cval, part, s);
+}
+
+template void launch_numeric<double>(int64_t, const int64_t *, const int32_t *, const double *,
+                                     const int64_t *, const int32_t *, const double *, int,
+                                     const int32_t *, const int32_t *, const int32_t *,
+                                     const int32_t *, const int *, const int64_t *, int32_t *,
+                                     double *, double *, cudaStream_t);
+template void launch_numeric<float>(int64_t, const int64_t *, const int32_t *, const float *,
+                                    const int64_t *, const int32_t *, const float *, int,
+                                    const int32_t *, const int32_t *, const int32_t *,
+                                    const int32_t *, const int *, const int64_t *, int32_t *,
+                                    float *, double *, cudaStream_t);
+
+}  // namespace sgn

@@ -1,0 +1,618 @@
+// C ABI and solve driver of the filtered Newton-Schulz sign solver.
+//
+// A solve (Alg. 3.2.1) is a loop of rounds. The matrices of a batch live in
+// stages, one per precision (FP32 for the first part of the mixed mode,
+// FP64 otherwise); a stage holds its matrices as one block-diagonal CSR with
+// global column indices, so every kernel launch serves all of them. Each
+// round, each non-empty stage:
+//   1. checks its iterates: T = X X and, per matrix, r = ||T - I||_F/sqrt(n),
+//      x = ||X||_F/sqrt(n) and the budget (steps a2, a4);
+//   2. per matrix: stops (r <= tol, step a7), diverges, runs out of updates,
+//      moves from FP32 to FP64 (r < fp32_until, step a8), or updates;
+//   3. for the updating matrices: Xbar = 1.5 X - 0.5 X T (step a3), the
+//      threshold (step a5) and the filter with CSR compaction (step a6).
+// A matrix that stops is copied out to its handle; the stage is rebuilt
+// without it at the next round. Per-matrix control flow is exactly that of a
+// lone solve, so every result is independent of the batch it ran in.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/sign.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace sgn;
+
+namespace {
+
+thread_local std::string g_err;
+
+// ------------------------------------------------------------------ CSR
+template <typename T>
+struct Csr {
+  int64_t n = 0, nnz = 0;
+  DevBuf rp, col, val;
+  int64_t *d_rp() const { return rp.as<int64_t>(); }
+  int32_t *d_col() const { return col.as<int32_t>(); }
+  T *d_val() const { return val.as<T>(); }
+  void ensure(int64_t rows, int64_t nz, cudaStream_t s) {
+    n = rows;
+    nnz = nz;
+    rp.ensure(sizeof(int64_t) * size_t(rows + 1), s);
+    col.ensure(sizeof(int32_t) * size_t(nz > 0 ? nz : 1), s);
+    val.ensure(sizeof(T) * size_t(nz > 0 ? nz : 1), s);
+  }
+  void swap(Csr &o) {
+    std::swap(n, o.n);
+    std::swap(nnz, o.nnz);
+    std::swap(rp.p, o.rp.p);
+    std::swap(rp.cap, o.rp.cap);
+    std::swap(rp.s, o.rp.s);
+    std::swap(col.p, o.col.p);
+    std::swap(col.cap, o.col.cap);
+    std::swap(col.s, o.col.s);
+    std::swap(val.p, o.val.p);
+    std::swap(val.cap, o.val.cap);
+    std::swap(val.s, o.val.s);
+  }
+};
+
+}  // namespace
+
+struct sign_ctx {
+  int64_t n = 0, nnz = 0;
+  cudaStream_t stream = nullptr;
+  Csr<double> a;       // input copy
+  Csr<double> result;  // last result
+  bool has_result = false;
+};
+
+namespace {
+
+template <typename T> constexpr int is_f32() { return sizeof(T) == 4; }
+
+void sync(cudaStream_t s) { SGN_CUDA(cudaStreamSynchronize(s)); }
+
+template <typename T>
+void d2h(T *dst, const void *src, size_t count, cudaStream_t s) {
+  SGN_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * count, cudaMemcpyDeviceToHost, s));
+}
+template <typename T>
+void h2d(void *dst, const T *src, size_t count, cudaStream_t s) {
+  SGN_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+}
+
+// Per-matrix bookkeeping of one solve call.
+struct MatState {
+  sign_t h = nullptr;
+  sign_info *info = nullptr;
+  int k = 0;            // updates done
+  int status = -1;      // -1 running, else sign_status
+  double resid = NAN;
+  int trace_count = 0;
+};
+
+void trace_put(MatState &ms, int64_t nnz_x, int64_t nnz_t, double r, double x, int prec) {
+  sign_info *in = ms.info;
+  if (!in) return;
+  int k = ms.trace_count;
+  if (k >= in->cap) return;
+  ms.trace_count++;
+  if (in->nnz_x) in->nnz_x[k] = nnz_x;
+  if (in->nnz_t) in->nnz_t[k] = nnz_t;
+  if (in->resid_k) in->resid_k[k] = r;
+  if (in->xnorm_k) in->xnorm_k[k] = x;
+  if (in->beta_k) in->beta_k[k] = 0.0;
+  if (in->tau_k) in->tau_k[k] = 0.0;
+  if (in->fnorm_k) in->fnorm_k[k] = 0.0;
+  if (in->nnz_bar) in->nnz_bar[k] = 0;
+  if (in->prec_k) in->prec_k[k] = prec;
+}
+
+void trace_filter(MatState &ms, double beta, double tau, double fnorm, int64_t nnz_bar) {
+  sign_info *in = ms.info;
+  if (!in || ms.trace_count == 0 || ms.trace_count > in->cap) return;
+  int k = ms.trace_count - 1;
+  if (in->beta_k) in->beta_k[k] = beta;
+  if (in->tau_k) in->tau_k[k] = tau;
+  if (in->fnorm_k) in->fnorm_k[k] = fnorm;
+  if (in->nnz_bar) in->nnz_bar[k] = nnz_bar;
+}
+
+// A matrix's rows taken out of a stage (moved to FP64 or pending assembly).
+struct Parked {
+  int mat;
+  Csr<double> x;  // its rows, local column indices
+};
+
+// Shared scratch of one solve call.
+struct Work {
+  DevBuf lo, len, cnt, wlist, clist, counters, part, scan_tmp, eoff, sums, ms, active, sel,
+      asm_blocks, asm_off, asm_lens, dropped, norm_work, norm;
+};
+
+template <typename T>
+struct Stage {
+  int prec = sizeof(T) == 4 ? 32 : 64;
+  std::vector<int> mats;          // matrix ids, in row order
+  std::vector<int64_t> moff;      // row offsets (host), size mats+1
+  DevBuf d_moff, d_seg;
+  Csr<T> X, Tm, Xb, Xh;
+  bool rebuild = false;           // membership changed: reassemble X
+  std::vector<Parked *> incoming; // matrices entering at the next rebuild
+};
+
+struct Solver {
+  cudaStream_t s;
+  sign_opts o;
+  std::vector<MatState> m;
+  Work w;
+  std::vector<std::unique_ptr<Parked>> parked_store;
+
+  // ---------------------------------------------------------------- helpers
+  void set_layout(std::vector<int64_t> &moff, const std::vector<int> &mats, DevBuf &d_moff,
+                  DevBuf &d_seg) {
+    moff.assign(mats.size() + 1, 0);
+    for (size_t i = 0; i < mats.size(); ++i) moff[i + 1] = moff[i] + m[mats[i]].h->n;
+    int64_t N = moff.back();
+    d_moff.ensure(sizeof(int64_t) * moff.size(), s);
+    h2d(d_moff.p, moff.data(), moff.size(), s);
+    d_seg.ensure(sizeof(int32_t) * size_t(N > 0 ? N : 1), s);
+    launch_fill_seg(int(mats.size()), d_moff.as<int64_t>(), N, d_seg.as<int32_t>(), s);
+  }
+
+  // Assembles dst (rows = sum of block rows) from blocks; returns its nnz.
+  template <typename TD>
+  void assemble(const std::vector<AsmBlock> &blocks, const std::vector<int64_t> &bnnz, Csr<TD> &dst) {
+    int nb = int(blocks.size());
+    std::vector<int64_t> boff(nb + 1, 0);
+    int64_t nnz = 0;
+    for (int b = 0; b < nb; ++b) {
+      boff[b + 1] = boff[b] + blocks[b].nrows;
+      nnz += bnnz[b];
+    }
+    int64_t N = boff[nb];
+    dst.ensure(N, nnz, s);
+    w.asm_blocks.ensure(sizeof(AsmBlock) * size_t(nb > 0 ? nb : 1), s);
+    w.asm_off.ensure(sizeof(int64_t) * size_t(nb + 1), s);
+    w.asm_lens.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
+    w.scan_tmp.ensure(sizeof(int64_t) * size_t(scan_tmp_elems(N)), s);
+    h2d(w.asm_blocks.p, blocks.data(), blocks.size(), s);
+    h2d(w.asm_off.p, boff.data(), boff.size(), s);
+    launch_assemble_rows(nb, w.asm_blocks.as<AsmBlock>(), w.asm_off.as<int64_t>(), N,
+                         w.asm_lens.as<int64_t>(), dst.d_rp(), w.scan_tmp.as<int64_t>(), s);
+    launch_assemble_vals(nb, w.asm_blocks.as<AsmBlock>(), w.asm_off.as<int64_t>(), N, dst.d_rp(),
+                         dst.d_col(), dst.val.p, is_f32<TD>(), s);
+    // the block and offset arrays are read by the kernels: keep them alive
+    sync(s);
+  }
+
+  // per-matrix entry offsets of a stage CSR (host copy)
+  std::vector<int64_t> entry_offsets(const std::vector<int64_t> &moff, DevBuf &d_moff,
+                                     const int64_t *rp) {
+    int nb = int(moff.size()) - 1;
+    w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
+    launch_gather_offsets(nb, d_moff.as<int64_t>(), rp, w.eoff.as<int64_t>(), s);
+    std::vector<int64_t> e(nb + 1);
+    d2h(e.data(), w.eoff.p, e.size(), s);
+    sync(s);
+    return e;
+  }
+
+  // Copies rows of matrix slot i of a stage CSR into a standalone FP64 CSR.
+  template <typename T>
+  void extract(const Stage<T> &st, const Csr<T> &X, const std::vector<int64_t> &eoff, int i,
+               Csr<double> &out) {
+    AsmBlock b{X.d_rp(), X.d_col(), X.val.p, st.moff[i], st.moff[i + 1] - st.moff[i],
+               -st.moff[i], is_f32<T>()};
+    assemble<double>({b}, {eoff[i + 1] - eoff[i]}, out);
+  }
+
+  // ---------------------------------------------------------------- product
+  // C = A B (MODE_SQUARE: B = A) for a stage; returns per-matrix nnz offsets.
+  template <typename T>
+  std::vector<int64_t> product(Stage<T> &st, const Csr<T> &A, const Csr<T> &B, int mode, Csr<T> &C,
+                               const int *active) {
+    int64_t N = A.n;
+    int nb = int(st.mats.size());
+    w.lo.ensure(sizeof(int32_t) * size_t(N), s);
+    w.len.ensure(sizeof(int32_t) * size_t(N), s);
+    w.cnt.ensure(sizeof(int64_t) * size_t(N), s);
+    w.wlist.ensure(sizeof(int32_t) * size_t(N), s);
+    w.clist.ensure(sizeof(int32_t) * size_t(N), s);
+    w.counters.ensure(sizeof(int) * 8, s);
+    w.scan_tmp.ensure(sizeof(int64_t) * size_t(scan_tmp_elems(N)), s);
+    SGN_CUDA(cudaMemsetAsync(w.counters.p, 0, sizeof(int) * 8, s));
+    launch_bounds(N, A.d_rp(), A.d_col(), B.d_rp(), B.d_col(), st.d_seg.template as<int32_t>(), active,
+                  mode, w.lo.as<int32_t>(), w.len.as<int32_t>(), w.cnt.as<int64_t>(),
+                  w.wlist.as<int32_t>(), w.clist.as<int32_t>(), w.counters.as<int>(), s);
+    launch_symbolic(N, A.d_rp(), A.d_col(), B.d_rp(), B.d_col(), mode, w.lo.as<int32_t>(),
+                    w.len.as<int32_t>(), w.wlist.as<int32_t>(), w.clist.as<int32_t>(),
+                    w.counters.as<int>(), w.cnt.as<int64_t>(), s);
+    C.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
+    launch_scan(N, w.cnt.as<int64_t>(), C.d_rp(), w.scan_tmp.as<int64_t>(), s);
+    std::vector<int64_t> eoff = entry_offsets(st.moff, st.d_moff, C.d_rp());
+    int64_t nnz = eoff[nb];
+    C.n = N;
+    C.nnz = nnz;
+    C.col.ensure(sizeof(int32_t) * size_t(nnz > 0 ? nnz : 1), s);
+    C.val.ensure(sizeof(T) * size_t(nnz > 0 ? nnz : 1), s);
+    if (mode == MODE_SQUARE) w.part.ensure(sizeof(double) * size_t(2 * N), s);
+    launch_numeric<T>(N, A.d_rp(), A.d_col(), A.d_val(), B.d_rp(), B.d_col(), B.d_val(), mode,
+                      w.lo.as<int32_t>(), w.len.as<int32_t>(), w.wlist.as<int32_t>(),
+                      w.clist.as<int32_t>(), w.counters.as<int>(), C.d_rp(), C.d_col(),
+                      C.d_val(), mode == MODE_SQUARE ? w.part.as<double>() : nullptr, s);
+    return eoff;
+  }
+
+  // ---------------------------------------------------------------- rounds
+  template <typename T>
+  void rebuild(Stage<T> &st, const std::vector<int> &keep_slots, const std::vector<int64_t> &eoff) {
+    std::vector<int> mats;
+    std::vector<AsmBlock> blocks;
+    std::vector<int64_t> bnnz;
+    int64_t off = 0;
+    for (int i : keep_slots) {
+      int id = st.mats[i];
+      blocks.push_back(AsmBlock{st.X.d_rp(), st.X.d_col(), st.X.val.p, st.moff[i],
+                                st.moff[i + 1] - st.moff[i], off - st.moff[i], is_f32<T>()});
+      bnnz.push_back(eoff[i + 1] - eoff[i]);
+      mats.push_back(id);
+      off += m[id].h->n;
+    }
+    for (Parked *p : st.incoming) {
+      blocks.push_back(AsmBlock{p->x.d_rp(), p->x.d_col(), p->x.val.p, 0, p->x.n, off, 0});
+      bnnz.push_back(p->x.nnz);
+      mats.push_back(p->mat);
+      off += p->x.n;
+    }
+    Csr<T> nx;
+    assemble<T>(blocks, bnnz, nx);
+    st.X.swap(nx);
+    st.mats = mats;
+    set_layout(st.moff, st.mats, st.d_moff, st.d_seg);
+    st.incoming.clear();
+    st.rebuild = false;
+  }
+
+  template <typename T, typename TN>
+  void round(Stage<T> &st, Stage<TN> *next) {
+    if (st.mats.empty() && st.incoming.empty()) return;
+    if (st.rebuild || !st.incoming.empty()) {
+      std::vector<int64_t> eoff =
+          st.mats.empty() ? std::vector<int64_t>{0} : entry_offsets(st.moff, st.d_moff, st.X.d_rp());
+      std::vector<int> all;
+      for (int i = 0; i < int(st.mats.size()); ++i) all.push_back(i);
+      rebuild(st, all, eoff);
+    }
+    int nb = int(st.mats.size());
+    if (nb == 0) return;
+    // all matrices of the stage take part in the check
+    std::vector<int> act(nb, 1);
+    w.active.ensure(sizeof(int) * size_t(nb), s);
+    h2d(w.active.p, act.data(), act.size(), s);
+    std::vector<int64_t> ex = entry_offsets(st.moff, st.d_moff, st.X.d_rp());
+    // ---- check: T = X X, r, x, budget (steps a2, a4)
+    std::vector<int64_t> et = product(st, st.X, st.X, MODE_SQUARE, st.Tm, w.active.as<int>());
+    w.sums.ensure(sizeof(double) * size_t(2 * nb), s);
+    w.ms.ensure(sizeof(MatScalars) * size_t(nb), s);
+    launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.part.as<double>(), 2, w.sums.as<double>(), s);
+    double tol_stage = st.prec == 32 ? o.fp32_until : o.tol;
+    launch_matrix_scalars(nb, st.d_moff.template as<int64_t>(), w.sums.as<double>(), o.c4, tol_stage,
+                          o.switch_resid, w.ms.as<MatScalars>(), s);
+    std::vector<MatScalars> hms(nb);
+    d2h(hms.data(), w.ms.p, size_t(nb), s);
+    sync(s);
+    // ---- per-matrix decisions (steps a7, a8)
+    std::vector<int> keep_slots;
+    bool changed = false;
+    for (int i = 0; i < nb; ++i) {
+      MatState &ms = m[st.mats[i]];
+      double r = hms[i].r;
+      trace_put(ms, ex[i + 1] - ex[i], et[i + 1] - et[i], r, hms[i].x, st.prec);
+      ms.resid = r;
+      int decision = 0;  // 0 update, 1 retire, 2 move
+      if (st.prec == 64 && r <= o.tol) {
+        ms.status = SIGN_OK;
+        decision = 1;
+      } else if (!std::isfinite(r) || r > o.div_limit) {
+        ms.status = SIGN_EDIVERGED;
+        decision = 1;
+      } else if (st.prec == 32 && r < o.fp32_until) {
+        decision = 2;
+      } else if (ms.k >= o.max_iter) {
+        ms.status = SIGN_ENOTCONV;
+        decision = 1;
+      }
+      if (decision == 0) {
+        keep_slots.push_back(i);
+        continue;
+      }
+      changed = true;
+      act[i] = 0;
+      if (decision == 1) {
+        extract(st, st.X, ex, i, ms.h->result);
+        ms.h->has_result = true;
+      } else {
+        auto p = std::make_unique<Parked>();
+        p->mat = st.mats[i];
+        extract(st, st.X, ex, i, p->x);
+        if (next) next->incoming.push_back(p.get());
+        parked_store.push_back(std::move(p));
+      }
+    }
+    if (keep_slots.empty()) {
+      st.mats.clear();
+      st.moff.assign(1, 0);
+      st.rebuild = false;
+      return;
+    }
+    if (changed) h2d(w.active.p, act.data(), act.size(), s);
+    // ---- update: Xbar = 1.5 X - 0.5 X T (step a3)
+    std::vector<int64_t> eb = product(st, st.X, st.Tm, MODE_UPDATE, st.Xb, w.active.as<int>());
+    for (int i = 0; i < nb; ++i) hms[i].nnz_bar = eb[i + 1] - eb[i];
+    h2d(w.ms.p, hms.data(), hms.size(), s);
+    const int *d_act = w.active.as<int>();
+    if (o.filter == SIGN_FILTER_NONE) {
+      st.Xh.swap(st.Xb);
+    } else {
+      // ---- threshold (step a5)
+      if (o.filter == SIGN_FILTER_EXACT) {
+        w.sel.ensure(select_scratch_bytes(nb, st.Xb.nnz), s);
+        w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
+        h2d(w.eoff.p, eb.data(), eb.size(), s);
+        launch_select_exact(nb, w.eoff.as<int64_t>(), d_act, st.Xb.nnz, st.Xb.val.p, is_f32<T>(),
+                            w.ms.as<MatScalars>(), w.sel.p, s);
+      } else {
+        launch_select_bound(nb, d_act, w.ms.as<MatScalars>(), s);
+      }
+      // ---- filter + compaction (step a6)
+      int64_t N = st.Xb.n;
+      w.dropped.ensure(sizeof(double) * size_t(N > 0 ? N : 1), s);
+      launch_filter_count(N, st.d_seg.template as<int32_t>(), d_act, st.Xb.d_rp(), st.Xb.val.p, is_f32<T>(),
+                          w.ms.as<MatScalars>(), w.cnt.as<int64_t>(), w.dropped.as<double>(), s);
+      st.Xh.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
+      launch_scan(N, w.cnt.as<int64_t>(), st.Xh.d_rp(), w.scan_tmp.as<int64_t>(), s);
+      launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.dropped.as<double>(), 1, w.sums.as<double>(), s);
+      std::vector<int64_t> eh = entry_offsets(st.moff, st.d_moff, st.Xh.d_rp());
+      st.Xh.n = N;
+      st.Xh.nnz = eh[nb];
+      st.Xh.col.ensure(sizeof(int32_t) * size_t(eh[nb] > 0 ? eh[nb] : 1), s);
+      st.Xh.val.ensure(sizeof(T) * size_t(eh[nb] > 0 ? eh[nb] : 1), s);
+      launch_filter_write(N, st.d_seg.template as<int32_t>(), d_act, st.Xb.d_rp(), st.Xb.d_col(), st.Xb.val.p,
+                          is_f32<T>(), w.ms.as<MatScalars>(), st.Xh.d_rp(), st.Xh.d_col(),
+                          st.Xh.val.p, s);
+      std::vector<double> dsum(nb);
+      d2h(hms.data(), w.ms.p, size_t(nb), s);
+      d2h(dsum.data(), w.sums.p, size_t(nb), s);
+      sync(s);
+      for (int i = 0; i < nb; ++i) hms[i].fnorm = std::sqrt(dsum[i]);
+    }
+    for (int i : keep_slots) {
+      MatState &ms = m[st.mats[i]];
+      trace_filter(ms, hms[i].beta, o.filter == SIGN_FILTER_NONE ? 0.0 : hms[i].tau,
+                   o.filter == SIGN_FILTER_NONE ? 0.0 : hms[i].fnorm, hms[i].nnz_bar);
+      ms.k++;
+    }
+    st.X.swap(st.Xh);
+    if (changed) {
+      // drop the rows of the matrices that left (their rows are empty now)
+      std::vector<int64_t> e2 = entry_offsets(st.moff, st.d_moff, st.X.d_rp());
+      rebuild(st, keep_slots, e2);
+    }
+  }
+
+  // ---------------------------------------------------------------- solve
+  void run(sign_t *hs, int count, sign_info *infos) {
+    m.resize(count);
+    for (int i = 0; i < count; ++i) {
+      m[i].h = hs[i];
+      m[i].info = infos ? &infos[i] : nullptr;
+      hs[i]->has_result = false;
+    }
+    // block-diagonal input (FP64), scaled per matrix (step a1)
+    Stage<double> s64;
+    Stage<float> s32;
+    std::vector<int> all(count);
+    for (int i = 0; i < count; ++i) all[i] = i;
+    std::vector<AsmBlock> blocks;
+    std::vector<int64_t> bnnz;
+    int64_t off = 0;
+    for (int i = 0; i < count; ++i) {
+      blocks.push_back(AsmBlock{hs[i]->a.d_rp(), hs[i]->a.d_col(), hs[i]->a.val.p, 0, hs[i]->n, off, 0});
+      bnnz.push_back(hs[i]->nnz);
+      off += hs[i]->n;
+    }
+    s64.mats = all;
+    set_layout(s64.moff, s64.mats, s64.d_moff, s64.d_seg);
+    assemble<double>(blocks, bnnz, s64.X);
+    int64_t N = off;
+    if (o.scale_1norm) {
+      w.norm_work.ensure(sizeof(unsigned long long) * size_t(2 * N + 4 * count), s);
+      w.norm.ensure(sizeof(double) * size_t(count), s);
+      launch_onenorm(count, s64.d_moff.as<int64_t>(), s64.d_seg.as<int32_t>(), N, s64.X.d_rp(),
+                     s64.X.d_col(), s64.X.d_val(), w.norm_work.as<unsigned long long>(),
+                     w.norm.as<double>(), s);
+      std::vector<double> nrm(count);
+      d2h(nrm.data(), w.norm.p, size_t(count), s);
+      sync(s);
+      for (int i = 0; i < count; ++i)
+        if (!(nrm[i] > 0.0) || !std::isfinite(nrm[i]))
+          throw Error(SIGN_EINVAL, "matrix " + std::to_string(i) + " has no finite nonzero 1-norm");
+      launch_scale(N, s64.d_seg.as<int32_t>(), s64.X.d_rp(), s64.X.d_val(), w.norm.as<double>(), s);
+    }
+    if (o.prec == SIGN_PREC_MIXED) {
+      std::vector<int64_t> ex = entry_offsets(s64.moff, s64.d_moff, s64.X.d_rp());
+      std::vector<AsmBlock> b1{AsmBlock{s64.X.d_rp(), s64.X.d_col(), s64.X.val.p, 0, N, 0, 0}};
+      assemble<float>(b1, {ex.back()}, s32.X);
+      s32.mats = all;
+      set_layout(s32.moff, s32.mats, s32.d_moff, s32.d_seg);
+      s64.mats.clear();
+      s64.moff.assign(1, 0);
+    }
+    for (int guard = 0; guard < 4 * o.max_iter + 16; ++guard) {
+      round<float, double>(s32, &s64);
+      round<double, double>(s64, nullptr);
+      if (s32.mats.empty() && s64.mats.empty() && s64.incoming.empty()) break;
+    }
+    for (int i = 0; i < count; ++i) {
+      MatState &ms = m[i];
+      if (ms.status < 0) throw Error(SIGN_ESTATE, "solve loop ended with a running matrix");
+      if (ms.info) {
+        ms.info->iters = ms.k;
+        ms.info->status = ms.status;
+        ms.info->resid = ms.resid;
+        ms.info->nnz_final = hs[i]->result.nnz;
+        ms.info->count = ms.trace_count;
+      }
+    }
+  }
+};
+
+sign_status fail(int status, const std::string &msg) {
+  g_err = msg;
+  return sign_status(status);
+}
+
+bool valid_opts(const sign_opts *o, std::string &why) {
+  if (!o) return why = "opts is NULL", false;
+  if (!(o->tol >= 0.0)) return why = "tol must be >= 0", false;
+  if (o->filter < 0 || o->filter > 2) return why = "unknown filter", false;
+  if (o->dense_frac < 0.0) return why = "dense_frac < 0", false;
+  if (o->prec < 0 || o->prec > 1) return why = "unknown precision", false;
+  if (o->max_iter < 0) return why = "max_iter < 0", false;
+  if (!(o->c4 >= 0.0) || !(o->switch_resid >= 0.0) || !(o->fp32_until > 0.0))
+    return why = "c4, switch_resid must be >= 0 and fp32_until > 0", false;
+  if (!(o->div_limit > 0.0)) return why = "div_limit must be > 0", false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sign_default_opts(sign_opts *o) {
+  if (!o) return;
+  o->tol = 1e-8;
+  o->filter = SIGN_FILTER_EXACT;
+  o->c4 = 1e-4;
+  o->switch_resid = 1e-6;
+  o->max_iter = 100;
+  o->prec = SIGN_PREC_FP64;
+  o->fp32_until = 1e-4;
+  o->dense_frac = 0.25;
+  o->scale_1norm = 1;
+  o->div_limit = 1e6;
+}
+
+const char *sign_last_error(void) { return g_err.c_str(); }
+
+sign_status sign_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col,
+                        const double *val, int on_device, void *cuda_stream, sign_t *out) {
+  g_err.clear();
+  if (!out) return fail(SIGN_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > INT32_MAX || nnz < 0) return fail(SIGN_EINVAL, "need 1 <= n < 2^31, nnz >= 0");
+  if (!rowptr || (nnz > 0 && (!col || !val))) return fail(SIGN_EINVAL, "NULL array");
+  sign_ctx *h = new (std::nothrow) sign_ctx;
+  if (!h) return fail(SIGN_ENOMEM, "host allocation failed");
+  try {
+    h->n = n;
+    h->nnz = nnz;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaStream_t s = h->stream;
+    h->a.ensure(n, nnz, s);
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    SGN_CUDA(cudaMemcpyAsync(h->a.rp.p, rowptr, sizeof(int64_t) * size_t(n + 1), kind, s));
+    if (nnz > 0) {
+      SGN_CUDA(cudaMemcpyAsync(h->a.col.p, col, sizeof(int32_t) * size_t(nnz), kind, s));
+      SGN_CUDA(cudaMemcpyAsync(h->a.val.p, val, sizeof(double) * size_t(nnz), kind, s));
+    }
+    DevBuf flag;
+    flag.ensure(sizeof(int), s);
+    SGN_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+    launch_validate(n, nnz, h->a.d_rp(), h->a.d_col(), h->a.d_val(), flag.as<int>(), s);
+    int hf = 0;
+    SGN_CUDA(cudaMemcpyAsync(&hf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SGN_CUDA(cudaStreamSynchronize(s));
+    if (hf) {
+      delete h;
+      return fail(SIGN_EINVAL, "malformed CSR (rowptr, column order/range or non-finite value)");
+    }
+  } catch (const Error &e) {
+    delete h;
+    return fail(e.status, e.what());
+  } catch (const std::exception &e) {
+    delete h;
+    return fail(SIGN_ECUDA, e.what());
+  }
+  *out = h;
+  return SIGN_OK;
+}
+
+sign_status sign_solve_batch(sign_t *hs, int count, const sign_opts *o, sign_info *infos) {
+  g_err.clear();
+  if (!hs || count < 1) return fail(SIGN_EINVAL, "need at least one handle");
+  for (int i = 0; i < count; ++i)
+    if (!hs[i]) return fail(SIGN_EINVAL, "NULL handle");
+  std::string why;
+  if (!valid_opts(o, why)) return fail(SIGN_EINVAL, why);
+  try {
+    Solver sv;
+    sv.s = hs[0]->stream;
+    sv.o = *o;
+    sv.run(hs, count, infos);
+    SGN_CUDA(cudaStreamSynchronize(sv.s));
+  } catch (const Error &e) {
+    return fail(e.status, e.what());
+  } catch (const std::bad_alloc &) {
+    return fail(SIGN_ENOMEM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(SIGN_ECUDA, e.what());
+  }
+  return SIGN_OK;
+}
+
+sign_status sign_solve(sign_t h, const sign_opts *o, sign_info *info) {
+  sign_info local;
+  std::memset(&local, 0, sizeof(local));
+  sign_info *in = info ? info : &local;
+  sign_status st = sign_solve_batch(&h, 1, o, in);
+  if (st != SIGN_OK) return st;
+  return sign_status(in->status);
+}
+
+sign_status sign_get_csr(sign_t h, int64_t *nnz_out, int64_t *row_ptr, int32_t *col, double *val,
+                         int on_device) {
+  g_err.clear();
+  if (!h) return fail(SIGN_EINVAL, "NULL handle");
+  if (!h->has_result) return fail(SIGN_ESTATE, "no result: call sign_solve first");
+  if (nnz_out) *nnz_out = h->result.nnz;
+  if (!row_ptr && !col && !val) return SIGN_OK;
+  try {
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaStream_t s = h->stream;
+    if (row_ptr)
+      SGN_CUDA(cudaMemcpyAsync(row_ptr, h->result.rp.p, sizeof(int64_t) * size_t(h->n + 1), kind, s));
+    if (col && h->result.nnz > 0)
+      SGN_CUDA(cudaMemcpyAsync(col, h->result.col.p, sizeof(int32_t) * size_t(h->result.nnz), kind, s));
+    if (val && h->result.nnz > 0)
+      SGN_CUDA(cudaMemcpyAsync(val, h->result.val.p, sizeof(double) * size_t(h->result.nnz), kind, s));
+    SGN_CUDA(cudaStreamSynchronize(s));
+  } catch (const Error &e) {
+    return fail(e.status, e.what());
+  }
+  return SIGN_OK;
+}
+
+void sign_destroy(sign_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  delete h;
+}
+
+}  // extern "C"

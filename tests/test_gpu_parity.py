@@ -1,0 +1,258 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Both sides accumulate every product in ascending k with one fused
+multiply-add, so the iterates are expected to agree bit for bit; the
+contract checked everywhere is the FP64 tolerance
+||S_gpu - S_ref||_F / ||S_ref||_F <= 1e-10 at equal iteration count, plus
+identical sparsity patterns and per-iteration nnz.
+"""
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+TOL_F64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def sg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2210_03356_gb300 as sg
+    from paper_2210_03356_gb300 import build
+    build.build()
+    sg.load()
+    return sg
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def assert_parity(res, ref, tol=TOL_F64, bitwise=True, trace=True):
+    assert res.status == ref.status, (res.status, ref.status)
+    assert res.iters == ref.iters, (res.iters, ref.iters)
+    assert np.array_equal(res.rowptr, ref.rowptr)
+    assert np.array_equal(res.col, ref.col)
+    assert _rel(res.val, ref.val) <= tol
+    if bitwise:
+        assert np.array_equal(res.val, ref.val)
+    if trace:
+        t, o = res.trace, ref.trace
+        assert np.array_equal(t["nnz_x"], o["nnz_x"])
+        assert np.array_equal(t["nnz_t"], o["nnz_t"])
+        assert np.array_equal(t["prec_k"], o["prec"])
+        np.testing.assert_allclose(t["resid_k"], o["resid"], rtol=1e-9, atol=1e-15)
+        np.testing.assert_allclose(t["tau_k"], o["tau"], rtol=1e-12)
+        np.testing.assert_allclose(t["fnorm_k"], o["fnorm"], rtol=1e-8, atol=1e-300)
+    assert abs(res.resid - ref.resid) <= 1e-9 * max(ref.resid, 1e-300) + 1e-16
+
+
+# ---------------------------------------------------------------- tridiagonal n = 2000
+@pytest.mark.parametrize("mode", ["exact", "bound"])
+def test_tridiagonal_2000(sg, orc, mode):
+    a = w.tridiagonal()
+    res = sg.solve(a, tol=1e-8, filter=mode)
+    ref = orc.nsf(a, tol=1e-8, filter=mode)
+    assert res.status == sg.SIGN_OK
+    assert_parity(res, ref)
+
+
+def test_tridiagonal_tight_tol_adaptive_budget(sg, orc):
+    """tol 1e-12 reaches the Eq. (1.18) phase (r < 1e-6)."""
+    a = w.tridiagonal(1200)
+    res = sg.solve(a, tol=1e-12, filter="exact")
+    ref = orc.nsf(a, tol=1e-12, filter="exact")
+    assert_parity(res, ref)
+    assert np.any(res.trace["resid_k"] < 1e-6) and np.any(res.trace["beta_k"] < 1e-16)
+
+
+def test_unfiltered_ns_dense_fill(sg, orc):
+    """filter NONE: plain NS; rows fill in past 1024 columns (CTA kernels)."""
+    a = w.tridiagonal(1500)
+    res = sg.solve(a, tol=1e-8, filter="none")
+    ref = orc.nsf(a, tol=1e-8, filter="none")
+    assert_parity(res, ref)
+    assert res.nnz > 0.9 * a.n * a.n
+
+
+def test_mixed_precision_matches_mixed_oracle(sg, orc):
+    a = w.tridiagonal()
+    res = sg.solve(a, tol=1e-8, filter="exact", prec=1)
+    ref = orc.nsf(a, tol=1e-8, filter="exact", mixed=True)
+    assert_parity(res, ref)
+    assert res.trace["prec_k"][0] == 32 and res.trace["prec_k"][-1] == 64
+    ref64 = orc.nsf(a, tol=1e-8, filter="exact")
+    d = ref64.to_dense(a.n) - res_dense(res, a.n)
+    assert np.linalg.norm(d) / np.linalg.norm(ref64.to_dense(a.n)) < 1e-6
+
+
+def res_dense(res, n):
+    d = np.zeros((n, n))
+    d[np.repeat(np.arange(n), np.diff(res.rowptr)), res.col] = res.val
+    return d
+
+
+def test_deterministic_runs(sg):
+    a = w.tridiagonal()
+    r1 = sg.solve(a, tol=1e-8, filter="exact")
+    r2 = sg.solve(a, tol=1e-8, filter="exact")
+    assert np.array_equal(r1.val, r2.val) and np.array_equal(r1.col, r2.col)
+
+
+# ---------------------------------------------------------------- wide rows
+@pytest.mark.parametrize("m,dim", [(24, 2), (8, 3)])
+def test_shifted_laplacians(sg, orc, m, dim):
+    a = w.laplacian(m, dim)
+    res = sg.solve(a, tol=1e-8, filter="exact", max_iter=200)
+    ref = orc.nsf(a, tol=1e-8, filter="exact", max_iter=200)
+    assert_parity(res, ref)
+    assert res.status == sg.SIGN_OK
+
+
+def _two_scale(n, far, seed):
+    rng = np.random.default_rng(seed)
+    i = np.arange(n)
+    d = np.where(rng.random(n) < 0.5, -1.0, 1.0) * (1.5 + 0.5 * rng.random(n))
+    rows, cols, vals = [i], [i], [d]
+    for off, scale in ((1, 0.2), (far, 0.15)):
+        j = np.arange(n - off)
+        v = scale * rng.uniform(-1, 1, n - off)
+        rows += [j, j + off]
+        cols += [j + off, j]
+        vals += [v, v]
+    return w.csr_from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def test_multichunk_rows(sg, orc):
+    """Rows whose column range spans several shared-memory chunks."""
+    a = _two_scale(30000, 10000, 5)
+    res = sg.solve(a, tol=1e-8, filter="exact")
+    ref = orc.nsf(a, tol=1e-8, filter="exact")
+    assert_parity(res, ref)
+
+
+# ---------------------------------------------------------------- the paper's Sec. 4.2 matrix
+def test_ode_block_unscaled_nonsymmetric(sg, orc):
+    a = w.ode_block(400)
+    res = sg.solve(a, tol=1e-12, filter="exact", scale_1norm=0)
+    ref = orc.nsf(a, tol=1e-12, filter="exact", scale_1norm=False)
+    assert_parity(res, ref)
+
+
+def test_nonsymmetric_onenorm_scaling(sg, orc):
+    a = w.ode_block(300)
+    res = sg.solve(a, tol=1e-10, filter="bound")
+    ref = orc.nsf(a, tol=1e-10, filter="bound")
+    assert_parity(res, ref)
+
+
+# ---------------------------------------------------------------- batches
+def test_batch_matches_lone_solves_and_oracle(sg, orc):
+    shapes = w.banded_batch_shapes(24, nmin=200, nmax=1500)
+    mats = [w.banded(n, b, s) for n, b, s in shapes]
+    out = sg.solve_batch(mats, tol=1e-8, filter="exact")
+    for a, res in zip(mats, out):
+        ref = orc.nsf(a, tol=1e-8, filter="exact")
+        assert_parity(res, ref)
+    for a, res in list(zip(mats, out))[:4]:
+        alone = sg.solve(a, tol=1e-8, filter="exact")
+        assert np.array_equal(alone.val, res.val) and alone.iters == res.iters
+
+
+def test_batch_mixed_precision_moves_per_matrix(sg, orc):
+    shapes = w.banded_batch_shapes(12, nmin=200, nmax=900)
+    mats = [w.banded(n, b, s) for n, b, s in shapes]
+    out = sg.solve_batch(mats, tol=1e-8, filter="exact", prec=1)
+    for a, res in zip(mats, out):
+        ref = orc.nsf(a, tol=1e-8, filter="exact", mixed=True)
+        assert_parity(res, ref)
+
+
+def test_batch_full_512_sampled(sg, orc):
+    """The 512-matrix banded batch in one call; sampled matrices vs the oracle."""
+    shapes = w.banded_batch_shapes()
+    mats = [w.banded(n, b, s) for n, b, s in shapes]
+    out = sg.solve_batch(mats, tol=1e-8, filter="exact", prec=1)
+    assert all(r.status == sg.SIGN_OK for r in out)
+    order = np.argsort([n * (b + 1) for n, b, _ in shapes])
+    sample = [int(order[-1]), int(order[len(order) // 2]), int(order[0]), 7]
+    for i in sample:
+        ref = orc.nsf(mats[i], tol=1e-8, filter="exact", mixed=True)
+        assert_parity(out[i], ref)
+    # every result is an involution to the requested tolerance
+    assert max(r.resid for r in out) <= 1e-8
+
+
+# ---------------------------------------------------------------- device pointers
+def test_device_pointers_in_and_out(sg, orc):
+    import torch
+    a = w.tridiagonal(800)
+    class T:  # CSR of CUDA tensors
+        n = a.n
+        rowptr = torch.from_numpy(a.rowptr).cuda()
+        col = torch.from_numpy(a.col).cuda()
+        val = torch.from_numpy(a.val).cuda()
+    res = sg.solve(T, tol=1e-8, filter="exact", device_out=True)
+    ref = orc.nsf(a, tol=1e-8, filter="exact")
+    assert res.val.is_cuda
+    assert np.array_equal(res.val.cpu().numpy(), ref.val)
+    assert np.array_equal(res.col.cpu().numpy(), ref.col)
+
+
+# ---------------------------------------------------------------- edge cases
+def test_edge_cases(sg, orc):
+    one = w.csr_from_dense(np.array([[-3.0]]))
+    r = sg.solve(one, tol=1e-14)
+    assert r.status == sg.SIGN_OK and r.val[0] == -1.0 and r.iters == 0
+    # singular (empty row): never converges
+    sing = w.csr_from_dense(np.diag([1.0, 0.0, -2.0]))
+    r = sg.solve(sing, tol=1e-12, max_iter=30)
+    ref = orc.nsf(sing, tol=1e-12, max_iter=30)
+    assert r.status == sg.SIGN_ENOTCONV and r.iters == 30
+    assert_parity(r, ref)
+    # unscaled 3I leaves the region of convergence
+    big = w.csr_from_dense(3.0 * np.eye(4))
+    r = sg.solve(big, scale_1norm=0, filter="none")
+    assert r.status == sg.SIGN_EDIVERGED == orc.nsf(big, scale_1norm=False, filter="none").status
+    # max_iter = 0: the scaled input comes back with its residual
+    a = w.tridiagonal(300)
+    r = sg.solve(a, max_iter=0)
+    ref = orc.nsf(a, max_iter=0)
+    assert r.status == sg.SIGN_ENOTCONV and r.iters == 0
+    assert_parity(r, ref)
+
+
+def test_invalid_inputs_rejected(sg):
+    from paper_2210_03356_gb300 import Handle, SignError
+    bad = w.CSR(2, np.array([0, 2, 3], np.int64), np.array([1, 0, 1], np.int32), np.ones(3))
+    with pytest.raises(SignError) as e:
+        Handle(bad)
+    assert e.value.status == sg.SIGN_EINVAL
+    nan = w.CSR(2, np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32),
+                np.array([1.0, np.nan]))
+    with pytest.raises(SignError):
+        Handle(nan)
+    out_of_range = w.CSR(2, np.array([0, 1, 2], np.int64), np.array([0, 2], np.int32), np.ones(2))
+    with pytest.raises(SignError):
+        Handle(out_of_range)
+    z = w.CSR(3, np.array([0, 0, 0, 0], np.int64), np.zeros(0, np.int32), np.zeros(0))
+    with pytest.raises(SignError) as e:
+        sg.solve(z)
+    assert e.value.status == sg.SIGN_EINVAL
+    with pytest.raises(SignError):
+        sg.solve(w.tridiagonal(10), filter=7)
