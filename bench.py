@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark: filtered Newton-Schulz sign solves/s on one GB300.
+
+Workload (one "step"): the batch of 512 independent symmetric banded matrices
+(n log-uniform in [200, 8000], half-bandwidth uniform in {1..10}, seeded
+synthetic inputs from workloads/), each solved to ||S^2 - I||_F/sqrt(n) <= 1e-8
+with the EXACT filter: FP32 iterations until the residual is below 1e-4, then
+FP64, all 512 in one sign_solve_batch call. Every step runs the whole path:
+1-norm scale, the two sparse products per iteration, residuals, budgets,
+thresholds, filtering and compaction, stage switches and stopping tests.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank solves its own batch of 512 (weak scaling, no
+collective on the data path); the time is the maximum over ranks.
+
+--impl reference times the CPU oracle (oracle/, plain C) on a bounded sample of
+the same workload with the host's cores, as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as w  # noqa: E402
+
+METRIC = "filtered-NS sign solves/s at ||S^2-I||_F/sqrt(n)<=1e-8 (vs unfiltered FP64 NS on the same GPU)"
+UNIT = "solves/s"
+BATCH = 512
+TOL = 1e-8
+WORKLOAD = ("banded batch: 512 symmetric banded matrices, n log-uniform [200,8000], "
+            "half-bandwidth U{1..10}, diag +-(1+U[0,1)), off-diag U[-1,1] scaled to row sum <= 0.8; "
+            "EXACT filter, FP32 until resid<1e-4 then FP64, tol 1e-8")
+# FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# FP32 peak: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+
+
+def batch_mats(rank: int, count: int = BATCH):
+    seed0 = w.BASE_SEED + 3000 + rank * count
+    return [w.banded(n, b, s) for n, b, s in w.banded_batch_shapes(count, seed0)]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------- CPU oracle
+def _oracle_one(args):
+    idx, rank = args
+    import oracle
+    a = _mat_by_index(rank, idx)
+    t = time.perf_counter()
+    r = oracle.nsf(a, tol=TOL, filter="exact", mixed=True)
+    return time.perf_counter() - t, r.status
+
+
+def _mat_by_index(rank, idx):
+    shapes = w.banded_batch_shapes(BATCH, w.BASE_SEED + 3000 + rank * BATCH)
+    n, b, s = shapes[idx]
+    return w.banded(n, b, s)
+
+
+def oracle_sample(indices, rank=0, cores=None):
+    """Times the oracle on the given batch members with a spawn pool."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = cores or min(len(indices), os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_one, [(i, rank) for i in indices])
+    wall = time.perf_counter() - t0
+    cpu = sum(r[0] for r in res)
+    return wall, cpu, cores, [r[1] for r in res]
+
+
+def sample_indices(k: int, offset: int = 0):
+    step = BATCH // k
+    return [(offset + i * step) % BATCH for i in range(k)]
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    k = args.ref_sample
+    for s in range(args.warmup):
+        oracle_sample(sample_indices(k, s))
+    walls = []
+    cores = 0
+    for s in range(args.steps):
+        wall, cpu, cores, st = oracle_sample(sample_indices(k, args.warmup + s))
+        walls.append(wall)
+    total = sum(walls)
+    value = k * args.steps / total
+    sample = f"{k} of the 512 matrices per step (every {BATCH // k}th, offset by step), mixed FP32->FP64, EXACT, tol 1e-8"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp32+fp64 (mixed)",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "global_batch": BATCH},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------- clocks
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------- our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--legs", default="all", choices=["all", "timed"],
+                    help="timed: only the device-timed leg (for profiler runs)")
+    ap.add_argument("--ref-sample", type=int, default=8)
+    ap.add_argument("--cpu-sample", type=int, default=16)
+    ap.add_argument("--unfiltered-sample", type=int, default=8)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # CPU baseline first: the spawn pool runs before this process touches CUDA
+    cpu = None
+    if args.legs == "all" and rank == 0 and world == 1:
+        idx = sample_indices(args.cpu_sample)
+        wall, cpu_s, cores, st = oracle_sample(idx)
+        cpu = {"value": len(idx) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{len(idx)} of the 512 matrices (every {BATCH // len(idx)}th), "
+                         f"same solve settings; {cpu_s:.1f} s of CPU work in {wall:.1f} s wall"}
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2210_03356_gb300 as sg
+    L = sg.load()
+
+    mats = batch_mats(rank)
+    opts = sg.default_opts(tol=TOL, filter="exact", prec="mixed")
+    stream = torch.cuda.current_stream()
+    batch = sg.Batch(mats, stream=None if stream.cuda_stream == 0 else
+                     __import__("ctypes").c_void_p(stream.cuda_stream))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        out = batch.solve(opts)
+    assert all(s == sg.SIGN_OK for s, _, _ in out), out[:4]
+
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    sg.prof_reset()
+    sg.prof_enable(True)
+    l0 = sg.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        out = batch.solve(opts)
+    e1.record(stream)
+    barrier()
+    launches = sg.kernel_launches() - l0
+    sg.prof_enable(False)
+    prof = sg.prof_read()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    assert all(s == sg.SIGN_OK and r <= TOL for s, _, r in out)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = BATCH * world * args.steps / (ms_max / 1000.0)
+
+    # roofline of the dominant kernel class
+    peaks, peak_kind = measured_peaks()
+    top = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    name, p = top
+    per_launch_ms = p["ms"] / max(p["launches"], 1)
+    if "numeric" in name and name.endswith("f64"):
+        bound, peak, unit = "alu", FP64_PEAK_GFLOPS, "GFLOP/s"
+        achieved = p["flops"] / (p["ms"] / 1e3) / 1e9
+        per_launch = p["flops"] / max(p["launches"], 1)
+    elif "numeric" in name:
+        fl = p["flops"] / (p["ms"] / 1e3) / 1e9
+        by = p["bytes"] / (p["ms"] / 1e3) / 1e9
+        if fl / FP32_PEAK_GFLOPS >= by / peaks["hbm_gbs"]:
+            bound, peak, unit, achieved = "alu", FP32_PEAK_GFLOPS, "GFLOP/s", fl
+            per_launch = p["flops"] / max(p["launches"], 1)
+        else:
+            bound, peak, unit, achieved = "hbm", peaks["hbm_gbs"], "GB/s", by
+            per_launch = p["bytes"] / max(p["launches"], 1)
+    else:
+        bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
+        achieved = p["bytes"] / (p["ms"] / 1e3) / 1e9
+        per_launch = p["bytes"] / max(p["launches"], 1)
+    total_ms = sum(v["ms"] for v in prof.values())
+    roofline = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": (f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if bound == "hbm"
+                                else "unit counts x 2.07 GHz (FP64: 2 FMA/clk/SM; FP32: 128)"),
+                "per_launch_work": per_launch, "avg_launch_ms": per_launch_ms,
+                "share_of_kernel_time": p["ms"] / total_ms if total_ms else None}
+    by_kernel = {k: {"share": v["ms"] / total_ms if total_ms else 0.0, "launches": v["launches"],
+                     "ms": round(v["ms"], 3),
+                     "gflops": v["flops"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else 0.0,
+                     "gbs": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else 0.0}
+                 for k, v in prof.items() if v["launches"]}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32+fp64 (mixed)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": BATCH * world,
+                       "rows_per_batch": int(sum(a.n for a in mats)),
+                       "parallelism": f"{world} independent batches (one per GPU)",
+                       "l2": "working set of every step (iterates, products) is several GB, > 129 MB L2"},
+            "gpu_launches": int(launches), "clocks": ck, "roofline": roofline,
+            "kernels": by_kernel}
+
+    if args.legs == "all":
+        # end to end through the public API: pinned host inputs -> device -> host result
+        pinned = []
+        h2d = d2h = 0
+        for a in mats:
+            rp = torch.from_numpy(a.rowptr).pin_memory()
+            col = torch.from_numpy(a.col).pin_memory()
+            val = torch.from_numpy(a.val).pin_memory()
+            pinned.append(type("P", (), {"n": a.n, "rowptr": rp.numpy(), "col": col.numpy(),
+                                         "val": val.numpy(), "_keep": (rp, col, val)}))
+            h2d += rp.numel() * 8 + col.numel() * 4 + val.numel() * 8
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            b2 = sg.Batch(pinned)
+            b2.solve(opts)
+            d2h = 0
+            for hnd in b2.handles:
+                rp, col, val = hnd.result()
+                d2h += rp.nbytes + col.nbytes + val.nbytes
+            b2.close()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        line["e2e"] = {"value": BATCH * world * args.steps / e2e_s, "unit": UNIT,
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+        # unfiltered FP64 Newton-Schulz on the same GPU, on a sample of the batch
+        idx = sample_indices(args.unfiltered_sample)
+        sub = sg.Batch([mats[i] for i in idx])
+        o_f = sg.default_opts(tol=TOL, filter="exact", prec="mixed")
+        o_u = sg.default_opts(tol=TOL, filter="none", prec="fp64")
+        sub.solve(o_f)
+        barrier()
+        t0 = time.perf_counter()
+        sub.solve(o_f)
+        barrier()
+        tf = time.perf_counter() - t0
+        sub.solve(o_u)  # warm-up of the unfiltered run
+        barrier()
+        t0 = time.perf_counter()
+        ru = sub.solve(o_u)
+        barrier()
+        tu = time.perf_counter() - t0
+        assert all(s == sg.SIGN_OK for s, _, _ in ru)
+        sub.close()
+        line["vs_unfiltered_fp64"] = {
+            "sample": f"{len(idx)} of the 512 matrices (every {BATCH // len(idx)}th), one batch call each",
+            "filtered_mixed_solves_per_s": len(idx) / tf,
+            "unfiltered_fp64_solves_per_s": len(idx) / tu, "speedup": tu / tf}
+        if cpu:
+            line["cpu_baseline"] = cpu
+    batch.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

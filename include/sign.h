@@ -106,6 +106,8 @@ typedef struct {
   double *fnorm_k;    /* ||F||_F dropped by the next filter                  */
   int64_t *nnz_bar;   /* nnz of Xbar before the next filter                  */
   int *prec_k;        /* 32 or 64                                            */
+  double *mults_t;    /* multiply-adds of T = X_k X_k                        */
+  double *mults_bar;  /* multiply-adds of X_k T of the next update           */
 } sign_info;
 
 /* Fills *o with the defaults listed in sign_opts. */
@@ -141,6 +143,33 @@ void sign_destroy(sign_t h);
 
 /* Message of the calling thread's last failed call ("" if none). */
 const char *sign_last_error(void);
+
+/* ---- observability (not part of the paper's method) -------------------- */
+
+/* Total CUDA kernel launches made by this library in this process. */
+int64_t sign_kernel_launches(void);
+
+/* Per-kernel-class timing. When enabled, every group of launches of one
+ * class is bracketed by CUDA events recorded on the stream it runs on.
+ * flops counts two per multiply-add of a sparse product (the products the
+ * method must do); bytes counts the algorithmic traffic of the class: each
+ * operand's values, column indices and row pointers read once and each
+ * output written once. */
+typedef struct {
+  char name[32];
+  int64_t launches; /* timed groups of launches                      */
+  double ms;        /* summed device time                              */
+  double flops;     /* algorithmic floating-point operations           */
+  double bytes;     /* algorithmic DRAM bytes                           */
+} sign_prof_entry;
+
+/* Turns timing on (1) or off (0); returns the previous setting. */
+int sign_prof_enable(int on);
+/* Waits for the recorded events, writes up to cap entries (one per kernel
+ * class) and returns the number written (out = NULL: the class count). */
+int sign_prof_read(sign_prof_entry *out, int cap);
+/* Clears the accumulated timings. */
+void sign_prof_reset(void);
 
 #ifdef __cplusplus
 }

@@ -533,7 +533,7 @@ int oracle_nsf(int64_t n, const int64_t *rowptr, const int32_t *col, const doubl
       int64_t *hrp;
       int32_t *hcol;
       float *hval;
-      double tau, fn;
+      double tau = 0.0, fn = 0.0;
       rc = filter_f32(n, brp, bcol, bval, o->filter, sqrt((double)n) * beta, &hrp, &hcol, &hval,
                       &tau, &fn);
       trace_filter(tr, beta, tau, fn, brp[n]);
@@ -578,7 +578,7 @@ int oracle_nsf(int64_t n, const int64_t *rowptr, const int32_t *col, const doubl
       int64_t *hrp;
       int32_t *hcol;
       double *hval;
-      double tau, fn;
+      double tau = 0.0, fn = 0.0;
       rc = oracle_filter(n, brp, bcol, bval, o->filter, sqrt((double)n) * beta, &hrp, &hcol, &hval,
                          &tau, &fn);
       trace_filter(tr, beta, tau, fn, brp[n]);

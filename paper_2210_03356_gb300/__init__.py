@@ -21,14 +21,16 @@ import numpy as np
 
 from . import _native as N
 from ._native import (SIGN_EDIVERGED, SIGN_EINVAL, SIGN_ENOTCONV, SIGN_OK, SignError,
-                      default_opts, last_error, load)
+                      default_opts, last_error, load, prof_read)
 
 __all__ = ["solve", "solve_batch", "Handle", "Result", "default_opts", "load", "last_error",
+           "prof_read", "kernel_launches", "prof_enable", "prof_reset",
            "SignError", "SIGN_OK", "SIGN_EINVAL", "SIGN_ENOTCONV", "SIGN_EDIVERGED"]
 
 _TRACE = [("nnz_x", np.int64), ("nnz_t", np.int64), ("resid_k", np.float64),
           ("xnorm_k", np.float64), ("beta_k", np.float64), ("tau_k", np.float64),
-          ("fnorm_k", np.float64), ("nnz_bar", np.int64), ("prec_k", np.int32)]
+          ("fnorm_k", np.float64), ("nnz_bar", np.int64), ("prec_k", np.int32),
+          ("mults_t", np.float64), ("mults_bar", np.float64)]
 
 
 def _is_torch_cuda(x) -> bool:
@@ -188,4 +190,47 @@ def solve_batch(mats, opts=None, trace_cap: int = 256, device_out: bool = False,
         return out
     finally:
         for h in hs:
+            h.close()
+
+
+def kernel_launches() -> int:
+    return int(load().sign_kernel_launches())
+
+
+def prof_enable(on: bool = True) -> bool:
+    return bool(load().sign_prof_enable(int(on)))
+
+
+def prof_reset() -> None:
+    load().sign_prof_reset()
+
+
+class Batch:
+    """Device-resident matrices solved together with sign_solve_batch.
+
+    The handles are created once (inputs copied to the device); every call of
+    solve() runs the whole batch again from those inputs.
+    """
+
+    def __init__(self, mats, stream=None):
+        self.handles = [Handle(a, stream) for a in mats]
+        self.arr = (N.sign_t * len(self.handles))(*[h.h for h in self.handles])
+        self.infos = None
+
+    def solve(self, opts, trace_cap: int = 0) -> list:
+        """Runs sign_solve_batch; returns per-matrix (status, iters, resid)."""
+        infos = [_Info(trace_cap) for _ in self.handles]
+        iarr = (N.sign_info * len(infos))(*[i.s for i in infos])
+        st = load().sign_solve_batch(self.arr, len(self.handles), C.byref(opts), iarr)
+        if st != SIGN_OK:
+            raise SignError(st, "sign_solve_batch")
+        self.infos = (infos, iarr)
+        return [(s.status, s.iters, s.resid) for s in iarr]
+
+    def traces(self) -> list:
+        infos, iarr = self.infos
+        return [i.trace(s) for i, s in zip(infos, iarr)]
+
+    def close(self):
+        for h in self.handles:
             h.close()

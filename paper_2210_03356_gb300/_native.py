@@ -33,7 +33,13 @@ class sign_info(C.Structure):
                 ("resid_k", C.POINTER(C.c_double)), ("xnorm_k", C.POINTER(C.c_double)),
                 ("beta_k", C.POINTER(C.c_double)), ("tau_k", C.POINTER(C.c_double)),
                 ("fnorm_k", C.POINTER(C.c_double)), ("nnz_bar", C.POINTER(C.c_int64)),
-                ("prec_k", C.POINTER(C.c_int))]
+                ("prec_k", C.POINTER(C.c_int)), ("mults_t", C.POINTER(C.c_double)),
+                ("mults_bar", C.POINTER(C.c_double))]
+
+
+class sign_prof_entry(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("ms", C.c_double),
+                ("flops", C.c_double), ("bytes", C.c_double)]
 
 
 sign_t = C.c_void_p
@@ -51,6 +57,10 @@ SIGNATURES = {
                                C.c_int]),
     "sign_destroy": (None, [sign_t]),
     "sign_last_error": (C.c_char_p, []),
+    "sign_kernel_launches": (C.c_int64, []),
+    "sign_prof_enable": (C.c_int, [C.c_int]),
+    "sign_prof_read": (C.c_int, [C.c_void_p, C.c_int]),
+    "sign_prof_reset": (None, []),
 }
 
 _lib = None
@@ -93,3 +103,13 @@ def default_opts(**kw) -> sign_opts:
             v = {"fp64": 0, "mixed": 1}[v]
         setattr(o, k, v)
     return o
+
+
+def prof_read() -> dict:
+    """Per-kernel-class timings accumulated since the last reset."""
+    L = load()
+    n = L.sign_prof_read(None, 0)
+    arr = (sign_prof_entry * n)()
+    n = L.sign_prof_read(C.cast(arr, C.c_void_p), n)
+    return {e.name.decode(): {"launches": e.launches, "ms": e.ms, "flops": e.flops,
+                              "bytes": e.bytes} for e in arr[:n]}

@@ -24,7 +24,14 @@ struct Error : std::runtime_error {
                          std::string(#call) + ": " + cudaGetErrorString(e_));               \
   } while (0)
 
-#define SGN_LAUNCH_CHECK() SGN_CUDA(cudaGetLastError())
+// Every kernel launch of the library goes through this check, which also
+// counts it (sign_kernel_launches).
+void count_launch();
+#define SGN_LAUNCH_CHECK()        \
+  do {                            \
+    ::sgn::count_launch();        \
+    SGN_CUDA(cudaGetLastError()); \
+  } while (0)
 
 // Shared-memory row accumulators: rows whose column range fits WARP_W slots
 // are handled by one warp; wider rows by one CTA in chunks of CTA_W slots.
@@ -37,6 +44,22 @@ template <> struct CtaW<float> { static constexpr int value = 20480; };
 // symbolic pass of wide rows: one bitmap covering up to SYM_BITS columns
 constexpr int SYM_BITS = 1 << 18;
 constexpr int K_BATCH = 256;  // k entries whose B-row ranges are located at once
+
+// Kernel classes timed when profiling is on (sign_prof_enable).
+enum KClass {
+  KC_NUM_SQUARE_F64, KC_NUM_UPDATE_F64, KC_NUM_SQUARE_F32, KC_NUM_UPDATE_F32, KC_BOUNDS,
+  KC_SYMBOLIC, KC_SCAN, KC_SELECT, KC_FILTER, KC_REDUCE, KC_ASSEMBLE, KC_NORM, KC_COUNT
+};
+// Records CUDA events around the enclosed launches on stream s (no-op when
+// profiling is off); flops and bytes are the algorithmic work they do.
+struct ProfScope {
+  int cls;
+  cudaStream_t s;
+  double flops, bytes;
+  void *ev0 = nullptr;
+  ProfScope(int c, cudaStream_t st, double f = 0.0, double b = 0.0);
+  ~ProfScope();
+};
 
 // Grow-only device buffer, allocated stream-ordered.
 struct DevBuf {

@@ -63,11 +63,12 @@ enum ProductMode { MODE_SQUARE = 0, MODE_UPDATE = 1 };
 // range [lo, lo+len) of the row (including A's own row in MODE_UPDATE),
 // sets cnt[i] = 0 for empty rows and appends non-empty rows to the warp list
 // (len <= WARP_W) or the CTA list. counters[0], counters[1] are the list
-// lengths (zeroed by the caller).
+// lengths (zeroed by the caller). work[i] = sum_{k in A_i} nnz(B_k), the
+// multiply-adds of the row.
 void launch_bounds(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
                    const int32_t *bcol, const int32_t *seg, const int *active, int mode,
                    int32_t *lo, int32_t *len, int64_t *cnt, int32_t *wlist, int32_t *clist,
-                   int *counters, cudaStream_t s);
+                   int *counters, double *work, cudaStream_t s);
 // Exact nnz of every listed row (symbolic product).
 void launch_symbolic(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
                      const int32_t *bcol, int mode, const int32_t *lo, const int32_t *len,

@@ -53,7 +53,7 @@ __device__ __forceinline__ int64_t lower_bound(const int32_t *a, int64_t lo, int
 __global__ void k_bounds(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
                          const int32_t *bcol, const int32_t *seg, const int *active, int mode,
                          int32_t *lo, int32_t *len, int64_t *cnt, int32_t *wlist, int32_t *clist,
-                         int *counters) {
+                         int *counters, double *work) {
   int lane = lane_id();
   int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -63,13 +63,16 @@ __global__ void k_bounds(int64_t n, const int64_t *arp, const int32_t *acol, con
         cnt[r] = 0;
         len[r] = 0;
         lo[r] = 0;
+        work[r] = 0.0;
       }
       continue;
     }
     int32_t mn = INT_MAX, mx = -1;
+    int64_t wk = 0;
     for (int64_t p = arp[r] + lane; p < arp[r + 1]; p += 32) {
       int32_t k = acol[p];
       int64_t b0 = brp[k], b1 = brp[k + 1];
+      wk += b1 - b0;
       if (b1 > b0) {
         mn = min(mn, bcol[b0]);
         mx = max(mx, bcol[b1 - 1]);
@@ -83,8 +86,10 @@ __global__ void k_bounds(int64_t n, const int64_t *arp, const int32_t *acol, con
     for (int o = 16; o > 0; o >>= 1) {
       mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
       mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      wk += __shfl_xor_sync(0xffffffffu, wk, o);
     }
     if (lane == 0) {
+      work[r] = double(wk);
       if (mx < 0) {
         cnt[r] = 0;
         len[r] = 0;
@@ -484,10 +489,10 @@ int grid_cap(int64_t items, int per_block, int per_sm) {
 void launch_bounds(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
                    const int32_t *bcol, const int32_t *seg, const int *active, int mode,
                    int32_t *lo, int32_t *len, int64_t *cnt, int32_t *wlist, int32_t *clist,
-                   int *counters, cudaStream_t s) {
+                   int *counters, double *work, cudaStream_t s) {
   if (n == 0) return;
   k_bounds<<<grid_cap(n, 8, 16), 256, 0, s>>>(n, arp, acol, brp, bcol, seg, active, mode, lo,
-                                               len, cnt, wlist, clist, counters);
+                                               len, cnt, wlist, clist, counters, work);
   SGN_LAUNCH_CHECK();
 }
 

@@ -96,7 +96,8 @@ struct MatState {
   int trace_count = 0;
 };
 
-void trace_put(MatState &ms, int64_t nnz_x, int64_t nnz_t, double r, double x, int prec) {
+void trace_put(MatState &ms, int64_t nnz_x, int64_t nnz_t, double r, double x, int prec,
+               double mults_t) {
   sign_info *in = ms.info;
   if (!in) return;
   int k = ms.trace_count;
@@ -111,9 +112,12 @@ void trace_put(MatState &ms, int64_t nnz_x, int64_t nnz_t, double r, double x, i
   if (in->fnorm_k) in->fnorm_k[k] = 0.0;
   if (in->nnz_bar) in->nnz_bar[k] = 0;
   if (in->prec_k) in->prec_k[k] = prec;
+  if (in->mults_t) in->mults_t[k] = mults_t;
+  if (in->mults_bar) in->mults_bar[k] = 0.0;
 }
 
-void trace_filter(MatState &ms, double beta, double tau, double fnorm, int64_t nnz_bar) {
+void trace_filter(MatState &ms, double beta, double tau, double fnorm, int64_t nnz_bar,
+                  double mults_bar) {
   sign_info *in = ms.info;
   if (!in || ms.trace_count == 0 || ms.trace_count > in->cap) return;
   int k = ms.trace_count - 1;
@@ -121,6 +125,7 @@ void trace_filter(MatState &ms, double beta, double tau, double fnorm, int64_t n
   if (in->tau_k) in->tau_k[k] = tau;
   if (in->fnorm_k) in->fnorm_k[k] = fnorm;
   if (in->nnz_bar) in->nnz_bar[k] = nnz_bar;
+  if (in->mults_bar) in->mults_bar[k] = mults_bar;
 }
 
 // A matrix's rows taken out of a stage (moved to FP64 or pending assembly).
@@ -132,7 +137,7 @@ struct Parked {
 // Shared scratch of one solve call.
 struct Work {
   DevBuf lo, len, cnt, wlist, clist, counters, part, scan_tmp, eoff, sums, ms, active, sel,
-      asm_blocks, asm_off, asm_lens, dropped, norm_work, norm;
+      asm_blocks, asm_off, asm_lens, dropped, norm_work, norm, work, mults;
 };
 
 template <typename T>
@@ -183,6 +188,7 @@ struct Solver {
     w.scan_tmp.ensure(sizeof(int64_t) * size_t(scan_tmp_elems(N)), s);
     h2d(w.asm_blocks.p, blocks.data(), blocks.size(), s);
     h2d(w.asm_off.p, boff.data(), boff.size(), s);
+    ProfScope ps(KC_ASSEMBLE, s, 0.0, double(nnz) * (8.0 + 4.0 + sizeof(TD)) + 16.0 * double(N));
     launch_assemble_rows(nb, w.asm_blocks.as<AsmBlock>(), w.asm_off.as<int64_t>(), N,
                          w.asm_lens.as<int64_t>(), dst.d_rp(), w.scan_tmp.as<int64_t>(), s);
     launch_assemble_vals(nb, w.asm_blocks.as<AsmBlock>(), w.asm_off.as<int64_t>(), N, dst.d_rp(),
@@ -213,10 +219,11 @@ struct Solver {
   }
 
   // ---------------------------------------------------------------- product
-  // C = A B (MODE_SQUARE: B = A) for a stage; returns per-matrix nnz offsets.
+  // C = A B (MODE_SQUARE: B = A) for a stage; returns per-matrix nnz offsets
+  // of C and fills mults with the per-matrix multiply-adds.
   template <typename T>
   std::vector<int64_t> product(Stage<T> &st, const Csr<T> &A, const Csr<T> &B, int mode, Csr<T> &C,
-                               const int *active) {
+                               const int *active, std::vector<double> &mults) {
     int64_t N = A.n;
     int nb = int(st.mats.size());
     w.lo.ensure(sizeof(int32_t) * size_t(N), s);
@@ -224,17 +231,33 @@ struct Solver {
     w.cnt.ensure(sizeof(int64_t) * size_t(N), s);
     w.wlist.ensure(sizeof(int32_t) * size_t(N), s);
     w.clist.ensure(sizeof(int32_t) * size_t(N), s);
+    w.work.ensure(sizeof(double) * size_t(N), s);
+    w.mults.ensure(sizeof(double) * size_t(nb), s);
     w.counters.ensure(sizeof(int) * 8, s);
     w.scan_tmp.ensure(sizeof(int64_t) * size_t(scan_tmp_elems(N)), s);
     SGN_CUDA(cudaMemsetAsync(w.counters.p, 0, sizeof(int) * 8, s));
-    launch_bounds(N, A.d_rp(), A.d_col(), B.d_rp(), B.d_col(), st.d_seg.template as<int32_t>(), active,
-                  mode, w.lo.as<int32_t>(), w.len.as<int32_t>(), w.cnt.as<int64_t>(),
-                  w.wlist.as<int32_t>(), w.clist.as<int32_t>(), w.counters.as<int>(), s);
-    launch_symbolic(N, A.d_rp(), A.d_col(), B.d_rp(), B.d_col(), mode, w.lo.as<int32_t>(),
-                    w.len.as<int32_t>(), w.wlist.as<int32_t>(), w.clist.as<int32_t>(),
-                    w.counters.as<int>(), w.cnt.as<int64_t>(), s);
+    {
+      ProfScope ps(KC_BOUNDS, s);
+      launch_bounds(N, A.d_rp(), A.d_col(), B.d_rp(), B.d_col(), st.d_seg.template as<int32_t>(),
+                    active, mode, w.lo.as<int32_t>(), w.len.as<int32_t>(), w.cnt.as<int64_t>(),
+                    w.wlist.as<int32_t>(), w.clist.as<int32_t>(), w.counters.as<int>(),
+                    w.work.as<double>(), s);
+      launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.work.as<double>(), 1,
+                        w.mults.as<double>(), s);
+    }
+    {
+      ProfScope ps(KC_SYMBOLIC, s);
+      launch_symbolic(N, A.d_rp(), A.d_col(), B.d_rp(), B.d_col(), mode, w.lo.as<int32_t>(),
+                      w.len.as<int32_t>(), w.wlist.as<int32_t>(), w.clist.as<int32_t>(),
+                      w.counters.as<int>(), w.cnt.as<int64_t>(), s);
+    }
     C.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
-    launch_scan(N, w.cnt.as<int64_t>(), C.d_rp(), w.scan_tmp.as<int64_t>(), s);
+    {
+      ProfScope ps(KC_SCAN, s);
+      launch_scan(N, w.cnt.as<int64_t>(), C.d_rp(), w.scan_tmp.as<int64_t>(), s);
+    }
+    mults.assign(nb, 0.0);
+    d2h(mults.data(), w.mults.p, size_t(nb), s);
     std::vector<int64_t> eoff = entry_offsets(st.moff, st.d_moff, C.d_rp());
     int64_t nnz = eoff[nb];
     C.n = N;
@@ -242,10 +265,21 @@ struct Solver {
     C.col.ensure(sizeof(int32_t) * size_t(nnz > 0 ? nnz : 1), s);
     C.val.ensure(sizeof(T) * size_t(nnz > 0 ? nnz : 1), s);
     if (mode == MODE_SQUARE) w.part.ensure(sizeof(double) * size_t(2 * N), s);
-    launch_numeric<T>(N, A.d_rp(), A.d_col(), A.d_val(), B.d_rp(), B.d_col(), B.d_val(), mode,
-                      w.lo.as<int32_t>(), w.len.as<int32_t>(), w.wlist.as<int32_t>(),
-                      w.clist.as<int32_t>(), w.counters.as<int>(), C.d_rp(), C.d_col(),
-                      C.d_val(), mode == MODE_SQUARE ? w.part.as<double>() : nullptr, s);
+    double fl = 0.0;
+    for (double v : mults) fl += 2.0 * v;
+    double per = 4.0 + sizeof(T);
+    double by = per * double(A.nnz + nnz) + 8.0 * 2.0 * double(N + 1);
+    if (mode == MODE_UPDATE) by += per * double(B.nnz) + 8.0 * double(N + 1);
+    else by += 16.0 * double(N);
+    int cls = mode == MODE_SQUARE ? (sizeof(T) == 8 ? KC_NUM_SQUARE_F64 : KC_NUM_SQUARE_F32)
+                                  : (sizeof(T) == 8 ? KC_NUM_UPDATE_F64 : KC_NUM_UPDATE_F32);
+    {
+      ProfScope ps(cls, s, fl, by);
+      launch_numeric<T>(N, A.d_rp(), A.d_col(), A.d_val(), B.d_rp(), B.d_col(), B.d_val(), mode,
+                        w.lo.as<int32_t>(), w.len.as<int32_t>(), w.wlist.as<int32_t>(),
+                        w.clist.as<int32_t>(), w.counters.as<int>(), C.d_rp(), C.d_col(),
+                        C.d_val(), mode == MODE_SQUARE ? w.part.as<double>() : nullptr, s);
+    }
     return eoff;
   }
 
@@ -297,13 +331,18 @@ struct Solver {
     h2d(w.active.p, act.data(), act.size(), s);
     std::vector<int64_t> ex = entry_offsets(st.moff, st.d_moff, st.X.d_rp());
     // ---- check: T = X X, r, x, budget (steps a2, a4)
-    std::vector<int64_t> et = product(st, st.X, st.X, MODE_SQUARE, st.Tm, w.active.as<int>());
+    std::vector<double> mt, mb;
+    std::vector<int64_t> et = product(st, st.X, st.X, MODE_SQUARE, st.Tm, w.active.as<int>(), mt);
     w.sums.ensure(sizeof(double) * size_t(2 * nb), s);
     w.ms.ensure(sizeof(MatScalars) * size_t(nb), s);
-    launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.part.as<double>(), 2, w.sums.as<double>(), s);
     double tol_stage = st.prec == 32 ? o.fp32_until : o.tol;
-    launch_matrix_scalars(nb, st.d_moff.template as<int64_t>(), w.sums.as<double>(), o.c4, tol_stage,
-                          o.switch_resid, w.ms.as<MatScalars>(), s);
+    {
+      ProfScope ps(KC_REDUCE, s);
+      launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.part.as<double>(), 2,
+                        w.sums.as<double>(), s);
+      launch_matrix_scalars(nb, st.d_moff.template as<int64_t>(), w.sums.as<double>(), o.c4,
+                            tol_stage, o.switch_resid, w.ms.as<MatScalars>(), s);
+    }
     std::vector<MatScalars> hms(nb);
     d2h(hms.data(), w.ms.p, size_t(nb), s);
     sync(s);
@@ -313,7 +352,7 @@ struct Solver {
     for (int i = 0; i < nb; ++i) {
       MatState &ms = m[st.mats[i]];
       double r = hms[i].r;
-      trace_put(ms, ex[i + 1] - ex[i], et[i + 1] - et[i], r, hms[i].x, st.prec);
+      trace_put(ms, ex[i + 1] - ex[i], et[i + 1] - et[i], r, hms[i].x, st.prec, mt[i]);
       ms.resid = r;
       int decision = 0;  // 0 update, 1 retire, 2 move
       if (st.prec == 64 && r <= o.tol) {
@@ -353,7 +392,7 @@ struct Solver {
     }
     if (changed) h2d(w.active.p, act.data(), act.size(), s);
     // ---- update: Xbar = 1.5 X - 0.5 X T (step a3)
-    std::vector<int64_t> eb = product(st, st.X, st.Tm, MODE_UPDATE, st.Xb, w.active.as<int>());
+    std::vector<int64_t> eb = product(st, st.X, st.Tm, MODE_UPDATE, st.Xb, w.active.as<int>(), mb);
     for (int i = 0; i < nb; ++i) hms[i].nnz_bar = eb[i + 1] - eb[i];
     h2d(w.ms.p, hms.data(), hms.size(), s);
     const int *d_act = w.active.as<int>();
@@ -361,6 +400,7 @@ struct Solver {
       st.Xh.swap(st.Xb);
     } else {
       // ---- threshold (step a5)
+      ProfScope psel(KC_SELECT, s, 0.0, double(st.Xb.nnz) * 3.0 * sizeof(T));
       if (o.filter == SIGN_FILTER_EXACT) {
         w.sel.ensure(select_scratch_bytes(nb, st.Xb.nnz), s);
         w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
@@ -373,6 +413,8 @@ struct Solver {
       // ---- filter + compaction (step a6)
       int64_t N = st.Xb.n;
       w.dropped.ensure(sizeof(double) * size_t(N > 0 ? N : 1), s);
+      ProfScope pf(KC_FILTER, s, 0.0,
+                   double(st.Xb.nnz) * (sizeof(T) + 4.0 + sizeof(T)) + 24.0 * double(N));
       launch_filter_count(N, st.d_seg.template as<int32_t>(), d_act, st.Xb.d_rp(), st.Xb.val.p, is_f32<T>(),
                           w.ms.as<MatScalars>(), w.cnt.as<int64_t>(), w.dropped.as<double>(), s);
       st.Xh.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
@@ -395,7 +437,7 @@ struct Solver {
     for (int i : keep_slots) {
       MatState &ms = m[st.mats[i]];
       trace_filter(ms, hms[i].beta, o.filter == SIGN_FILTER_NONE ? 0.0 : hms[i].tau,
-                   o.filter == SIGN_FILTER_NONE ? 0.0 : hms[i].fnorm, hms[i].nnz_bar);
+                   o.filter == SIGN_FILTER_NONE ? 0.0 : hms[i].fnorm, hms[i].nnz_bar, mb[i]);
       ms.k++;
     }
     st.X.swap(st.Xh);
@@ -434,6 +476,7 @@ struct Solver {
     if (o.scale_1norm) {
       w.norm_work.ensure(sizeof(unsigned long long) * size_t(2 * N + 4 * count), s);
       w.norm.ensure(sizeof(double) * size_t(count), s);
+      ProfScope ps(KC_NORM, s);
       launch_onenorm(count, s64.d_moff.as<int64_t>(), s64.d_seg.as<int32_t>(), N, s64.X.d_rp(),
                      s64.X.d_col(), s64.X.d_val(), w.norm_work.as<unsigned long long>(),
                      w.norm.as<double>(), s);
