@@ -144,6 +144,21 @@ void sign_destroy(sign_t h);
 /* Message of the calling thread's last failed call ("" if none). */
 const char *sign_last_error(void);
 
+/* EXACT element threshold (step a5) for one array of values, the rule the
+ * solver applies per matrix: tau is the smallest magnitude v such that the
+ * squares of all values with |x| <= v sum to more than b^2, so that dropping
+ * every |x| < tau keeps the dropped Frobenius norm <= b (Sec. 3.1: the
+ * threshold derived from a bound on ||F_k||; equal magnitudes share their
+ * fate). If all values with |x| <= b fit, tau is the smallest magnitude above
+ * b, and +inf if there is none.
+ *   val: nnz doubles, device pointer if on_device = 1, else host.
+ *   b:   the absolute Frobenius budget, finite and >= 0.
+ *   tau_out: host pointer receiving tau.
+ * Allocates its scratch stream-ordered (cudaMallocAsync) on cuda_stream and
+ * returns after the stream has finished. SIGN_EINVAL for bad arguments. */
+sign_status sign_threshold_exact(const double *val, int64_t nnz, double b, int on_device,
+                                 void *cuda_stream, double *tau_out);
+
 /* ---- observability (not part of the paper's method) -------------------- */
 
 /* Total CUDA kernel launches made by this library in this process. */

@@ -193,6 +193,20 @@ def solve_batch(mats, opts=None, trace_cap: int = 256, device_out: bool = False,
             h.close()
 
 
+def threshold_exact(values, b: float, stream=None) -> float:
+    """sign_threshold_exact on a numpy array (host) or CUDA torch tensor."""
+    on_dev = _is_torch_cuda(values)
+    if not on_dev:
+        values = np.ascontiguousarray(values, dtype=np.float64)
+    tau = C.c_double()
+    st = load().sign_threshold_exact(_ptr(values), int(values.shape[0]), float(b), int(on_dev),
+                                     stream if stream is not None else current_stream(),
+                                     C.byref(tau))
+    if st != SIGN_OK:
+        raise SignError(st, "sign_threshold_exact")
+    return tau.value
+
+
 def kernel_launches() -> int:
     return int(load().sign_kernel_launches())
 

@@ -516,6 +516,14 @@ struct Solver {
   }
 };
 
+}  // namespace
+
+namespace sgn {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace sgn
+
+namespace {
+
 sign_status fail(int status, const std::string &msg) {
   g_err = msg;
   return sign_status(status);

@@ -256,3 +256,37 @@ def test_invalid_inputs_rejected(sg):
     assert e.value.status == sg.SIGN_EINVAL
     with pytest.raises(SignError):
         sg.solve(w.tridiagonal(10), filter=7)
+
+
+# ---------------------------------------------------------------- threshold select (step a5)
+def _tau_ref(orc, vals, b):
+    """tau of the oracle's EXACT filter for an array (laid out as one CSR row per value)."""
+    n = len(vals)
+    rp = np.arange(n + 1, dtype=np.int64)
+    col = np.zeros(n, np.int32)
+    _, tau, _ = orc.filter_csr(n, (rp, col, vals), "exact", b)
+    return tau
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_threshold_exact_matches_oracle(sg, orc, seed):
+    rng = np.random.default_rng(seed)
+    n = 200_000
+    vals = rng.standard_normal(n) * 10.0 ** rng.uniform(-14, 0, n)
+    vals[rng.integers(0, n, 500)] = 0.0
+    ties = rng.integers(0, n, 3000)
+    vals[ties] = np.sign(vals[ties]) * 3.0e-9  # a tie group near the crossing
+    for b in [0.0, 1e-12, 1e-9, 2e-7, 1e-4, 1.0, 1e6]:
+        t_gpu = sg.threshold_exact(vals, b)
+        t_ref = _tau_ref(orc, vals, b)
+        assert t_gpu == t_ref, (b, t_gpu, t_ref)
+
+
+def test_threshold_exact_edge_cases(sg, orc):
+    assert sg.threshold_exact(np.zeros(0), 1.0) == math.inf
+    assert sg.threshold_exact(np.zeros(5), 1.0) == math.inf
+    v = np.array([1e-3, -1e-3, 2e-3, 5.0])
+    for b in (0.0, 1e-3, 1.5e-3, 2.5e-3, 1e3):
+        assert sg.threshold_exact(v, b) == _tau_ref(orc, v, b)
+    with pytest.raises(Exception):
+        sg.threshold_exact(v, -1.0)
