@@ -159,6 +159,23 @@ const char *sign_last_error(void);
 sign_status sign_threshold_exact(const double *val, int64_t nnz, double b, int on_device,
                                  void *cuda_stream, double *tau_out);
 
+/* The same threshold as sign_threshold_exact without any device allocation,
+ * for callers that cannot allocate: a process whose own pool already holds
+ * the GPU's memory (so a library cudaMalloc would fail or eat into it), or a
+ * loop that cannot afford the device-wide synchronization cudaMalloc/cudaFree
+ * may cause. The paper has no counterpart; it is a deployment convenience.
+ *   val: nnz doubles on the device (no host input: staging would allocate).
+ *   nnz: at most SIGN_NOALLOC_MAX_NNZ, else SIGN_EINVAL with a message.
+ * Scratch lives in one file-scope device array (about 8 MiB per GPU that
+ * loads the library, held until exit). The first call on each device, made
+ * with that device current, looks up the array's address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race, so the
+ * caller must serialize them. Returns after cuda_stream has finished. */
+#define SIGN_NOALLOC_MAX_NNZ ((int64_t)1 << 20)
+sign_status sign_threshold_exact_noalloc(const double *val, int64_t nnz, double b,
+                                         void *cuda_stream, double *tau_out);
+
 /* ---- observability (not part of the paper's method) -------------------- */
 
 /* Total CUDA kernel launches made by this library in this process. */

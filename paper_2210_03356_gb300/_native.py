@@ -59,6 +59,8 @@ SIGNATURES = {
     "sign_last_error": (C.c_char_p, []),
     "sign_threshold_exact": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_int, C.c_void_p,
                                        C.POINTER(C.c_double)]),
+    "sign_threshold_exact_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
+                                               C.POINTER(C.c_double)]),
     "sign_kernel_launches": (C.c_int64, []),
     "sign_prof_enable": (C.c_int, [C.c_int]),
     "sign_prof_read": (C.c_int, [C.c_void_p, C.c_int]),

@@ -100,8 +100,16 @@ void launch_matrix_scalars(int nb, const int64_t *moff, const double *sums, doub
                            double tol_stage, double switch_resid, MatScalars *ms, cudaStream_t s);
 
 // Threshold selection (EXACT) for every active matrix; writes ms[m].tau.
-// Scratch sizes: see select_scratch_bytes.
-size_t select_scratch_bytes(int nb, int64_t nnz);
+// The scratch holds, 256-byte aligned each: the level-0 histograms, the digit
+// histograms, one minimum per matrix, one select state of at most
+// kSelStateBytes per matrix, the candidate offsets and nnz candidate keys.
+constexpr size_t kSelStateBytes = 64;
+constexpr size_t sel_align(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t select_scratch_bytes(int nb, int64_t nnz) {
+  return sel_align(size_t(nb) * 1024 * 3 * 8) + sel_align(size_t(nb) * 256 * 3 * 8) +
+         sel_align(size_t(nb) * 8) + sel_align(size_t(nb) * kSelStateBytes) +
+         sel_align(size_t(nb + 1) * 8) + sel_align(size_t(nnz > 0 ? nnz : 1) * 8);
+}
 void launch_select_exact(int nb, const int64_t *eoff, const int *active, int64_t nnz,
                          const void *val, int val_f32, MatScalars *ms, void *scratch,
                          cudaStream_t s);

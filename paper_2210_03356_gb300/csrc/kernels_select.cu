@@ -72,7 +72,10 @@ struct SelScratch {
   unsigned long long *cand_off; // nb + 1
 };
 
-__host__ __device__ inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+static_assert(sizeof(SelState) <= kSelStateBytes, "select state outgrew its scratch slot");
+static_assert(NB0 == 1024 && NDIG == 256, "scratch layout in kernels.h assumes these sizes");
+
+__host__ __device__ inline size_t align_up(size_t x) { return sel_align(x); }
 
 SelScratch carve(void *base, int nb, int64_t nnz) {
   char *p = static_cast<char *>(base);
@@ -84,7 +87,7 @@ SelScratch carve(void *base, int nb, int64_t nnz) {
   s.minabove = reinterpret_cast<unsigned long long *>(p);
   p += align_up(size_t(nb) * 8);
   s.st = reinterpret_cast<SelState *>(p);
-  p += align_up(size_t(nb) * sizeof(SelState));
+  p += align_up(size_t(nb) * kSelStateBytes);
   s.cand_off = reinterpret_cast<unsigned long long *>(p);
   p += align_up(size_t(nb + 1) * 8);
   s.cand = reinterpret_cast<unsigned long long *>(p);
@@ -360,12 +363,6 @@ void launch_matrix_scalars(int nb, const int64_t *moff, const double *sums, doub
 void launch_select_bound(int nb, const int *active, MatScalars *ms, cudaStream_t s) {
   k_select_bound<<<(nb + 127) / 128, 128, 0, s>>>(nb, active, ms);
   SGN_LAUNCH_CHECK();
-}
-
-size_t select_scratch_bytes(int nb, int64_t nnz) {
-  return align_up(size_t(nb) * NB0 * 3 * 8) + align_up(size_t(nb) * NDIG * 3 * 8) +
-         align_up(size_t(nb) * 8) + align_up(size_t(nb) * sizeof(SelState)) +
-         align_up(size_t(nb + 1) * 8) + align_up(size_t(nnz > 0 ? nnz : 1) * 8);
 }
 
 void launch_select_exact(int nb, const int64_t *eoff, const int *active, int64_t nnz,
