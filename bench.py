@@ -272,7 +272,7 @@ def main():
             per_launch = p["bytes"] / max(p["launches"], 1)
     else:
         bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
-        achieved = p["bytes"] / (p["ms"] / 1e3) / 1e9
+        achieved = p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] else 0.0
         per_launch = p["bytes"] / max(p["launches"], 1)
     total_ms = sum(v["ms"] for v in prof.values())
     roofline = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,

@@ -47,6 +47,34 @@ void launch_onenorm(int nb, const int64_t *moff, const int32_t *seg, int64_t n, 
 void launch_scale(int64_t n, const int32_t *seg, const int64_t *rp, double *val,
                   const double *norm, cudaStream_t s);
 
+// out[m] = sum over the rows r of matrix m of (re[r] - rs[r]) (entries per
+// matrix of a slotted CSR).
+void launch_seg_count(int nb, const int64_t *moff, const int64_t *rs, const int64_t *re,
+                      int64_t *out, cudaStream_t s);
+
+// out[r] = re[r] - rs[r]; and the copy of slotted rows into a compact CSR
+// whose row pointers orp are the scan of those lengths (vsize: 4 or 8 bytes).
+void launch_row_lengths(int64_t n, const int64_t *rs, const int64_t *re, int64_t *out,
+                        cudaStream_t s);
+void launch_compact_rows(int64_t n, const int64_t *rs, const int64_t *re, const int32_t *col,
+                         const void *val, int vsize, const int64_t *orp, int32_t *ocol,
+                         void *oval, cudaStream_t s);
+
+// Copies whole matrices out of a compact stage CSR in one launch: block b
+// takes rows [row0, row0 + nrows) of (rp, col, val), rebases the row pointers
+// to start at 0, shifts the columns by col_shift and widens FP32 values.
+struct ExtractBlock {
+  const int64_t *rp;
+  const int32_t *col;
+  const void *val;
+  int val_f32;
+  int64_t row0, nrows, col_shift;
+  int64_t *drp;
+  int32_t *dcol;
+  double *dval;
+};
+void launch_extract(int nblocks, const ExtractBlock *blocks, cudaStream_t s);
+
 // out[m] = rp[moff[m]] for m = 0..nb (entry offsets of the matrices).
 void launch_gather_offsets(int nb, const int64_t *moff, const int64_t *rp, int64_t *out,
                            cudaStream_t s);
@@ -59,30 +87,32 @@ void launch_seg_reduce(int nb, const int64_t *moff, const double *part, int ncom
 // ---------------------------------------------------------------- spgemm
 enum ProductMode { MODE_SQUARE = 0, MODE_UPDATE = 1 };
 
+// An operand's rows: row i holds entries [rs[i], re[i]) of col (and the
+// values), columns ascending. Compact CSR: rs = rowptr, re = rowptr + 1.
+struct Rows {
+  const int64_t *rs;
+  const int64_t *re;
+  const int32_t *col;
+};
+
 // Per row i of C = A B (rows of inactive matrices are empty): the column
-// range [lo, lo+len) of the row (including A's own row in MODE_UPDATE),
-// sets cnt[i] = 0 for empty rows and appends non-empty rows to the warp list
-// (len <= WARP_W) or the CTA list. counters[0], counters[1] are the list
-// lengths (zeroed by the caller). work[i] = sum_{k in A_i} nnz(B_k), the
-// multiply-adds of the row.
-void launch_bounds(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
-                   const int32_t *bcol, const int32_t *seg, const int *active, int mode,
-                   int32_t *lo, int32_t *len, int64_t *cnt, int32_t *wlist, int32_t *clist,
-                   int *counters, double *work, cudaStream_t s);
-// Exact nnz of every listed row (symbolic product).
-void launch_symbolic(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
-                     const int32_t *bcol, int mode, const int32_t *lo, const int32_t *len,
-                     const int32_t *wlist, const int32_t *clist, const int *counters,
-                     int64_t *cnt, cudaStream_t s);
-// Numeric product into the pattern of crp. MODE_SQUARE: C = A A, and
-// part[2i] = sum_j (C_ij - delta_ij)^2, part[2i+1] = sum_k a_ik^2.
-// MODE_UPDATE: C = 1.5 A - 0.5 A B.
+// range [lo, lo+len) of the row (including A's own row in MODE_UPDATE), the
+// slot size ub[i] = min(len, work + (UPDATE ? nnz(A_i) : 0)) >= nnz(C_i), and
+// work[i] = sum_{k in A_i} nnz(B_k), the multiply-adds of the row. Non-empty
+// rows go to the warp list (len <= WARP_W) or the CTA list; counters[0],
+// counters[1] are the list lengths and counters[4], counters[5] the work-queue
+// heads of the numeric kernels (all zeroed by the caller).
+void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
+                   int mode, int32_t *lo, int32_t *len, int64_t *ub, int32_t *wlist,
+                   int32_t *clist, int *counters, double *work, cudaStream_t s);
+// Numeric product. Row i is written at cs[i] (exclusive scan of ub) and its
+// end stored in ce[i]. MODE_SQUARE: C = A A, and part[2i] = sum_j (C_ij -
+// delta_ij)^2, part[2i+1] = sum_k a_ik^2. MODE_UPDATE: C = 1.5 A - 0.5 A B.
 template <typename T>
-void launch_numeric(int64_t n, const int64_t *arp, const int32_t *acol, const T *aval,
-                    const int64_t *brp, const int32_t *bcol, const T *bval, int mode,
-                    const int32_t *lo, const int32_t *len, const int32_t *wlist,
-                    const int32_t *clist, const int *counters, const int64_t *crp, int32_t *ccol,
-                    T *cval, double *part, cudaStream_t s);
+void launch_numeric(int64_t n, const Rows &A, const T *aval, const Rows &B, const T *bval,
+                    int mode, const int32_t *lo, const int32_t *len, const int32_t *wlist,
+                    const int32_t *clist, const int *counters, const int64_t *cs, int64_t *ce,
+                    int32_t *ccol, T *cval, double *part, cudaStream_t s);
 
 // ---------------------------------------------------------------- filter
 // Per-matrix scalars after the check of the current iterates.
@@ -99,6 +129,18 @@ struct MatScalars {
 void launch_matrix_scalars(int nb, const int64_t *moff, const double *sums, double c4,
                            double tol_stage, double switch_resid, MatScalars *ms, cudaStream_t s);
 
+// The values a threshold is selected over: row r holds entries [rs[r], re[r])
+// of matrix seg[r]; rs == nullptr means one flat array of flat_nnz values of
+// matrix 0, cut into rows of kFlatRow values.
+constexpr int64_t kFlatRow = 16384;
+struct SelRows {
+  int64_t nrows;
+  const int32_t *seg;
+  const int64_t *rs;
+  const int64_t *re;
+  int64_t flat_nnz;
+};
+
 // Threshold selection (EXACT) for every active matrix; writes ms[m].tau.
 // The scratch holds, 256-byte aligned each: the level-0 histograms, the digit
 // histograms, one minimum per matrix, one select state of at most
@@ -110,19 +152,20 @@ constexpr size_t select_scratch_bytes(int nb, int64_t nnz) {
          sel_align(size_t(nb) * 8) + sel_align(size_t(nb) * kSelStateBytes) +
          sel_align(size_t(nb + 1) * 8) + sel_align(size_t(nnz > 0 ? nnz : 1) * 8);
 }
-void launch_select_exact(int nb, const int64_t *eoff, const int *active, int64_t nnz,
-                         const void *val, int val_f32, MatScalars *ms, void *scratch,
-                         cudaStream_t s);
+// The candidate capacity of the scratch must be at least the number of values.
+void launch_select_exact(int nb, const SelRows &R, const int *active, const void *val,
+                         int val_f32, MatScalars *ms, void *scratch, cudaStream_t s);
 // BOUND: tau = b / sqrt(nnz_bar) per matrix.
 void launch_select_bound(int nb, const int *active, MatScalars *ms, cudaStream_t s);
 
 // Keeps |x| >= tau_m and x != 0 (filter != NONE), counts kept entries per
 // row and the dropped sum of squares per row.
-void launch_filter_count(int64_t n, const int32_t *seg, const int *active, const int64_t *rp,
-                         const void *val, int val_f32, const MatScalars *ms, int64_t *cnt,
-                         double *dropped, cudaStream_t s);
-void launch_filter_write(int64_t n, const int32_t *seg, const int *active, const int64_t *rp,
-                         const int32_t *col, const void *val, int val_f32, const MatScalars *ms,
-                         const int64_t *orp, int32_t *ocol, void *oval, cudaStream_t s);
+void launch_filter_count(int64_t n, const int32_t *seg, const int *active, const int64_t *rs,
+                         const int64_t *re, const void *val, int val_f32, const MatScalars *ms,
+                         int64_t *cnt, double *dropped, cudaStream_t s);
+void launch_filter_write(int64_t n, const int32_t *seg, const int *active, const int64_t *rs,
+                         const int64_t *re, const int32_t *col, const void *val, int val_f32,
+                         const MatScalars *ms, const int64_t *orp, int32_t *ocol, void *oval,
+                         cudaStream_t s);
 
 }  // namespace sgn

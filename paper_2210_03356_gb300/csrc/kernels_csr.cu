@@ -288,7 +288,86 @@ __global__ void __launch_bounds__(RED_T) k_seg_reduce(const int64_t *moff, const
   }
 }
 
+__global__ void __launch_bounds__(RED_T) k_seg_count(const int64_t *moff, const int64_t *rs,
+                                                     const int64_t *re, int64_t *out) {
+  __shared__ int64_t sm[RED_T];
+  int m = blockIdx.x;
+  int64_t acc = 0;
+  for (int64_t r = moff[m] + threadIdx.x; r < moff[m + 1]; r += RED_T) acc += re[r] - rs[r];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = RED_T / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[m] = sm[0];
+}
+
+// One CTA per extracted matrix: rebased row pointers, shifted columns,
+// values widened to FP64.
+__global__ void k_extract(const ExtractBlock *blocks) {
+  const ExtractBlock B = blocks[blockIdx.x];
+  int64_t e0 = B.rp[B.row0];
+  for (int64_t i = threadIdx.x; i <= B.nrows; i += blockDim.x) B.drp[i] = B.rp[B.row0 + i] - e0;
+  int64_t ne = B.rp[B.row0 + B.nrows] - e0;
+  for (int64_t p = threadIdx.x; p < ne; p += blockDim.x) {
+    B.dcol[p] = int32_t(B.col[e0 + p] + B.col_shift);
+    B.dval[p] = B.val_f32 ? double(static_cast<const float *>(B.val)[e0 + p])
+                          : static_cast<const double *>(B.val)[e0 + p];
+  }
+}
+
+__global__ void k_row_lengths(int64_t n, const int64_t *rs, const int64_t *re, int64_t *out) {
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += int64_t(gridDim.x) * blockDim.x)
+    out[r] = re[r] - rs[r];
+}
+
+__global__ void k_compact_rows(int64_t n, const int64_t *rs, const int64_t *re,
+                               const int32_t *col, const void *val, int vsize, const int64_t *orp,
+                               int32_t *ocol, void *oval) {
+  int lane = lane_id();
+  for_each_row_warp(n, [&](int64_t r) {
+    int64_t b = rs[r], e = re[r], d = orp[r];
+    for (int64_t p = b + lane; p < e; p += 32) {
+      ocol[d + (p - b)] = col[p];
+      if (vsize == 8)
+        static_cast<double *>(oval)[d + (p - b)] = static_cast<const double *>(val)[p];
+      else
+        static_cast<float *>(oval)[d + (p - b)] = static_cast<const float *>(val)[p];
+    }
+  });
+}
+
 }  // namespace
+
+void launch_row_lengths(int64_t n, const int64_t *rs, const int64_t *re, int64_t *out,
+                        cudaStream_t s) {
+  if (n == 0) return;
+  k_row_lengths<<<grid_for(n, 256), 256, 0, s>>>(n, rs, re, out);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_compact_rows(int64_t n, const int64_t *rs, const int64_t *re, const int32_t *col,
+                         const void *val, int vsize, const int64_t *orp, int32_t *ocol,
+                         void *oval, cudaStream_t s) {
+  if (n == 0) return;
+  k_compact_rows<<<grid_for(n, 8), 256, 0, s>>>(n, rs, re, col, val, vsize, orp, ocol, oval);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_seg_count(int nb, const int64_t *moff, const int64_t *rs, const int64_t *re,
+                      int64_t *out, cudaStream_t s) {
+  if (nb == 0) return;
+  k_seg_count<<<nb, RED_T, 0, s>>>(moff, rs, re, out);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_extract(int nblocks, const ExtractBlock *blocks, cudaStream_t s) {
+  if (nblocks == 0) return;
+  k_extract<<<nblocks, 512, 0, s>>>(blocks);
+  SGN_LAUNCH_CHECK();
+}
 
 void launch_validate(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col,
                      const double *val, int *flag, cudaStream_t s) {

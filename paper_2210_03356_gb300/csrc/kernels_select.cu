@@ -77,7 +77,7 @@ static_assert(NB0 == 1024 && NDIG == 256, "scratch layout in kernels.h assumes t
 
 __host__ __device__ inline size_t align_up(size_t x) { return sel_align(x); }
 
-SelScratch carve(void *base, int nb, int64_t nnz) {
+SelScratch carve(void *base, int nb, int64_t nnz_unused) {
   char *p = static_cast<char *>(base);
   SelScratch s;
   s.hist0 = reinterpret_cast<unsigned long long *>(p);
@@ -91,20 +91,30 @@ SelScratch carve(void *base, int nb, int64_t nnz) {
   s.cand_off = reinterpret_cast<unsigned long long *>(p);
   p += align_up(size_t(nb + 1) * 8);
   s.cand = reinterpret_cast<unsigned long long *>(p);
-  (void)nnz;
+  (void)nnz_unused;
   return s;
 }
 
-__device__ __forceinline__ int find_seg(const int64_t *off, int nb, int64_t p) {
-  int lo = 0, hi = nb;  // off[lo] <= p < off[hi]
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (off[mid] <= p)
-      lo = mid;
-    else
-      hi = mid;
+// Rows of the values to select over: row r holds entries [rs[r], re[r]) and
+// belongs to matrix seg[r]; with rs == nullptr the values are one flat array
+// of flat_nnz entries cut into rows of FLAT_ROW, all of matrix 0.
+constexpr int64_t FLAT_ROW = kFlatRow;
+constexpr int64_t ROWS_PER_CHUNK = 64;
+
+__device__ __forceinline__ int row_mat(const SelRows &R, int64_t r) { return R.seg ? R.seg[r] : 0; }
+
+__device__ __forceinline__ void row_range(const SelRows &R, int64_t r, int64_t &b, int64_t &e) {
+  if (R.rs) {
+    b = R.rs[r];
+    e = R.re[r];
+  } else {
+    b = r * FLAT_ROW;
+    e = min(b + FLAT_ROW, R.flat_nnz);
   }
-  return lo;
+}
+
+__device__ __forceinline__ int64_t rows_per_chunk(const SelRows &R) {
+  return R.rs ? ROWS_PER_CHUNK : 1;
 }
 
 __device__ __forceinline__ unsigned long long key_of(const void *val, int f32, int64_t p) {
@@ -131,23 +141,72 @@ __device__ __forceinline__ int bucket0(unsigned long long key, unsigned long lon
   return t <= base ? 0 : int(t - base);
 }
 
-__global__ void k_sel_hist0(int nb, const int64_t *eoff, const int *active, int64_t nnz,
-                            const void *val, int f32, const MatScalars *ms, SelScratch sc) {
-  for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < nnz;
-       p += int64_t(gridDim.x) * blockDim.x) {
-    int m = find_seg(eoff, nb, p);
-    if (!active[m]) continue;
-    double b = ms[m].b;
-    unsigned long long bkey = (unsigned long long)__double_as_longlong(b);
-    unsigned long long key = key_of(val, f32, p);
-    if (key > bkey) {
-      atomicMin(&sc.minabove[m], key);
-      continue;
+// Level-0 histogram. A CTA takes a chunk of consecutive rows; the entries of
+// the chunk's first matrix (almost all of them: matrices span many chunks) go
+// to a shared-memory histogram flushed once per chunk, the rest straight to
+// the global one.
+__global__ void __launch_bounds__(256)
+    k_sel_hist0(int nb, SelRows R, const int *active, const void *val, int f32,
+                const MatScalars *ms, SelScratch sc) {
+  __shared__ unsigned int s_cnt[NB0];
+  __shared__ unsigned long long s_lo[NB0], s_hi[NB0];
+  __shared__ unsigned long long s_min;
+  (void)nb;
+  const int64_t rpc = rows_per_chunk(R);
+  const int64_t nchunks = (R.nrows + rpc - 1) / rpc;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    int64_t r0 = c * rpc, r1 = min(r0 + rpc, R.nrows);
+    int m0 = row_mat(R, r0);
+    for (int t = threadIdx.x; t < NB0; t += blockDim.x) {
+      s_cnt[t] = 0u;
+      s_lo[t] = 0ULL;
+      s_hi[t] = 0ULL;
     }
-    unsigned long long *h = sc.hist0 + (size_t(m) * NB0 + bucket0(key, bkey)) * 3;
-    atomicAdd(&h[0], 1ULL);
-    unsigned long long q = qval(key, b);
-    if (q) add128(h + 1, q);
+    if (threadIdx.x == 0) s_min = ~0ULL;
+    __syncthreads();
+    for (int64_t r = r0; r < r1; ++r) {
+      int m = row_mat(R, r);
+      if (!active[m]) continue;
+      double b = ms[m].b;
+      unsigned long long bkey = (unsigned long long)__double_as_longlong(b);
+      int64_t e0, e1;
+      row_range(R, r, e0, e1);
+      for (int64_t p = e0 + threadIdx.x; p < e1; p += blockDim.x) {
+        unsigned long long key = key_of(val, f32, p);
+        if (key > bkey) {
+          if (m == m0)
+            atomicMin(&s_min, key);
+          else
+            atomicMin(&sc.minabove[m], key);
+          continue;
+        }
+        int bk = bucket0(key, bkey);
+        unsigned long long q = qval(key, b);
+        if (m == m0) {
+          atomicAdd(&s_cnt[bk], 1u);
+          if (q) {
+            unsigned long long old = atomicAdd(&s_lo[bk], q);
+            if (old + q < old) atomicAdd(&s_hi[bk], 1ULL);
+          }
+        } else {
+          unsigned long long *h = sc.hist0 + (size_t(m) * NB0 + bk) * 3;
+          atomicAdd(&h[0], 1ULL);
+          if (q) add128(h + 1, q);
+        }
+      }
+    }
+    __syncthreads();
+    if (active[m0]) {
+      for (int t = threadIdx.x; t < NB0; t += blockDim.x) {
+        if (!s_cnt[t]) continue;
+        unsigned long long *h = sc.hist0 + (size_t(m0) * NB0 + t) * 3;
+        atomicAdd(&h[0], (unsigned long long)s_cnt[t]);
+        if (s_lo[t]) add128(h + 1, s_lo[t]);
+        if (s_hi[t]) atomicAdd(&h[2], s_hi[t]);
+      }
+      if (threadIdx.x == 0 && s_min != ~0ULL) atomicMin(&sc.minabove[m0], s_min);
+    }
+    __syncthreads();
   }
 }
 
@@ -202,17 +261,28 @@ __global__ void k_sel_candoff(int nb, SelScratch sc) {
   sc.cand_off[nb] = off;
 }
 
-__global__ void k_sel_extract(int nb, const int64_t *eoff, const int *active, int64_t nnz,
-                              const void *val, int f32, const MatScalars *ms, SelScratch sc) {
-  for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < nnz;
-       p += int64_t(gridDim.x) * blockDim.x) {
-    int m = find_seg(eoff, nb, p);
-    if (!active[m] || !sc.st[m].found) continue;
-    unsigned long long bkey = (unsigned long long)__double_as_longlong(ms[m].b);
-    unsigned long long key = key_of(val, f32, p);
-    if (key > bkey || (key >> 48) != (sc.st[m].prefix >> 48)) continue;
-    unsigned long long slot = atomicAdd(&sc.st[m].cursor, 1ULL);
-    sc.cand[sc.st[m].cand_off + slot] = key;
+__global__ void __launch_bounds__(256)
+    k_sel_extract(int nb, SelRows R, const int *active, const void *val, int f32,
+                  const MatScalars *ms, SelScratch sc) {
+  (void)nb;
+  const int64_t rpc = rows_per_chunk(R);
+  const int64_t nchunks = (R.nrows + rpc - 1) / rpc;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    int64_t r0 = c * rpc, r1 = min(r0 + rpc, R.nrows);
+    for (int64_t r = r0; r < r1; ++r) {
+      int m = row_mat(R, r);
+      if (!active[m] || !sc.st[m].found) continue;
+      unsigned long long bkey = (unsigned long long)__double_as_longlong(ms[m].b);
+      unsigned long long top = sc.st[m].prefix >> 48;
+      int64_t e0, e1;
+      row_range(R, r, e0, e1);
+      for (int64_t p = e0 + threadIdx.x; p < e1; p += blockDim.x) {
+        unsigned long long key = key_of(val, f32, p);
+        if (key > bkey || (key >> 48) != top) continue;
+        unsigned long long slot = atomicAdd(&sc.st[m].cursor, 1ULL);
+        sc.cand[sc.st[m].cand_off + slot] = key;
+      }
+    }
   }
 }
 
@@ -275,7 +345,7 @@ __global__ void k_sel_final(int nb, const int *active, SelScratch sc, MatScalars
 
 // ------------------------------------------------------------ filter
 __global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
-                               const int64_t *rp, const void *val, int f32,
+                               const int64_t *rs, const int64_t *re, const void *val, int f32,
                                const MatScalars *ms, int64_t *cnt, double *dropped) {
   int lane = lane_id();
   int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -286,7 +356,7 @@ __global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
     int c = 0;
     double d2 = 0.0;
     if (active[m]) {
-      for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) {
+      for (int64_t p = rs[r] + lane; p < re[r]; p += 32) {
         double x = f32 ? double(static_cast<const float *>(val)[p])
                        : static_cast<const double *>(val)[p];
         double ax = fabs(x);
@@ -309,7 +379,8 @@ __global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
 }
 
 __global__ void k_filter_write(int64_t n, const int32_t *seg, const int *active,
-                               const int64_t *rp, const int32_t *col, const void *val, int f32,
+                               const int64_t *rs, const int64_t *re, const int32_t *col,
+                               const void *val, int f32,
                                const MatScalars *ms, const int64_t *orp, int32_t *ocol,
                                void *oval) {
   int lane = lane_id();
@@ -321,7 +392,7 @@ __global__ void k_filter_write(int64_t n, const int32_t *seg, const int *active,
     if (!active[m]) continue;
     double tau = ms[m].tau;
     int64_t out = orp[r];
-    int64_t b = rp[r], e = rp[r + 1];
+    int64_t b = rs[r], e = re[r];
     for (int64_t p0 = b; p0 < e; p0 += 32) {
       int64_t p = p0 + lane;
       bool keep = false;
@@ -365,29 +436,29 @@ void launch_select_bound(int nb, const int *active, MatScalars *ms, cudaStream_t
   SGN_LAUNCH_CHECK();
 }
 
-void launch_select_exact(int nb, const int64_t *eoff, const int *active, int64_t nnz,
-                         const void *val, int val_f32, MatScalars *ms, void *scratch,
-                         cudaStream_t s) {
-  SelScratch sc = carve(scratch, nb, nnz);
+void launch_select_exact(int nb, const SelRows &R, const int *active, const void *val,
+                         int val_f32, MatScalars *ms, void *scratch, cudaStream_t s) {
+  SelScratch sc = carve(scratch, nb, 0);
   SGN_CUDA(cudaMemsetAsync(sc.hist0, 0, size_t(nb) * NB0 * 3 * 8, s));
   SGN_CUDA(cudaMemsetAsync(sc.minabove, 0xff, size_t(nb) * 8, s));
-  int g = grid_for(nnz, 256);
-  if (nnz > 0) {
-    k_sel_hist0<<<g, 256, 0, s>>>(nb, eoff, active, nnz, val, val_f32, ms, sc);
+  int64_t rpc = R.rs ? 64 : 1;
+  int g = grid_for((R.nrows + rpc - 1) / rpc, 1, 152 * 8);
+  if (R.nrows > 0) {
+    k_sel_hist0<<<g, 256, 0, s>>>(nb, R, active, val, val_f32, ms, sc);
     SGN_LAUNCH_CHECK();
   }
   k_sel_find0<<<(nb + 127) / 128, 128, 0, s>>>(nb, active, ms, sc);
   SGN_LAUNCH_CHECK();
   k_sel_candoff<<<1, 32, 0, s>>>(nb, sc);
   SGN_LAUNCH_CHECK();
-  if (nnz > 0) {
-    k_sel_extract<<<g, 256, 0, s>>>(nb, eoff, active, nnz, val, val_f32, ms, sc);
+  if (R.nrows > 0) {
+    k_sel_extract<<<g, 256, 0, s>>>(nb, R, active, val, val_f32, ms, sc);
     SGN_LAUNCH_CHECK();
   }
   for (int level = 0; level < 6; ++level) {
     int shift = 40 - 8 * level;
     SGN_CUDA(cudaMemsetAsync(sc.hdig, 0, size_t(nb) * NDIG * 3 * 8, s));
-    k_sel_hist_digit<<<grid_for(nnz, 256, 152 * 4), 256, 0, s>>>(nb, ms, sc, shift);
+    k_sel_hist_digit<<<152 * 4, 256, 0, s>>>(nb, ms, sc, shift);
     SGN_LAUNCH_CHECK();
     k_sel_find_digit<<<(nb + 127) / 128, 128, 0, s>>>(nb, sc, shift);
     SGN_LAUNCH_CHECK();
@@ -396,21 +467,22 @@ void launch_select_exact(int nb, const int64_t *eoff, const int *active, int64_t
   SGN_LAUNCH_CHECK();
 }
 
-void launch_filter_count(int64_t n, const int32_t *seg, const int *active, const int64_t *rp,
-                         const void *val, int val_f32, const MatScalars *ms, int64_t *cnt,
-                         double *dropped, cudaStream_t s) {
+void launch_filter_count(int64_t n, const int32_t *seg, const int *active, const int64_t *rs,
+                         const int64_t *re, const void *val, int val_f32, const MatScalars *ms,
+                         int64_t *cnt, double *dropped, cudaStream_t s) {
   if (n == 0) return;
-  k_filter_count<<<grid_for(n, 8), 256, 0, s>>>(n, seg, active, rp, val, val_f32, ms, cnt,
+  k_filter_count<<<grid_for(n, 8), 256, 0, s>>>(n, seg, active, rs, re, val, val_f32, ms, cnt,
                                                  dropped);
   SGN_LAUNCH_CHECK();
 }
 
-void launch_filter_write(int64_t n, const int32_t *seg, const int *active, const int64_t *rp,
-                         const int32_t *col, const void *val, int val_f32, const MatScalars *ms,
-                         const int64_t *orp, int32_t *ocol, void *oval, cudaStream_t s) {
+void launch_filter_write(int64_t n, const int32_t *seg, const int *active, const int64_t *rs,
+                         const int64_t *re, const int32_t *col, const void *val, int val_f32,
+                         const MatScalars *ms, const int64_t *orp, int32_t *ocol, void *oval,
+                         cudaStream_t s) {
   if (n == 0) return;
-  k_filter_write<<<grid_for(n, 8), 256, 0, s>>>(n, seg, active, rp, col, val, val_f32, ms, orp,
-                                                 ocol, oval);
+  k_filter_write<<<grid_for(n, 8), 256, 0, s>>>(n, seg, active, rs, re, col, val, val_f32, ms,
+                                                 orp, ocol, oval);
   SGN_LAUNCH_CHECK();
 }
 

@@ -2,11 +2,20 @@
 //   MODE_SQUARE:  T = X X, plus per-row partial sums for ||T - I||_F and ||X||_F
 //   MODE_UPDATE:  Xbar = 1.5 X - 0.5 X T   (= 1/2 X (3I - X^2), Alg. 3.2.1 step 3)
 //
+// Operands are row ranges [rs[i], re[i]) into (col, val) with ascending
+// columns, so both compact CSR (rs = rowptr, re = rowptr + 1) and the slotted
+// outputs of earlier products can be read.
+//
 // Row i of C = A B is accumulated in shared memory over its column range
 // [lo_i, lo_i + len_i) (union of the ranges of the rows B_k, k in A_i), indexed
 // by column - lo_i, so the output comes out in ascending column order without
 // hashing or sorting. Rows with len <= WARP_W go to one warp each; wider rows
 // to one CTA each, in chunks of CTA_W columns.
+//
+// No symbolic pass: each output row gets a slot of ub_i = min(len_i, work_i)
+// entries (work_i = multiply-adds of the row, plus the row of A itself in
+// MODE_UPDATE), which bounds its number of distinct columns; the numeric
+// kernel writes the row at the start of its slot and records where it ends.
 //
 // Accumulation order: the k of A_i are visited in ascending order, one at a
 // time; within one k the lanes (threads) stride over the entries of B_k,
@@ -48,19 +57,19 @@ __device__ __forceinline__ int64_t lower_bound(const int32_t *a, int64_t lo, int
   return lo;
 }
 
-// counters: [0] warp-list length, [1] CTA-list length, [2],[3] symbolic
-// queue heads, [4],[5] numeric queue heads.
-__global__ void k_bounds(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
-                         const int32_t *bcol, const int32_t *seg, const int *active, int mode,
-                         int32_t *lo, int32_t *len, int64_t *cnt, int32_t *wlist, int32_t *clist,
-                         int *counters, double *work) {
+// counters: [0] warp-list length, [1] CTA-list length, [4],[5] work-queue heads.
+__global__ void k_bounds(int64_t n, const int64_t *ars, const int64_t *are, const int32_t *acol,
+                         const int64_t *brs, const int64_t *bre, const int32_t *bcol,
+                         const int32_t *seg, const int *active, int mode, int32_t *lo,
+                         int32_t *len, int64_t *ub, int32_t *wlist, int32_t *clist, int *counters,
+                         double *work) {
   int lane = lane_id();
   int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t r = warp; r < n; r += nwarps) {
     if (!active[seg[r]]) {
       if (lane == 0) {
-        cnt[r] = 0;
+        ub[r] = 0;
         len[r] = 0;
         lo[r] = 0;
         work[r] = 0.0;
@@ -69,9 +78,10 @@ __global__ void k_bounds(int64_t n, const int64_t *arp, const int32_t *acol, con
     }
     int32_t mn = INT_MAX, mx = -1;
     int64_t wk = 0;
-    for (int64_t p = arp[r] + lane; p < arp[r + 1]; p += 32) {
+    int64_t a0 = ars[r], a1 = are[r];
+    for (int64_t p = a0 + lane; p < a1; p += 32) {
       int32_t k = acol[p];
-      int64_t b0 = brp[k], b1 = brp[k + 1];
+      int64_t b0 = brs[k], b1 = bre[k];
       wk += b1 - b0;
       if (b1 > b0) {
         mn = min(mn, bcol[b0]);
@@ -91,13 +101,15 @@ __global__ void k_bounds(int64_t n, const int64_t *arp, const int32_t *acol, con
     if (lane == 0) {
       work[r] = double(wk);
       if (mx < 0) {
-        cnt[r] = 0;
+        ub[r] = 0;
         len[r] = 0;
         lo[r] = 0;
       } else {
         int32_t L = mx - mn + 1;
+        int64_t bound = wk + (mode == MODE_UPDATE ? a1 - a0 : 0);
         lo[r] = mn;
         len[r] = L;
+        ub[r] = bound < L ? bound : L;
         if (L <= WARP_W)
           wlist[atomicAdd(&counters[0], 1)] = int32_t(r);
         else
@@ -107,113 +119,40 @@ __global__ void k_bounds(int64_t n, const int64_t *arp, const int32_t *acol, con
   }
 }
 
-// ---------------------------------------------------------------- symbolic
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32)
-    k_sym_warp(const int64_t *arp, const int32_t *acol, const int64_t *brp, const int32_t *bcol,
-               int mode, const int32_t *lo, const int32_t *len, const int32_t *wlist,
-               int *counters, int64_t *cnt) {
-  __shared__ unsigned char flags[WARPS_PER_CTA][WARP_W];
-  int lane = lane_id(), w = threadIdx.x >> 5;
-  unsigned char *f = flags[w];
-  for (;;) {
-    int idx = 0;
-    if (lane == 0) idx = atomicAdd(&counters[2], 1);
-    idx = __shfl_sync(0xffffffffu, idx, 0);
-    if (idx >= counters[0]) break;
-    int32_t r = wlist[idx];
-    int L = len[r];
-    int32_t c0 = lo[r];
-    for (int s = lane; s < L; s += 32) f[s] = 0;
-    __syncwarp();
-    int64_t a0 = arp[r], a1 = arp[r + 1];
-    if (a1 - a0 >= 16) {
-      for (int64_t p = a0 + lane; p < a1; p += 32) {
-        int32_t k = acol[p];
-        for (int64_t q = brp[k]; q < brp[k + 1]; ++q) f[bcol[q] - c0] = 1;
-      }
-    } else {
-      for (int64_t p = a0; p < a1; ++p) {
-        int32_t k = acol[p];
-        for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) f[bcol[q] - c0] = 1;
-      }
-    }
-    if (mode == MODE_UPDATE)
-      for (int64_t p = a0 + lane; p < a1; p += 32) f[acol[p] - c0] = 1;
-    __syncwarp();
-    int c = 0;
-    for (int s = lane; s < L; s += 32) c += f[s];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) cnt[r] = c;
-    __syncwarp();
+// One k of the accumulation: lanes stride over B_k = [q0, q1) and add
+// a * b_kj into acc[col - c0]; four independent products per lane in flight.
+// The columns of B_k are distinct, so the slots of one call never collide.
+template <typename T, int STRIDE>
+__device__ __forceinline__ void accumulate_k(T a, int64_t q0, int64_t q1, const int32_t *bcol,
+                                             const T *bval, int64_t c0, T *acc,
+                                             unsigned char *f, int tid) {
+  int64_t q = q0 + tid;
+  for (; q + 3 * STRIDE < q1; q += 4 * STRIDE) {
+    int j0 = int(bcol[q] - c0), j1 = int(bcol[q + STRIDE] - c0);
+    int j2 = int(bcol[q + 2 * STRIDE] - c0), j3 = int(bcol[q + 3 * STRIDE] - c0);
+    T v0 = bval[q], v1 = bval[q + STRIDE], v2 = bval[q + 2 * STRIDE], v3 = bval[q + 3 * STRIDE];
+    acc[j0] = fma_rn(a, v0, acc[j0]);
+    acc[j1] = fma_rn(a, v1, acc[j1]);
+    acc[j2] = fma_rn(a, v2, acc[j2]);
+    acc[j3] = fma_rn(a, v3, acc[j3]);
+    f[j0] = 1;
+    f[j1] = 1;
+    f[j2] = 1;
+    f[j3] = 1;
+  }
+  for (; q < q1; q += STRIDE) {
+    int j = int(bcol[q] - c0);
+    acc[j] = fma_rn(a, bval[q], acc[j]);
+    f[j] = 1;
   }
 }
 
-constexpr int SYM_WORDS = SYM_BITS / 32;
-
-__global__ void __launch_bounds__(CTA_THREADS)
-    k_sym_cta(const int64_t *arp, const int32_t *acol, const int64_t *brp, const int32_t *bcol,
-              int mode, const int32_t *lo, const int32_t *len, const int32_t *clist,
-              int *counters, int64_t *cnt) {
-  extern __shared__ unsigned int bits[];  // SYM_WORDS
-  __shared__ int s_idx;
-  __shared__ int s_red[CTA_THREADS / 32];
-  int lane = lane_id(), w = threadIdx.x >> 5, nw = CTA_THREADS / 32;
-  for (;;) {
-    if (threadIdx.x == 0) s_idx = atomicAdd(&counters[3], 1);
-    __syncthreads();
-    int idx = s_idx;
-    __syncthreads();
-    if (idx >= counters[1]) break;
-    int32_t r = clist[idx];
-    int64_t L = len[r];
-    int64_t base = lo[r];
-    int64_t a0 = arp[r], a1 = arp[r + 1];
-    bool multi = L > SYM_BITS;
-    int64_t total = 0;
-    for (int64_t c0 = base; c0 < base + L; c0 += SYM_BITS) {
-      int64_t W = min(int64_t(SYM_BITS), base + L - c0);
-      int nwords = int((W + 31) / 32);
-      for (int s = threadIdx.x; s < nwords; s += CTA_THREADS) bits[s] = 0u;
-      __syncthreads();
-      for (int64_t p = a0 + w; p < a1; p += nw) {
-        int32_t k = acol[p];
-        int64_t s = brp[k], e = brp[k + 1];
-        if (multi) {
-          s = lower_bound(bcol, s, e, c0);
-          e = lower_bound(bcol, s, e, c0 + W);
-        }
-        for (int64_t q = s + lane; q < e; q += 32) {
-          int64_t j = bcol[q] - c0;
-          atomicOr(&bits[j >> 5], 1u << (j & 31));
-        }
-      }
-      if (mode == MODE_UPDATE)
-        for (int64_t p = a0 + threadIdx.x; p < a1; p += CTA_THREADS) {
-          int64_t j = int64_t(acol[p]) - c0;
-          if (j >= 0 && j < W) atomicOr(&bits[j >> 5], 1u << (j & 31));
-        }
-      __syncthreads();
-      int c = 0;
-      for (int s = threadIdx.x; s < nwords; s += CTA_THREADS) c += __popc(bits[s]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-      if (lane == 0) s_red[w] = c;
-      __syncthreads();
-      for (int i = 0; i < nw; ++i) total += s_red[i];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) cnt[r] = total;
-  }
-}
-
-// ---------------------------------------------------------------- numeric
 template <typename T, int MODE>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
-    k_num_warp(const int64_t *arp, const int32_t *acol, const T *aval, const int64_t *brp,
-               const int32_t *bcol, const T *bval, const int32_t *lo, const int32_t *len,
-               const int32_t *wlist, int *counters, const int64_t *crp, int32_t *ccol, T *cval,
-               double *part) {
+    k_num_warp(const int64_t *ars, const int64_t *are, const int32_t *acol, const T *aval,
+               const int64_t *brs, const int64_t *bre, const int32_t *bcol, const T *bval,
+               const int32_t *lo, const int32_t *len, const int32_t *wlist, int *counters,
+               const int64_t *cs, int64_t *ce, int32_t *ccol, T *cval, double *part) {
   __shared__ T acc_all[WARPS_PER_CTA][WARP_W];
   __shared__ unsigned char flags[WARPS_PER_CTA][WARP_W];
   int lane = lane_id(), w = threadIdx.x >> 5;
@@ -233,16 +172,10 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
       f[s] = 0;
     }
     __syncwarp();
-    int64_t a0 = arp[r], a1 = arp[r + 1];
+    int64_t a0 = ars[r], a1 = are[r];
     for (int64_t p = a0; p < a1; ++p) {  // ascending k
       int32_t k = acol[p];
-      T a = aval[p];
-      int64_t q1 = brp[k + 1];
-      for (int64_t q = brp[k] + lane; q < q1; q += 32) {
-        int j = bcol[q] - c0;
-        acc[j] = fma_rn(a, bval[q], acc[j]);
-        f[j] = 1;
-      }
+      accumulate_k<T, 32>(aval[p], brs[k], bre[k], bcol, bval, c0, acc, f, lane);
       __syncwarp();
     }
     if (MODE == MODE_UPDATE) {
@@ -253,7 +186,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
       }
       __syncwarp();
     }
-    int64_t out = crp[r];
+    int64_t out = cs[r];
     double rs = 0.0;
     bool diag = false;
     for (int s0 = 0; s0 < L; s0 += 32) {
@@ -278,6 +211,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
       }
       out += __popc(m);
     }
+    if (lane == 0) ce[r] = out;
     if (MODE == MODE_SQUARE) {
       double xs = 0.0;
       for (int64_t p = a0 + lane; p < a1; p += 32) {
@@ -306,10 +240,10 @@ constexpr size_t num_cta_smem() {
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(CTA_THREADS)
-    k_num_cta(const int64_t *arp, const int32_t *acol, const T *aval, const int64_t *brp,
-              const int32_t *bcol, const T *bval, const int32_t *lo, const int32_t *len,
-              const int32_t *clist, int *counters, const int64_t *crp, int32_t *ccol, T *cval,
-              double *part) {
+    k_num_cta(const int64_t *ars, const int64_t *are, const int32_t *acol, const T *aval,
+              const int64_t *brs, const int64_t *bre, const int32_t *bcol, const T *bval,
+              const int32_t *lo, const int32_t *len, const int32_t *clist, int *counters,
+              const int64_t *cs, int64_t *ce, int32_t *ccol, T *cval, double *part) {
   constexpr int CW = CtaW<T>::value;
   constexpr int NW = CTA_THREADS / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -331,10 +265,10 @@ __global__ void __launch_bounds__(CTA_THREADS)
     int32_t r = clist[idx];
     int64_t L = len[r];
     int64_t base = lo[r];
-    int64_t a0 = arp[r], a1 = arp[r + 1];
+    int64_t a0 = ars[r], a1 = are[r];
     int64_t nA = a1 - a0;
     bool multi = L > CW;
-    int64_t out = crp[r];
+    int64_t out = cs[r];
     double rs = 0.0;
     bool diag = false;
     for (int64_t c0 = base; c0 < base + L; c0 += CW) {
@@ -348,7 +282,7 @@ __global__ void __launch_bounds__(CTA_THREADS)
         int nk = int(min(int64_t(K_BATCH), nA - kb));
         if (threadIdx.x < nk) {
           int32_t k = acol[a0 + kb + threadIdx.x];
-          int64_t s = brp[k], e = brp[k + 1];
+          int64_t s = brs[k], e = bre[k];
           if (multi) {
             s = lower_bound(bcol, s, e, c0);
             e = lower_bound(bcol, s, e, c0 + W);
@@ -358,13 +292,8 @@ __global__ void __launch_bounds__(CTA_THREADS)
         }
         __syncthreads();
         for (int t = 0; t < nk; ++t) {  // ascending k
-          T a = aval[a0 + kb + t];
-          int64_t e = ke[t];
-          for (int64_t q = ks[t] + threadIdx.x; q < e; q += CTA_THREADS) {
-            int j = int(bcol[q] - c0);
-            acc[j] = fma_rn(a, bval[q], acc[j]);
-            f[j] = 1;
-          }
+          accumulate_k<T, CTA_THREADS>(aval[a0 + kb + t], ks[t], ke[t], bcol, bval, c0, acc, f,
+                                       threadIdx.x);
           __syncthreads();
         }
       }
@@ -411,6 +340,7 @@ __global__ void __launch_bounds__(CTA_THREADS)
         __syncthreads();
       }
     }
+    if (threadIdx.x == 0) ce[r] = out;
     if (MODE == MODE_SQUARE) {
       double xs = 0.0;
       for (int64_t p = a0 + threadIdx.x; p < a1; p += CTA_THREADS) {
@@ -442,18 +372,21 @@ __global__ void __launch_bounds__(CTA_THREADS)
   }
 }
 
-// Rows of T = X X with an empty pattern still contribute to the norms:
-// (0 - 1)^2 = 1 for the missing diagonal, and sum_k a_ik^2 for ||X||.
+// Rows with an empty column range: their slot stays empty (ce = cs) and, in
+// MODE_SQUARE, they still contribute (0 - 1)^2 = 1 for the missing diagonal
+// and sum_k a_ik^2 to the norms.
 template <typename T>
-__global__ void k_part_empty(int64_t n, const int64_t *arp, const T *aval, const int32_t *len,
-                             double *part) {
+__global__ void k_rows_empty(int64_t n, const int64_t *ars, const int64_t *are, const T *aval,
+                             const int32_t *len, const int64_t *cs, int64_t *ce, double *part) {
   int lane = lane_id();
   int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t r = warp; r < n; r += nwarps) {
     if (len[r] != 0) continue;
+    if (lane == 0) ce[r] = cs[r];
+    if (!part) continue;
     double xs = 0.0;
-    for (int64_t p = arp[r] + lane; p < arp[r + 1]; p += 32) {
+    for (int64_t p = ars[r] + lane; p < are[r]; p += 32) {
       double x = double(aval[p]);
       xs += x * x;
     }
@@ -486,43 +419,23 @@ int grid_cap(int64_t items, int per_block, int per_sm) {
 
 }  // namespace
 
-void launch_bounds(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
-                   const int32_t *bcol, const int32_t *seg, const int *active, int mode,
-                   int32_t *lo, int32_t *len, int64_t *cnt, int32_t *wlist, int32_t *clist,
-                   int *counters, double *work, cudaStream_t s) {
+void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
+                   int mode, int32_t *lo, int32_t *len, int64_t *ub, int32_t *wlist,
+                   int32_t *clist, int *counters, double *work, cudaStream_t s) {
   if (n == 0) return;
-  k_bounds<<<grid_cap(n, 8, 16), 256, 0, s>>>(n, arp, acol, brp, bcol, seg, active, mode, lo,
-                                               len, cnt, wlist, clist, counters, work);
-  SGN_LAUNCH_CHECK();
-}
-
-void launch_symbolic(int64_t n, const int64_t *arp, const int32_t *acol, const int64_t *brp,
-                     const int32_t *bcol, int mode, const int32_t *lo, const int32_t *len,
-                     const int32_t *wlist, const int32_t *clist, const int *counters,
-                     int64_t *cnt, cudaStream_t s) {
-  if (n == 0) return;
-  int *ctr = const_cast<int *>(counters);
-  k_sym_warp<<<grid_cap(n, WARPS_PER_CTA, 12), WARPS_PER_CTA * 32, 0, s>>>(
-      arp, acol, brp, bcol, mode, lo, len, wlist, ctr, cnt);
-  SGN_LAUNCH_CHECK();
-  static bool attr = false;
-  size_t sm = size_t(SYM_WORDS) * 4;
-  if (!attr) {
-    SGN_CUDA(cudaFuncSetAttribute(k_sym_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-    attr = true;
-  }
-  k_sym_cta<<<grid_cap(n, 1, 4), CTA_THREADS, sm, s>>>(arp, acol, brp, bcol, mode, lo, len, clist,
-                                                       ctr, cnt);
+  k_bounds<<<grid_cap(n, 8, 16), 256, 0, s>>>(n, A.rs, A.re, A.col, B.rs, B.re, B.col, seg, active,
+                                               mode, lo, len, ub, wlist, clist, counters, work);
   SGN_LAUNCH_CHECK();
 }
 
 template <typename T, int MODE>
-static void num_launch(int64_t n, const int64_t *arp, const int32_t *acol, const T *aval,
-                       const int64_t *brp, const int32_t *bcol, const T *bval, const int32_t *lo,
-                       const int32_t *len, const int32_t *wlist, const int32_t *clist, int *ctr,
-                       const int64_t *crp, int32_t *ccol, T *cval, double *part, cudaStream_t s) {
+static void num_launch(int64_t n, const Rows &A, const T *aval, const Rows &B, const T *bval,
+                       const int32_t *lo, const int32_t *len, const int32_t *wlist,
+                       const int32_t *clist, int *ctr, const int64_t *cs, int64_t *ce,
+                       int32_t *ccol, T *cval, double *part, cudaStream_t s) {
   k_num_warp<T, MODE><<<grid_cap(n, WARPS_PER_CTA, 6), WARPS_PER_CTA * 32, 0, s>>>(
-      arp, acol, aval, brp, bcol, bval, lo, len, wlist, ctr, crp, ccol, cval, part);
+      A.rs, A.re, A.col, aval, B.rs, B.re, B.col, bval, lo, len, wlist, ctr, cs, ce, ccol, cval,
+      part);
   SGN_LAUNCH_CHECK();
   static bool attr = false;
   constexpr size_t sm = num_cta_smem<T>();
@@ -532,39 +445,38 @@ static void num_launch(int64_t n, const int64_t *arp, const int32_t *acol, const
     attr = true;
   }
   k_num_cta<T, MODE><<<grid_cap(n, 1, 2), CTA_THREADS, sm, s>>>(
-      arp, acol, aval, brp, bcol, bval, lo, len, clist, ctr, crp, ccol, cval, part);
+      A.rs, A.re, A.col, aval, B.rs, B.re, B.col, bval, lo, len, clist, ctr, cs, ce, ccol, cval,
+      part);
   SGN_LAUNCH_CHECK();
 }
 
 template <typename T>
-void launch_numeric(int64_t n, const int64_t *arp, const int32_t *acol, const T *aval,
-                    const int64_t *brp, const int32_t *bcol, const T *bval, int mode,
-                    const int32_t *lo, const int32_t *len, const int32_t *wlist,
-                    const int32_t *clist, const int *counters, const int64_t *crp, int32_t *ccol,
-                    T *cval, double *part, cudaStream_t s) {
+void launch_numeric(int64_t n, const Rows &A, const T *aval, const Rows &B, const T *bval,
+                    int mode, const int32_t *lo, const int32_t *len, const int32_t *wlist,
+                    const int32_t *clist, const int *counters, const int64_t *cs, int64_t *ce,
+                    int32_t *ccol, T *cval, double *part, cudaStream_t s) {
   if (n == 0) return;
   int *ctr = const_cast<int *>(counters);
-  if (mode == MODE_SQUARE) {
-    k_part_empty<T><<<grid_cap(n, 8, 16), 256, 0, s>>>(n, arp, aval, len, part);
-    SGN_LAUNCH_CHECK();
-  }
+  k_rows_empty<T><<<grid_cap(n, 8, 16), 256, 0, s>>>(n, A.rs, A.re, aval, len, cs, ce,
+                                                      mode == MODE_SQUARE ? part : nullptr);
+  SGN_LAUNCH_CHECK();
   if (mode == MODE_SQUARE)
-    num_launch<T, MODE_SQUARE>(n, arp, acol, aval, brp, bcol, bval, lo, len, wlist, clist, ctr,
-                               crp, ccol, cval, part, s);
+    num_launch<T, MODE_SQUARE>(n, A, aval, B, bval, lo, len, wlist, clist, ctr, cs, ce, ccol, cval,
+                               part, s);
   else
-    num_launch<T, MODE_UPDATE>(n, arp, acol, aval, brp, bcol, bval, lo, len, wlist, clist, ctr,
-                               crp, ccol, cval, part, s);
+    num_launch<T, MODE_UPDATE>(n, A, aval, B, bval, lo, len, wlist, clist, ctr, cs, ce, ccol, cval,
+                               part, s);
 }
 
-template void launch_numeric<double>(int64_t, const int64_t *, const int32_t *, const double *,
-                                     const int64_t *, const int32_t *, const double *, int,
-                                     const int32_t *, const int32_t *, const int32_t *,
-                                     const int32_t *, const int *, const int64_t *, int32_t *,
-                                     double *, double *, cudaStream_t);
-template void launch_numeric<float>(int64_t, const int64_t *, const int32_t *, const float *,
-                                    const int64_t *, const int32_t *, const float *, int,
-                                    const int32_t *, const int32_t *, const int32_t *,
-                                    const int32_t *, const int *, const int64_t *, int32_t *,
-                                    float *, double *, cudaStream_t);
+template void launch_numeric<double>(int64_t, const Rows &, const double *, const Rows &,
+                                     const double *, int, const int32_t *, const int32_t *,
+                                     const int32_t *, const int32_t *, const int *,
+                                     const int64_t *, int64_t *, int32_t *, double *, double *,
+                                     cudaStream_t);
+template void launch_numeric<float>(int64_t, const Rows &, const float *, const Rows &,
+                                    const float *, int, const int32_t *, const int32_t *,
+                                    const int32_t *, const int32_t *, const int *,
+                                    const int64_t *, int64_t *, int32_t *, float *, double *,
+                                    cudaStream_t);
 
 }  // namespace sgn

@@ -128,27 +128,74 @@ void trace_filter(MatState &ms, double beta, double tau, double fnorm, int64_t n
   if (in->mults_bar) in->mults_bar[k] = mults_bar;
 }
 
-// A matrix's rows taken out of a stage (moved to FP64 or pending assembly).
+// A matrix's rows taken out of a stage (moving from FP32 to FP64).
 struct Parked {
   int mat;
   Csr<double> x;  // its rows, local column indices
 };
 
+// Output of a sparse product: row i occupies [rs[i], re[i]) of (col, val);
+// rs is the exclusive scan of the row slot sizes, so gaps may follow a row.
+template <typename T>
+struct Slotted {
+  int64_t n = 0, slots = 0;
+  DevBuf rs, re, col, val;
+  Rows rows() const { return Rows{rs.as<int64_t>(), re.as<int64_t>(), col.as<int32_t>()}; }
+  T *d_val() const { return val.as<T>(); }
+};
+
+template <typename T>
+Rows compact_rows(const Csr<T> &c) {
+  return Rows{c.d_rp(), c.d_rp() + 1, c.d_col()};
+}
+
 // Shared scratch of one solve call.
 struct Work {
-  DevBuf lo, len, cnt, wlist, clist, counters, part, scan_tmp, eoff, sums, ms, active, sel,
-      asm_blocks, asm_off, asm_lens, dropped, norm_work, norm, work, mults;
+  DevBuf lo, len, ub, wlist, clist, counters, part, scan_tmp, eoff, sums, ms, active, sel,
+      asm_blocks, asm_off, asm_lens, dropped, norm_work, norm, work, mults, cnt, nnzc, xblocks;
+};
+
+// Page-locked host mirrors of the per-matrix values read back every round.
+struct HostMirror {
+  void *p = nullptr;
+  MatScalars *ms = nullptr;
+  int64_t *ex = nullptr, *nnz_t = nullptr, *nnz_bar = nullptr, *tot = nullptr;
+  double *mults = nullptr, *dsum = nullptr;
+  ExtractBlock *xb = nullptr;
+  void alloc(int nb) {
+    size_t bytes = sizeof(MatScalars) * nb + sizeof(int64_t) * (4 * size_t(nb) + 8) +
+                   sizeof(double) * 2 * size_t(nb) + sizeof(ExtractBlock) * nb + 1024;
+    SGN_CUDA(cudaMallocHost(&p, bytes));
+    char *c = static_cast<char *>(p);
+    auto take = [&](size_t b) {
+      char *r = c;
+      c += (b + 63) & ~size_t(63);
+      return r;
+    };
+    ms = reinterpret_cast<MatScalars *>(take(sizeof(MatScalars) * nb));
+    ex = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (nb + 1)));
+    nnz_t = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * nb));
+    nnz_bar = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * nb));
+    tot = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * 4));
+    mults = reinterpret_cast<double *>(take(sizeof(double) * nb));
+    dsum = reinterpret_cast<double *>(take(sizeof(double) * nb));
+    xb = reinterpret_cast<ExtractBlock *>(take(sizeof(ExtractBlock) * nb));
+  }
+  ~HostMirror() {
+    if (p) cudaFreeHost(p);
+  }
 };
 
 template <typename T>
 struct Stage {
   int prec = sizeof(T) == 4 ? 32 : 64;
   std::vector<int> mats;          // matrix ids, in row order
+  std::vector<int> alive;         // 0 once a matrix has left (its rows are empty)
   std::vector<int64_t> moff;      // row offsets (host), size mats+1
   DevBuf d_moff, d_seg;
-  Csr<T> X, Tm, Xb, Xh;
-  bool rebuild = false;           // membership changed: reassemble X
-  std::vector<Parked *> incoming; // matrices entering at the next rebuild
+  Csr<T> X, Xh;                   // compact iterate and filtered update
+  Slotted<T> Tm, Xb;              // X X and 1.5 X - 0.5 X T
+  std::vector<Parked *> incoming; // matrices entering at the next round
 };
 
 struct Solver {
@@ -156,6 +203,7 @@ struct Solver {
   sign_opts o;
   std::vector<MatState> m;
   Work w;
+  HostMirror hm;
   std::vector<std::unique_ptr<Parked>> parked_store;
 
   // ---------------------------------------------------------------- helpers
@@ -170,7 +218,7 @@ struct Solver {
     launch_fill_seg(int(mats.size()), d_moff.as<int64_t>(), N, d_seg.as<int32_t>(), s);
   }
 
-  // Assembles dst (rows = sum of block rows) from blocks; returns its nnz.
+  // Assembles dst from blocks laid out one after another (block-diagonal).
   template <typename TD>
   void assemble(const std::vector<AsmBlock> &blocks, const std::vector<int64_t> &bnnz, Csr<TD> &dst) {
     int nb = int(blocks.size());
@@ -193,104 +241,93 @@ struct Solver {
                          w.asm_lens.as<int64_t>(), dst.d_rp(), w.scan_tmp.as<int64_t>(), s);
     launch_assemble_vals(nb, w.asm_blocks.as<AsmBlock>(), w.asm_off.as<int64_t>(), N, dst.d_rp(),
                          dst.d_col(), dst.val.p, is_f32<TD>(), s);
-    // the block and offset arrays are read by the kernels: keep them alive
+    // the block and offset arrays are pageable host copies: keep the stream in step
     sync(s);
-  }
-
-  // per-matrix entry offsets of a stage CSR (host copy)
-  std::vector<int64_t> entry_offsets(const std::vector<int64_t> &moff, DevBuf &d_moff,
-                                     const int64_t *rp) {
-    int nb = int(moff.size()) - 1;
-    w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
-    launch_gather_offsets(nb, d_moff.as<int64_t>(), rp, w.eoff.as<int64_t>(), s);
-    std::vector<int64_t> e(nb + 1);
-    d2h(e.data(), w.eoff.p, e.size(), s);
-    sync(s);
-    return e;
-  }
-
-  // Copies rows of matrix slot i of a stage CSR into a standalone FP64 CSR.
-  template <typename T>
-  void extract(const Stage<T> &st, const Csr<T> &X, const std::vector<int64_t> &eoff, int i,
-               Csr<double> &out) {
-    AsmBlock b{X.d_rp(), X.d_col(), X.val.p, st.moff[i], st.moff[i + 1] - st.moff[i],
-               -st.moff[i], is_f32<T>()};
-    assemble<double>({b}, {eoff[i + 1] - eoff[i]}, out);
   }
 
   // ---------------------------------------------------------------- product
-  // C = A B (MODE_SQUARE: B = A) for a stage; returns per-matrix nnz offsets
-  // of C and fills mults with the per-matrix multiply-adds.
+  // C = A B for a stage. Enqueues everything; on return C is allocated and the
+  // product queued, hm.mults holds the per-matrix multiply-adds (synced) and
+  // w.nnzc the per-matrix nnz of C (device, read with the next sync).
   template <typename T>
-  std::vector<int64_t> product(Stage<T> &st, const Csr<T> &A, const Csr<T> &B, int mode, Csr<T> &C,
-                               const int *active, std::vector<double> &mults) {
-    int64_t N = A.n;
+  void product(Stage<T> &st, const Rows &A, const T *aval, int64_t nnzA, const Rows &B,
+               const T *bval, int64_t nnzB, int mode, Slotted<T> &C, const int *active) {
+    int64_t N = int64_t(st.moff.back());
     int nb = int(st.mats.size());
     w.lo.ensure(sizeof(int32_t) * size_t(N), s);
     w.len.ensure(sizeof(int32_t) * size_t(N), s);
-    w.cnt.ensure(sizeof(int64_t) * size_t(N), s);
+    w.ub.ensure(sizeof(int64_t) * size_t(N), s);
     w.wlist.ensure(sizeof(int32_t) * size_t(N), s);
     w.clist.ensure(sizeof(int32_t) * size_t(N), s);
     w.work.ensure(sizeof(double) * size_t(N), s);
     w.mults.ensure(sizeof(double) * size_t(nb), s);
+    w.nnzc.ensure(sizeof(int64_t) * size_t(nb), s);
     w.counters.ensure(sizeof(int) * 8, s);
     w.scan_tmp.ensure(sizeof(int64_t) * size_t(scan_tmp_elems(N)), s);
     SGN_CUDA(cudaMemsetAsync(w.counters.p, 0, sizeof(int) * 8, s));
     {
       ProfScope ps(KC_BOUNDS, s);
-      launch_bounds(N, A.d_rp(), A.d_col(), B.d_rp(), B.d_col(), st.d_seg.template as<int32_t>(),
-                    active, mode, w.lo.as<int32_t>(), w.len.as<int32_t>(), w.cnt.as<int64_t>(),
-                    w.wlist.as<int32_t>(), w.clist.as<int32_t>(), w.counters.as<int>(),
-                    w.work.as<double>(), s);
+      launch_bounds(N, A, B, st.d_seg.template as<int32_t>(), active, mode, w.lo.as<int32_t>(),
+                    w.len.as<int32_t>(), w.ub.as<int64_t>(), w.wlist.as<int32_t>(),
+                    w.clist.as<int32_t>(), w.counters.as<int>(), w.work.as<double>(), s);
       launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.work.as<double>(), 1,
                         w.mults.as<double>(), s);
     }
-    {
-      ProfScope ps(KC_SYMBOLIC, s);
-      launch_symbolic(N, A.d_rp(), A.d_col(), B.d_rp(), B.d_col(), mode, w.lo.as<int32_t>(),
-                      w.len.as<int32_t>(), w.wlist.as<int32_t>(), w.clist.as<int32_t>(),
-                      w.counters.as<int>(), w.cnt.as<int64_t>(), s);
-    }
-    C.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
+    C.n = N;
+    C.rs.ensure(sizeof(int64_t) * size_t(N + 1), s);
+    C.re.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
     {
       ProfScope ps(KC_SCAN, s);
-      launch_scan(N, w.cnt.as<int64_t>(), C.d_rp(), w.scan_tmp.as<int64_t>(), s);
+      launch_scan(N, w.ub.as<int64_t>(), C.rs.template as<int64_t>(), w.scan_tmp.as<int64_t>(), s);
     }
-    mults.assign(nb, 0.0);
-    d2h(mults.data(), w.mults.p, size_t(nb), s);
-    std::vector<int64_t> eoff = entry_offsets(st.moff, st.d_moff, C.d_rp());
-    int64_t nnz = eoff[nb];
-    C.n = N;
-    C.nnz = nnz;
-    C.col.ensure(sizeof(int32_t) * size_t(nnz > 0 ? nnz : 1), s);
-    C.val.ensure(sizeof(T) * size_t(nnz > 0 ? nnz : 1), s);
+    d2h(hm.tot, C.rs.template as<int64_t>() + N, 1, s);
+    d2h(hm.mults, w.mults.p, size_t(nb), s);
+    sync(s);
+    int64_t slots = hm.tot[0];
+    C.slots = slots;
+    C.col.ensure(sizeof(int32_t) * size_t(slots > 0 ? slots : 1), s);
+    C.val.ensure(sizeof(T) * size_t(slots > 0 ? slots : 1), s);
     if (mode == MODE_SQUARE) w.part.ensure(sizeof(double) * size_t(2 * N), s);
     double fl = 0.0;
-    for (double v : mults) fl += 2.0 * v;
+    for (int i = 0; i < nb; ++i) fl += 2.0 * hm.mults[i];
     double per = 4.0 + sizeof(T);
-    double by = per * double(A.nnz + nnz) + 8.0 * 2.0 * double(N + 1);
-    if (mode == MODE_UPDATE) by += per * double(B.nnz) + 8.0 * double(N + 1);
-    else by += 16.0 * double(N);
+    // algorithmic bytes: A and B read once, C written once (its size is known
+    // after the launch; the slot total bounds it and is used here)
+    double by = per * double(nnzA + (mode == MODE_UPDATE ? nnzB : 0) + slots) +
+                8.0 * double(N + 1) * (mode == MODE_UPDATE ? 3.0 : 2.0) +
+                (mode == MODE_SQUARE ? 16.0 * double(N) : 0.0);
     int cls = mode == MODE_SQUARE ? (sizeof(T) == 8 ? KC_NUM_SQUARE_F64 : KC_NUM_SQUARE_F32)
                                   : (sizeof(T) == 8 ? KC_NUM_UPDATE_F64 : KC_NUM_UPDATE_F32);
     {
       ProfScope ps(cls, s, fl, by);
-      launch_numeric<T>(N, A.d_rp(), A.d_col(), A.d_val(), B.d_rp(), B.d_col(), B.d_val(), mode,
-                        w.lo.as<int32_t>(), w.len.as<int32_t>(), w.wlist.as<int32_t>(),
-                        w.clist.as<int32_t>(), w.counters.as<int>(), C.d_rp(), C.d_col(),
-                        C.d_val(), mode == MODE_SQUARE ? w.part.as<double>() : nullptr, s);
+      launch_numeric<T>(N, A, aval, B, bval, mode, w.lo.as<int32_t>(), w.len.as<int32_t>(),
+                        w.wlist.as<int32_t>(), w.clist.as<int32_t>(), w.counters.as<int>(),
+                        C.rs.template as<int64_t>(), C.re.template as<int64_t>(), C.col.template as<int32_t>(), C.d_val(),
+                        mode == MODE_SQUARE ? w.part.as<double>() : nullptr, s);
     }
-    return eoff;
+    launch_seg_count(nb, st.d_moff.template as<int64_t>(), C.rs.template as<int64_t>(),
+                     C.re.template as<int64_t>(), w.nnzc.as<int64_t>(), s);
   }
 
   // ---------------------------------------------------------------- rounds
+  // Re-lays out a stage with its live matrices and the incoming ones.
   template <typename T>
-  void rebuild(Stage<T> &st, const std::vector<int> &keep_slots, const std::vector<int64_t> &eoff) {
+  void rebuild(Stage<T> &st) {
+    int nb = int(st.mats.size());
+    std::vector<int64_t> eoff(nb + 1, 0);
+    if (nb > 0) {
+      w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
+      launch_gather_offsets(nb, st.d_moff.template as<int64_t>(), st.X.d_rp(),
+                            w.eoff.as<int64_t>(), s);
+      d2h(eoff.data(), w.eoff.p, eoff.size(), s);
+      sync(s);
+    }
     std::vector<int> mats;
     std::vector<AsmBlock> blocks;
     std::vector<int64_t> bnnz;
     int64_t off = 0;
-    for (int i : keep_slots) {
+    for (int i = 0; i < nb; ++i) {
+      if (!st.alive[i]) continue;
       int id = st.mats[i];
       blocks.push_back(AsmBlock{st.X.d_rp(), st.X.d_col(), st.X.val.p, st.moff[i],
                                 st.moff[i + 1] - st.moff[i], off - st.moff[i], is_f32<T>()});
@@ -308,31 +345,31 @@ struct Solver {
     assemble<T>(blocks, bnnz, nx);
     st.X.swap(nx);
     st.mats = mats;
+    st.alive.assign(mats.size(), 1);
     set_layout(st.moff, st.mats, st.d_moff, st.d_seg);
     st.incoming.clear();
-    st.rebuild = false;
   }
 
   template <typename T, typename TN>
   void round(Stage<T> &st, Stage<TN> *next) {
-    if (st.mats.empty() && st.incoming.empty()) return;
-    if (st.rebuild || !st.incoming.empty()) {
-      std::vector<int64_t> eoff =
-          st.mats.empty() ? std::vector<int64_t>{0} : entry_offsets(st.moff, st.d_moff, st.X.d_rp());
-      std::vector<int> all;
-      for (int i = 0; i < int(st.mats.size()); ++i) all.push_back(i);
-      rebuild(st, all, eoff);
-    }
+    if (!st.incoming.empty()) rebuild(st);
     int nb = int(st.mats.size());
-    if (nb == 0) return;
-    // all matrices of the stage take part in the check
-    std::vector<int> act(nb, 1);
+    int live = 0;
+    for (int a : st.alive) live += a;
+    if (live == 0) return;
+    int64_t N = st.moff.back();
     w.active.ensure(sizeof(int) * size_t(nb), s);
-    h2d(w.active.p, act.data(), act.size(), s);
-    std::vector<int64_t> ex = entry_offsets(st.moff, st.d_moff, st.X.d_rp());
+    h2d(w.active.p, st.alive.data(), st.alive.size(), s);
+    const int *d_act = w.active.as<int>();
+    // entry offsets of the iterate per matrix (read with the product's sync)
+    w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
+    launch_gather_offsets(nb, st.d_moff.template as<int64_t>(), st.X.d_rp(), w.eoff.as<int64_t>(), s);
+    d2h(hm.ex, w.eoff.p, size_t(nb + 1), s);
     // ---- check: T = X X, r, x, budget (steps a2, a4)
-    std::vector<double> mt, mb;
-    std::vector<int64_t> et = product(st, st.X, st.X, MODE_SQUARE, st.Tm, w.active.as<int>(), mt);
+    Rows xr = compact_rows(st.X);
+    product(st, xr, st.X.d_val(), st.X.nnz, xr, st.X.d_val(), st.X.nnz, MODE_SQUARE, st.Tm, d_act);
+    std::vector<int64_t> ex(hm.ex, hm.ex + nb + 1);
+    std::vector<double> mt(hm.mults, hm.mults + nb);
     w.sums.ensure(sizeof(double) * size_t(2 * nb), s);
     w.ms.ensure(sizeof(MatScalars) * size_t(nb), s);
     double tol_stage = st.prec == 32 ? o.fp32_until : o.tol;
@@ -343,16 +380,18 @@ struct Solver {
       launch_matrix_scalars(nb, st.d_moff.template as<int64_t>(), w.sums.as<double>(), o.c4,
                             tol_stage, o.switch_resid, w.ms.as<MatScalars>(), s);
     }
-    std::vector<MatScalars> hms(nb);
-    d2h(hms.data(), w.ms.p, size_t(nb), s);
+    d2h(hm.ms, w.ms.p, size_t(nb), s);
+    d2h(hm.nnz_t, w.nnzc.p, size_t(nb), s);
     sync(s);
-    // ---- per-matrix decisions (steps a7, a8)
-    std::vector<int> keep_slots;
+    std::vector<MatScalars> hms(hm.ms, hm.ms + nb);
+    // ---- per-matrix decisions (steps a7, a8); leavers copied out in one launch
+    int nx = 0;
     bool changed = false;
     for (int i = 0; i < nb; ++i) {
+      if (!st.alive[i]) continue;
       MatState &ms = m[st.mats[i]];
       double r = hms[i].r;
-      trace_put(ms, ex[i + 1] - ex[i], et[i + 1] - et[i], r, hms[i].x, st.prec, mt[i]);
+      trace_put(ms, ex[i + 1] - ex[i], hm.nnz_t[i], r, hms[i].x, st.prec, mt[i]);
       ms.resid = r;
       int decision = 0;  // 0 update, 1 retire, 2 move
       if (st.prec == 64 && r <= o.tol) {
@@ -367,90 +406,139 @@ struct Solver {
         ms.status = SIGN_ENOTCONV;
         decision = 1;
       }
-      if (decision == 0) {
-        keep_slots.push_back(i);
-        continue;
-      }
+      if (decision == 0) continue;
       changed = true;
-      act[i] = 0;
+      st.alive[i] = 0;
+      int64_t n_i = st.moff[i + 1] - st.moff[i], nnz_i = ex[i + 1] - ex[i];
+      Csr<double> *dst;
       if (decision == 1) {
-        extract(st, st.X, ex, i, ms.h->result);
+        dst = &ms.h->result;
         ms.h->has_result = true;
       } else {
         auto p = std::make_unique<Parked>();
         p->mat = st.mats[i];
-        extract(st, st.X, ex, i, p->x);
+        dst = &p->x;
         if (next) next->incoming.push_back(p.get());
         parked_store.push_back(std::move(p));
       }
+      dst->ensure(n_i, nnz_i, s);
+      hm.xb[nx++] = ExtractBlock{st.X.d_rp(), st.X.d_col(), st.X.val.p, is_f32<T>(), st.moff[i],
+                                 n_i, -st.moff[i], dst->d_rp(), dst->d_col(), dst->d_val()};
     }
-    if (keep_slots.empty()) {
-      st.mats.clear();
-      st.moff.assign(1, 0);
-      st.rebuild = false;
+    if (nx > 0) {
+      w.xblocks.ensure(sizeof(ExtractBlock) * size_t(nx), s);
+      h2d(w.xblocks.p, hm.xb, size_t(nx), s);
+      ProfScope ps(KC_ASSEMBLE, s);
+      launch_extract(nx, w.xblocks.as<ExtractBlock>(), s);
+    }
+    live = 0;
+    for (int a : st.alive) live += a;
+    if (live == 0) {
+      sync(s);  // the extraction reads X and the pinned block list
       return;
     }
-    if (changed) h2d(w.active.p, act.data(), act.size(), s);
+    if (changed) h2d(w.active.p, st.alive.data(), st.alive.size(), s);
     // ---- update: Xbar = 1.5 X - 0.5 X T (step a3)
-    std::vector<int64_t> eb = product(st, st.X, st.Tm, MODE_UPDATE, st.Xb, w.active.as<int>(), mb);
-    for (int i = 0; i < nb; ++i) hms[i].nnz_bar = eb[i + 1] - eb[i];
-    h2d(w.ms.p, hms.data(), hms.size(), s);
-    const int *d_act = w.active.as<int>();
+    int64_t nnz_t_all = 0;
+    for (int i = 0; i < nb; ++i) nnz_t_all += hm.nnz_t[i];
+    product(st, xr, st.X.d_val(), st.X.nnz, st.Tm.rows(), st.Tm.d_val(), nnz_t_all, MODE_UPDATE,
+            st.Xb, d_act);
+    std::vector<double> mb(hm.mults, hm.mults + nb);
+    d2h(hm.nnz_bar, w.nnzc.p, size_t(nb), s);
+    sync(s);
+    for (int i = 0; i < nb; ++i) hms[i].nnz_bar = hm.nnz_bar[i];
+    std::memcpy(hm.ms, hms.data(), sizeof(MatScalars) * nb);
+    h2d(w.ms.p, hm.ms, size_t(nb), s);
     if (o.filter == SIGN_FILTER_NONE) {
-      st.Xh.swap(st.Xb);
+      // keep every entry: compact the slotted rows as they are
+      hms_none(st, hms);
     } else {
-      // ---- threshold (step a5)
-      ProfScope psel(KC_SELECT, s, 0.0, double(st.Xb.nnz) * 3.0 * sizeof(T));
-      if (o.filter == SIGN_FILTER_EXACT) {
-        w.sel.ensure(select_scratch_bytes(nb, st.Xb.nnz), s);
-        w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
-        h2d(w.eoff.p, eb.data(), eb.size(), s);
-        launch_select_exact(nb, w.eoff.as<int64_t>(), d_act, st.Xb.nnz, st.Xb.val.p, is_f32<T>(),
-                            w.ms.as<MatScalars>(), w.sel.p, s);
-      } else {
-        launch_select_bound(nb, d_act, w.ms.as<MatScalars>(), s);
+      {
+        // ---- threshold (step a5)
+        ProfScope psel(KC_SELECT, s, 0.0, double(st.Xb.slots) * 2.0 * sizeof(T));
+        if (o.filter == SIGN_FILTER_EXACT) {
+          w.sel.ensure(select_scratch_bytes(nb, st.Xb.slots), s);
+          SelRows R{N, st.d_seg.template as<int32_t>(), st.Xb.rs.template as<int64_t>(),
+                    st.Xb.re.template as<int64_t>(), 0};
+          launch_select_exact(nb, R, d_act, st.Xb.val.p, is_f32<T>(), w.ms.as<MatScalars>(), w.sel.p,
+                              s);
+        } else {
+          launch_select_bound(nb, d_act, w.ms.as<MatScalars>(), s);
+        }
       }
-      // ---- filter + compaction (step a6)
-      int64_t N = st.Xb.n;
-      w.dropped.ensure(sizeof(double) * size_t(N > 0 ? N : 1), s);
-      ProfScope pf(KC_FILTER, s, 0.0,
-                   double(st.Xb.nnz) * (sizeof(T) + 4.0 + sizeof(T)) + 24.0 * double(N));
-      launch_filter_count(N, st.d_seg.template as<int32_t>(), d_act, st.Xb.d_rp(), st.Xb.val.p, is_f32<T>(),
-                          w.ms.as<MatScalars>(), w.cnt.as<int64_t>(), w.dropped.as<double>(), s);
-      st.Xh.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
-      launch_scan(N, w.cnt.as<int64_t>(), st.Xh.d_rp(), w.scan_tmp.as<int64_t>(), s);
-      launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.dropped.as<double>(), 1, w.sums.as<double>(), s);
-      std::vector<int64_t> eh = entry_offsets(st.moff, st.d_moff, st.Xh.d_rp());
-      st.Xh.n = N;
-      st.Xh.nnz = eh[nb];
-      st.Xh.col.ensure(sizeof(int32_t) * size_t(eh[nb] > 0 ? eh[nb] : 1), s);
-      st.Xh.val.ensure(sizeof(T) * size_t(eh[nb] > 0 ? eh[nb] : 1), s);
-      launch_filter_write(N, st.d_seg.template as<int32_t>(), d_act, st.Xb.d_rp(), st.Xb.d_col(), st.Xb.val.p,
-                          is_f32<T>(), w.ms.as<MatScalars>(), st.Xh.d_rp(), st.Xh.d_col(),
-                          st.Xh.val.p, s);
-      std::vector<double> dsum(nb);
-      d2h(hms.data(), w.ms.p, size_t(nb), s);
-      d2h(dsum.data(), w.sums.p, size_t(nb), s);
-      sync(s);
-      for (int i = 0; i < nb; ++i) hms[i].fnorm = std::sqrt(dsum[i]);
+      filter(st, d_act, hms);
     }
-    for (int i : keep_slots) {
+    for (int i = 0; i < nb; ++i) {
+      if (!st.alive[i]) continue;
       MatState &ms = m[st.mats[i]];
       trace_filter(ms, hms[i].beta, o.filter == SIGN_FILTER_NONE ? 0.0 : hms[i].tau,
                    o.filter == SIGN_FILTER_NONE ? 0.0 : hms[i].fnorm, hms[i].nnz_bar, mb[i]);
       ms.k++;
     }
     st.X.swap(st.Xh);
-    if (changed) {
-      // drop the rows of the matrices that left (their rows are empty now)
-      std::vector<int64_t> e2 = entry_offsets(st.moff, st.d_moff, st.X.d_rp());
-      rebuild(st, keep_slots, e2);
+  }
+
+  // Filter + compaction (step a6): Xh = entries of Xb with |x| >= tau, x != 0.
+  template <typename T>
+  void filter(Stage<T> &st, const int *d_act, std::vector<MatScalars> &hms) {
+    int64_t N = st.moff.back();
+    int nb = int(st.mats.size());
+    w.dropped.ensure(sizeof(double) * size_t(N > 0 ? N : 1), s);
+    w.cnt.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
+    ProfScope pf(KC_FILTER, s, 0.0, double(st.Xb.slots) * (2.0 * sizeof(T) + 4.0) + 24.0 * double(N));
+    launch_filter_count(N, st.d_seg.template as<int32_t>(), d_act, st.Xb.rs.template as<int64_t>(),
+                        st.Xb.re.template as<int64_t>(), st.Xb.val.p, is_f32<T>(),
+                        w.ms.as<MatScalars>(), w.cnt.as<int64_t>(), w.dropped.as<double>(), s);
+    st.Xh.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
+    launch_scan(N, w.cnt.as<int64_t>(), st.Xh.d_rp(), w.scan_tmp.as<int64_t>(), s);
+    launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.dropped.as<double>(), 1,
+                      w.sums.as<double>(), s);
+    d2h(hm.tot, st.Xh.d_rp() + N, 1, s);
+    d2h(hm.ms, w.ms.p, size_t(nb), s);
+    d2h(hm.dsum, w.sums.p, size_t(nb), s);
+    sync(s);
+    int64_t nnz = hm.tot[0];
+    st.Xh.n = N;
+    st.Xh.nnz = nnz;
+    st.Xh.col.ensure(sizeof(int32_t) * size_t(nnz > 0 ? nnz : 1), s);
+    st.Xh.val.ensure(sizeof(T) * size_t(nnz > 0 ? nnz : 1), s);
+    launch_filter_write(N, st.d_seg.template as<int32_t>(), d_act, st.Xb.rs.template as<int64_t>(),
+                        st.Xb.re.template as<int64_t>(), st.Xb.col.template as<int32_t>(),
+                        st.Xb.val.p, is_f32<T>(), w.ms.as<MatScalars>(), st.Xh.d_rp(),
+                        st.Xh.d_col(), st.Xh.val.p, s);
+    for (int i = 0; i < nb; ++i) {
+      hms[i].tau = hm.ms[i].tau;
+      hms[i].fnorm = std::sqrt(hm.dsum[i]);
     }
+  }
+
+  // No filter: the update is compacted with every entry kept (exact zeros too).
+  template <typename T>
+  void hms_none(Stage<T> &st, std::vector<MatScalars> &hms) {
+    (void)hms;
+    int64_t N = st.moff.back();
+    w.cnt.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
+    ProfScope pf(KC_FILTER, s, 0.0, double(st.Xb.slots) * (2.0 * sizeof(T) + 8.0));
+    launch_row_lengths(N, st.Xb.rs.template as<int64_t>(), st.Xb.re.template as<int64_t>(),
+                       w.cnt.as<int64_t>(), s);
+    st.Xh.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
+    launch_scan(N, w.cnt.as<int64_t>(), st.Xh.d_rp(), w.scan_tmp.as<int64_t>(), s);
+    d2h(hm.tot, st.Xh.d_rp() + N, 1, s);
+    sync(s);
+    int64_t nnz = hm.tot[0];
+    st.Xh.n = N;
+    st.Xh.nnz = nnz;
+    st.Xh.col.ensure(sizeof(int32_t) * size_t(nnz > 0 ? nnz : 1), s);
+    st.Xh.val.ensure(sizeof(T) * size_t(nnz > 0 ? nnz : 1), s);
+    launch_compact_rows(N, st.Xb.rs.template as<int64_t>(), st.Xb.re.template as<int64_t>(),
+                        st.Xb.col.template as<int32_t>(), st.Xb.val.p, sizeof(T), st.Xh.d_rp(),
+                        st.Xh.d_col(), st.Xh.val.p, s);
   }
 
   // ---------------------------------------------------------------- solve
   void run(sign_t *hs, int count, sign_info *infos) {
     m.resize(count);
+    hm.alloc(count);
     for (int i = 0; i < count; ++i) {
       m[i].h = hs[i];
       m[i].info = infos ? &infos[i] : nullptr;
@@ -470,17 +558,20 @@ struct Solver {
       off += hs[i]->n;
     }
     s64.mats = all;
+    s64.alive.assign(count, 1);
     set_layout(s64.moff, s64.mats, s64.d_moff, s64.d_seg);
     assemble<double>(blocks, bnnz, s64.X);
     int64_t N = off;
     if (o.scale_1norm) {
       w.norm_work.ensure(sizeof(unsigned long long) * size_t(2 * N + 4 * count), s);
       w.norm.ensure(sizeof(double) * size_t(count), s);
-      ProfScope ps(KC_NORM, s);
-      launch_onenorm(count, s64.d_moff.as<int64_t>(), s64.d_seg.as<int32_t>(), N, s64.X.d_rp(),
-                     s64.X.d_col(), s64.X.d_val(), w.norm_work.as<unsigned long long>(),
-                     w.norm.as<double>(), s);
       std::vector<double> nrm(count);
+      {
+        ProfScope ps(KC_NORM, s);
+        launch_onenorm(count, s64.d_moff.as<int64_t>(), s64.d_seg.as<int32_t>(), N, s64.X.d_rp(),
+                       s64.X.d_col(), s64.X.d_val(), w.norm_work.as<unsigned long long>(),
+                       w.norm.as<double>(), s);
+      }
       d2h(nrm.data(), w.norm.p, size_t(count), s);
       sync(s);
       for (int i = 0; i < count; ++i)
@@ -489,19 +580,26 @@ struct Solver {
       launch_scale(N, s64.d_seg.as<int32_t>(), s64.X.d_rp(), s64.X.d_val(), w.norm.as<double>(), s);
     }
     if (o.prec == SIGN_PREC_MIXED) {
-      std::vector<int64_t> ex = entry_offsets(s64.moff, s64.d_moff, s64.X.d_rp());
+      int64_t nnz = 0;
+      for (int64_t b : bnnz) nnz += b;
       std::vector<AsmBlock> b1{AsmBlock{s64.X.d_rp(), s64.X.d_col(), s64.X.val.p, 0, N, 0, 0}};
-      assemble<float>(b1, {ex.back()}, s32.X);
+      assemble<float>(b1, {nnz}, s32.X);
       s32.mats = all;
+      s32.alive.assign(count, 1);
       set_layout(s32.moff, s32.mats, s32.d_moff, s32.d_seg);
       s64.mats.clear();
+      s64.alive.clear();
       s64.moff.assign(1, 0);
     }
     for (int guard = 0; guard < 4 * o.max_iter + 16; ++guard) {
       round<float, double>(s32, &s64);
       round<double, double>(s64, nullptr);
-      if (s32.mats.empty() && s64.mats.empty() && s64.incoming.empty()) break;
+      bool any = !s64.incoming.empty();
+      for (int a : s32.alive) any |= a != 0;
+      for (int a : s64.alive) any |= a != 0;
+      if (!any) break;
     }
+    sync(s);
     for (int i = 0; i < count; ++i) {
       MatState &ms = m[i];
       if (ms.status < 0) throw Error(SIGN_ESTATE, "solve loop ended with a running matrix");

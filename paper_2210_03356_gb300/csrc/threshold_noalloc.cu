@@ -95,7 +95,8 @@ extern "C" sign_status sign_threshold_exact_noalloc(const double *val, int64_t n
     NoAllocHead *d = reinterpret_cast<NoAllocHead *>(base);
     SGN_CUDA(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     // the select kernels clear their histograms and state themselves
-    launch_select_exact(1, d->eoff, d->active, nnz, val, 0, &d->ms, base + kHeadBytes, s);
+    SelRows R{(nnz + kFlatRow - 1) / kFlatRow, nullptr, nullptr, nullptr, nnz};
+    launch_select_exact(1, R, d->active, val, 0, &d->ms, base + kHeadBytes, s);
     SGN_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
     SGN_CUDA(cudaStreamSynchronize(s));
     *tau_out = h.ms.tau;
