@@ -61,7 +61,12 @@ struct ProfScope {
   ~ProfScope();
 };
 
-// Grow-only device buffer, allocated stream-ordered.
+// The library's stream-ordered memory pool on the current device: it keeps
+// freed memory for reuse (release threshold = unlimited), so repeated solves
+// do not map and unmap device memory at every synchronization.
+cudaMemPool_t lib_pool();
+
+// Grow-only device buffer, allocated stream-ordered from lib_pool().
 struct DevBuf {
   void *p = nullptr;
   size_t cap = 0;
@@ -80,7 +85,7 @@ struct DevBuf {
     release();
     s = st;
     size_t want = bytes + bytes / 4 + 256;
-    SGN_CUDA(cudaMallocAsync(&p, want, st));
+    SGN_CUDA(cudaMallocFromPoolAsync(&p, want, lib_pool(), st));
     cap = want;
     return p;
   }

@@ -120,8 +120,9 @@ __global__ void k_bounds(int64_t n, const int64_t *ars, const int64_t *are, cons
 }
 
 // One k of the accumulation: lanes stride over B_k = [q0, q1) and add
-// a * b_kj into acc[col - c0]; four independent products per lane in flight.
-// The columns of B_k are distinct, so the slots of one call never collide.
+// a * b_kj into acc[col - c0], up to four independent products per lane in
+// flight. The columns of B_k are distinct, so the slots of one call never
+// collide.
 template <typename T, int STRIDE>
 __device__ __forceinline__ void accumulate_k(T a, int64_t q0, int64_t q1, const int32_t *bcol,
                                              const T *bval, int64_t c0, T *acc,
@@ -140,15 +141,29 @@ __device__ __forceinline__ void accumulate_k(T a, int64_t q0, int64_t q1, const 
     f[j2] = 1;
     f[j3] = 1;
   }
-  for (; q < q1; q += STRIDE) {
+  if (q + STRIDE < q1) {
+    int j0 = int(bcol[q] - c0), j1 = int(bcol[q + STRIDE] - c0);
+    T v0 = bval[q], v1 = bval[q + STRIDE];
+    acc[j0] = fma_rn(a, v0, acc[j0]);
+    acc[j1] = fma_rn(a, v1, acc[j1]);
+    f[j0] = 1;
+    f[j1] = 1;
+    q += 2 * STRIDE;
+  }
+  if (q < q1) {
     int j = int(bcol[q] - c0);
     acc[j] = fma_rn(a, bval[q], acc[j]);
     f[j] = 1;
   }
 }
 
+template <typename T>
+struct WarpOcc;  // CTAs per SM of the warp kernel (shared memory and registers)
+template <> struct WarpOcc<double> { static constexpr int value = 6; };
+template <> struct WarpOcc<float> { static constexpr int value = 8; };
+
 template <typename T, int MODE>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32)
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, WarpOcc<T>::value)
     k_num_warp(const int64_t *ars, const int64_t *are, const int32_t *acol, const T *aval,
                const int64_t *brs, const int64_t *bre, const int32_t *bcol, const T *bval,
                const int32_t *lo, const int32_t *len, const int32_t *wlist, int *counters,
@@ -173,10 +188,26 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
     }
     __syncwarp();
     int64_t a0 = ars[r], a1 = are[r];
-    for (int64_t p = a0; p < a1; ++p) {  // ascending k
-      int32_t k = acol[p];
-      accumulate_k<T, 32>(aval[p], brs[k], bre[k], bcol, bval, c0, acc, f, lane);
-      __syncwarp();
+    // ascending k; the (a_ik, start, end) of 32 k at a time are fetched by the
+    // lanes together and broadcast, so the dependent load chain
+    // acol -> row bounds -> B entries is paid once per 32 k
+    for (int64_t pb = a0; pb < a1; pb += 32) {
+      int nk = int(min(int64_t(32), a1 - pb));
+      T av = T(0);
+      int64_t qs = 0, qe = 0;
+      if (lane < nk) {
+        int32_t k = acol[pb + lane];
+        av = aval[pb + lane];
+        qs = brs[k];
+        qe = bre[k];
+      }
+      for (int t = 0; t < nk; ++t) {
+        T a = __shfl_sync(0xffffffffu, av, t);
+        int64_t q0 = __shfl_sync(0xffffffffu, qs, t);
+        int64_t q1 = __shfl_sync(0xffffffffu, qe, t);
+        accumulate_k<T, 32>(a, q0, q1, bcol, bval, c0, acc, f, lane);
+        __syncwarp();
+      }
     }
     if (MODE == MODE_UPDATE) {
       for (int64_t p = a0 + lane; p < a1; p += 32) {
@@ -433,7 +464,7 @@ static void num_launch(int64_t n, const Rows &A, const T *aval, const Rows &B, c
                        const int32_t *lo, const int32_t *len, const int32_t *wlist,
                        const int32_t *clist, int *ctr, const int64_t *cs, int64_t *ce,
                        int32_t *ccol, T *cval, double *part, cudaStream_t s) {
-  k_num_warp<T, MODE><<<grid_cap(n, WARPS_PER_CTA, 6), WARPS_PER_CTA * 32, 0, s>>>(
+  k_num_warp<T, MODE><<<grid_cap(n, WARPS_PER_CTA, WarpOcc<T>::value), WARPS_PER_CTA * 32, 0, s>>>(
       A.rs, A.re, A.col, aval, B.rs, B.re, B.col, bval, lo, len, wlist, ctr, cs, ce, ccol, cval,
       part);
   SGN_LAUNCH_CHECK();

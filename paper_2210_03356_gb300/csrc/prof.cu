@@ -65,6 +65,27 @@ void drain() {
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+cudaMemPool_t lib_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  SGN_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw Error(5, "device index out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    SGN_CUDA(cudaMemPoolCreate(&p, &props));
+    uint64_t keep = ~uint64_t(0);
+    SGN_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
 ProfScope::ProfScope(int c, cudaStream_t st, double f, double b) : cls(c), s(st), flops(f), bytes(b) {
   if (!g_prof_on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lk(g_mu);
