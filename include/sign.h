@@ -166,7 +166,7 @@ sign_status sign_threshold_exact(const double *val, int64_t nnz, double b, int o
  * may cause. The paper has no counterpart; it is a deployment convenience.
  *   val: nnz doubles on the device (no host input: staging would allocate).
  *   nnz: at most SIGN_NOALLOC_MAX_NNZ, else SIGN_EINVAL with a message.
- * Scratch lives in one file-scope device array (about 8 MiB per GPU that
+ * Scratch lives in one file-scope device array (about 12 MiB per GPU that
  * loads the library, held until exit). The first call on each device, made
  * with that device current, looks up the array's address
  * (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -48,7 +48,8 @@ constexpr int K_BATCH = 256;  // k entries whose B-row ranges are located at onc
 // Kernel classes timed when profiling is on (sign_prof_enable).
 enum KClass {
   KC_NUM_SQUARE_F64, KC_NUM_UPDATE_F64, KC_NUM_SQUARE_F32, KC_NUM_UPDATE_F32, KC_BOUNDS,
-  KC_SYMBOLIC, KC_SCAN, KC_SELECT, KC_FILTER, KC_REDUCE, KC_ASSEMBLE, KC_NORM, KC_COUNT
+  KC_SCAN, KC_SEL_HIST, KC_SEL_EXTRACT, KC_SEL_DIGITS, KC_SELECT, KC_FILTER, KC_REDUCE,
+  KC_ASSEMBLE, KC_NORM, KC_COUNT
 };
 // Records CUDA events around the enclosed launches on stream s (no-op when
 // profiling is off); flops and bytes are the algorithmic work they do.

@@ -142,19 +142,21 @@ struct SelRows {
 };
 
 // Threshold selection (EXACT) for every active matrix; writes ms[m].tau.
-// The scratch holds, 256-byte aligned each: the level-0 histograms, the digit
-// histograms, one minimum per matrix, one select state of at most
-// kSelStateBytes per matrix, the candidate offsets and nnz candidate keys.
+// The scratch holds, 256-byte aligned each: the level-0 histograms (1024
+// 128-bit sums per matrix), the digit histograms (256 per matrix), one
+// minimum per matrix, one select state of at most kSelStateBytes per matrix,
+// the candidate count, and room for cap candidates (8-byte key + matrix id).
 constexpr size_t kSelStateBytes = 64;
 constexpr size_t sel_align(size_t x) { return (x + 255) & ~size_t(255); }
-constexpr size_t select_scratch_bytes(int nb, int64_t nnz) {
-  return sel_align(size_t(nb) * 1024 * 3 * 8) + sel_align(size_t(nb) * 256 * 3 * 8) +
-         sel_align(size_t(nb) * 8) + sel_align(size_t(nb) * kSelStateBytes) +
-         sel_align(size_t(nb + 1) * 8) + sel_align(size_t(nnz > 0 ? nnz : 1) * 8);
+constexpr size_t select_scratch_bytes(int nb, int64_t cap) {
+  return sel_align(size_t(nb) * 1024 * 2 * 8) + sel_align(size_t(nb) * 256 * 2 * 8) +
+         sel_align(size_t(nb) * 8) + sel_align(size_t(nb) * kSelStateBytes) + sel_align(8) +
+         sel_align(size_t(cap > 0 ? cap : 1) * 8) + sel_align(size_t(cap > 0 ? cap : 1) * 4);
 }
-// The candidate capacity of the scratch must be at least the number of values.
-void launch_select_exact(int nb, const SelRows &R, const int *active, const void *val,
-                         int val_f32, MatScalars *ms, void *scratch, cudaStream_t s);
+// cand_cap (the scratch's candidate room) must be at least the number of values.
+void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *active,
+                         const void *val, int val_f32, MatScalars *ms, void *scratch,
+                         cudaStream_t s);
 // BOUND: tau = b / sqrt(nnz_bar) per matrix.
 void launch_select_bound(int nb, const int *active, MatScalars *ms, cudaStream_t s);
 

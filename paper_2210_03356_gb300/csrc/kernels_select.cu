@@ -56,20 +56,23 @@ __global__ void k_select_bound(int nb, const int *active, MatScalars *ms) {
 
 // ------------------------------------------------------------ EXACT select
 struct SelState {
-  unsigned long long prefix;  // key bits known so far
+  unsigned long long prefix;              // key bits known so far
   unsigned long long below_lo, below_hi;  // 128-bit sum of q strictly below the prefix range
-  unsigned long long cand_cnt, cand_off, cursor;
-  int found;  // 1: a crossing exists; 0: everything <= b fits
+  int found;                              // 1: a crossing exists; 0: everything <= b fits
   int pad;
 };
 
+// Scratch: 128-bit sums (lo, hi) per bucket for the level-0 and digit
+// histograms, the smallest key above b per matrix, the select states, the
+// candidate count and the candidates (key, matrix).
 struct SelScratch {
-  unsigned long long *hist0;    // nb * NB0 * 3  (count, lo, hi)
-  unsigned long long *hdig;     // nb * NDIG * 3
+  unsigned long long *hist0;    // nb * NB0 * 2
+  unsigned long long *hdig;     // nb * NDIG * 2
   unsigned long long *minabove; // nb
   SelState *st;                 // nb
-  unsigned long long *cand;     // nnz
-  unsigned long long *cand_off; // nb + 1
+  unsigned long long *ncand;    // 1
+  unsigned long long *cand;     // cap
+  int *cand_m;                  // cap
 };
 
 static_assert(sizeof(SelState) <= kSelStateBytes, "select state outgrew its scratch slot");
@@ -77,21 +80,22 @@ static_assert(NB0 == 1024 && NDIG == 256, "scratch layout in kernels.h assumes t
 
 __host__ __device__ inline size_t align_up(size_t x) { return sel_align(x); }
 
-SelScratch carve(void *base, int nb, int64_t nnz_unused) {
+SelScratch carve(void *base, int nb, int64_t cap) {
   char *p = static_cast<char *>(base);
   SelScratch s;
   s.hist0 = reinterpret_cast<unsigned long long *>(p);
-  p += align_up(size_t(nb) * NB0 * 3 * 8);
+  p += align_up(size_t(nb) * NB0 * 2 * 8);
   s.hdig = reinterpret_cast<unsigned long long *>(p);
-  p += align_up(size_t(nb) * NDIG * 3 * 8);
+  p += align_up(size_t(nb) * NDIG * 2 * 8);
   s.minabove = reinterpret_cast<unsigned long long *>(p);
   p += align_up(size_t(nb) * 8);
   s.st = reinterpret_cast<SelState *>(p);
   p += align_up(size_t(nb) * kSelStateBytes);
-  s.cand_off = reinterpret_cast<unsigned long long *>(p);
-  p += align_up(size_t(nb + 1) * 8);
+  s.ncand = reinterpret_cast<unsigned long long *>(p);
+  p += align_up(8);
   s.cand = reinterpret_cast<unsigned long long *>(p);
-  (void)nnz_unused;
+  p += align_up(size_t(cap > 0 ? cap : 1) * 8);
+  s.cand_m = reinterpret_cast<int *>(p);
   return s;
 }
 
@@ -100,6 +104,7 @@ SelScratch carve(void *base, int nb, int64_t nnz_unused) {
 // of flat_nnz entries cut into rows of FLAT_ROW, all of matrix 0.
 constexpr int64_t FLAT_ROW = kFlatRow;
 constexpr int64_t ROWS_PER_CHUNK = 64;
+constexpr int SEL_THREADS = 256;
 
 __device__ __forceinline__ int row_mat(const SelRows &R, int64_t r) { return R.seg ? R.seg[r] : 0; }
 
@@ -113,25 +118,26 @@ __device__ __forceinline__ void row_range(const SelRows &R, int64_t r, int64_t &
   }
 }
 
-__device__ __forceinline__ int64_t rows_per_chunk(const SelRows &R) {
-  return R.rs ? ROWS_PER_CHUNK : 1;
-}
-
 __device__ __forceinline__ unsigned long long key_of(const void *val, int f32, int64_t p) {
   double x = f32 ? double(static_cast<const float *>(val)[p]) : static_cast<const double *>(val)[p];
   return (unsigned long long)__double_as_longlong(fabs(x));
 }
 
-// q = round((x / b)^2 * 2^62), x <= b; 0 when b == 0.
+// q = round((x / b)^2 * 2^62), x <= b; 0 when b == 0. Entries with q == 0
+// (x < b 2^-31) add nothing to any sum and are always dropped, so the
+// histograms skip them.
 __device__ __forceinline__ unsigned long long qval(unsigned long long key, double b) {
   if (b == 0.0) return 0ULL;
   double r = __ddiv_rn(__longlong_as_double((long long)key), b);
   return __double2ull_rn(__dmul_rn(__dmul_rn(r, r), 4611686018427387904.0));
 }
 
-__device__ __forceinline__ void add128(unsigned long long *lohi, unsigned long long q) {
-  unsigned long long old = atomicAdd(&lohi[0], q);
-  if (old + q < old) atomicAdd(&lohi[1], 1ULL);
+// (lo, hi) += (alo, ahi) atomically in memory; exact, order-independent.
+__device__ __forceinline__ void add128(unsigned long long *lohi, unsigned long long alo,
+                                       unsigned long long ahi) {
+  unsigned long long old = atomicAdd(&lohi[0], alo);
+  if (old + alo < old) ++ahi;
+  if (ahi) atomicAdd(&lohi[1], ahi);
 }
 
 __device__ __forceinline__ int bucket0(unsigned long long key, unsigned long long bkey) {
@@ -141,69 +147,81 @@ __device__ __forceinline__ int bucket0(unsigned long long key, unsigned long lon
   return t <= base ? 0 : int(t - base);
 }
 
-// Level-0 histogram. A CTA takes a chunk of consecutive rows; the entries of
-// the chunk's first matrix (almost all of them: matrices span many chunks) go
-// to a shared-memory histogram flushed once per chunk, the rest straight to
-// the global one.
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+// Level-0 histogram. A CTA takes a chunk of consecutive rows, a warp one row
+// at a time, each lane a contiguous run of the row's entries. Neighbouring
+// entries of a row have similar magnitudes, so a lane sums its run per bucket
+// in registers and adds the run's total once when the bucket changes: into a
+// shared histogram for the chunk's first matrix (almost every row: matrices
+// span many chunks), else into the global one.
+__global__ void __launch_bounds__(SEL_THREADS)
     k_sel_hist0(int nb, SelRows R, const int *active, const void *val, int f32,
                 const MatScalars *ms, SelScratch sc) {
-  __shared__ unsigned int s_cnt[NB0];
-  __shared__ unsigned long long s_lo[NB0], s_hi[NB0];
+  __shared__ unsigned long long s_h[NB0 * 2];
   __shared__ unsigned long long s_min;
   (void)nb;
-  const int64_t rpc = rows_per_chunk(R);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = SEL_THREADS / 32;
+  const int64_t rpc = R.rs ? ROWS_PER_CHUNK : 1;
   const int64_t nchunks = (R.nrows + rpc - 1) / rpc;
   for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
     int64_t r0 = c * rpc, r1 = min(r0 + rpc, R.nrows);
     int m0 = row_mat(R, r0);
-    for (int t = threadIdx.x; t < NB0; t += blockDim.x) {
-      s_cnt[t] = 0u;
-      s_lo[t] = 0ULL;
-      s_hi[t] = 0ULL;
-    }
+    for (int t = threadIdx.x; t < 2 * NB0; t += SEL_THREADS) s_h[t] = 0ULL;
     if (threadIdx.x == 0) s_min = ~0ULL;
     __syncthreads();
-    for (int64_t r = r0; r < r1; ++r) {
+    for (int64_t r = r0 + warp; r < r1; r += nw) {
       int m = row_mat(R, r);
       if (!active[m]) continue;
       double b = ms[m].b;
       unsigned long long bkey = (unsigned long long)__double_as_longlong(b);
+      unsigned long long *hist = m == m0 ? s_h : sc.hist0 + size_t(m) * NB0 * 2;
       int64_t e0, e1;
       row_range(R, r, e0, e1);
-      for (int64_t p = e0 + threadIdx.x; p < e1; p += blockDim.x) {
+      int64_t per = (e1 - e0 + 31) / 32;
+      int64_t p0 = e0 + lane * per, p1 = min(p0 + per, e1);
+      int cur = -1;
+      unsigned long long clo = 0, chi = 0, mymin = ~0ULL;
+      for (int64_t p = p0; p < p1; ++p) {
         unsigned long long key = key_of(val, f32, p);
         if (key > bkey) {
-          if (m == m0)
-            atomicMin(&s_min, key);
-          else
-            atomicMin(&sc.minabove[m], key);
+          mymin = key < mymin ? key : mymin;
           continue;
         }
-        int bk = bucket0(key, bkey);
         unsigned long long q = qval(key, b);
-        if (m == m0) {
-          atomicAdd(&s_cnt[bk], 1u);
-          if (q) {
-            unsigned long long old = atomicAdd(&s_lo[bk], q);
-            if (old + q < old) atomicAdd(&s_hi[bk], 1ULL);
-          }
+        if (!q) continue;
+        int bk = bucket0(key, bkey);
+        if (bk != cur) {
+          if (cur >= 0) add128(hist + 2 * cur, clo, chi);
+          cur = bk;
+          clo = q;
+          chi = 0;
         } else {
-          unsigned long long *h = sc.hist0 + (size_t(m) * NB0 + bk) * 3;
-          atomicAdd(&h[0], 1ULL);
-          if (q) add128(h + 1, q);
+          clo += q;
+          if (clo < q) ++chi;
         }
+      }
+      if (cur >= 0) add128(hist + 2 * cur, clo, chi);
+      mymin = warp_min_u64(mymin);
+      if (lane == 0 && mymin != ~0ULL) {
+        if (m == m0)
+          atomicMin(&s_min, mymin);
+        else
+          atomicMin(&sc.minabove[m], mymin);
       }
     }
     __syncthreads();
     if (active[m0]) {
-      for (int t = threadIdx.x; t < NB0; t += blockDim.x) {
-        if (!s_cnt[t]) continue;
-        unsigned long long *h = sc.hist0 + (size_t(m0) * NB0 + t) * 3;
-        atomicAdd(&h[0], (unsigned long long)s_cnt[t]);
-        if (s_lo[t]) add128(h + 1, s_lo[t]);
-        if (s_hi[t]) atomicAdd(&h[2], s_hi[t]);
-      }
+      unsigned long long *g = sc.hist0 + size_t(m0) * NB0 * 2;
+      for (int t = threadIdx.x; t < NB0; t += SEL_THREADS)
+        if (s_h[2 * t] | s_h[2 * t + 1]) add128(g + 2 * t, s_h[2 * t], s_h[2 * t + 1]);
       if (threadIdx.x == 0 && s_min != ~0ULL) atomicMin(&sc.minabove[m0], s_min);
     }
     __syncthreads();
@@ -224,6 +242,7 @@ __device__ __forceinline__ bool exceeds(unsigned long long lo, unsigned long lon
 
 __global__ void k_sel_find0(int nb, const int *active, const MatScalars *ms, SelScratch sc) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m == 0) *sc.ncand = 0ULL;
   if (m >= nb) return;
   SelState st = {};
   if (active[m]) {
@@ -231,16 +250,15 @@ __global__ void k_sel_find0(int nb, const int *active, const MatScalars *ms, Sel
     long long base = (long long)(bkey >> 48) - (NB0 - 1);
     if (base < 0) base = 0;
     unsigned long long lo = 0, hi = 0;
-    const unsigned long long *h = sc.hist0 + size_t(m) * NB0 * 3;
+    const unsigned long long *h = sc.hist0 + size_t(m) * NB0 * 2;
     for (int c = 0; c < NB0; ++c) {
       unsigned long long nlo = lo, nhi = hi;
-      u128_add(nlo, nhi, h[3 * c + 1], h[3 * c + 2]);
+      u128_add(nlo, nhi, h[2 * c], h[2 * c + 1]);
       if (exceeds(nlo, nhi)) {
         st.found = 1;
         st.prefix = (unsigned long long)(base + c) << 48;
         st.below_lo = lo;
         st.below_hi = hi;
-        st.cand_cnt = h[3 * c];
         break;
       }
       lo = nlo;
@@ -250,63 +268,55 @@ __global__ void k_sel_find0(int nb, const int *active, const MatScalars *ms, Sel
   sc.st[m] = st;
 }
 
-__global__ void k_sel_candoff(int nb, SelScratch sc) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  unsigned long long off = 0;
-  for (int m = 0; m < nb; ++m) {
-    sc.cand_off[m] = off;
-    sc.st[m].cand_off = off;
-    off += sc.st[m].cand_cnt;
-  }
-  sc.cand_off[nb] = off;
-}
-
-__global__ void __launch_bounds__(256)
+// Candidates: the entries of the crossing bucket (top 16 bits of the key equal
+// to the prefix, key <= b), appended with one atomic per warp.
+__global__ void __launch_bounds__(SEL_THREADS)
     k_sel_extract(int nb, SelRows R, const int *active, const void *val, int f32,
                   const MatScalars *ms, SelScratch sc) {
   (void)nb;
-  const int64_t rpc = rows_per_chunk(R);
-  const int64_t nchunks = (R.nrows + rpc - 1) / rpc;
-  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-    int64_t r0 = c * rpc, r1 = min(r0 + rpc, R.nrows);
-    for (int64_t r = r0; r < r1; ++r) {
-      int m = row_mat(R, r);
-      if (!active[m] || !sc.st[m].found) continue;
-      unsigned long long bkey = (unsigned long long)__double_as_longlong(ms[m].b);
-      unsigned long long top = sc.st[m].prefix >> 48;
-      int64_t e0, e1;
-      row_range(R, r, e0, e1);
-      for (int64_t p = e0 + threadIdx.x; p < e1; p += blockDim.x) {
-        unsigned long long key = key_of(val, f32, p);
-        if (key > bkey || (key >> 48) != top) continue;
-        unsigned long long slot = atomicAdd(&sc.st[m].cursor, 1ULL);
-        sc.cand[sc.st[m].cand_off + slot] = key;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = warp; r < R.nrows; r += nwarps) {
+    int m = row_mat(R, r);
+    if (!active[m] || !sc.st[m].found) continue;
+    unsigned long long bkey = (unsigned long long)__double_as_longlong(ms[m].b);
+    unsigned long long top = sc.st[m].prefix >> 48;
+    int64_t e0, e1;
+    row_range(R, r, e0, e1);
+    for (int64_t p0 = e0; p0 < e1; p0 += 32) {
+      int64_t p = p0 + lane;
+      bool take = false;
+      unsigned long long key = 0;
+      if (p < e1) {
+        key = key_of(val, f32, p);
+        take = key <= bkey && (key >> 48) == top;
+      }
+      unsigned mask = __ballot_sync(0xffffffffu, take);
+      if (!mask) continue;
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(sc.ncand, (unsigned long long)__popc(mask));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (take) {
+        unsigned long long i = base + __popc(mask & lt);
+        sc.cand[i] = key;
+        sc.cand_m[i] = m;
       }
     }
   }
 }
 
-__global__ void k_sel_hist_digit(int nb, const MatScalars *ms, SelScratch sc, int shift) {
-  unsigned long long total = sc.cand_off[nb];
+__global__ void k_sel_hist_digit(const MatScalars *ms, SelScratch sc, int shift) {
+  unsigned long long total = *sc.ncand;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (unsigned long long)gridDim.x * blockDim.x) {
-    int lo = 0, hi = nb;
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (sc.cand_off[mid] <= i)
-        lo = mid;
-      else
-        hi = mid;
-    }
-    int m = lo;
+    int m = sc.cand_m[i];
     unsigned long long key = sc.cand[i];
-    unsigned long long pre = sc.st[m].prefix;
-    if ((key >> (shift + 8)) != (pre >> (shift + 8))) continue;
+    if ((key >> (shift + 8)) != (sc.st[m].prefix >> (shift + 8))) continue;
     int d = int((key >> shift) & 255ULL);
-    unsigned long long *h = sc.hdig + (size_t(m) * NDIG + d) * 3;
-    atomicAdd(&h[0], 1ULL);
     unsigned long long q = qval(key, ms[m].b);
-    if (q) add128(h + 1, q);
+    if (q) add128(sc.hdig + (size_t(m) * NDIG + d) * 2, q, 0ULL);
   }
 }
 
@@ -315,12 +325,12 @@ __global__ void k_sel_find_digit(int nb, SelScratch sc, int shift) {
   if (m >= nb) return;
   SelState &st = sc.st[m];
   if (!st.found) return;
-  const unsigned long long *h = sc.hdig + size_t(m) * NDIG * 3;
+  const unsigned long long *h = sc.hdig + size_t(m) * NDIG * 2;
   unsigned long long lo = st.below_lo, hi = st.below_hi;
   for (int d = 0; d < NDIG; ++d) {
     unsigned long long nlo = lo, nhi = hi;
-    u128_add(nlo, nhi, h[3 * d + 1], h[3 * d + 2]);
-    if (exceeds(nlo, nhi) && h[3 * d] > 0) {
+    u128_add(nlo, nhi, h[2 * d], h[2 * d + 1]);
+    if (exceeds(nlo, nhi)) {
       st.prefix |= (unsigned long long)d << shift;
       st.below_lo = lo;
       st.below_hi = hi;
@@ -436,29 +446,36 @@ void launch_select_bound(int nb, const int *active, MatScalars *ms, cudaStream_t
   SGN_LAUNCH_CHECK();
 }
 
-void launch_select_exact(int nb, const SelRows &R, const int *active, const void *val,
-                         int val_f32, MatScalars *ms, void *scratch, cudaStream_t s) {
-  SelScratch sc = carve(scratch, nb, 0);
-  SGN_CUDA(cudaMemsetAsync(sc.hist0, 0, size_t(nb) * NB0 * 3 * 8, s));
+void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *active,
+                         const void *val, int val_f32, MatScalars *ms, void *scratch,
+                         cudaStream_t s) {
+  SelScratch sc = carve(scratch, nb, cand_cap);
+  SGN_CUDA(cudaMemsetAsync(sc.hist0, 0, size_t(nb) * NB0 * 2 * 8, s));
   SGN_CUDA(cudaMemsetAsync(sc.minabove, 0xff, size_t(nb) * 8, s));
-  int64_t rpc = R.rs ? 64 : 1;
-  int g = grid_for((R.nrows + rpc - 1) / rpc, 1, 152 * 8);
-  if (R.nrows > 0) {
-    k_sel_hist0<<<g, 256, 0, s>>>(nb, R, active, val, val_f32, ms, sc);
+  int64_t rpc = R.rs ? ROWS_PER_CHUNK : 1;
+  {
+    ProfScope ps(KC_SEL_HIST, s, 0.0, 0.0);
+    if (R.nrows > 0) {
+      k_sel_hist0<<<grid_for((R.nrows + rpc - 1) / rpc, 1, 152 * 8), SEL_THREADS, 0, s>>>(
+          nb, R, active, val, val_f32, ms, sc);
+      SGN_LAUNCH_CHECK();
+    }
+    k_sel_find0<<<(nb + 127) / 128, 128, 0, s>>>(nb, active, ms, sc);
     SGN_LAUNCH_CHECK();
   }
-  k_sel_find0<<<(nb + 127) / 128, 128, 0, s>>>(nb, active, ms, sc);
-  SGN_LAUNCH_CHECK();
-  k_sel_candoff<<<1, 32, 0, s>>>(nb, sc);
-  SGN_LAUNCH_CHECK();
-  if (R.nrows > 0) {
-    k_sel_extract<<<g, 256, 0, s>>>(nb, R, active, val, val_f32, ms, sc);
-    SGN_LAUNCH_CHECK();
+  {
+    ProfScope ps(KC_SEL_EXTRACT, s, 0.0, 0.0);
+    if (R.nrows > 0) {
+      k_sel_extract<<<grid_for(R.nrows, 8, 152 * 8), SEL_THREADS, 0, s>>>(nb, R, active, val,
+                                                                          val_f32, ms, sc);
+      SGN_LAUNCH_CHECK();
+    }
   }
+  ProfScope ps(KC_SEL_DIGITS, s, 0.0, 0.0);
   for (int level = 0; level < 6; ++level) {
     int shift = 40 - 8 * level;
-    SGN_CUDA(cudaMemsetAsync(sc.hdig, 0, size_t(nb) * NDIG * 3 * 8, s));
-    k_sel_hist_digit<<<152 * 4, 256, 0, s>>>(nb, ms, sc, shift);
+    SGN_CUDA(cudaMemsetAsync(sc.hdig, 0, size_t(nb) * NDIG * 2 * 8, s));
+    k_sel_hist_digit<<<152 * 4, 256, 0, s>>>(ms, sc, shift);
     SGN_LAUNCH_CHECK();
     k_sel_find_digit<<<(nb + 127) / 128, 128, 0, s>>>(nb, sc, shift);
     SGN_LAUNCH_CHECK();

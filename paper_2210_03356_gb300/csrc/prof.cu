@@ -29,9 +29,10 @@ struct Acc {
 Acc g_acc[KC_COUNT];
 
 const char *kNames[KC_COUNT] = {"numeric_square_f64", "numeric_update_f64", "numeric_square_f32",
-                                "numeric_update_f32", "bounds",             "symbolic",
-                                "scan",               "select",             "filter",
-                                "reduce",             "assemble",           "onenorm"};
+                                "numeric_update_f32", "bounds",             "scan",
+                                "select_hist",        "select_extract",     "select_digits",
+                                "select_bound",       "filter",             "reduce",
+                                "assemble",           "onenorm"};
 
 cudaEvent_t get_event() {
   if (!g_pool.empty()) {

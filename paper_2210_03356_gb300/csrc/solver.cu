@@ -455,14 +455,14 @@ struct Solver {
     } else {
       {
         // ---- threshold (step a5)
-        ProfScope psel(KC_SELECT, s, 0.0, double(st.Xb.slots) * 2.0 * sizeof(T));
         if (o.filter == SIGN_FILTER_EXACT) {
           w.sel.ensure(select_scratch_bytes(nb, st.Xb.slots), s);
           SelRows R{N, st.d_seg.template as<int32_t>(), st.Xb.rs.template as<int64_t>(),
                     st.Xb.re.template as<int64_t>(), 0};
-          launch_select_exact(nb, R, d_act, st.Xb.val.p, is_f32<T>(), w.ms.as<MatScalars>(), w.sel.p,
-                              s);
+          launch_select_exact(nb, R, st.Xb.slots, d_act, st.Xb.val.p, is_f32<T>(),
+                              w.ms.as<MatScalars>(), w.sel.p, s);
         } else {
+          ProfScope psel(KC_SELECT, s);
           launch_select_bound(nb, d_act, w.ms.as<MatScalars>(), s);
         }
       }

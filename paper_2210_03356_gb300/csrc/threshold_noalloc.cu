@@ -9,7 +9,7 @@
 // values and keeps all of its scratch in one file-scope __device__ array, so
 // it calls no cudaMalloc, cudaFree or other allocating routine.
 //
-// The array (about 8 MiB) exists on every GPU that loads this library until
+// The array (about 12 MiB) exists on every GPU that loads this library until
 // the process exits. Its host-side name is only a stand-in: the device
 // address is looked up once per device with cudaGetSymbolAddress, with that
 // device current, on the first call made while it is current; that first
@@ -96,7 +96,7 @@ extern "C" sign_status sign_threshold_exact_noalloc(const double *val, int64_t n
     SGN_CUDA(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     // the select kernels clear their histograms and state themselves
     SelRows R{(nnz + kFlatRow - 1) / kFlatRow, nullptr, nullptr, nullptr, nnz};
-    launch_select_exact(1, R, d->active, val, 0, &d->ms, base + kHeadBytes, s);
+    launch_select_exact(1, R, nnz, d->active, val, 0, &d->ms, base + kHeadBytes, s);
     SGN_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
     SGN_CUDA(cudaStreamSynchronize(s));
     *tau_out = h.ms.tau;
