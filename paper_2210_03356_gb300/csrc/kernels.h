@@ -124,6 +124,8 @@ struct MatScalars {
   double tau;    // element threshold of the filter
   double fnorm;  // ||F||_F dropped
   int64_t nnz_x, nnz_t, nnz_bar, nnz_hat;
+  double qs;                // threshold select: 2^31 / b (0 if b == 0 or too small)
+  unsigned long long tiny;  // keys below this (|x| < b 2^-33) have q == 0
 };
 // From sums[2m] = sum (T-I)^2, sums[2m+1] = sum X^2: r, x, beta, b.
 void launch_matrix_scalars(int nb, const int64_t *moff, const double *sums, double c4,

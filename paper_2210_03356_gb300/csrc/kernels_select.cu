@@ -123,13 +123,26 @@ __device__ __forceinline__ unsigned long long key_of(const void *val, int f32, i
   return (unsigned long long)__double_as_longlong(fabs(x));
 }
 
-// q = round((x / b)^2 * 2^62), x <= b; 0 when b == 0. Entries with q == 0
-// (x < b 2^-31) add nothing to any sum and are always dropped, so the
-// histograms skip them.
-__device__ __forceinline__ unsigned long long qval(unsigned long long key, double b) {
-  if (b == 0.0) return 0ULL;
-  double r = __ddiv_rn(__longlong_as_double((long long)key), b);
-  return __double2ull_rn(__dmul_rn(__dmul_rn(r, r), 4611686018427387904.0));
+// q = round((x * s)^2) with s = 2^31 / b, i.e. (x/b)^2 in units of 2^-62 of
+// b^2: two FP64 multiplies per entry (the division is done once per matrix).
+// Entries with q == 0 add nothing to any sum and are always dropped, so the
+// histograms skip them; keys below ms.tiny (|x| < b 2^-33) are known to have
+// q == 0 without any floating-point work.
+__device__ __forceinline__ unsigned long long qval(unsigned long long key, double qs) {
+  double t = __dmul_rn(__longlong_as_double((long long)key), qs);
+  return __double2ull_rn(__dmul_rn(t, t));
+}
+
+// Per matrix: qs = 2^31 / b and the key of b 2^-33 (b = 0, or b so small that
+// 2^31 / b overflows, gives qs = 0: every q is 0).
+__global__ void k_sel_prepare(int nb, MatScalars *ms) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nb) return;
+  double b = ms[m].b;
+  double qs = b > 0.0 ? __ddiv_rn(2147483648.0, b) : 0.0;
+  if (!isfinite(qs)) qs = 0.0;
+  ms[m].qs = qs;
+  ms[m].tiny = (unsigned long long)__double_as_longlong(__dmul_rn(b, 0x1p-33));
 }
 
 // (lo, hi) += (alo, ahi) atomically in memory; exact, order-independent.
@@ -180,8 +193,9 @@ __global__ void __launch_bounds__(SEL_THREADS)
     for (int64_t r = r0 + warp; r < r1; r += nw) {
       int m = row_mat(R, r);
       if (!active[m]) continue;
-      double b = ms[m].b;
-      unsigned long long bkey = (unsigned long long)__double_as_longlong(b);
+      unsigned long long bkey = (unsigned long long)__double_as_longlong(ms[m].b);
+      double qs = ms[m].qs;
+      unsigned long long tiny = ms[m].tiny;
       unsigned long long *hist = m == m0 ? s_h : sc.hist0 + size_t(m) * NB0 * 2;
       int64_t e0, e1;
       row_range(R, r, e0, e1);
@@ -195,7 +209,8 @@ __global__ void __launch_bounds__(SEL_THREADS)
           mymin = key < mymin ? key : mymin;
           continue;
         }
-        unsigned long long q = qval(key, b);
+        if (key < tiny) continue;
+        unsigned long long q = qval(key, qs);
         if (!q) continue;
         int bk = bucket0(key, bkey);
         if (bk != cur) {
@@ -315,7 +330,7 @@ __global__ void k_sel_hist_digit(const MatScalars *ms, SelScratch sc, int shift)
     unsigned long long key = sc.cand[i];
     if ((key >> (shift + 8)) != (sc.st[m].prefix >> (shift + 8))) continue;
     int d = int((key >> shift) & 255ULL);
-    unsigned long long q = qval(key, ms[m].b);
+    unsigned long long q = qval(key, ms[m].qs);
     if (q) add128(sc.hdig + (size_t(m) * NDIG + d) * 2, q, 0ULL);
   }
 }
@@ -366,14 +381,28 @@ __global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
     int c = 0;
     double d2 = 0.0;
     if (active[m]) {
-      for (int64_t p = rs[r] + lane; p < re[r]; p += 32) {
-        double x = f32 ? double(static_cast<const float *>(val)[p])
-                       : static_cast<const double *>(val)[p];
-        double ax = fabs(x);
-        if (ax >= tau && x != 0.0)
-          ++c;
-        else
-          d2 += x * x;
+      if (f32) {
+        // the smallest float >= tau: for a float x, |x| >= tf exactly when |x| >= tau
+        float tf = __double2float_ru(tau);
+        const float *v = static_cast<const float *>(val);
+        for (int64_t p = rs[r] + lane; p < re[r]; p += 32) {
+          float x = v[p];
+          if (fabsf(x) >= tf && x != 0.0f) {
+            ++c;
+          } else {
+            double xd = double(x);
+            d2 = __fma_rn(xd, xd, d2);
+          }
+        }
+      } else {
+        const double *v = static_cast<const double *>(val);
+        for (int64_t p = rs[r] + lane; p < re[r]; p += 32) {
+          double x = v[p];
+          if (fabs(x) >= tau && x != 0.0)
+            ++c;
+          else
+            d2 = __fma_rn(x, x, d2);
+        }
       }
     }
 #pragma unroll
@@ -401,15 +430,20 @@ __global__ void k_filter_write(int64_t n, const int32_t *seg, const int *active,
     int m = seg[r];
     if (!active[m]) continue;
     double tau = ms[m].tau;
+    float tf = __double2float_ru(tau);  // |x| >= tf  <=>  |x| >= tau for a float x
     int64_t out = orp[r];
     int64_t b = rs[r], e = re[r];
     for (int64_t p0 = b; p0 < e; p0 += 32) {
       int64_t p = p0 + lane;
       bool keep = false;
-      double x = 0.0;
       if (p < e) {
-        x = f32 ? double(static_cast<const float *>(val)[p]) : static_cast<const double *>(val)[p];
-        keep = fabs(x) >= tau && x != 0.0;
+        if (f32) {
+          float x = static_cast<const float *>(val)[p];
+          keep = fabsf(x) >= tf && x != 0.0f;
+        } else {
+          double x = static_cast<const double *>(val)[p];
+          keep = fabs(x) >= tau && x != 0.0;
+        }
       }
       unsigned m32 = __ballot_sync(0xffffffffu, keep);
       if (keep) {
@@ -418,7 +452,7 @@ __global__ void k_filter_write(int64_t n, const int32_t *seg, const int *active,
         if (f32)
           static_cast<float *>(oval)[pos] = static_cast<const float *>(val)[p];
         else
-          static_cast<double *>(oval)[pos] = x;
+          static_cast<double *>(oval)[pos] = static_cast<const double *>(val)[p];
       }
       out += __popc(m32);
     }
@@ -452,6 +486,8 @@ void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *
   SelScratch sc = carve(scratch, nb, cand_cap);
   SGN_CUDA(cudaMemsetAsync(sc.hist0, 0, size_t(nb) * NB0 * 2 * 8, s));
   SGN_CUDA(cudaMemsetAsync(sc.minabove, 0xff, size_t(nb) * 8, s));
+  k_sel_prepare<<<(nb + 127) / 128, 128, 0, s>>>(nb, ms);
+  SGN_LAUNCH_CHECK();
   int64_t rpc = R.rs ? ROWS_PER_CHUNK : 1;
   {
     ProfScope ps(KC_SEL_HIST, s, 0.0, 0.0);
