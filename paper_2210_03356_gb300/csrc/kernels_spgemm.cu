@@ -45,6 +45,37 @@ __device__ __forceinline__ float ns_combine(float x, float p) {
   return __fsub_rn(__fmul_rn(1.5f, x), __fmul_rn(0.5f, p));
 }
 
+// Sum of squares of the values of one type, in FP64 precision. For float
+// values it avoids FP64 arithmetic (1/64 rate on this part): v^2 = p + e
+// exactly (p = v*v rounded, e = fma(v, v, -p)), accumulated as an unevaluated
+// float pair with an error-free two-sum, so the sum carries ~48 bits.
+template <typename T>
+struct SqAcc;
+template <>
+struct SqAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add_sq(double v) { s = __fma_rn(v, v, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct SqAcc<float> {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float a) {
+    float t = __fadd_rn(hi, a);
+    float bb = __fsub_rn(t, hi);
+    float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(a, bb));
+    hi = t;
+    lo = __fadd_rn(lo, err);
+  }
+  __device__ __forceinline__ void add_sq(float v) {
+    float p = __fmul_rn(v, v);
+    float e = __fmaf_rn(v, v, -p);
+    add(p);
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
 __device__ __forceinline__ int64_t lower_bound(const int32_t *a, int64_t lo, int64_t hi,
                                                int64_t v) {
   while (lo < hi) {
@@ -160,7 +191,7 @@ __device__ __forceinline__ void accumulate_k(T a, int64_t q0, int64_t q1, const 
 template <typename T>
 struct WarpOcc;  // CTAs per SM of the warp kernel (shared memory and registers)
 template <> struct WarpOcc<double> { static constexpr int value = 6; };
-template <> struct WarpOcc<float> { static constexpr int value = 8; };
+template <> struct WarpOcc<float> { static constexpr int value = 10; };
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32, WarpOcc<T>::value)
@@ -218,7 +249,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, WarpOcc<T>::value)
       __syncwarp();
     }
     int64_t out = cs[r];
-    double rs = 0.0;
+    SqAcc<T> racc;
+    double rdiag = 0.0;
     bool diag = false;
     for (int s0 = 0; s0 < L; s0 += 32) {
       int s = s0 + lane;
@@ -232,23 +264,22 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, WarpOcc<T>::value)
         ccol[pos] = cj;
         cval[pos] = v;
         if (MODE == MODE_SQUARE) {
-          double d = double(v);
-          if (cj == r) {
-            d = d - 1.0;
+          if (cj == r) {  // (t_ii - 1)^2 in FP64, once per row
+            double d = double(v) - 1.0;
+            rdiag = d * d;
             diag = true;
+          } else {
+            racc.add_sq(v);
           }
-          rs += d * d;
         }
       }
       out += __popc(m);
     }
     if (lane == 0) ce[r] = out;
     if (MODE == MODE_SQUARE) {
-      double xs = 0.0;
-      for (int64_t p = a0 + lane; p < a1; p += 32) {
-        double x = double(aval[p]);
-        xs += x * x;
-      }
+      SqAcc<T> xacc;
+      for (int64_t p = a0 + lane; p < a1; p += 32) xacc.add_sq(aval[p]);
+      double rs = racc.value() + rdiag, xs = xacc.value();
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         rs += __shfl_xor_sync(0xffffffffu, rs, o);
