@@ -244,7 +244,10 @@ def main():
     barrier()
     launches = sg.kernel_launches() - l0
     sg.prof_enable(False)
-    prof = sg.prof_read()
+    prof_all = sg.prof_read()
+    prof = {k: v for k, v in prof_all.items() if not k.startswith("host_")}
+    host = {k: round(v["ms"] / args.steps, 3) for k, v in prof_all.items()
+            if k.startswith("host_") and v["launches"]}
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
     assert all(s == sg.SIGN_OK and r <= TOL for s, _, r in out)
@@ -299,7 +302,7 @@ def main():
                        "parallelism": f"{world} independent batches (one per GPU)",
                        "l2": "working set of every step (iterates, products) is several GB, > 129 MB L2"},
             "gpu_launches": int(launches), "clocks": ck, "roofline": roofline,
-            "kernels": by_kernel}
+            "kernels": by_kernel, "host_ms_per_step": host}
 
     if args.legs == "all":
         # end to end through the public API: pinned host inputs -> device -> host result

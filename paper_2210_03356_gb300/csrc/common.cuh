@@ -49,7 +49,9 @@ constexpr int K_BATCH = 256;  // k entries whose B-row ranges are located at onc
 enum KClass {
   KC_NUM_SQUARE_F64, KC_NUM_UPDATE_F64, KC_NUM_SQUARE_F32, KC_NUM_UPDATE_F32, KC_BOUNDS,
   KC_SCAN, KC_SEL_HIST, KC_SEL_EXTRACT, KC_SEL_DIGITS, KC_SELECT, KC_FILTER, KC_REDUCE,
-  KC_ASSEMBLE, KC_NORM, KC_COUNT
+  KC_ASSEMBLE, KC_NORM,
+  // host wall time of driver phases (synchronizations included)
+  KH_SETUP, KH_CHECK, KH_DECIDE, KH_UPDATE, KH_FILTER, KH_REBUILD, KC_COUNT
 };
 // Records CUDA events around the enclosed launches on stream s (no-op when
 // profiling is off); flops and bytes are the algorithmic work they do.
@@ -66,6 +68,15 @@ struct ProfScope {
 // freed memory for reuse (release threshold = unlimited), so repeated solves
 // do not map and unmap device memory at every synchronization.
 cudaMemPool_t lib_pool();
+
+// Host wall time of the enclosed driver code, when profiling is on.
+struct HostScope {
+  int cls;
+  long long t0 = -1;
+  explicit HostScope(int c);
+  void stop();  // records now; later calls and the destructor do nothing
+  ~HostScope() { stop(); }
+};
 
 // Grow-only device buffer, allocated stream-ordered from lib_pool().
 struct DevBuf {

@@ -1,5 +1,6 @@
 // Launch counting and per-kernel-class timing with CUDA events.
 #include <atomic>
+#include <chrono>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -32,7 +33,15 @@ const char *kNames[KC_COUNT] = {"numeric_square_f64", "numeric_update_f64", "num
                                 "numeric_update_f32", "bounds",             "scan",
                                 "select_hist",        "select_extract",     "select_digits",
                                 "select_bound",       "filter",             "reduce",
-                                "assemble",           "onenorm"};
+                                "assemble",           "onenorm",            "host_setup",
+                                "host_check",         "host_decide",        "host_update",
+                                "host_filter",        "host_rebuild"};
+
+long long now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
 
 cudaEvent_t get_event() {
   if (!g_pool.empty()) {
@@ -63,6 +72,19 @@ void drain() {
 }
 
 }  // namespace
+
+HostScope::HostScope(int c) : cls(c) {
+  if (g_prof_on.load(std::memory_order_relaxed)) t0 = now_ns();
+}
+
+void HostScope::stop() {
+  if (t0 < 0) return;
+  double ms = double(now_ns() - t0) * 1e-6;
+  t0 = -1;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_acc[cls].launches += 1;
+  g_acc[cls].ms += ms;
+}
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 

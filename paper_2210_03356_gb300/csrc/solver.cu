@@ -313,6 +313,7 @@ struct Solver {
   // Re-lays out a stage with its live matrices and the incoming ones.
   template <typename T>
   void rebuild(Stage<T> &st) {
+    HostScope hr(KH_REBUILD);
     int nb = int(st.mats.size());
     std::vector<int64_t> eoff(nb + 1, 0);
     if (nb > 0) {
@@ -367,6 +368,7 @@ struct Solver {
     d2h(hm.ex, w.eoff.p, size_t(nb + 1), s);
     // ---- check: T = X X, r, x, budget (steps a2, a4)
     Rows xr = compact_rows(st.X);
+    HostScope hcheck(KH_CHECK);
     product(st, xr, st.X.d_val(), st.X.nnz, xr, st.X.d_val(), st.X.nnz, MODE_SQUARE, st.Tm, d_act);
     std::vector<int64_t> ex(hm.ex, hm.ex + nb + 1);
     std::vector<double> mt(hm.mults, hm.mults + nb);
@@ -383,8 +385,10 @@ struct Solver {
     d2h(hm.ms, w.ms.p, size_t(nb), s);
     d2h(hm.nnz_t, w.nnzc.p, size_t(nb), s);
     sync(s);
+    hcheck.stop();
     std::vector<MatScalars> hms(hm.ms, hm.ms + nb);
     // ---- per-matrix decisions (steps a7, a8); leavers copied out in one launch
+    HostScope hdecide(KH_DECIDE);
     int nx = 0;
     bool changed = false;
     for (int i = 0; i < nb; ++i) {
@@ -438,7 +442,9 @@ struct Solver {
       return;
     }
     if (changed) h2d(w.active.p, st.alive.data(), st.alive.size(), s);
+    hdecide.stop();
     // ---- update: Xbar = 1.5 X - 0.5 X T (step a3)
+    HostScope hupdate(KH_UPDATE);
     int64_t nnz_t_all = 0;
     for (int i = 0; i < nb; ++i) nnz_t_all += hm.nnz_t[i];
     product(st, xr, st.X.d_val(), st.X.nnz, st.Tm.rows(), st.Tm.d_val(), nnz_t_all, MODE_UPDATE,
@@ -449,6 +455,8 @@ struct Solver {
     for (int i = 0; i < nb; ++i) hms[i].nnz_bar = hm.nnz_bar[i];
     std::memcpy(hm.ms, hms.data(), sizeof(MatScalars) * nb);
     h2d(w.ms.p, hm.ms, size_t(nb), s);
+    hupdate.stop();
+    HostScope hfilter(KH_FILTER);
     if (o.filter == SIGN_FILTER_NONE) {
       // keep every entry: compact the slotted rows as they are
       hms_none(st, hms);
@@ -545,6 +553,7 @@ struct Solver {
       hs[i]->has_result = false;
     }
     // block-diagonal input (FP64), scaled per matrix (step a1)
+    HostScope hsetup(KH_SETUP);
     Stage<double> s64;
     Stage<float> s32;
     std::vector<int> all(count);
@@ -591,6 +600,7 @@ struct Solver {
       s64.alive.clear();
       s64.moff.assign(1, 0);
     }
+    hsetup.stop();
     for (int guard = 0; guard < 4 * o.max_iter + 16; ++guard) {
       round<float, double>(s32, &s64);
       round<double, double>(s64, nullptr);
