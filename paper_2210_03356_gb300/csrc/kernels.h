@@ -99,20 +99,21 @@ struct Rows {
 // range [lo, lo+len) of the row (including A's own row in MODE_UPDATE), the
 // slot size ub[i] = min(len, work + (UPDATE ? nnz(A_i) : 0)) >= nnz(C_i), and
 // work[i] = sum_{k in A_i} nnz(B_k), the multiply-adds of the row. Non-empty
-// rows go to the warp list (len <= WARP_W) or the CTA list; counters[0],
-// counters[1] are the list lengths and counters[4], counters[5] the work-queue
-// heads of the numeric kernels (all zeroed by the caller).
+// rows are listed, in row order within tiles, by the numeric kernel that takes
+// them: lists holds 4 lists of n entries (32-, 16- or 8-lane groups, or one
+// CTA per row); counters[0..3] are their lengths and counters[4..7] the
+// work-queue heads of the numeric kernels (all zeroed by the caller).
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
-                   int mode, int32_t *lo, int32_t *len, int64_t *ub, int32_t *wlist,
-                   int32_t *clist, int *counters, double *work, cudaStream_t s);
+                   int mode, int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists,
+                   int *counters, double *work, cudaStream_t s);
 // Numeric product. Row i is written at cs[i] (exclusive scan of ub) and its
 // end stored in ce[i]. MODE_SQUARE: C = A A, and part[2i] = sum_j (C_ij -
 // delta_ij)^2, part[2i+1] = sum_k a_ik^2. MODE_UPDATE: C = 1.5 A - 0.5 A B.
 template <typename T>
 void launch_numeric(int64_t n, const Rows &A, const T *aval, const Rows &B, const T *bval,
-                    int mode, const int32_t *lo, const int32_t *len, const int32_t *wlist,
-                    const int32_t *clist, const int *counters, const int64_t *cs, int64_t *ce,
-                    int32_t *ccol, T *cval, double *part, cudaStream_t s);
+                    int mode, const int32_t *lo, const int32_t *len, const int32_t *lists,
+                    const int *counters, const int64_t *cs, int64_t *ce, int32_t *ccol, T *cval,
+                    double *part, cudaStream_t s);
 
 // ---------------------------------------------------------------- filter
 // Per-matrix scalars after the check of the current iterates.
@@ -159,6 +160,8 @@ constexpr size_t select_scratch_bytes(int nb, int64_t cap) {
 void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *active,
                          const void *val, int val_f32, MatScalars *ms, void *scratch,
                          cudaStream_t s);
+// ms[m].nnz_bar = nnz[m].
+void launch_store_nnz_bar(int nb, const int64_t *nnz, MatScalars *ms, cudaStream_t s);
 // BOUND: tau = b / sqrt(nnz_bar) per matrix.
 void launch_select_bound(int nb, const int *active, MatScalars *ms, cudaStream_t s);
 

@@ -466,12 +466,22 @@ int grid_for(int64_t items, int per_block, int cap = 152 * 16) {
   return int(g);
 }
 
+__global__ void k_store_nnz_bar(int nb, const int64_t *nnz, MatScalars *ms) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < nb) ms[m].nnz_bar = nnz[m];
+}
+
 }  // namespace
 
 void launch_matrix_scalars(int nb, const int64_t *moff, const double *sums, double c4,
                            double tol_stage, double switch_resid, MatScalars *ms, cudaStream_t s) {
   k_matrix_scalars<<<(nb + 127) / 128, 128, 0, s>>>(nb, moff, sums, c4, tol_stage, switch_resid,
                                                     ms);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_store_nnz_bar(int nb, const int64_t *nnz, MatScalars *ms, cudaStream_t s) {
+  k_store_nnz_bar<<<(nb + 127) / 128, 128, 0, s>>>(nb, nnz, ms);
   SGN_LAUNCH_CHECK();
 }
 

@@ -88,65 +88,119 @@ __device__ __forceinline__ int64_t lower_bound(const int32_t *a, int64_t lo, int
   return lo;
 }
 
-// counters: [0] warp-list length, [1] CTA-list length, [4],[5] work-queue heads.
-__global__ void k_bounds(int64_t n, const int64_t *ars, const int64_t *are, const int32_t *acol,
-                         const int64_t *brs, const int64_t *bre, const int32_t *bcol,
-                         const int32_t *seg, const int *active, int mode, int32_t *lo,
-                         int32_t *len, int64_t *ub, int32_t *wlist, int32_t *clist, int *counters,
-                         double *work) {
-  int lane = lane_id();
-  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t r = warp; r < n; r += nwarps) {
-    if (!active[seg[r]]) {
-      if (lane == 0) {
-        ub[r] = 0;
-        len[r] = 0;
-        lo[r] = 0;
-        work[r] = 0.0;
-      }
-      continue;
-    }
-    int32_t mn = INT_MAX, mx = -1;
-    int64_t wk = 0;
-    int64_t a0 = ars[r], a1 = are[r];
-    for (int64_t p = a0 + lane; p < a1; p += 32) {
-      int32_t k = acol[p];
-      int64_t b0 = brs[k], b1 = bre[k];
-      wk += b1 - b0;
-      if (b1 > b0) {
-        mn = min(mn, bcol[b0]);
-        mx = max(mx, bcol[b1 - 1]);
-      }
-      if (mode == MODE_UPDATE) {
-        mn = min(mn, k);
-        mx = max(mx, k);
-      }
-    }
+// Row classes of the numeric kernels: groups of 32, 16 or 8 lanes per row
+// (rows whose column range fits the group's share of a warp's accumulator),
+// or one CTA per row.
+enum RowClass { RC_G32 = 0, RC_CTA = 1, RC_G16 = 2, RC_G8 = 3, RC_NONE = 4, RC_N = 4 };
+constexpr int BOUNDS_TILE = 256;  // rows per CTA of k_bounds; lists keep this order
+
+// Lane utilization of one k-step with g lanes and a B row of avg entries.
+__device__ __forceinline__ float lane_use(float avg, int g) {
+  float rounds = ceilf(avg / float(g));
+  return avg / (rounds * float(g));
+}
+
+// counters: [RC_*] list lengths, [4 + RC_*] work-queue heads of the numeric kernels.
+__global__ void __launch_bounds__(BOUNDS_TILE)
+    k_bounds(int64_t n, const int64_t *ars, const int64_t *are, const int32_t *acol,
+             const int64_t *brs, const int64_t *bre, const int32_t *bcol, const int32_t *seg,
+             const int *active, int mode, int32_t *lo, int32_t *len, int64_t *ub,
+             int32_t *lists, int *counters, double *work) {
+  __shared__ unsigned char s_cls[BOUNDS_TILE];
+  __shared__ int s_cnt[BOUNDS_TILE / 32][RC_N];
+  __shared__ int s_base[RC_N];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = BOUNDS_TILE / 32;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t ntiles = (n + BOUNDS_TILE - 1) / BOUNDS_TILE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t t0 = tile * BOUNDS_TILE;
+    for (int i = warp; i < BOUNDS_TILE; i += nw) {
+      int64_t r = t0 + i;
+      int cls = RC_NONE;
+      if (r < n) {
+        if (!active[seg[r]]) {
+          if (lane == 0) {
+            ub[r] = 0;
+            len[r] = 0;
+            lo[r] = 0;
+            work[r] = 0.0;
+          }
+        } else {
+          int32_t mn = INT_MAX, mx = -1;
+          int64_t wk = 0;
+          int64_t a0 = ars[r], a1 = are[r];
+          for (int64_t p = a0 + lane; p < a1; p += 32) {
+            int32_t k = acol[p];
+            int64_t b0 = brs[k], b1 = bre[k];
+            wk += b1 - b0;
+            if (b1 > b0) {
+              mn = min(mn, bcol[b0]);
+              mx = max(mx, bcol[b1 - 1]);
+            }
+            if (mode == MODE_UPDATE) {
+              mn = min(mn, k);
+              mx = max(mx, k);
+            }
+          }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      wk += __shfl_xor_sync(0xffffffffu, wk, o);
-    }
-    if (lane == 0) {
-      work[r] = double(wk);
-      if (mx < 0) {
-        ub[r] = 0;
-        len[r] = 0;
-        lo[r] = 0;
-      } else {
-        int32_t L = mx - mn + 1;
-        int64_t bound = wk + (mode == MODE_UPDATE ? a1 - a0 : 0);
-        lo[r] = mn;
-        len[r] = L;
-        ub[r] = bound < L ? bound : L;
-        if (L <= WARP_W)
-          wlist[atomicAdd(&counters[0], 1)] = int32_t(r);
-        else
-          clist[atomicAdd(&counters[1], 1)] = int32_t(r);
+          for (int o = 16; o > 0; o >>= 1) {
+            mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            wk += __shfl_xor_sync(0xffffffffu, wk, o);
+          }
+          if (mx < 0) {
+            if (lane == 0) {
+              ub[r] = 0;
+              len[r] = 0;
+              lo[r] = 0;
+              work[r] = double(wk);
+            }
+          } else {
+            int32_t L = mx - mn + 1;
+            int64_t bound = wk + (mode == MODE_UPDATE ? a1 - a0 : 0);
+            if (L > WARP_W) {
+              cls = RC_CTA;
+            } else {
+              float avg = float(wk) / float(a1 > a0 ? a1 - a0 : 1);
+              float u32 = lane_use(avg, 32), u16 = lane_use(avg, 16), u8 = lane_use(avg, 8);
+              cls = RC_G32;
+              if (L <= WARP_W / 2 && u16 > u32 + 0.05f) cls = RC_G16;
+              if (L <= WARP_W / 4 && u8 > (cls == RC_G16 ? u16 : u32) + 0.05f) cls = RC_G8;
+            }
+            if (lane == 0) {
+              lo[r] = mn;
+              len[r] = L;
+              ub[r] = bound < L ? bound : L;
+              work[r] = double(wk);
+            }
+          }
+        }
       }
+      if (lane == 0) s_cls[i] = (unsigned char)cls;
     }
+    __syncthreads();
+    // ordered compaction of the tile's rows into one list per class
+    int my = s_cls[threadIdx.x];
+    unsigned bal[RC_N];
+#pragma unroll
+    for (int c = 0; c < RC_N; ++c) {
+      bal[c] = __ballot_sync(0xffffffffu, my == c);
+      if (lane == 0) s_cnt[warp][c] = __popc(bal[c]);
+    }
+    __syncthreads();
+    if (threadIdx.x < RC_N) {
+      int c = threadIdx.x, tot = 0;
+      for (int w = 0; w < nw; ++w) tot += s_cnt[w][c];
+      s_base[c] = tot ? atomicAdd(&counters[c], tot) : 0;
+    }
+    __syncthreads();
+    if (my < RC_N) {
+      int off = s_base[my];
+      for (int w = 0; w < warp; ++w) off += s_cnt[w][my];
+      off += __popc(bal[my] & lt);
+      lists[int64_t(my) * n + off] = int32_t(t0 + threadIdx.x);
+    }
+    __syncthreads();
   }
 }
 
@@ -193,103 +247,115 @@ struct WarpOcc;  // CTAs per SM of the warp kernel (shared memory and registers)
 template <> struct WarpOcc<double> { static constexpr int value = 6; };
 template <> struct WarpOcc<float> { static constexpr int value = 10; };
 
-template <typename T, int MODE>
+// G lanes per row, 32/G rows per warp; each group owns WARP_W*G/32 slots of
+// its warp's accumulator and runs the ascending-k accumulation of its own row
+// with group-wide barriers, so the result is the same as with a whole warp.
+template <typename T, int MODE, int G>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32, WarpOcc<T>::value)
-    k_num_warp(const int64_t *ars, const int64_t *are, const int32_t *acol, const T *aval,
-               const int64_t *brs, const int64_t *bre, const int32_t *bcol, const T *bval,
-               const int32_t *lo, const int32_t *len, const int32_t *wlist, int *counters,
-               const int64_t *cs, int64_t *ce, int32_t *ccol, T *cval, double *part) {
+    k_num_group(const int64_t *ars, const int64_t *are, const int32_t *acol, const T *aval,
+                const int64_t *brs, const int64_t *bre, const int32_t *bcol, const T *bval,
+                const int32_t *lo, const int32_t *len, const int32_t *list, int *counters,
+                int cls, const int64_t *cs, int64_t *ce, int32_t *ccol, T *cval, double *part) {
+  constexpr int NG = 32 / G;
+  constexpr int SLOTS = WARP_W / NG;
   __shared__ T acc_all[WARPS_PER_CTA][WARP_W];
   __shared__ unsigned char flags[WARPS_PER_CTA][WARP_W];
-  int lane = lane_id(), w = threadIdx.x >> 5;
-  T *acc = acc_all[w];
-  unsigned char *f = flags[w];
-  const unsigned lt = (1u << lane) - 1u;
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const int g = lane / G, gl = lane % G;
+  const unsigned gbits = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+  const unsigned gmask = gbits << (g * G);
+  const unsigned lt = (1u << gl) - 1u;
+  T *acc = acc_all[w] + g * SLOTS;
+  unsigned char *f = flags[w] + g * SLOTS;
+  const int total = counters[cls];
   for (;;) {
-    int idx = 0;
-    if (lane == 0) idx = atomicAdd(&counters[4], 1);
-    idx = __shfl_sync(0xffffffffu, idx, 0);
-    if (idx >= counters[0]) break;
-    int32_t r = wlist[idx];
-    int L = len[r];
-    int32_t c0 = lo[r];
-    for (int s = lane; s < L; s += 32) {
-      acc[s] = T(0);
-      f[s] = 0;
-    }
-    __syncwarp();
-    int64_t a0 = ars[r], a1 = are[r];
-    // ascending k; the (a_ik, start, end) of 32 k at a time are fetched by the
-    // lanes together and broadcast, so the dependent load chain
-    // acol -> row bounds -> B entries is paid once per 32 k
-    for (int64_t pb = a0; pb < a1; pb += 32) {
-      int nk = int(min(int64_t(32), a1 - pb));
-      T av = T(0);
-      int64_t qs = 0, qe = 0;
-      if (lane < nk) {
-        int32_t k = acol[pb + lane];
-        av = aval[pb + lane];
-        qs = brs[k];
-        qe = bre[k];
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&counters[4 + cls], NG);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= total) break;
+    const int idx = base + g;
+    if (idx < total) {
+      const int32_t r = list[idx];
+      const int L = len[r];
+      const int32_t c0 = lo[r];
+      for (int s = gl; s < L; s += G) {
+        acc[s] = T(0);
+        f[s] = 0;
       }
-      for (int t = 0; t < nk; ++t) {
-        T a = __shfl_sync(0xffffffffu, av, t);
-        int64_t q0 = __shfl_sync(0xffffffffu, qs, t);
-        int64_t q1 = __shfl_sync(0xffffffffu, qe, t);
-        accumulate_k<T, 32>(a, q0, q1, bcol, bval, c0, acc, f, lane);
-        __syncwarp();
-      }
-    }
-    if (MODE == MODE_UPDATE) {
-      for (int64_t p = a0 + lane; p < a1; p += 32) {
-        int j = acol[p] - c0;
-        acc[j] = ns_combine(aval[p], acc[j]);
-        f[j] = 3;
-      }
-      __syncwarp();
-    }
-    int64_t out = cs[r];
-    SqAcc<T> racc;
-    double rdiag = 0.0;
-    bool diag = false;
-    for (int s0 = 0; s0 < L; s0 += 32) {
-      int s = s0 + lane;
-      int fl = s < L ? f[s] : 0;
-      unsigned m = __ballot_sync(0xffffffffu, fl != 0);
-      if (fl) {
-        int64_t pos = out + __popc(m & lt);
-        int32_t cj = c0 + s;
-        T v = acc[s];
-        if (MODE == MODE_UPDATE && !(fl & 2)) v = ns_combine(T(0), v);
-        ccol[pos] = cj;
-        cval[pos] = v;
-        if (MODE == MODE_SQUARE) {
-          if (cj == r) {  // (t_ii - 1)^2 in FP64, once per row
-            double d = double(v) - 1.0;
-            rdiag = d * d;
-            diag = true;
-          } else {
-            racc.add_sq(v);
-          }
+      __syncwarp(gmask);
+      const int64_t a0 = ars[r], a1 = are[r];
+      // ascending k; the (a_ik, start, end) of G k at a time are fetched by the
+      // group's lanes together and broadcast inside the group
+      for (int64_t pb = a0; pb < a1; pb += G) {
+        const int nk = int(min(int64_t(G), a1 - pb));
+        T av = T(0);
+        int64_t qs = 0, qe = 0;
+        if (gl < nk) {
+          int32_t k = acol[pb + gl];
+          av = aval[pb + gl];
+          qs = brs[k];
+          qe = bre[k];
+        }
+        for (int t = 0; t < nk; ++t) {
+          T a = __shfl_sync(gmask, av, t, G);
+          int64_t q0 = __shfl_sync(gmask, qs, t, G);
+          int64_t q1 = __shfl_sync(gmask, qe, t, G);
+          accumulate_k<T, G>(a, q0, q1, bcol, bval, c0, acc, f, gl);
+          __syncwarp(gmask);
         }
       }
-      out += __popc(m);
-    }
-    if (lane == 0) ce[r] = out;
-    if (MODE == MODE_SQUARE) {
-      SqAcc<T> xacc;
-      for (int64_t p = a0 + lane; p < a1; p += 32) xacc.add_sq(aval[p]);
-      double rs = racc.value() + rdiag, xs = xacc.value();
+      if (MODE == MODE_UPDATE) {
+        for (int64_t p = a0 + gl; p < a1; p += G) {
+          int j = acol[p] - c0;
+          acc[j] = ns_combine(aval[p], acc[j]);
+          f[j] = 3;
+        }
+        __syncwarp(gmask);
+      }
+      int64_t out = cs[r];
+      SqAcc<T> racc;
+      double rdiag = 0.0;
+      bool diag = false;
+      for (int s0 = 0; s0 < L; s0 += G) {
+        int s = s0 + gl;
+        int fl = s < L ? f[s] : 0;
+        unsigned m = (__ballot_sync(gmask, fl != 0) >> (g * G)) & gbits;
+        if (fl) {
+          int64_t pos = out + __popc(m & lt);
+          int32_t cj = c0 + s;
+          T v = acc[s];
+          if (MODE == MODE_UPDATE && !(fl & 2)) v = ns_combine(T(0), v);
+          ccol[pos] = cj;
+          cval[pos] = v;
+          if (MODE == MODE_SQUARE) {
+            if (cj == r) {  // (t_ii - 1)^2 in FP64, once per row
+              double d = double(v) - 1.0;
+              rdiag = d * d;
+              diag = true;
+            } else {
+              racc.add_sq(v);
+            }
+          }
+        }
+        out += __popc(m);
+      }
+      if (gl == 0) ce[r] = out;
+      if (MODE == MODE_SQUARE) {
+        SqAcc<T> xacc;
+        for (int64_t p = a0 + gl; p < a1; p += G) xacc.add_sq(aval[p]);
+        double rs = racc.value() + rdiag, xs = xacc.value();
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        rs += __shfl_xor_sync(0xffffffffu, rs, o);
-        xs += __shfl_xor_sync(0xffffffffu, xs, o);
+        for (int o = G / 2; o > 0; o >>= 1) {
+          rs += __shfl_xor_sync(gmask, rs, o, G);
+          xs += __shfl_xor_sync(gmask, xs, o, G);
+        }
+        bool any_diag = __any_sync(gmask, diag);
+        if (gl == 0) {
+          part[2 * int64_t(r)] = any_diag ? rs : rs + 1.0;
+          part[2 * int64_t(r) + 1] = xs;
+        }
       }
-      bool any_diag = __any_sync(0xffffffffu, diag);
-      if (lane == 0) {
-        part[2 * int64_t(r)] = any_diag ? rs : rs + 1.0;
-        part[2 * int64_t(r) + 1] = xs;
-      }
+      __syncwarp(gmask);
     }
     __syncwarp();
   }
@@ -307,6 +373,7 @@ __global__ void __launch_bounds__(CTA_THREADS)
               const int32_t *lo, const int32_t *len, const int32_t *clist, int *counters,
               const int64_t *cs, int64_t *ce, int32_t *ccol, T *cval, double *part) {
   constexpr int CW = CtaW<T>::value;
+  // the CTA class uses counters[RC_CTA] (length) and counters[4 + RC_CTA] (queue head)
   constexpr int NW = CTA_THREADS / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int64_t *ks = reinterpret_cast<int64_t *>(smem_raw);
@@ -319,11 +386,11 @@ __global__ void __launch_bounds__(CTA_THREADS)
   int lane = lane_id(), w = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   for (;;) {
-    if (threadIdx.x == 0) s_idx = atomicAdd(&counters[5], 1);
+    if (threadIdx.x == 0) s_idx = atomicAdd(&counters[4 + RC_CTA], 1);
     __syncthreads();
     int idx = s_idx;
     __syncthreads();
-    if (idx >= counters[1]) break;
+    if (idx >= counters[RC_CTA]) break;
     int32_t r = clist[idx];
     int64_t L = len[r];
     int64_t base = lo[r];
@@ -482,23 +549,39 @@ int grid_cap(int64_t items, int per_block, int per_sm) {
 }  // namespace
 
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
-                   int mode, int32_t *lo, int32_t *len, int64_t *ub, int32_t *wlist,
-                   int32_t *clist, int *counters, double *work, cudaStream_t s) {
+                   int mode, int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists,
+                   int *counters, double *work, cudaStream_t s) {
   if (n == 0) return;
-  k_bounds<<<grid_cap(n, 8, 16), 256, 0, s>>>(n, A.rs, A.re, A.col, B.rs, B.re, B.col, seg, active,
-                                               mode, lo, len, ub, wlist, clist, counters, work);
+  int tiles = int((n + BOUNDS_TILE - 1) / BOUNDS_TILE);
+  int g = tiles < sm_count() * 8 ? tiles : sm_count() * 8;
+  k_bounds<<<g, BOUNDS_TILE, 0, s>>>(n, A.rs, A.re, A.col, B.rs, B.re, B.col, seg, active, mode,
+                                     lo, len, ub, lists, counters, work);
+  SGN_LAUNCH_CHECK();
+}
+
+template <typename T, int MODE, int G>
+static void group_launch(int64_t n, const Rows &A, const T *aval, const Rows &B, const T *bval,
+                         const int32_t *lo, const int32_t *len, const int32_t *lists, int *ctr,
+                         int cls, const int64_t *cs, int64_t *ce, int32_t *ccol, T *cval,
+                         double *part, cudaStream_t s) {
+  k_num_group<T, MODE, G><<<grid_cap(n, WARPS_PER_CTA * (32 / G), WarpOcc<T>::value),
+                            WARPS_PER_CTA * 32, 0, s>>>(
+      A.rs, A.re, A.col, aval, B.rs, B.re, B.col, bval, lo, len, lists + int64_t(cls) * n, ctr,
+      cls, cs, ce, ccol, cval, part);
   SGN_LAUNCH_CHECK();
 }
 
 template <typename T, int MODE>
 static void num_launch(int64_t n, const Rows &A, const T *aval, const Rows &B, const T *bval,
-                       const int32_t *lo, const int32_t *len, const int32_t *wlist,
-                       const int32_t *clist, int *ctr, const int64_t *cs, int64_t *ce,
-                       int32_t *ccol, T *cval, double *part, cudaStream_t s) {
-  k_num_warp<T, MODE><<<grid_cap(n, WARPS_PER_CTA, WarpOcc<T>::value), WARPS_PER_CTA * 32, 0, s>>>(
-      A.rs, A.re, A.col, aval, B.rs, B.re, B.col, bval, lo, len, wlist, ctr, cs, ce, ccol, cval,
-      part);
-  SGN_LAUNCH_CHECK();
+                       const int32_t *lo, const int32_t *len, const int32_t *lists, int *ctr,
+                       const int64_t *cs, int64_t *ce, int32_t *ccol, T *cval, double *part,
+                       cudaStream_t s) {
+  group_launch<T, MODE, 32>(n, A, aval, B, bval, lo, len, lists, ctr, RC_G32, cs, ce, ccol, cval,
+                            part, s);
+  group_launch<T, MODE, 16>(n, A, aval, B, bval, lo, len, lists, ctr, RC_G16, cs, ce, ccol, cval,
+                            part, s);
+  group_launch<T, MODE, 8>(n, A, aval, B, bval, lo, len, lists, ctr, RC_G8, cs, ce, ccol, cval,
+                           part, s);
   static bool attr = false;
   constexpr size_t sm = num_cta_smem<T>();
   if (!attr) {
@@ -507,38 +590,36 @@ static void num_launch(int64_t n, const Rows &A, const T *aval, const Rows &B, c
     attr = true;
   }
   k_num_cta<T, MODE><<<grid_cap(n, 1, 2), CTA_THREADS, sm, s>>>(
-      A.rs, A.re, A.col, aval, B.rs, B.re, B.col, bval, lo, len, clist, ctr, cs, ce, ccol, cval,
-      part);
+      A.rs, A.re, A.col, aval, B.rs, B.re, B.col, bval, lo, len, lists + int64_t(RC_CTA) * n, ctr,
+      cs, ce, ccol, cval, part);
   SGN_LAUNCH_CHECK();
 }
 
 template <typename T>
 void launch_numeric(int64_t n, const Rows &A, const T *aval, const Rows &B, const T *bval,
-                    int mode, const int32_t *lo, const int32_t *len, const int32_t *wlist,
-                    const int32_t *clist, const int *counters, const int64_t *cs, int64_t *ce,
-                    int32_t *ccol, T *cval, double *part, cudaStream_t s) {
+                    int mode, const int32_t *lo, const int32_t *len, const int32_t *lists,
+                    const int *counters, const int64_t *cs, int64_t *ce, int32_t *ccol, T *cval,
+                    double *part, cudaStream_t s) {
   if (n == 0) return;
   int *ctr = const_cast<int *>(counters);
   k_rows_empty<T><<<grid_cap(n, 8, 16), 256, 0, s>>>(n, A.rs, A.re, aval, len, cs, ce,
                                                       mode == MODE_SQUARE ? part : nullptr);
   SGN_LAUNCH_CHECK();
   if (mode == MODE_SQUARE)
-    num_launch<T, MODE_SQUARE>(n, A, aval, B, bval, lo, len, wlist, clist, ctr, cs, ce, ccol, cval,
-                               part, s);
+    num_launch<T, MODE_SQUARE>(n, A, aval, B, bval, lo, len, lists, ctr, cs, ce, ccol, cval, part,
+                               s);
   else
-    num_launch<T, MODE_UPDATE>(n, A, aval, B, bval, lo, len, wlist, clist, ctr, cs, ce, ccol, cval,
-                               part, s);
+    num_launch<T, MODE_UPDATE>(n, A, aval, B, bval, lo, len, lists, ctr, cs, ce, ccol, cval, part,
+                               s);
 }
 
 template void launch_numeric<double>(int64_t, const Rows &, const double *, const Rows &,
                                      const double *, int, const int32_t *, const int32_t *,
-                                     const int32_t *, const int32_t *, const int *,
-                                     const int64_t *, int64_t *, int32_t *, double *, double *,
-                                     cudaStream_t);
+                                     const int32_t *, const int *, const int64_t *, int64_t *,
+                                     int32_t *, double *, double *, cudaStream_t);
 template void launch_numeric<float>(int64_t, const Rows &, const float *, const Rows &,
                                     const float *, int, const int32_t *, const int32_t *,
-                                    const int32_t *, const int32_t *, const int *,
-                                    const int64_t *, int64_t *, int32_t *, float *, double *,
-                                    cudaStream_t);
+                                    const int32_t *, const int *, const int64_t *, int64_t *,
+                                    int32_t *, float *, double *, cudaStream_t);
 
 }  // namespace sgn

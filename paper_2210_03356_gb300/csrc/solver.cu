@@ -156,8 +156,11 @@ struct Work {
 };
 
 // Page-locked host mirrors of the per-matrix values read back every round.
+// Kept per host thread and grown only (cudaFreeHost would synchronize the
+// device), so repeated solves reuse them.
 struct HostMirror {
   void *p = nullptr;
+  size_t cap = 0;
   MatScalars *ms = nullptr;
   int64_t *ex = nullptr, *nnz_t = nullptr, *nnz_bar = nullptr, *tot = nullptr;
   double *mults = nullptr, *dsum = nullptr;
@@ -165,7 +168,12 @@ struct HostMirror {
   void alloc(int nb) {
     size_t bytes = sizeof(MatScalars) * nb + sizeof(int64_t) * (4 * size_t(nb) + 8) +
                    sizeof(double) * 2 * size_t(nb) + sizeof(ExtractBlock) * nb + 1024;
-    SGN_CUDA(cudaMallocHost(&p, bytes));
+    if (bytes > cap) {
+      if (p) cudaFreeHost(p);
+      p = nullptr;
+      SGN_CUDA(cudaMallocHost(&p, bytes));
+      cap = bytes;
+    }
     char *c = static_cast<char *>(p);
     auto take = [&](size_t b) {
       char *r = c;
@@ -186,6 +194,11 @@ struct HostMirror {
   }
 };
 
+HostMirror &host_mirror() {
+  static thread_local HostMirror hm;
+  return hm;
+}
+
 template <typename T>
 struct Stage {
   int prec = sizeof(T) == 4 ? 32 : 64;
@@ -203,7 +216,7 @@ struct Solver {
   sign_opts o;
   std::vector<MatState> m;
   Work w;
-  HostMirror hm;
+  HostMirror &hm = host_mirror();
   std::vector<std::unique_ptr<Parked>> parked_store;
 
   // ---------------------------------------------------------------- helpers
@@ -257,8 +270,7 @@ struct Solver {
     w.lo.ensure(sizeof(int32_t) * size_t(N), s);
     w.len.ensure(sizeof(int32_t) * size_t(N), s);
     w.ub.ensure(sizeof(int64_t) * size_t(N), s);
-    w.wlist.ensure(sizeof(int32_t) * size_t(N), s);
-    w.clist.ensure(sizeof(int32_t) * size_t(N), s);
+    w.wlist.ensure(sizeof(int32_t) * size_t(4 * N), s);
     w.work.ensure(sizeof(double) * size_t(N), s);
     w.mults.ensure(sizeof(double) * size_t(nb), s);
     w.nnzc.ensure(sizeof(int64_t) * size_t(nb), s);
@@ -269,7 +281,7 @@ struct Solver {
       ProfScope ps(KC_BOUNDS, s);
       launch_bounds(N, A, B, st.d_seg.template as<int32_t>(), active, mode, w.lo.as<int32_t>(),
                     w.len.as<int32_t>(), w.ub.as<int64_t>(), w.wlist.as<int32_t>(),
-                    w.clist.as<int32_t>(), w.counters.as<int>(), w.work.as<double>(), s);
+                    w.counters.as<int>(), w.work.as<double>(), s);
       launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.work.as<double>(), 1,
                         w.mults.as<double>(), s);
     }
@@ -301,8 +313,8 @@ struct Solver {
     {
       ProfScope ps(cls, s, fl, by);
       launch_numeric<T>(N, A, aval, B, bval, mode, w.lo.as<int32_t>(), w.len.as<int32_t>(),
-                        w.wlist.as<int32_t>(), w.clist.as<int32_t>(), w.counters.as<int>(),
-                        C.rs.template as<int64_t>(), C.re.template as<int64_t>(), C.col.template as<int32_t>(), C.d_val(),
+                        w.wlist.as<int32_t>(), w.counters.as<int>(), C.rs.template as<int64_t>(),
+                        C.re.template as<int64_t>(), C.col.template as<int32_t>(), C.d_val(),
                         mode == MODE_SQUARE ? w.part.as<double>() : nullptr, s);
     }
     launch_seg_count(nb, st.d_moff.template as<int64_t>(), C.rs.template as<int64_t>(),
@@ -450,11 +462,8 @@ struct Solver {
     product(st, xr, st.X.d_val(), st.X.nnz, st.Tm.rows(), st.Tm.d_val(), nnz_t_all, MODE_UPDATE,
             st.Xb, d_act);
     std::vector<double> mb(hm.mults, hm.mults + nb);
-    d2h(hm.nnz_bar, w.nnzc.p, size_t(nb), s);
-    sync(s);
-    for (int i = 0; i < nb; ++i) hms[i].nnz_bar = hm.nnz_bar[i];
-    std::memcpy(hm.ms, hms.data(), sizeof(MatScalars) * nb);
-    h2d(w.ms.p, hm.ms, size_t(nb), s);
+    // per-matrix nnz(Xbar) straight into the device scalars (BOUND needs it)
+    launch_store_nnz_bar(nb, w.nnzc.as<int64_t>(), w.ms.as<MatScalars>(), s);
     hupdate.stop();
     HostScope hfilter(KH_FILTER);
     if (o.filter == SIGN_FILTER_NONE) {
@@ -516,6 +525,7 @@ struct Solver {
                         st.Xh.d_col(), st.Xh.val.p, s);
     for (int i = 0; i < nb; ++i) {
       hms[i].tau = hm.ms[i].tau;
+      hms[i].nnz_bar = hm.ms[i].nnz_bar;
       hms[i].fnorm = std::sqrt(hm.dsum[i]);
     }
   }
@@ -523,7 +533,6 @@ struct Solver {
   // No filter: the update is compacted with every entry kept (exact zeros too).
   template <typename T>
   void hms_none(Stage<T> &st, std::vector<MatScalars> &hms) {
-    (void)hms;
     int64_t N = st.moff.back();
     w.cnt.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
     ProfScope pf(KC_FILTER, s, 0.0, double(st.Xb.slots) * (2.0 * sizeof(T) + 8.0));
@@ -532,7 +541,9 @@ struct Solver {
     st.Xh.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
     launch_scan(N, w.cnt.as<int64_t>(), st.Xh.d_rp(), w.scan_tmp.as<int64_t>(), s);
     d2h(hm.tot, st.Xh.d_rp() + N, 1, s);
+    d2h(hm.ms, w.ms.p, size_t(st.mats.size()), s);
     sync(s);
+    for (size_t i = 0; i < st.mats.size(); ++i) hms[i].nnz_bar = hm.ms[i].nnz_bar;
     int64_t nnz = hm.tot[0];
     st.Xh.n = N;
     st.Xh.nnz = nnz;
