@@ -70,14 +70,17 @@ class Result:
 
 
 class _Info:
-    """A sign_info with numpy-owned trace arrays."""
+    """A sign_info with numpy-owned trace arrays (none when cap == 0)."""
 
     def __init__(self, cap: int):
-        self.arrays = {k: np.zeros(max(cap, 1), dtype=t) for k, t in _TRACE}
         self.s = N.sign_info()
         self.s.cap = cap
-        for k, t in _TRACE:
-            setattr(self.s, k, self.arrays[k].ctypes.data_as(C.POINTER(np.ctypeslib.as_ctypes_type(t))))
+        self.arrays = {}
+        if cap > 0:
+            self.arrays = {k: np.zeros(cap, dtype=t) for k, t in _TRACE}
+            for k, t in _TRACE:
+                setattr(self.s, k,
+                        self.arrays[k].ctypes.data_as(C.POINTER(np.ctypeslib.as_ctypes_type(t))))
 
     def trace(self, s=None) -> dict:
         c = (s if s is not None else self.s).count
@@ -233,16 +236,18 @@ class Batch:
 
     def solve(self, opts, trace_cap: int = 0) -> list:
         """Runs sign_solve_batch; returns per-matrix (status, iters, resid)."""
-        infos = [_Info(trace_cap) for _ in self.handles]
-        iarr = (N.sign_info * len(infos))(*[i.s for i in infos])
+        if self.infos is None or self.infos[2] != trace_cap:
+            infos = [_Info(trace_cap) for _ in self.handles]
+            iarr = (N.sign_info * len(infos))(*[i.s for i in infos])
+            self.infos = (infos, iarr, trace_cap)
+        infos, iarr, _ = self.infos
         st = load().sign_solve_batch(self.arr, len(self.handles), C.byref(opts), iarr)
         if st != SIGN_OK:
             raise SignError(st, "sign_solve_batch")
-        self.infos = (infos, iarr)
         return [(s.status, s.iters, s.resid) for s in iarr]
 
     def traces(self) -> list:
-        infos, iarr = self.infos
+        infos, iarr, _ = self.infos
         return [i.trace(s) for i, s in zip(infos, iarr)]
 
     def close(self):

@@ -103,8 +103,10 @@ struct Rows {
 // them: lists holds 4 lists of n entries (32-, 16- or 8-lane groups, or one
 // CTA per row); counters[0..3] are their lengths and counters[4..7] the
 // work-queue heads of the numeric kernels (all zeroed by the caller).
+// groups = 0 keeps every warp-sized row on 32 lanes (the FP32 products are
+// latency-bound; narrower groups pay off only for the FP64 pipe).
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
-                   int mode, int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists,
+                   int mode, int groups, int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists,
                    int *counters, double *work, cudaStream_t s);
 // Numeric product. Row i is written at cs[i] (exclusive scan of ub) and its
 // end stored in ce[i]. MODE_SQUARE: C = A A, and part[2i] = sum_j (C_ij -

@@ -104,8 +104,8 @@ __device__ __forceinline__ float lane_use(float avg, int g) {
 __global__ void __launch_bounds__(BOUNDS_TILE)
     k_bounds(int64_t n, const int64_t *ars, const int64_t *are, const int32_t *acol,
              const int64_t *brs, const int64_t *bre, const int32_t *bcol, const int32_t *seg,
-             const int *active, int mode, int32_t *lo, int32_t *len, int64_t *ub,
-             int32_t *lists, int *counters, double *work) {
+             const int *active, int mode, int groups, int32_t *lo, int32_t *len,
+             int64_t *ub, int32_t *lists, int *counters, double *work) {
   __shared__ unsigned char s_cls[BOUNDS_TILE];
   __shared__ int s_cnt[BOUNDS_TILE / 32][RC_N];
   __shared__ int s_base[RC_N];
@@ -160,6 +160,8 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
             int64_t bound = wk + (mode == MODE_UPDATE ? a1 - a0 : 0);
             if (L > WARP_W) {
               cls = RC_CTA;
+            } else if (!groups) {
+              cls = RC_G32;
             } else {
               float avg = float(wk) / float(a1 > a0 ? a1 - a0 : 1);
               float u32 = lane_use(avg, 32), u16 = lane_use(avg, 16), u8 = lane_use(avg, 8);
@@ -549,13 +551,13 @@ int grid_cap(int64_t items, int per_block, int per_sm) {
 }  // namespace
 
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
-                   int mode, int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists,
+                   int mode, int groups, int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists,
                    int *counters, double *work, cudaStream_t s) {
   if (n == 0) return;
   int tiles = int((n + BOUNDS_TILE - 1) / BOUNDS_TILE);
   int g = tiles < sm_count() * 8 ? tiles : sm_count() * 8;
   k_bounds<<<g, BOUNDS_TILE, 0, s>>>(n, A.rs, A.re, A.col, B.rs, B.re, B.col, seg, active, mode,
-                                     lo, len, ub, lists, counters, work);
+                                     groups, lo, len, ub, lists, counters, work);
   SGN_LAUNCH_CHECK();
 }
 

@@ -279,7 +279,8 @@ struct Solver {
     SGN_CUDA(cudaMemsetAsync(w.counters.p, 0, sizeof(int) * 8, s));
     {
       ProfScope ps(KC_BOUNDS, s);
-      launch_bounds(N, A, B, st.d_seg.template as<int32_t>(), active, mode, w.lo.as<int32_t>(),
+      launch_bounds(N, A, B, st.d_seg.template as<int32_t>(), active, mode, sizeof(T) == 8 ? 1 : 0,
+                    w.lo.as<int32_t>(),
                     w.len.as<int32_t>(), w.ub.as<int64_t>(), w.wlist.as<int32_t>(),
                     w.counters.as<int>(), w.work.as<double>(), s);
       launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.work.as<double>(), 1,
