@@ -176,6 +176,19 @@ sign_status sign_threshold_exact(const double *val, int64_t nnz, double b, int o
 sign_status sign_threshold_exact_noalloc(const double *val, int64_t nnz, double b,
                                          void *cuda_stream, double *tau_out);
 
+/* Dense product C = A B on the tensor cores: the dense path (a9) for
+ * matrices whose iterate has filled in. A (M x K), B (K x N) and C (M x N)
+ * are row-major FP32 device arrays with leading dimensions lda, ldb, ldc
+ * (elements). The product is split TF32: every operand is split as
+ * hi + lo (hi rounded to TF32) and C = A_hi B_hi + A_hi B_lo + A_lo B_hi is
+ * accumulated in FP32 by tcgen05 MMAs, which keeps about FP32 accuracy
+ * (the sparse FP32 stage's products are FP32 FMAs). K, N and the leading
+ * dimensions must be multiples of 4 and the arrays 16-byte aligned, else
+ * SIGN_EINVAL. SIGN_ETIMEOUT if a bounded wait on the tensor cores gave up.
+ * Returns after cuda_stream has finished. */
+sign_status sign_dense_product(int M, int N, int K, const float *A, int lda, const float *B,
+                               int ldb, float *C, int ldc, void *cuda_stream);
+
 /* ---- observability (not part of the paper's method) -------------------- */
 
 /* Total CUDA kernel launches made by this library in this process. */

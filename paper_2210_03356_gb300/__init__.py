@@ -210,6 +210,22 @@ def threshold_exact(values, b: float, stream=None) -> float:
     return tau.value
 
 
+def dense_product(a, b, out=None, stream=None):
+    """sign_dense_product for CUDA torch float32 matrices (row-major)."""
+    import torch
+    M, K = a.shape
+    K2, N = b.shape
+    assert K == K2 and a.dtype == b.dtype == torch.float32 and a.is_cuda and b.is_cuda
+    if out is None:
+        out = torch.empty(M, N, dtype=torch.float32, device=a.device)
+    st = load().sign_dense_product(M, N, K, _ptr(a), a.stride(0), _ptr(b), b.stride(0), _ptr(out),
+                                   out.stride(0),
+                                   stream if stream is not None else current_stream())
+    if st != SIGN_OK:
+        raise SignError(st, "sign_dense_product")
+    return out
+
+
 def kernel_launches() -> int:
     return int(load().sign_kernel_launches())
 

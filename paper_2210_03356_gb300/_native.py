@@ -61,6 +61,8 @@ SIGNATURES = {
                                        C.POINTER(C.c_double)]),
     "sign_threshold_exact_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
                                                C.POINTER(C.c_double)]),
+    "sign_dense_product": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                                     C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     "sign_kernel_launches": (C.c_int64, []),
     "sign_prof_enable": (C.c_int, [C.c_int]),
     "sign_prof_read": (C.c_int, [C.c_void_p, C.c_int]),

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsign_gb300.so")
 SOURCES = ["kernels_csr.cu", "kernels_spgemm.cu", "kernels_select.cu", "solver.cu", "prof.cu", "threshold.cu",
-           "threshold_noalloc.cu"]
+           "threshold_noalloc.cu", "kernels_dense.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("common.cuh", "kernels.h")] + [
     os.path.join(ROOT, "include", "sign.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -177,4 +177,13 @@ void launch_filter_write(int64_t n, const int32_t *seg, const int *active, const
                          const MatScalars *ms, const int64_t *orp, int32_t *ocol, void *oval,
                          cudaStream_t s);
 
+// ---------------------------------------------------------------- dense (a9)
+// C = A B for dense row-major FP32 matrices on the tensor cores (split TF32,
+// three kind::tf32 MMAs per K step, FP32 accumulation in tensor memory).
+// K, N and the leading dimensions must be multiples of 4, arrays 16-byte
+// aligned. *err |= 1 if a bounded wait gave up.
+size_t dense_gemm_smem();
+void launch_dense_gemm_tf32x3(int M, int N, int K, const float *A, int lda, const float *B,
+                              int ldb, float *C, int ldc, int *err, cudaStream_t s);
+
 }  // namespace sgn
