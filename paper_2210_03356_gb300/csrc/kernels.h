@@ -105,9 +105,13 @@ struct Rows {
 // work-queue heads of the numeric kernels (all zeroed by the caller).
 // groups = 0 keeps every warp-sized row on 32 lanes (the FP32 products are
 // latency-bound; narrower groups pay off only for the FP64 pipe).
+// dslot (nullable, per matrix): matrices with dslot[m] >= 0 take the dense
+// path; their rows get no sparse work, and in MODE_UPDATE a whole row of
+// slots (moff gives the matrix sizes).
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
-                   int mode, int groups, int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists,
-                   int *counters, double *work, cudaStream_t s);
+                   int mode, int groups, const int *dslot, const int64_t *moff, int32_t *lo,
+                   int32_t *len, int64_t *ub, int32_t *lists, int *counters, double *work,
+                   cudaStream_t s);
 // Numeric product. Row i is written at cs[i] (exclusive scan of ub) and its
 // end stored in ce[i]. MODE_SQUARE: C = A A, and part[2i] = sum_j (C_ij -
 // delta_ij)^2, part[2i+1] = sum_k a_ik^2. MODE_UPDATE: C = 1.5 A - 0.5 A B.
@@ -185,5 +189,35 @@ void launch_filter_write(int64_t n, const int32_t *seg, const int *active, const
 size_t dense_gemm_smem();
 void launch_dense_gemm_tf32x3(int M, int N, int K, const float *A, int lda, const float *B,
                               int ldb, float *C, int ldc, int *err, cudaStream_t s);
+
+// One product of a batched launch (all operands row-major FP32, same rules).
+struct DenseJob {
+  int M, N, K;
+  const float *A;
+  int lda;
+  const float *B;
+  int ldb;
+  float *C;
+  int ldc;
+};
+void launch_dense_jobs(int njobs, const DenseJob *jobs, int max_m, int max_n, int *err,
+                       cudaStream_t s);
+
+// The dense blocks of one matrix on the dense path: X, T = X X and P = X T,
+// each n x n (leading dimension ld >= n, a multiple of 4).
+struct DenseBuf {
+  float *X, *T, *P;
+  int n, ld;
+};
+// dslot[m] = index into bufs for matrices on the dense path, -1 otherwise.
+void launch_densify(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                    const int64_t *rp, const int32_t *col, const float *val, const DenseBuf *bufs,
+                    cudaStream_t s);
+void launch_dense_resid(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                        const DenseBuf *bufs, double *part, unsigned long long *tcount,
+                        cudaStream_t s);
+void launch_dense_emit(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                       const int *active, const DenseBuf *bufs, const int64_t *cs, int64_t *ce,
+                       int32_t *ccol, float *cval, cudaStream_t s);
 
 }  // namespace sgn

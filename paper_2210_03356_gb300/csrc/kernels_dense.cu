@@ -156,11 +156,11 @@ __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
   lo = __fsub_rn(x, hi);
 }
 
-__global__ void __launch_bounds__(DTHREADS)
-    k_gemm_tf32x3(int M, int N, int K, const float *__restrict__ A, int lda,
-                  const float *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
-                  int *err) {
-  extern __shared__ __align__(1024) unsigned char smem[];
+// One 128 x 128 tile (m0, n0) of C = A B; smem = 4 operand tiles.
+__device__ __forceinline__ void gemm_tile(int M, int N, int K, const float *__restrict__ A,
+                                          int lda, const float *__restrict__ B, int ldb,
+                                          float *__restrict__ C, int ldc, int m0, int n0,
+                                          unsigned char *smem, int *err) {
   unsigned char *a_hi = smem;
   unsigned char *a_lo = smem + TILE_BYTES;
   unsigned char *b_hi = smem + 2 * TILE_BYTES;
@@ -169,7 +169,6 @@ __global__ void __launch_bounds__(DTHREADS)
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * DM, n0 = blockIdx.x * DN;
 
   if (warp == 0) {
     tmem_alloc(&tmem_base, TMEM_COLS);
@@ -288,9 +287,177 @@ __global__ void __launch_bounds__(DTHREADS)
   if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
 
+__global__ void __launch_bounds__(DTHREADS)
+    k_gemm_tf32x3(int M, int N, int K, const float *__restrict__ A, int lda,
+                  const float *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
+                  int *err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  gemm_tile(M, N, K, A, lda, B, ldb, C, ldc, blockIdx.y * DM, blockIdx.x * DN, smem, err);
+}
+
+// Several independent products in one launch: blockIdx.z is the job.
+__global__ void __launch_bounds__(DTHREADS) k_gemm_tf32x3_jobs(const DenseJob *jobs, int *err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const DenseJob J = jobs[blockIdx.z];
+  const int m0 = blockIdx.y * DM, n0 = blockIdx.x * DN;
+  if (m0 >= J.M || n0 >= J.N) return;  // before any tensor-memory allocation
+  gemm_tile(J.M, J.N, J.K, J.A, J.lda, J.B, J.ldb, J.C, J.ldc, m0, n0, smem, err);
+}
+
+// Densify: rows of the dense matrices of a stage CSR into their zeroed
+// row-major blocks (global columns minus the matrix's first row).
+__global__ void k_densify(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                          const int64_t *rp, const int32_t *col, const float *val,
+                          const DenseBuf *bufs) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nwarps) {
+    int m = seg[r];
+    int d = dslot[m];
+    if (d < 0) continue;
+    const DenseBuf Bf = bufs[d];
+    int64_t r0 = moff[m];
+    float *row = Bf.X + (r - r0) * Bf.ld;
+    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) row[col[p] - r0] = val[p];
+  }
+}
+
+// Residual partials of the dense matrices from T = X X: part[2r] =
+// sum_j (t_rj - delta_rj)^2 and part[2r+1] = sum_j x_rj^2, as exact float
+// pairs; tcount[d] counts the nonzero entries of T.
+__global__ void k_dense_resid(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                              const DenseBuf *bufs, double *part, unsigned long long *tcount) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nwarps) {
+    int m = seg[r];
+    int d = dslot[m];
+    if (d < 0) continue;
+    const DenseBuf Bf = bufs[d];
+    int64_t i = r - moff[m];
+    const float *trow = Bf.T + i * Bf.ld;
+    const float *xrow = Bf.X + i * Bf.ld;
+    float rh = 0.f, rl = 0.f, xh = 0.f, xl = 0.f;
+    double rdiag = 0.0;
+    unsigned cnt = 0;
+    for (int j = lane; j < Bf.n; j += 32) {
+      float t = trow[j], x = xrow[j];
+      cnt += t != 0.0f;
+      if (j == i) {
+        double dd = double(t) - 1.0;
+        rdiag = dd * dd;
+      } else {
+        float pp = __fmul_rn(t, t), ee = __fmaf_rn(t, t, -pp);
+        float s = __fadd_rn(rh, pp), bb = __fsub_rn(s, rh);
+        rl = __fadd_rn(rl, __fadd_rn(__fadd_rn(__fsub_rn(rh, __fsub_rn(s, bb)), __fsub_rn(pp, bb)), ee));
+        rh = s;
+      }
+      float px = __fmul_rn(x, x), ex = __fmaf_rn(x, x, -px);
+      float sx = __fadd_rn(xh, px), bx = __fsub_rn(sx, xh);
+      xl = __fadd_rn(xl, __fadd_rn(__fadd_rn(__fsub_rn(xh, __fsub_rn(sx, bx)), __fsub_rn(px, bx)), ex));
+      xh = sx;
+    }
+    double rs = double(rh) + double(rl) + rdiag, xs = double(xh) + double(xl);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rs += __shfl_xor_sync(0xffffffffu, rs, o);
+      xs += __shfl_xor_sync(0xffffffffu, xs, o);
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) {
+      part[2 * r] = rs;
+      part[2 * r + 1] = xs;
+      atomicAdd(&tcount[d], (unsigned long long)cnt);
+    }
+  }
+}
+
+// Xbar = 1.5 X - 0.5 P for the dense matrices, nonzero entries written in
+// column order into the row slots [cs[r], ...), the end stored in ce[r].
+__global__ void k_dense_emit(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                             const int *active, const DenseBuf *bufs, const int64_t *cs,
+                             int64_t *ce, int32_t *ccol, float *cval) {
+  int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nwarps) {
+    int m = seg[r];
+    int d = dslot[m];
+    if (d < 0 || !active[m]) continue;
+    const DenseBuf Bf = bufs[d];
+    int64_t r0 = moff[m];
+    int64_t i = r - r0;
+    const float *xrow = Bf.X + i * Bf.ld;
+    const float *prow = Bf.P + i * Bf.ld;
+    int64_t out = cs[r];
+    for (int j0 = 0; j0 < Bf.n; j0 += 32) {
+      int j = j0 + lane;
+      float v = 0.0f;
+      if (j < Bf.n)
+        v = __fsub_rn(__fmul_rn(1.5f, xrow[j]), __fmul_rn(0.5f, prow[j]));
+      bool keep = v != 0.0f;
+      unsigned mk = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        int64_t pos = out + __popc(mk & lt);
+        ccol[pos] = int32_t(r0 + j);
+        cval[pos] = v;
+      }
+      out += __popc(mk);
+    }
+    if (lane == 0) ce[r] = out;
+  }
+}
+
 }  // namespace
 
 size_t dense_gemm_smem() { return size_t(4) * TILE_BYTES; }
+
+int dense_grid(int64_t n) {
+  int64_t g = (n + 7) / 8;
+  return int(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
+}
+
+void launch_dense_jobs(int njobs, const DenseJob *jobs, int max_m, int max_n, int *err,
+                       cudaStream_t s) {
+  if (njobs <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    SGN_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_jobs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(dense_gemm_smem())));
+    attr = true;
+  }
+  dim3 grid((max_n + DN - 1) / DN, (max_m + DM - 1) / DM, njobs);
+  k_gemm_tf32x3_jobs<<<grid, DTHREADS, dense_gemm_smem(), s>>>(jobs, err);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_densify(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                    const int64_t *rp, const int32_t *col, const float *val, const DenseBuf *bufs,
+                    cudaStream_t s) {
+  if (n == 0) return;
+  k_densify<<<dense_grid(n), 256, 0, s>>>(n, seg, dslot, moff, rp, col, val, bufs);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_dense_resid(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                        const DenseBuf *bufs, double *part, unsigned long long *tcount,
+                        cudaStream_t s) {
+  if (n == 0) return;
+  k_dense_resid<<<dense_grid(n), 256, 0, s>>>(n, seg, dslot, moff, bufs, part, tcount);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_dense_emit(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                       const int *active, const DenseBuf *bufs, const int64_t *cs, int64_t *ce,
+                       int32_t *ccol, float *cval, cudaStream_t s) {
+  if (n == 0) return;
+  k_dense_emit<<<dense_grid(n), 256, 0, s>>>(n, seg, dslot, moff, active, bufs, cs, ce, ccol,
+                                             cval);
+  SGN_LAUNCH_CHECK();
+}
 
 void launch_dense_gemm_tf32x3(int M, int N, int K, const float *A, int lda, const float *B,
                               int ldb, float *C, int ldc, int *err, cudaStream_t s) {
@@ -346,3 +513,4 @@ extern "C" sign_status sign_dense_product(int M, int N, int K, const float *A, i
   }
   return SIGN_OK;
 }
+

@@ -104,8 +104,9 @@ __device__ __forceinline__ float lane_use(float avg, int g) {
 __global__ void __launch_bounds__(BOUNDS_TILE)
     k_bounds(int64_t n, const int64_t *ars, const int64_t *are, const int32_t *acol,
              const int64_t *brs, const int64_t *bre, const int32_t *bcol, const int32_t *seg,
-             const int *active, int mode, int groups, int32_t *lo, int32_t *len,
-             int64_t *ub, int32_t *lists, int *counters, double *work) {
+             const int *active, int mode, int groups, const int *dslot, const int64_t *moff,
+             int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists, int *counters,
+             double *work) {
   __shared__ unsigned char s_cls[BOUNDS_TILE];
   __shared__ int s_cnt[BOUNDS_TILE / 32][RC_N];
   __shared__ int s_base[RC_N];
@@ -118,9 +119,13 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
       int64_t r = t0 + i;
       int cls = RC_NONE;
       if (r < n) {
-        if (!active[seg[r]]) {
+        const int m = seg[r];
+        if (!active[m] || (dslot && dslot[m] >= 0)) {
+          // inactive, or on the dense path: no sparse work; a dense row of an
+          // update gets a whole row of slots for 1.5 X - 0.5 X T
           if (lane == 0) {
-            ub[r] = 0;
+            bool dense = active[m] && dslot && dslot[m] >= 0;
+            ub[r] = dense && mode == MODE_UPDATE ? moff[m + 1] - moff[m] : 0;
             len[r] = 0;
             lo[r] = 0;
             work[r] = 0.0;
@@ -551,13 +556,14 @@ int grid_cap(int64_t items, int per_block, int per_sm) {
 }  // namespace
 
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
-                   int mode, int groups, int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists,
-                   int *counters, double *work, cudaStream_t s) {
+                   int mode, int groups, const int *dslot, const int64_t *moff, int32_t *lo,
+                   int32_t *len, int64_t *ub, int32_t *lists, int *counters, double *work,
+                   cudaStream_t s) {
   if (n == 0) return;
   int tiles = int((n + BOUNDS_TILE - 1) / BOUNDS_TILE);
   int g = tiles < sm_count() * 8 ? tiles : sm_count() * 8;
   k_bounds<<<g, BOUNDS_TILE, 0, s>>>(n, A.rs, A.re, A.col, B.rs, B.re, B.col, seg, active, mode,
-                                     groups, lo, len, ub, lists, counters, work);
+                                     groups, dslot, moff, lo, len, ub, lists, counters, work);
   SGN_LAUNCH_CHECK();
 }
 

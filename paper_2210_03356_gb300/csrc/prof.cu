@@ -33,7 +33,8 @@ const char *kNames[KC_COUNT] = {"numeric_square_f64", "numeric_update_f64", "num
                                 "numeric_update_f32", "bounds",             "scan",
                                 "select_hist",        "select_extract",     "select_digits",
                                 "select_bound",       "filter",             "reduce",
-                                "assemble",           "onenorm",            "host_setup",
+                                "assemble",           "onenorm",            "dense_tf32x3",
+                                "host_setup",
                                 "host_check",         "host_decide",        "host_update",
                                 "host_filter",        "host_rebuild"};
 

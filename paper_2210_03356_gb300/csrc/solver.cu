@@ -14,6 +14,7 @@
 // A matrix that stops is copied out to its handle; the stage is rebuilt
 // without it at the next round. Per-matrix control flow is exactly that of a
 // lone solve, so every result is independent of the batch it ran in.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -152,7 +153,18 @@ Rows compact_rows(const Csr<T> &c) {
 // Shared scratch of one solve call.
 struct Work {
   DevBuf lo, len, ub, wlist, clist, counters, part, scan_tmp, eoff, sums, ms, active, sel,
-      asm_blocks, asm_off, asm_lens, dropped, norm_work, norm, work, mults, cnt, nnzc, xblocks;
+      asm_blocks, asm_off, asm_lens, dropped, norm_work, norm, work, mults, cnt, nnzc, xblocks,
+      dslot, dmem, dbufs, djobs, dcount, derr;
+};
+
+// The matrices of one round on the dense path (FP32 stage): their slots,
+// dense blocks and the batched product jobs.
+struct DensePlan {
+  std::vector<int> slot;          // per matrix of the stage: dense index or -1
+  std::vector<DenseBuf> bufs;     // host copies of the device DenseBuf array
+  std::vector<int> mat;           // stage slot of each dense matrix
+  int nd = 0, max_ld = 0;
+  bool any() const { return nd > 0; }
 };
 
 // Page-locked host mirrors of the per-matrix values read back every round.
@@ -205,6 +217,7 @@ struct Stage {
   std::vector<int> mats;          // matrix ids, in row order
   std::vector<int> alive;         // 0 once a matrix has left (its rows are empty)
   std::vector<int64_t> moff;      // row offsets (host), size mats+1
+  std::vector<int64_t> ex;        // entry offsets of X per matrix (host), size mats+1
   DevBuf d_moff, d_seg;
   Csr<T> X, Xh;                   // compact iterate and filtered update
   Slotted<T> Tm, Xb;              // X X and 1.5 X - 0.5 X T
@@ -264,7 +277,8 @@ struct Solver {
   // w.nnzc the per-matrix nnz of C (device, read with the next sync).
   template <typename T>
   void product(Stage<T> &st, const Rows &A, const T *aval, int64_t nnzA, const Rows &B,
-               const T *bval, int64_t nnzB, int mode, Slotted<T> &C, const int *active) {
+               const T *bval, int64_t nnzB, int mode, Slotted<T> &C, const int *active,
+               const DensePlan *dp = nullptr) {
     int64_t N = int64_t(st.moff.back());
     int nb = int(st.mats.size());
     w.lo.ensure(sizeof(int32_t) * size_t(N), s);
@@ -280,7 +294,8 @@ struct Solver {
     {
       ProfScope ps(KC_BOUNDS, s);
       launch_bounds(N, A, B, st.d_seg.template as<int32_t>(), active, mode, sizeof(T) == 8 ? 1 : 0,
-                    w.lo.as<int32_t>(),
+                    dp && dp->any() ? w.dslot.as<int>() : nullptr,
+                    st.d_moff.template as<int64_t>(), w.lo.as<int32_t>(),
                     w.len.as<int32_t>(), w.ub.as<int64_t>(), w.wlist.as<int32_t>(),
                     w.counters.as<int>(), w.work.as<double>(), s);
       launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.work.as<double>(), 1,
@@ -318,8 +333,98 @@ struct Solver {
                         C.re.template as<int64_t>(), C.col.template as<int32_t>(), C.d_val(),
                         mode == MODE_SQUARE ? w.part.as<double>() : nullptr, s);
     }
+    if (dp && dp->any()) dense_step(st, mode, C, active, *dp);
     launch_seg_count(nb, st.d_moff.template as<int64_t>(), C.rs.template as<int64_t>(),
                      C.re.template as<int64_t>(), w.nnzc.as<int64_t>(), s);
+  }
+
+  // ---------------------------------------------------------------- dense path (a9)
+  // Chooses the FP32-stage matrices whose iterate has filled in (density >=
+  // dense_frac, n <= 4096) and lays out their dense blocks.
+  template <typename T>
+  DensePlan plan_dense(Stage<T> &st) {
+    DensePlan dp;
+    int nb = int(st.mats.size());
+    dp.slot.assign(nb, -1);
+    if (sizeof(T) != 4 || !(o.dense_frac <= 1.0) || o.filter == SIGN_FILTER_NONE) return dp;
+    size_t total = 0;
+    for (int i = 0; i < nb; ++i) {
+      if (!st.alive[i]) continue;
+      int64_t n = st.moff[i + 1] - st.moff[i];
+      int64_t nnz = st.ex[i + 1] - st.ex[i];
+      if (n > 4096 || double(nnz) < o.dense_frac * double(n) * double(n)) continue;
+      int ld = int((n + 3) / 4 * 4);
+      dp.slot[i] = dp.nd++;
+      dp.mat.push_back(i);
+      dp.bufs.push_back(DenseBuf{nullptr, nullptr, nullptr, int(n), ld});
+      dp.max_ld = std::max(dp.max_ld, ld);
+      total += 3 * size_t(ld) * size_t(ld);
+    }
+    if (!dp.nd) return dp;
+    float *mem = static_cast<float *>(w.dmem.ensure(sizeof(float) * total, s));
+    size_t off = 0;
+    for (DenseBuf &b : dp.bufs) {
+      size_t blk = size_t(b.ld) * size_t(b.ld);
+      b.X = mem + off;
+      b.T = mem + off + blk;
+      b.P = mem + off + 2 * blk;
+      off += 3 * blk;
+    }
+    w.dslot.ensure(sizeof(int) * size_t(nb), s);
+    h2d(w.dslot.p, dp.slot.data(), size_t(nb), s);
+    w.dbufs.ensure(sizeof(DenseBuf) * size_t(dp.nd), s);
+    h2d(w.dbufs.p, dp.bufs.data(), size_t(dp.nd), s);
+    w.dcount.ensure(sizeof(unsigned long long) * size_t(dp.nd), s);
+    w.derr.ensure(sizeof(int), s);
+    SGN_CUDA(cudaMemsetAsync(w.derr.p, 0, sizeof(int), s));
+    sync(s);  // the host vectors above are pageable
+    return dp;
+  }
+
+  // The dense steps of a product: SQUARE densifies X and forms T = X X and the
+  // residual partials; UPDATE forms P = X T and emits 1.5 X - 0.5 P.
+  template <typename T>
+  void dense_step(Stage<T> &st, int mode, Slotted<T> &C, const int *active, const DensePlan &dp) {
+    if constexpr (sizeof(T) == 4) {
+      int64_t N = st.moff.back();
+      std::vector<DenseJob> jobs;
+      double fl = 0.0;
+      for (const DenseBuf &b : dp.bufs) {
+        if (mode == MODE_SQUARE)
+          jobs.push_back(DenseJob{b.ld, b.ld, b.ld, b.X, b.ld, b.X, b.ld, b.T, b.ld});
+        else
+          jobs.push_back(DenseJob{b.ld, b.ld, b.ld, b.X, b.ld, b.T, b.ld, b.P, b.ld});
+        fl += 3.0 * 2.0 * double(b.ld) * double(b.ld) * double(b.ld);
+      }
+      w.djobs.ensure(sizeof(DenseJob) * jobs.size(), s);
+      h2d(w.djobs.p, jobs.data(), jobs.size(), s);
+      const DenseBuf *bufs = w.dbufs.as<DenseBuf>();
+      if (mode == MODE_SQUARE) {
+        size_t total = 0;
+        for (const DenseBuf &b : dp.bufs) total += 3 * size_t(b.ld) * size_t(b.ld);
+        SGN_CUDA(cudaMemsetAsync(w.dmem.p, 0, sizeof(float) * total, s));
+        launch_densify(N, st.d_seg.template as<int32_t>(), w.dslot.as<int>(),
+                       st.d_moff.template as<int64_t>(), st.X.d_rp(), st.X.d_col(),
+                       reinterpret_cast<const float *>(st.X.val.p), bufs, s);
+      }
+      {
+        ProfScope ps(KC_DENSE, s, fl, 0.0);
+        launch_dense_jobs(int(jobs.size()), w.djobs.as<DenseJob>(), dp.max_ld, dp.max_ld,
+                          w.derr.as<int>(), s);
+      }
+      if (mode == MODE_SQUARE) {
+        SGN_CUDA(cudaMemsetAsync(w.dcount.p, 0, sizeof(unsigned long long) * size_t(dp.nd), s));
+        launch_dense_resid(N, st.d_seg.template as<int32_t>(), w.dslot.as<int>(),
+                           st.d_moff.template as<int64_t>(), bufs, w.part.as<double>(),
+                           w.dcount.as<unsigned long long>(), s);
+      } else {
+        launch_dense_emit(N, st.d_seg.template as<int32_t>(), w.dslot.as<int>(),
+                          st.d_moff.template as<int64_t>(), active, bufs,
+                          C.rs.template as<int64_t>(), C.re.template as<int64_t>(),
+                          C.col.template as<int32_t>(), reinterpret_cast<float *>(C.val.p), s);
+      }
+      sync(s);  // the job list is a pageable host vector
+    }
   }
 
   // ---------------------------------------------------------------- rounds
@@ -360,6 +465,8 @@ struct Solver {
     st.X.swap(nx);
     st.mats = mats;
     st.alive.assign(mats.size(), 1);
+    st.ex.assign(1, 0);
+    for (int64_t b : bnnz) st.ex.push_back(st.ex.back() + b);
     set_layout(st.moff, st.mats, st.d_moff, st.d_seg);
     st.incoming.clear();
   }
@@ -375,16 +482,14 @@ struct Solver {
     w.active.ensure(sizeof(int) * size_t(nb), s);
     h2d(w.active.p, st.alive.data(), st.alive.size(), s);
     const int *d_act = w.active.as<int>();
-    // entry offsets of the iterate per matrix (read with the product's sync)
-    w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
-    launch_gather_offsets(nb, st.d_moff.template as<int64_t>(), st.X.d_rp(), w.eoff.as<int64_t>(), s);
-    d2h(hm.ex, w.eoff.p, size_t(nb + 1), s);
+    const std::vector<int64_t> ex = st.ex;  // entry offsets of the iterate per matrix
     // ---- check: T = X X, r, x, budget (steps a2, a4)
     Rows xr = compact_rows(st.X);
     HostScope hcheck(KH_CHECK);
-    product(st, xr, st.X.d_val(), st.X.nnz, xr, st.X.d_val(), st.X.nnz, MODE_SQUARE, st.Tm, d_act);
-    std::vector<int64_t> ex(hm.ex, hm.ex + nb + 1);
-    std::vector<double> mt(hm.mults, hm.mults + nb);
+    DensePlan dp = plan_dense(st);
+    product(st, xr, st.X.d_val(), st.X.nnz, xr, st.X.d_val(), st.X.nnz, MODE_SQUARE, st.Tm, d_act,
+            &dp);
+    std::vector<double> mt(hm.mults, hm.mults + nb);  // sparse multiply-adds of T
     w.sums.ensure(sizeof(double) * size_t(2 * nb), s);
     w.ms.ensure(sizeof(MatScalars) * size_t(nb), s);
     double tol_stage = st.prec == 32 ? o.fp32_until : o.tol;
@@ -397,7 +502,15 @@ struct Solver {
     }
     d2h(hm.ms, w.ms.p, size_t(nb), s);
     d2h(hm.nnz_t, w.nnzc.p, size_t(nb), s);
+    std::vector<unsigned long long> dcount(dp.nd);
+    if (dp.any()) d2h(dcount.data(), w.dcount.p, size_t(dp.nd), s);
     sync(s);
+    for (int d = 0; d < dp.nd; ++d) {  // the dense path's T: its nonzeros and multiply-adds
+      int i = dp.mat[d];
+      hm.nnz_t[i] += int64_t(dcount[d]);
+      double n = double(st.moff[i + 1] - st.moff[i]);
+      mt[i] = n * n * n;
+    }
     hcheck.stop();
     std::vector<MatScalars> hms(hm.ms, hm.ms + nb);
     // ---- per-matrix decisions (steps a7, a8); leavers copied out in one launch
@@ -461,8 +574,12 @@ struct Solver {
     int64_t nnz_t_all = 0;
     for (int i = 0; i < nb; ++i) nnz_t_all += hm.nnz_t[i];
     product(st, xr, st.X.d_val(), st.X.nnz, st.Tm.rows(), st.Tm.d_val(), nnz_t_all, MODE_UPDATE,
-            st.Xb, d_act);
+            st.Xb, d_act, &dp);
     std::vector<double> mb(hm.mults, hm.mults + nb);
+    for (int d = 0; d < dp.nd; ++d) {
+      double n = double(st.moff[dp.mat[d] + 1] - st.moff[dp.mat[d]]);
+      mb[dp.mat[d]] = n * n * n;
+    }
     // per-matrix nnz(Xbar) straight into the device scalars (BOUND needs it)
     launch_store_nnz_bar(nb, w.nnzc.as<int64_t>(), w.ms.as<MatScalars>(), s);
     hupdate.stop();
@@ -511,6 +628,9 @@ struct Solver {
     launch_scan(N, w.cnt.as<int64_t>(), st.Xh.d_rp(), w.scan_tmp.as<int64_t>(), s);
     launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.dropped.as<double>(), 1,
                       w.sums.as<double>(), s);
+    w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
+    launch_gather_offsets(nb, st.d_moff.template as<int64_t>(), st.Xh.d_rp(), w.eoff.as<int64_t>(), s);
+    d2h(hm.ex, w.eoff.p, size_t(nb + 1), s);
     d2h(hm.tot, st.Xh.d_rp() + N, 1, s);
     d2h(hm.ms, w.ms.p, size_t(nb), s);
     d2h(hm.dsum, w.sums.p, size_t(nb), s);
@@ -529,6 +649,7 @@ struct Solver {
       hms[i].nnz_bar = hm.ms[i].nnz_bar;
       hms[i].fnorm = std::sqrt(hm.dsum[i]);
     }
+    st.ex.assign(hm.ex, hm.ex + nb + 1);
   }
 
   // No filter: the update is compacted with every entry kept (exact zeros too).
@@ -541,10 +662,15 @@ struct Solver {
                        w.cnt.as<int64_t>(), s);
     st.Xh.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
     launch_scan(N, w.cnt.as<int64_t>(), st.Xh.d_rp(), w.scan_tmp.as<int64_t>(), s);
+    int nbm = int(st.mats.size());
+    w.eoff.ensure(sizeof(int64_t) * size_t(nbm + 1), s);
+    launch_gather_offsets(nbm, st.d_moff.template as<int64_t>(), st.Xh.d_rp(), w.eoff.as<int64_t>(), s);
+    d2h(hm.ex, w.eoff.p, size_t(nbm + 1), s);
     d2h(hm.tot, st.Xh.d_rp() + N, 1, s);
-    d2h(hm.ms, w.ms.p, size_t(st.mats.size()), s);
+    d2h(hm.ms, w.ms.p, size_t(nbm), s);
     sync(s);
-    for (size_t i = 0; i < st.mats.size(); ++i) hms[i].nnz_bar = hm.ms[i].nnz_bar;
+    for (int i = 0; i < nbm; ++i) hms[i].nnz_bar = hm.ms[i].nnz_bar;
+    st.ex.assign(hm.ex, hm.ex + nbm + 1);
     int64_t nnz = hm.tot[0];
     st.Xh.n = N;
     st.Xh.nnz = nnz;
@@ -582,6 +708,8 @@ struct Solver {
     s64.alive.assign(count, 1);
     set_layout(s64.moff, s64.mats, s64.d_moff, s64.d_seg);
     assemble<double>(blocks, bnnz, s64.X);
+    s64.ex.assign(1, 0);
+    for (int64_t b : bnnz) s64.ex.push_back(s64.ex.back() + b);
     int64_t N = off;
     if (o.scale_1norm) {
       w.norm_work.ensure(sizeof(unsigned long long) * size_t(2 * N + 4 * count), s);
@@ -607,10 +735,12 @@ struct Solver {
       assemble<float>(b1, {nnz}, s32.X);
       s32.mats = all;
       s32.alive.assign(count, 1);
+      s32.ex = s64.ex;
       set_layout(s32.moff, s32.mats, s32.d_moff, s32.d_seg);
       s64.mats.clear();
       s64.alive.clear();
       s64.moff.assign(1, 0);
+      s64.ex.assign(1, 0);
     }
     hsetup.stop();
     for (int guard = 0; guard < 4 * o.max_iter + 16; ++guard) {

@@ -92,7 +92,7 @@ def test_unfiltered_ns_dense_fill(sg, orc):
 
 def test_mixed_precision_matches_mixed_oracle(sg, orc):
     a = w.tridiagonal()
-    res = sg.solve(a, tol=1e-8, filter="exact", prec=1)
+    res = sg.solve(a, tol=1e-8, filter="exact", prec=1, dense_frac=2.0)
     ref = orc.nsf(a, tol=1e-8, filter="exact", mixed=True)
     assert_parity(res, ref)
     assert res.trace["prec_k"][0] == 32 and res.trace["prec_k"][-1] == 64
@@ -177,7 +177,8 @@ def test_batch_matches_lone_solves_and_oracle(sg, orc):
 def test_batch_mixed_precision_moves_per_matrix(sg, orc):
     shapes = w.banded_batch_shapes(12, nmin=200, nmax=900)
     mats = [w.banded(n, b, s) for n, b, s in shapes]
-    out = sg.solve_batch(mats, tol=1e-8, filter="exact", prec=1)
+    # sparse FP32 products only (dense_frac > 1): bit-for-bit with the oracle
+    out = sg.solve_batch(mats, tol=1e-8, filter="exact", prec=1, dense_frac=2.0)
     for a, res in zip(mats, out):
         ref = orc.nsf(a, tol=1e-8, filter="exact", mixed=True)
         assert_parity(res, ref)
@@ -187,7 +188,7 @@ def test_batch_full_512_sampled(sg, orc):
     """The 512-matrix banded batch in one call; sampled matrices vs the oracle."""
     shapes = w.banded_batch_shapes()
     mats = [w.banded(n, b, s) for n, b, s in shapes]
-    out = sg.solve_batch(mats, tol=1e-8, filter="exact", prec=1)
+    out = sg.solve_batch(mats, tol=1e-8, filter="exact", prec=1, dense_frac=2.0)
     assert all(r.status == sg.SIGN_OK for r in out)
     order = np.argsort([n * (b + 1) for n, b, _ in shapes])
     sample = [int(order[-1]), int(order[len(order) // 2]), int(order[0]), 7]
