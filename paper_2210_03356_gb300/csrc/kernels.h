@@ -182,31 +182,37 @@ void launch_filter_write(int64_t n, const int32_t *seg, const int *active, const
                          cudaStream_t s);
 
 // ---------------------------------------------------------------- dense (a9)
-// C = A B for dense row-major FP32 matrices on the tensor cores (split TF32,
-// three kind::tf32 MMAs per K step, FP32 accumulation in tensor memory).
-// K, N and the leading dimensions must be multiples of 4, arrays 16-byte
-// aligned. *err |= 1 if a bounded wait gave up.
-size_t dense_gemm_smem();
-void launch_dense_gemm_tf32x3(int M, int N, int K, const float *A, int lda, const float *B,
-                              int ldb, float *C, int ldc, int *err, cudaStream_t s);
-
-// One product of a batched launch (all operands row-major FP32, same rules).
+// C = A Bt^T on the tensor cores (split TF32: three kind::tf32 MMAs per K step,
+// FP32 accumulation in tensor memory). A (M x K) and Bt (N x K) are row-major
+// FP32, each given split into hi (rounded to TF32) and lo = x - hi, with
+// leading dimensions multiples of 4 and 16-byte aligned rows. C is written
+// as FP32, or split into hi (C) and lo (C_lo) when C_lo is not null.
 struct DenseJob {
   int M, N, K;
-  const float *A;
+  const float *A_hi, *A_lo;
   int lda;
-  const float *B;
+  const float *B_hi, *B_lo;
   int ldb;
-  float *C;
+  float *C, *C_lo;
   int ldc;
 };
-void launch_dense_jobs(int njobs, const DenseJob *jobs, int max_m, int max_n, int *err,
-                       cudaStream_t s);
+size_t dense_gemm_smem();
+// Device scratch launch_dense_jobs needs for njobs jobs (tensor maps, tile offsets).
+size_t dense_jobs_scratch_bytes(int njobs);
+// jobs_host: the jobs on the host; jobs_dev: room for njobs DenseJob on the
+// device; scratch: dense_jobs_scratch_bytes(njobs) device bytes, 64-byte
+// aligned. *err |= 1 if a bounded wait gave up.
+void launch_dense_jobs(int njobs, const DenseJob *jobs_host, DenseJob *jobs_dev, void *scratch,
+                       int *err, cudaStream_t s);
+// hi/lo split of a rows x cols matrix (or of the transpose of in), ldo >= cols.
+void launch_split(int rows, int cols, const float *in, int ldi, int transpose, float *hi,
+                  float *lo, int ldo, cudaStream_t s);
 
-// The dense blocks of one matrix on the dense path: X, T = X X and P = X T,
-// each n x n (leading dimension ld >= n, a multiple of 4).
+// The dense blocks of one matrix on the dense path, n x n with leading
+// dimension ld (a multiple of 4): X and X^T split, T^T = (X X)^T split, and
+// P = X T.
 struct DenseBuf {
-  float *X, *T, *P;
+  float *X_hi, *X_lo, *XT_hi, *XT_lo, *TT_hi, *TT_lo, *P;
   int n, ld;
 };
 // dslot[m] = index into bufs for matrices on the dense path, -1 otherwise.

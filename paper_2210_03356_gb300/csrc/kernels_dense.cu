@@ -8,17 +8,32 @@
 // term is below 2^-22 relative, so the product carries about FP32 accuracy
 // (a single TF32 pass would keep only ~10 bits).
 //
-// One CTA of 128 threads computes a 128 x 128 tile of C:
-//   - the threads stage a 128 x 32 slice of A and of B^T (split into hi and
-//     lo) in shared memory, in the no-swizzle K-major core-matrix layout
-//     (core matrix = 8 rows x 16 bytes; along K the cores are 128 bytes apart,
-//     along M/N the 8-row groups 1024 bytes apart);
-//   - thread 0 issues the 12 MMAs of the slice (4 K steps of 8 x 3 splits)
-//     and commits them to an mbarrier; everybody waits on it (with a clock
-//     budget) before the slice is overwritten;
-//   - at the end each warp reads its 32 TMEM lanes (rows) with tcgen05.ld.
+// Operands are K-major and already split: C = A Bt^T with A (M x K) and Bt
+// (N x K) row-major, each given as a hi and a lo array. The kernel is
+// persistent (one CTA per SM, tiles of 128 x 256 handed out round-robin over
+// all jobs of the launch) and warp-specialised:
+//   - warp 0 (one thread) streams K slices of A_hi, A_lo, Bt_hi, Bt_lo with
+//     TMA (cp.async.bulk.tensor) into a ring of shared-memory stages laid out
+//     in the swizzled K-major canonical form, each stage completing on an
+//     mbarrier by transaction count;
+//   - warp 1 owns the tensor memory (two 256-column FP32 accumulators) and one
+//     of its threads issues the tcgen05.mma (three per K step of 8), releasing
+//     a stage with tcgen05.commit once its MMAs have read it and signalling a
+//     finished accumulator the same way;
+//   - warps 2-5 drain an accumulator with tcgen05.ld (each warp its 32 lanes)
+//     while the MMAs of the next tile run in the other one, and write C as
+//     FP32 or already split into hi and lo.
+// Every wait has a clock budget; a wait that runs out raises a shared abort
+// flag, all roles leave their loops, the copies and MMAs already issued are
+// waited for (again with a budget) and the tensor memory is freed.
 #include <stdint.h>
 
+#include <algorithm>
+#include <vector>
+
+#include <cuda.h>
+
+#include "../../include/sign.h"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -26,13 +41,18 @@ namespace sgn {
 
 namespace {
 
-constexpr int DM = 128;  // tile rows (UMMA M)
-constexpr int DN = 128;  // tile columns (UMMA N)
-constexpr int DK = 32;   // K slice staged per round
-constexpr int DTHREADS = 128;
-constexpr int TILE_BYTES = DM * DK * 4;  // one 128 x 32 FP32 operand tile (16 KB)
-constexpr uint32_t TMEM_COLS = 128;      // FP32 accumulator: 128 lanes x 128 columns
+constexpr int DM = 128;   // tile rows (UMMA M)
+constexpr int DN = 256;   // tile columns (UMMA N)
+constexpr int DK = 16;    // K slice per stage: 16 FP32 = 64 bytes = one swizzle span
+constexpr int NSTAGE = 4; // ring of stages
+constexpr int SWIZZLE_BYTES = DK * 4;
+constexpr int A_BYTES = DM * DK * 4;  // one 128 x 16 operand slice (8 KB)
+constexpr int B_BYTES = DN * DK * 4;  // one 256 x 16 operand slice (16 KB)
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int DTHREADS = 192;          // producer, MMA, four epilogue warps
+constexpr uint32_t TMEM_COLS = 2 * DN; // two FP32 accumulators of 128 lanes x 256 columns
 constexpr long long WAIT_BUDGET = 4000000000LL;  // clock cycles (~2 s) per wait
+static_assert(SWIZZLE_BYTES == 64 || SWIZZLE_BYTES == 128, "one swizzle span per slice");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -124,15 +144,20 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: no swizzle, K-major, start address,
-// leading-dimension byte offset (between core matrices along K) and stride
-// byte offset (between 8-row groups), version 1 (tcgen05).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor of a K-major operand slice whose rows are
+// one swizzle span wide (64 or 128 bytes, the pattern TMA writes): start
+// address, stride byte offset between 8-row groups (8 x span), version 1
+// (tcgen05), swizzle mode (4 = 64 B, 2 = 128 B). The leading byte offset is
+// unused when the K extent of one MMA (8 x 4 bytes) lies inside the span; a
+// K step inside the span advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t saddr) {
+  constexpr uint64_t mode = SWIZZLE_BYTES == 128 ? 2u : 4u;
   uint64_t d = 0;
   d |= uint64_t((saddr >> 4) & 0x3FFFu);
-  d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
-  d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
+  d |= uint64_t(1) << 16;
+  d |= uint64_t(((8 * SWIZZLE_BYTES) >> 4) & 0x3FFFu) << 32;
   d |= uint64_t(1) << 46;
+  d |= mode << 61;
   return d;
 }
 
@@ -142,12 +167,29 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(m >> 4) << 24);
 }
 
-// Byte offset of element (row, k) of a 128 x 32 tile in the core-matrix layout.
-__device__ __forceinline__ uint32_t core_off(int row, int k) {
-  return uint32_t(((row >> 3) * (DK / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
 }
 
-// hi = x rounded to nearest TF32 (10 explicit mantissa bits), lo = x - hi.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 2-D TMA load of the box at (x = k, y = row) into shared memory, completing
+// on bar by transaction bytes. Out-of-range elements are filled with zeros.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// hi = x rounded to nearest TF32 (10 explicit mantissa bits), lo = x - hi
+// (exact, so hi + lo == x).
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
   uint32_t b = __float_as_uint(x);
   uint32_t r = (b + 0x1000u) & 0xFFFFE000u;
@@ -156,156 +198,222 @@ __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
   lo = __fsub_rn(x, hi);
 }
 
-// One 128 x 128 tile (m0, n0) of C = A B; smem = 4 operand tiles.
-__device__ __forceinline__ void gemm_tile(int M, int N, int K, const float *__restrict__ A,
-                                          int lda, const float *__restrict__ B, int ldb,
-                                          float *__restrict__ C, int ldc, int m0, int n0,
-                                          unsigned char *smem, int *err) {
-  unsigned char *a_hi = smem;
-  unsigned char *a_lo = smem + TILE_BYTES;
-  unsigned char *b_hi = smem + 2 * TILE_BYTES;
-  unsigned char *b_lo = smem + 3 * TILE_BYTES;
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+// Waits for phase parity `ph` of `bar`. Gives up, raising *abort, when the
+// clock budget runs out, and returns false at once when another role has
+// raised *abort.
+__device__ __forceinline__ bool bounded_wait(uint64_t *bar, uint32_t ph, volatile int *abort) {
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, ph)) {
+    if (*abort) return false;
+    if (clock64() - t0 > WAIT_BUDGET) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
 
-  if (warp == 0) {
-    tmem_alloc(&tmem_base, TMEM_COLS);
+// Waits for phase parity `ph` of `bar` for at most `budget` clock cycles,
+// whatever the abort flag says (draining work already issued).
+__device__ __forceinline__ bool drain_wait(uint64_t *bar, uint32_t ph, long long budget) {
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, ph))
+    if (clock64() - t0 > budget) return false;
+  return true;
+}
+
+// Tile t of the launch -> job and tile origin (m0, n0); M blocks run fastest.
+__device__ __forceinline__ void tile_of(int t, const DenseJob *jobs, const int *tile_start,
+                                        int njobs, int &j, int &m0, int &n0) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {  // last job with tile_start[j] <= t
+    int mid = (lo + hi + 1) >> 1;
+    if (tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  j = lo;
+  const int local = t - tile_start[j];
+  const int tm = (jobs[j].M + DM - 1) / DM;
+  m0 = (local % tm) * DM;
+  n0 = (local / tm) * DN;
+}
+
+// maps[4 j + 0..3]: A_hi, A_lo, Bt_hi, Bt_lo of job j (boxes DK x DM and DK x DN).
+__global__ void __launch_bounds__(DTHREADS, 1)
+    k_gemm_nt(const DenseJob *jobs, const CUtensorMap *maps, const int *tile_start, int njobs,
+              int ntiles, int *err) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2], done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_abort, s_consumed;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // stages 1024-byte aligned (the swizzle pattern follows address bits)
+  const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  volatile int *abort = &s_abort;
+
+  if (tid == 0) {
+    for (int i = 0; i < NSTAGE; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 4);
+    }
+    mbar_init(&done, 1);
+    s_abort = 0;
+    s_consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_slot, TMEM_COLS);
     tmem_relinquish();
   }
-  if (tid == 0) {
-    mbar_init(&bar, 1);
-    s_fail = 0;
-  }
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = tmem_base;
-  const uint32_t idesc = idesc_tf32(DM, DN);
-  const uint32_t sa_hi = smem_u32(a_hi), sa_lo = smem_u32(a_lo);
-  const uint32_t sb_hi = smem_u32(b_hi), sb_lo = smem_u32(b_lo);
+  const uint32_t tmem = tmem_slot;
+  int issued = 0;  // producer: stages filled
 
-  const int nk = (K + DK - 1) / DK;
-  uint32_t phase = 0;
-  for (int kb = 0; kb < nk; ++kb) {
-    const int k0 = kb * DK;
-    // A slice: rows m0.., k0..k0+31 ; 128 rows x 8 float4
-    for (int i = tid; i < DM * (DK / 4); i += DTHREADS) {
-      int row = i / (DK / 4), kc = i % (DK / 4);
-      int gr = m0 + row, gk = k0 + kc * 4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gr < M && gk < K) v = *reinterpret_cast<const float4 *>(A + int64_t(gr) * lda + gk);
-      float4 h, l;
-      split_tf32(v.x, h.x, l.x);
-      split_tf32(v.y, h.y, l.y);
-      split_tf32(v.z, h.z, l.z);
-      split_tf32(v.w, h.w, l.w);
-      uint32_t off = core_off(row, kc * 4);
-      *reinterpret_cast<float4 *>(a_hi + off) = h;
-      *reinterpret_cast<float4 *>(a_lo + off) = l;
-    }
-    // B^T slice: tile row n = column n0+n of B, k = k0..k0+31 ; read B rows (k) as float4 along n
-    for (int i = tid; i < DK * (DN / 4); i += DTHREADS) {
-      int kk = i / (DN / 4), nc = i % (DN / 4);
-      int gk = k0 + kk, gn = n0 + nc * 4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gk < K && gn < N) v = *reinterpret_cast<const float4 *>(B + int64_t(gk) * ldb + gn);
-      float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        float h, l;
-        split_tf32(vv[e], h, l);
-        uint32_t off = core_off(nc * 4 + e, kk);
-        *reinterpret_cast<float *>(b_hi + off) = h;
-        *reinterpret_cast<float *>(b_lo + off) = l;
-      }
-    }
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-#pragma unroll
-      for (int s = 0; s < DK / 8; ++s) {
-        uint32_t koff = uint32_t(s) * 2u * 128u;  // K step of 8 = two core matrices
-        uint64_t ah = smem_desc(sa_hi + koff, 128, 1024), al = smem_desc(sa_lo + koff, 128, 1024);
-        uint64_t bh = smem_desc(sb_hi + koff, 128, 1024), bl = smem_desc(sb_lo + koff, 128, 1024);
-        uint32_t first = (kb == 0 && s == 0) ? 0u : 1u;
-        mma_tf32(tmem, ah, bh, idesc, first);
-        mma_tf32(tmem, ah, bl, idesc, 1u);
-        mma_tf32(tmem, al, bh, idesc, 1u);
-      }
-      mma_commit(&bar);
-    }
-    // wait for the MMAs of this slice before the buffers are overwritten
-    long long t0 = clock64();
-    bool done = false;
-    while (!done) {
-      done = mbar_try_wait(&bar, phase);
-      if (!done && clock64() - t0 > WAIT_BUDGET) {
-        s_fail = 1;
-        break;
-      }
-    }
-    phase ^= 1u;
-    __syncthreads();
-    if (s_fail) break;
-  }
-  tc_fence_after();
-  if (!s_fail && nk > 0) {
-    // epilogue: warp w holds rows 32w..32w+31 of the tile
-#pragma unroll 1
-    for (int c = 0; c < DN / 32; ++c) {
-      uint32_t v[32];
-      tmem_ld_32x32(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c * 32), v);
-      tmem_wait_ld();
-      int gr = m0 + warp * 32 + lane;
-      int gc = n0 + c * 32;
-      if (gr < M) {
-        float *dst = C + int64_t(gr) * ldc + gc;
-        if (gc + 32 <= N) {
-#pragma unroll
-          for (int j = 0; j < 32; j += 4)
-            *reinterpret_cast<float4 *>(dst + j) =
-                make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
-                            __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
-        } else {
-          for (int j = 0; j < 32 && gc + j < N; ++j) dst[j] = __uint_as_float(v[j]);
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+        int j, m0, n0;
+        tile_of(t, jobs, tile_start, njobs, j, m0, n0);
+        const CUtensorMap *mp = maps + 4 * j;
+        const int nk = (jobs[j].K + DK - 1) / DK;
+        for (int kb = 0; kb < nk; ++kb, ++issued) {
+          const int st = issued % NSTAGE;
+          if (!bounded_wait(&empty[st], ((issued / NSTAGE) & 1) ^ 1, abort)) break;
+          const uint32_t d = sbase + uint32_t(st * STAGE_BYTES);
+          mbar_expect_tx(&full[st], STAGE_BYTES);
+          tma_load_2d(d, mp + 0, kb * DK, m0, &full[st]);
+          tma_load_2d(d + A_BYTES, mp + 1, kb * DK, m0, &full[st]);
+          tma_load_2d(d + 2 * A_BYTES, mp + 2, kb * DK, n0, &full[st]);
+          tma_load_2d(d + 2 * A_BYTES + B_BYTES, mp + 3, kb * DK, n0, &full[st]);
         }
       }
     }
-  } else if (nk == 0) {
-    for (int i = tid; i < DM * DN; i += DTHREADS) {
-      int r = m0 + i / DN, c = n0 + i % DN;
-      if (r < M && c < N) C[int64_t(r) * ldc + c] = 0.0f;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(DM, DN);
+      int it = 0, tc = 0;
+      bool any = false;
+      for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++tc) {
+        int j, m0, n0;
+        tile_of(t, jobs, tile_start, njobs, j, m0, n0);
+        const int nkj = (jobs[j].K + DK - 1) / DK;
+        const int a = tc & 1;
+        if (!bounded_wait(&tempty[a], ((tc >> 1) & 1) ^ 1, abort)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + uint32_t(a * DN);
+        bool ok = true;
+        for (int kb = 0; kb < nkj; ++kb, ++it) {
+          const int st = it % NSTAGE;
+          if (!bounded_wait(&full[st], (it / NSTAGE) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = sbase + uint32_t(st * STAGE_BYTES);
+#pragma unroll
+          for (int s = 0; s < DK / 8; ++s) {
+            const uint32_t ko = uint32_t(s) * 32u;
+            const uint64_t ah = smem_desc_sw(d + ko), al = smem_desc_sw(d + A_BYTES + ko);
+            const uint64_t bh = smem_desc_sw(d + 2 * A_BYTES + ko);
+            const uint64_t bl = smem_desc_sw(d + 2 * A_BYTES + B_BYTES + ko);
+            mma_tf32(acc, ah, bh, idesc, (kb | s) != 0 ? 1u : 0u);
+            mma_tf32(acc, ah, bl, idesc, 1u);
+            mma_tf32(acc, al, bh, idesc, 1u);
+          }
+          any = true;
+          mma_commit(&empty[st]);  // the stage is free once these MMAs have read it
+        }
+        if (!ok) break;
+        mma_commit(&tfull[a]);
+      }
+      s_consumed = it;
+      if (any) {  // nothing may still write tensor memory when it is freed
+        mma_commit(&done);
+        if (!drain_wait(&done, 0, WAIT_BUDGET)) *abort = 1;
+      }
+    }
+  } else {
+    const int q = warp & 3;  // this warp's 32 TMEM lanes
+    int tc = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
+      int j, m0, n0;
+      tile_of(t, jobs, tile_start, njobs, j, m0, n0);
+      const DenseJob J = jobs[j];
+      const int a = tc & 1;
+      if (!bounded_wait(&tfull[a], (tc >> 1) & 1, abort)) break;
+      tc_fence_after();
+      const int gr = m0 + q * 32 + lane;
+      float *dh = J.C + int64_t(gr) * J.ldc;
+      float *dl = J.C_lo ? J.C_lo + int64_t(gr) * J.ldc : nullptr;
+#pragma unroll 1
+      for (int c = 0; c < DN / 32; ++c) {
+        uint32_t v[32];
+        __syncwarp();
+        tmem_ld_32x32(tmem + (uint32_t(q * 32) << 16) + uint32_t(a * DN + c * 32), v);
+        tmem_wait_ld();
+        const int gc = n0 + c * 32;
+        // N is a multiple of 4 and the rows 16-byte aligned: whole float4 groups
+#pragma unroll
+        for (int k = 0; k < 32; k += 4) {
+          if (gr >= J.M || gc + k >= J.N) break;
+          float4 h = make_float4(__uint_as_float(v[k]), __uint_as_float(v[k + 1]),
+                                 __uint_as_float(v[k + 2]), __uint_as_float(v[k + 3]));
+          if (dl) {
+            float4 l;
+            split_tf32(h.x, h.x, l.x);
+            split_tf32(h.y, h.y, l.y);
+            split_tf32(h.z, h.z, l.z);
+            split_tf32(h.w, h.w, l.w);
+            *reinterpret_cast<float4 *>(dl + gc + k) = l;
+          }
+          *reinterpret_cast<float4 *>(dh + gc + k) = h;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[a]);
     }
   }
-  if (s_fail && tid == 0) atomicOr(err, 1);
+
+  __syncthreads();
+  if (warp == 0 && lane == 0) {
+    // TMA copies still landing in shared memory (only after an abort)
+    for (int i = s_consumed; i < issued; ++i)
+      if (!drain_wait(&full[i % NSTAGE], (i / NSTAGE) & 1, WAIT_BUDGET)) {
+        *abort = 1;
+        break;
+      }
+  }
+  if (tid == 0 && *abort) atomicOr(err, 1);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
 
-__global__ void __launch_bounds__(DTHREADS)
-    k_gemm_tf32x3(int M, int N, int K, const float *__restrict__ A, int lda,
-                  const float *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
-                  int *err) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  gemm_tile(M, N, K, A, lda, B, ldb, C, ldc, blockIdx.y * DM, blockIdx.x * DN, smem, err);
+// Split into hi/lo, optionally transposing: out[i][j] = in[i][j] (or in[j][i]),
+// rows x cols of out, padded columns up to ldo zeroed.
+__global__ void k_split(int rows, int cols, const float *in, int ldi, int transpose, float *hi,
+                        float *lo, int ldo) {
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < int64_t(rows) * ldo;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    int i = int(t / ldo), j = int(t % ldo);
+    float x = 0.0f;
+    if (j < cols) x = transpose ? in[int64_t(j) * ldi + i] : in[int64_t(i) * ldi + j];
+    float h, l;
+    split_tf32(x, h, l);
+    hi[t] = h;
+    lo[t] = l;
+  }
 }
 
-// Several independent products in one launch: blockIdx.z is the job.
-__global__ void __launch_bounds__(DTHREADS) k_gemm_tf32x3_jobs(const DenseJob *jobs, int *err) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  const DenseJob J = jobs[blockIdx.z];
-  const int m0 = blockIdx.y * DM, n0 = blockIdx.x * DN;
-  if (m0 >= J.M || n0 >= J.N) return;  // before any tensor-memory allocation
-  gemm_tile(J.M, J.N, J.K, J.A, J.lda, J.B, J.ldb, J.C, J.ldc, m0, n0, smem, err);
-}
-
-// Densify: rows of the dense matrices of a stage CSR into their zeroed
-// row-major blocks (global columns minus the matrix's first row).
+// Densify: the rows of the dense-path matrices of a stage CSR into their
+// zeroed blocks, split: X (row-major) and X^T.
 __global__ void k_densify(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
                           const int64_t *rp, const int32_t *col, const float *val,
                           const DenseBuf *bufs) {
@@ -317,15 +425,23 @@ __global__ void k_densify(int64_t n, const int32_t *seg, const int *dslot, const
     int d = dslot[m];
     if (d < 0) continue;
     const DenseBuf Bf = bufs[d];
-    int64_t r0 = moff[m];
-    float *row = Bf.X + (r - r0) * Bf.ld;
-    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) row[col[p] - r0] = val[p];
+    int64_t r0 = moff[m], i = r - r0;
+    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) {
+      int64_t j = col[p] - r0;
+      float h, l;
+      split_tf32(val[p], h, l);
+      Bf.X_hi[i * Bf.ld + j] = h;
+      Bf.X_lo[i * Bf.ld + j] = l;
+      Bf.XT_hi[j * Bf.ld + i] = h;
+      Bf.XT_lo[j * Bf.ld + i] = l;
+    }
   }
 }
 
-// Residual partials of the dense matrices from T = X X: part[2r] =
+// Residual partials of the dense matrices from T^T (hi + lo): part[2r] =
 // sum_j (t_rj - delta_rj)^2 and part[2r+1] = sum_j x_rj^2, as exact float
-// pairs; tcount[d] counts the nonzero entries of T.
+// pairs (the Frobenius norm of T^T - I is that of T - I, and the diagonal is
+// shared); tcount[d] counts the nonzero entries of T.
 __global__ void k_dense_resid(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
                               const DenseBuf *bufs, double *part, unsigned long long *tcount) {
   int lane = threadIdx.x & 31;
@@ -337,13 +453,12 @@ __global__ void k_dense_resid(int64_t n, const int32_t *seg, const int *dslot, c
     if (d < 0) continue;
     const DenseBuf Bf = bufs[d];
     int64_t i = r - moff[m];
-    const float *trow = Bf.T + i * Bf.ld;
-    const float *xrow = Bf.X + i * Bf.ld;
     float rh = 0.f, rl = 0.f, xh = 0.f, xl = 0.f;
     double rdiag = 0.0;
     unsigned cnt = 0;
     for (int j = lane; j < Bf.n; j += 32) {
-      float t = trow[j], x = xrow[j];
+      float t = __fadd_rn(Bf.TT_hi[i * Bf.ld + j], Bf.TT_lo[i * Bf.ld + j]);
+      float x = __fadd_rn(Bf.X_hi[i * Bf.ld + j], Bf.X_lo[i * Bf.ld + j]);
       cnt += t != 0.0f;
       if (j == i) {
         double dd = double(t) - 1.0;
@@ -388,16 +503,15 @@ __global__ void k_dense_emit(int64_t n, const int32_t *seg, const int *dslot, co
     int d = dslot[m];
     if (d < 0 || !active[m]) continue;
     const DenseBuf Bf = bufs[d];
-    int64_t r0 = moff[m];
-    int64_t i = r - r0;
-    const float *xrow = Bf.X + i * Bf.ld;
-    const float *prow = Bf.P + i * Bf.ld;
+    int64_t r0 = moff[m], i = r - r0;
     int64_t out = cs[r];
     for (int j0 = 0; j0 < Bf.n; j0 += 32) {
       int j = j0 + lane;
       float v = 0.0f;
-      if (j < Bf.n)
-        v = __fsub_rn(__fmul_rn(1.5f, xrow[j]), __fmul_rn(0.5f, prow[j]));
+      if (j < Bf.n) {
+        float x = __fadd_rn(Bf.X_hi[i * Bf.ld + j], Bf.X_lo[i * Bf.ld + j]);
+        v = __fsub_rn(__fmul_rn(1.5f, x), __fmul_rn(0.5f, Bf.P[i * Bf.ld + j]));
+      }
       bool keep = v != 0.0f;
       unsigned mk = __ballot_sync(0xffffffffu, keep);
       if (keep) {
@@ -411,26 +525,108 @@ __global__ void k_dense_emit(int64_t n, const int32_t *seg, const int *dslot, co
   }
 }
 
-}  // namespace
-
-size_t dense_gemm_smem() { return size_t(4) * TILE_BYTES; }
-
 int dense_grid(int64_t n) {
   int64_t g = (n + 7) / 8;
   return int(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
 }
 
-void launch_dense_jobs(int njobs, const DenseJob *jobs, int max_m, int max_n, int *err,
-                       cudaStream_t s) {
+}  // namespace
+
+size_t dense_gemm_smem() { return size_t(NSTAGE) * STAGE_BYTES + 1024; }
+
+// Tensor maps (4 per job) followed by the tile offsets, in CUtensorMap units.
+static size_t scratch_maps(int njobs) {
+  return size_t(njobs) * 4 + (size_t(njobs + 1) * sizeof(int) + sizeof(CUtensorMap) - 1) /
+                                 sizeof(CUtensorMap);
+}
+
+size_t dense_jobs_scratch_bytes(int njobs) { return scratch_maps(njobs) * sizeof(CUtensorMap); }
+
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    SGN_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                              cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p)
+      throw Error(SIGN_ECUDA, "cuTensorMapEncodeTiled is not available");
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// Row-major rows x K FP32 array with leading dimension ld, read in boxes of
+// DK x box_rows with the swizzle of one span.
+CUtensorMap operand_map(const float *base, int rows, int K, int ld, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(rows)};
+  cuuint64_t strides[1] = {cuuint64_t(ld) * sizeof(float)};
+  cuuint32_t box[2] = {cuuint32_t(DK), cuuint32_t(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_tiled()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base),
+                              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              SWIZZLE_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                                   : CU_TENSOR_MAP_SWIZZLE_64B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(SIGN_ECUDA, "cuTensorMapEncodeTiled failed");
+  return m;
+}
+}  // namespace
+
+void launch_dense_jobs(int njobs, const DenseJob *jobs_host, DenseJob *jobs_dev, void *scratch,
+                       int *err, cudaStream_t s) {
   if (njobs <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    SGN_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3_jobs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    SGN_CUDA(cudaGetDevice(&dev));
+    SGN_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    SGN_CUDA(cudaFuncSetAttribute(k_gemm_nt, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   int(dense_gemm_smem())));
-    attr = true;
   }
-  dim3 grid((max_n + DN - 1) / DN, (max_m + DM - 1) / DM, njobs);
-  k_gemm_tf32x3_jobs<<<grid, DTHREADS, dense_gemm_smem(), s>>>(jobs, err);
+  thread_local std::vector<CUtensorMap> host;  // 64-byte aligned elements
+  host.resize(scratch_maps(njobs));
+  CUtensorMap *maps = host.data();
+  int *tile_start = reinterpret_cast<int *>(host.data() + size_t(njobs) * 4);
+  int ntiles = 0;
+  for (int j = 0; j < njobs; ++j) {
+    const DenseJob &J = jobs_host[j];
+    if (J.M <= 0 || J.N <= 0 || J.K <= 0 || J.lda % 4 || J.ldb % 4 || J.ldc % 4 || J.N % 4)
+      throw Error(SIGN_EINVAL, "dense job with bad shape");
+    maps[4 * j + 0] = operand_map(J.A_hi, J.M, J.K, J.lda, DM);
+    maps[4 * j + 1] = operand_map(J.A_lo, J.M, J.K, J.lda, DM);
+    maps[4 * j + 2] = operand_map(J.B_hi, J.N, J.K, J.ldb, DN);
+    maps[4 * j + 3] = operand_map(J.B_lo, J.N, J.K, J.ldb, DN);
+    tile_start[j] = ntiles;
+    ntiles += ((J.M + DM - 1) / DM) * ((J.N + DN - 1) / DN);
+  }
+  tile_start[njobs] = ntiles;
+  // pageable source: the copy has taken the bytes when it returns
+  SGN_CUDA(cudaMemcpyAsync(scratch, host.data(), host.size() * sizeof(CUtensorMap),
+                           cudaMemcpyHostToDevice, s));
+  SGN_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host, sizeof(DenseJob) * size_t(njobs),
+                           cudaMemcpyHostToDevice, s));
+  const unsigned char *sc = static_cast<const unsigned char *>(scratch);
+  k_gemm_nt<<<std::min(ntiles, nsm), DTHREADS, dense_gemm_smem(), s>>>(
+      jobs_dev, reinterpret_cast<const CUtensorMap *>(sc),
+      reinterpret_cast<const int *>(sc + size_t(njobs) * 4 * sizeof(CUtensorMap)), njobs, ntiles,
+      err);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_split(int rows, int cols, const float *in, int ldi, int transpose, float *hi,
+                  float *lo, int ldo, cudaStream_t s) {
+  int64_t total = int64_t(rows) * ldo;
+  if (total == 0) return;
+  int g = int(std::min<int64_t>((total + 255) / 256, 152 * 32));
+  k_split<<<g, 256, 0, s>>>(rows, cols, in, ldi, transpose, hi, lo, ldo);
   SGN_LAUNCH_CHECK();
 }
 
@@ -459,27 +655,9 @@ void launch_dense_emit(int64_t n, const int32_t *seg, const int *dslot, const in
   SGN_LAUNCH_CHECK();
 }
 
-void launch_dense_gemm_tf32x3(int M, int N, int K, const float *A, int lda, const float *B,
-                              int ldb, float *C, int ldc, int *err, cudaStream_t s) {
-  if (M <= 0 || N <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    SGN_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  int(dense_gemm_smem())));
-    attr = true;
-  }
-  dim3 grid((N + DN - 1) / DN, (M + DM - 1) / DM);
-  k_gemm_tf32x3<<<grid, DTHREADS, dense_gemm_smem(), s>>>(M, N, K, A, lda, B, ldb, C, ldc, err);
-  SGN_LAUNCH_CHECK();
-}
-
 }  // namespace sgn
 
 // ---------------------------------------------------------------------------
-#include <string>
-
-#include "../../include/sign.h"
-
 namespace sgn {
 void set_last_error(const std::string &msg);
 }
@@ -497,12 +675,32 @@ extern "C" sign_status sign_dense_product(int M, int N, int K, const float *A, i
     return set_last_error("K, N and the leading dimensions must be multiples of 4 and the "
                           "arrays 16-byte aligned"),
            SIGN_EINVAL;
+  if (M == 0 || N == 0) return SIGN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   try {
-    DevBuf err;
+    if (K == 0) {
+      SGN_CUDA(cudaMemset2DAsync(C, sizeof(float) * size_t(ldc), 0, sizeof(float) * size_t(N),
+                                 size_t(M), s));
+      SGN_CUDA(cudaStreamSynchronize(s));
+      return SIGN_OK;
+    }
+    // split A (M x K) and B^T (N x K) into TF32 hi/lo parts, K padded to 4
+    const int kp = (K + 3) / 4 * 4;
+    DevBuf ws, err, job, scratch;
+    size_t na = size_t(M) * kp, nbt = size_t(N) * kp;
+    float *w = static_cast<float *>(ws.ensure(sizeof(float) * 2 * (na + nbt) + 64, s));
+    float *a_hi = w, *a_lo = w + na, *b_hi = w + 2 * na, *b_lo = w + 2 * na + nbt;
+    launch_split(M, K, A, lda, 0, a_hi, a_lo, kp, s);
+    launch_split(N, K, B, ldb, 1, b_hi, b_lo, kp, s);
+    DenseJob J{M, N, K, a_hi, a_lo, kp, b_hi, b_lo, kp, C, nullptr, ldc};
+    job.ensure(sizeof(DenseJob), s);
+    scratch.ensure(dense_jobs_scratch_bytes(1), s);
     err.ensure(sizeof(int), s);
     SGN_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    launch_dense_gemm_tf32x3(M, N, K, A, lda, B, ldb, C, ldc, err.as<int>(), s);
+    {
+      ProfScope ps(KC_DENSE, s, 3.0 * 2.0 * double(M) * double(N) * double(K), 0.0);
+      launch_dense_jobs(1, &J, job.as<DenseJob>(), scratch.p, err.as<int>(), s);
+    }
     int herr = 0;
     SGN_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     SGN_CUDA(cudaStreamSynchronize(s));
@@ -513,4 +711,3 @@ extern "C" sign_status sign_dense_product(int M, int N, int K, const float *A, i
   }
   return SIGN_OK;
 }
-

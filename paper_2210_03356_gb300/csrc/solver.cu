@@ -154,7 +154,7 @@ Rows compact_rows(const Csr<T> &c) {
 struct Work {
   DevBuf lo, len, ub, wlist, clist, counters, part, scan_tmp, eoff, sums, ms, active, sel,
       asm_blocks, asm_off, asm_lens, dropped, norm_work, norm, work, mults, cnt, nnzc, xblocks,
-      dslot, dmem, dbufs, djobs, dcount, derr;
+      dslot, dmem, dbufs, djobs, dscratch, dcount, derr;
 };
 
 // The matrices of one round on the dense path (FP32 stage): their slots,
@@ -356,19 +356,27 @@ struct Solver {
       int ld = int((n + 3) / 4 * 4);
       dp.slot[i] = dp.nd++;
       dp.mat.push_back(i);
-      dp.bufs.push_back(DenseBuf{nullptr, nullptr, nullptr, int(n), ld});
+      DenseBuf b = {};
+      b.n = int(n);
+      b.ld = ld;
+      dp.bufs.push_back(b);
       dp.max_ld = std::max(dp.max_ld, ld);
-      total += 3 * size_t(ld) * size_t(ld);
+      total += 7 * size_t(ld) * size_t(ld);
     }
     if (!dp.nd) return dp;
     float *mem = static_cast<float *>(w.dmem.ensure(sizeof(float) * total, s));
     size_t off = 0;
     for (DenseBuf &b : dp.bufs) {
       size_t blk = size_t(b.ld) * size_t(b.ld);
-      b.X = mem + off;
-      b.T = mem + off + blk;
-      b.P = mem + off + 2 * blk;
-      off += 3 * blk;
+      float *base = mem + off;
+      b.X_hi = base;
+      b.X_lo = base + blk;
+      b.XT_hi = base + 2 * blk;
+      b.XT_lo = base + 3 * blk;
+      b.TT_hi = base + 4 * blk;
+      b.TT_lo = base + 5 * blk;
+      b.P = base + 6 * blk;
+      off += 7 * blk;
     }
     w.dslot.ensure(sizeof(int) * size_t(nb), s);
     h2d(w.dslot.p, dp.slot.data(), size_t(nb), s);
@@ -390,18 +398,20 @@ struct Solver {
       std::vector<DenseJob> jobs;
       double fl = 0.0;
       for (const DenseBuf &b : dp.bufs) {
-        if (mode == MODE_SQUARE)
-          jobs.push_back(DenseJob{b.ld, b.ld, b.ld, b.X, b.ld, b.X, b.ld, b.T, b.ld});
-        else
-          jobs.push_back(DenseJob{b.ld, b.ld, b.ld, b.X, b.ld, b.T, b.ld, b.P, b.ld});
+        if (mode == MODE_SQUARE)  // T^T = X^T X^T: C = A Bt^T with A = X^T, Bt = X
+          jobs.push_back(DenseJob{b.ld, b.ld, b.ld, b.XT_hi, b.XT_lo, b.ld, b.X_hi, b.X_lo, b.ld,
+                                  b.TT_hi, b.TT_lo, b.ld});
+        else  // P = X T as C = A Bt^T with A = X, Bt = T^T
+          jobs.push_back(DenseJob{b.ld, b.ld, b.ld, b.X_hi, b.X_lo, b.ld, b.TT_hi, b.TT_lo, b.ld,
+                                  b.P, nullptr, b.ld});
         fl += 3.0 * 2.0 * double(b.ld) * double(b.ld) * double(b.ld);
       }
       w.djobs.ensure(sizeof(DenseJob) * jobs.size(), s);
-      h2d(w.djobs.p, jobs.data(), jobs.size(), s);
+      w.dscratch.ensure(dense_jobs_scratch_bytes(int(jobs.size())), s);
       const DenseBuf *bufs = w.dbufs.as<DenseBuf>();
       if (mode == MODE_SQUARE) {
         size_t total = 0;
-        for (const DenseBuf &b : dp.bufs) total += 3 * size_t(b.ld) * size_t(b.ld);
+        for (const DenseBuf &b : dp.bufs) total += 7 * size_t(b.ld) * size_t(b.ld);
         SGN_CUDA(cudaMemsetAsync(w.dmem.p, 0, sizeof(float) * total, s));
         launch_densify(N, st.d_seg.template as<int32_t>(), w.dslot.as<int>(),
                        st.d_moff.template as<int64_t>(), st.X.d_rp(), st.X.d_col(),
@@ -409,7 +419,7 @@ struct Solver {
       }
       {
         ProfScope ps(KC_DENSE, s, fl, 0.0);
-        launch_dense_jobs(int(jobs.size()), w.djobs.as<DenseJob>(), dp.max_ld, dp.max_ld,
+        launch_dense_jobs(int(jobs.size()), jobs.data(), w.djobs.as<DenseJob>(), w.dscratch.p,
                           w.derr.as<int>(), s);
       }
       if (mode == MODE_SQUARE) {

@@ -19,7 +19,8 @@ def sg():
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 32), (128, 128, 128), (256, 384, 160),
-                                   (200, 300, 100), (1000, 516, 260), (64, 4, 12)])
+                                   (200, 300, 100), (1000, 516, 260), (64, 4, 12),
+                                   (4096, 2048, 64), (3000, 1284, 36)])
 def test_dense_product_matches_fp64(sg, M, N, K):
     import torch
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N * 3 + K)
