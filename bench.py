@@ -9,6 +9,10 @@ FP64, all 512 in one sign_solve_batch call. Every step runs the whole path:
 1-norm scale, the two sparse products per iteration, residuals, budgets,
 thresholds, filtering and compaction, stage switches and stopping tests.
 
+The serving leg (rank 0) streams Poisson arrivals at 50, 200 and 800 requests/s
+through the continuous-batching server and reports p50/p99 latency and
+throughput per rate.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank solves its own batch of 512 (weak scaling, no
 collective on the data path); the time is the maximum over ranks.
@@ -125,6 +129,88 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------------- serving
+SERVE_MIX = ("Poisson arrivals; each request drawn from the generators: 45% banded (n log-uniform "
+             "[1000,8000], half-bandwidth U{1..10}), 35% tridiagonal (n log-uniform [1000,262144]), "
+             "14% shifted 2-D Laplacian (m U{32..48}, n 1024-2304), 5% shifted 3-D Laplacian "
+             "(m U{10..16}, n 1000-4096), 1% shifted 3-D Laplacian m=64 (n=262,144, refused by "
+             "the footprint budget); mixed FP32->FP64, EXACT, tol 1e-8")
+
+
+def serve_pool(seed: int = w.BASE_SEED + 4000, size: int = 160):
+    """Distinct request matrices and their draw weights (host CSR)."""
+    rng = np.random.default_rng(seed)
+    pool, weights = [], []
+    for i in range(size):
+        u = rng.random()
+        if u < 0.45:
+            n = int(round(math.exp(rng.uniform(math.log(1000), math.log(8000)))))
+            pool.append(w.banded(n, int(rng.integers(1, 11)), seed + i))
+        elif u < 0.80:
+            n = int(round(math.exp(rng.uniform(math.log(1000), math.log(262144)))))
+            pool.append(w.tridiagonal(n, seed + i))
+        elif u < 0.94:
+            pool.append(w.laplacian(int(rng.integers(32, 49)), 2))
+        else:
+            pool.append(w.laplacian(int(rng.integers(10, 17)), 3))
+        weights.append(1.0)
+    pool.append(w.laplacian(64, 3))
+    weights = np.array(weights + [len(weights) / 99.0])
+    return pool, weights / weights.sum()
+
+
+def serve_leg(sg, rates, seconds: float, seed: int = 7):
+    """Open-loop Poisson stream per rate through a fresh server; latency is
+    completion minus scheduled arrival (both CLOCK_MONOTONIC)."""
+    pool, p = serve_pool()
+    rng = np.random.default_rng(seed)
+    opts = sg.default_opts(tol=TOL, filter="exact", prec="mixed")
+    with sg.Server(opts) as srv:  # warm-up: allocations, first launches
+        ts = [srv.submit(pool[i]) for i in range(0, 40, 2)]
+        for t in ts:
+            srv.poll(t, wait_ms=120000)
+    out = []
+    for rate in rates:
+        k = max(1, int(rng.poisson(rate * seconds)))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, k))
+        picks = rng.choice(len(pool), size=k, p=p)
+        tickets, refused, t_arr = [], 0, []
+        with sg.Server(opts) as srv:
+            t0 = time.monotonic() + 0.05
+            for at, i in zip(arrivals, picks):
+                wait = t0 + at - time.monotonic()
+                if wait > 0:
+                    time.sleep(wait)
+                try:
+                    tickets.append(srv.submit(pool[i]))
+                    t_arr.append(t0 + at)
+                except sg.SignError as e:
+                    if e.status != sg.SIGN_ENOMEM:
+                        raise
+                    refused += 1
+            lat, done, bad = [], [], 0
+            for t, ta in zip(tickets, t_arr):
+                r = None
+                while r is None:
+                    r = srv.poll(t, wait_ms=10000)
+                bad += r["status"] != sg.SIGN_OK
+                lat.append(r["t_done"] - ta)
+                done.append(r["t_done"])
+            st = srv.stats()
+        lat_ms = np.array(lat) * 1e3
+        span = (max(done) - t0) if done else float("nan")
+        out.append({"rate_req_per_s": rate, "requests": k, "refused": refused,
+                    "completed": len(tickets), "not_converged": int(bad),
+                    "p50_ms": float(np.percentile(lat_ms, 50)) if lat else None,
+                    "p99_ms": float(np.percentile(lat_ms, 99)) if lat else None,
+                    "mean_ms": float(lat_ms.mean()) if lat else None,
+                    "solves_per_s": len(tickets) / span if done else 0.0,
+                    "max_active_seen": st["max_active_seen"], "rounds": st["rounds"]})
+    return {"mix": SERVE_MIX, "seconds_per_rate": seconds, "mem_budget_bytes": 120e9,
+            "latency": "completion minus scheduled arrival, both on CLOCK_MONOTONIC",
+            "rates": out}
+
+
 # ---------------------------------------------------------------------- clocks
 class Clocks:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -184,6 +270,9 @@ def main():
     ap.add_argument("--unfiltered-sample", type=int, default=8)
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="matrices per batch (smaller only for profiler captures)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0,
+                    help="length of the Poisson stream at each serving rate (0: skip)")
+    ap.add_argument("--serve-rates", default="50,200,800")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -356,6 +445,9 @@ def main():
         if cpu:
             line["cpu_baseline"] = cpu
     batch.close()
+    if args.legs == "all" and args.serve_seconds > 0 and rank == 0:
+        rates = [float(x) for x in args.serve_rates.split(",") if x]
+        line["serving"] = serve_leg(sg, rates, args.serve_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -54,7 +54,8 @@ typedef enum {
                          convergence needs ||I - X_1^2|| < 1)                 */
   SIGN_ECUDA = 5,     /* a CUDA runtime call failed                          */
   SIGN_ETIMEOUT = 6,  /* reserved: a bounded device wait gave up             */
-  SIGN_ESTATE = 7     /* call out of order (e.g. sign_get_csr before solve)  */
+  SIGN_ESTATE = 7,    /* call out of order (e.g. sign_get_csr before solve)  */
+  SIGN_EAGAIN = 8     /* server: the request has not finished yet            */
 } sign_status;
 
 typedef enum {
@@ -188,6 +189,94 @@ sign_status sign_threshold_exact_noalloc(const double *val, int64_t nnz, double 
  * Returns after cuda_stream has finished. */
 sign_status sign_dense_product(int M, int N, int K, const float *A, int lda, const float *B,
                                int ldb, float *C, int ldc, void *cuda_stream);
+
+/* ---- serving (not part of the paper's method) ---------------------------
+ *
+ * A server owns a worker thread and two CUDA streams of its own, on the
+ * device current at creation. Requests are submitted from any thread;
+ * the worker runs the solver's rounds continuously and admits waiting
+ * requests at each round boundary, first come first served, while the sum of
+ * the admitted requests' predicted footprints stays within mem_budget and
+ * fewer than max_active are on the GPU. An admitted request joins the next
+ * round of the entry stage beside the requests already in flight; each
+ * request's arithmetic is that of a lone sign_solve with the server's
+ * options, so its result is the same alone or in any mix. A request whose
+ * predicted footprint alone exceeds mem_budget is refused at submission.
+ *
+ * Predicted footprint (bytes) of a request, from its n, nnz, Gershgorin
+ * gap delta = min_i (|a_ii| - sum_{j!=i} |a_ij|), row-sum bound
+ * rho = max_i sum_j |a_ij| and half-bandwidth bw = max |i - j|:
+ *   w = n                                          if delta <= 0,
+ *   w = min(n, max(32, ceil(1.5 (rho/delta) (2 bw + 1))))  otherwise,
+ *   bytes = 96 n w + 24 nnz.
+ * w predicts the filtered iterate's entries per row: the sign of a matrix
+ * whose spectrum avoids (-delta, delta) decays away from the band at a rate
+ * set by rho/delta; without a Gershgorin gap no decay is assumed (dense).
+ * 96 bytes per predicted entry covers the iterate, its square, the update
+ * slots and the filtered copy in FP64 (12 bytes per entry each, with the
+ * products' upper-bound slots counted twice); 24 bytes per input entry the
+ * input and its scaled copy. */
+typedef struct sign_server_s *sign_server_t;
+
+typedef struct {
+  sign_opts solve;   /* options of every request                        */
+  double mem_budget; /* bytes of predicted footprints in flight (120e9)  */
+  int max_active;    /* requests on the GPU at once (1024)               */
+  int max_queue;     /* requests waiting for admission (65536)           */
+} sign_server_opts;
+
+typedef struct {
+  double t_submit, t_admit, t_done; /* seconds on the server's steady clock */
+  double footprint;                 /* predicted bytes, reserved while on the GPU */
+} sign_request_times;
+
+typedef struct {
+  /* requests, cumulative: submitted counts valid inputs (sign_create's
+   * checks passed), refused those of them turned away at submission */
+  int64_t submitted, refused, admitted, completed;
+  int64_t queued, active;                          /* requests, now          */
+  int64_t max_active_seen;  /* most requests on the GPU at once so far       */
+  int64_t rounds;           /* solver rounds run                             */
+  double reserved;          /* bytes of predicted footprint now in flight    */
+} sign_server_stats;
+
+/* The footprint model above (host arithmetic only). */
+double sign_footprint_bytes(int64_t n, int64_t nnz, double delta, double rho, int64_t bw);
+
+/* Defaults: sign_default_opts with SIGN_PREC_MIXED, mem_budget 120e9,
+ * max_active 1024, max_queue 65536. */
+void sign_server_default_opts(sign_server_opts *o);
+
+/* Starts a server. SIGN_EINVAL for bad options. */
+sign_status sign_server_create(const sign_server_opts *o, sign_server_t *out);
+
+/* Copies a CSR matrix (the arguments of sign_create) and queues it. Returns
+ * after the copy: the caller may reuse its arrays at once. *ticket names the
+ * request. SIGN_EINVAL for malformed input, SIGN_ENOMEM when the predicted
+ * footprint exceeds mem_budget or max_queue requests are waiting (the
+ * request is then refused and has no ticket). */
+sign_status sign_server_submit(sign_server_t srv, int64_t n, int64_t nnz, const int64_t *rowptr,
+                               const int32_t *col, const double *val, int on_device,
+                               uint64_t *ticket);
+
+/* SIGN_EAGAIN while the request is queued or running (after waiting up to
+ * wait_ms milliseconds for it); SIGN_OK once it has finished, with its
+ * outcome in info->status (iters, resid, nnz_final filled; no per-iteration
+ * arrays) and its times in *times (either may be NULL). SIGN_EINVAL for an
+ * unknown or already taken ticket. */
+sign_status sign_server_poll(sign_server_t srv, uint64_t ticket, int wait_ms, sign_info *info,
+                             sign_request_times *times);
+
+/* Hands a finished request's result over as a handle (read it with
+ * sign_get_csr, free it with sign_destroy); later work on the handle goes to
+ * cuda_stream. The ticket is then forgotten. SIGN_EAGAIN if not finished. */
+sign_status sign_server_take(sign_server_t srv, uint64_t ticket, void *cuda_stream, sign_t *out);
+
+sign_status sign_server_get_stats(sign_server_t srv, sign_server_stats *out);
+
+/* Stops admitting, lets the requests on the GPU finish, and frees the server
+ * with every request not yet taken. */
+void sign_server_destroy(sign_server_t srv);
 
 /* ---- observability (not part of the paper's method) -------------------- */
 

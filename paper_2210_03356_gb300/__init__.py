@@ -20,10 +20,10 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import _native as N
-from ._native import (SIGN_EDIVERGED, SIGN_EINVAL, SIGN_ENOTCONV, SIGN_OK, SignError,
-                      default_opts, last_error, load, prof_read)
+from ._native import (SIGN_EAGAIN, SIGN_EDIVERGED, SIGN_EINVAL, SIGN_ENOMEM, SIGN_ENOTCONV,
+                      SIGN_OK, SignError, default_opts, last_error, load, prof_read)
 
-__all__ = ["solve", "solve_batch", "Handle", "Result", "default_opts", "load", "last_error",
+__all__ = ["solve", "solve_batch", "Handle", "Result", "Server", "default_opts", "load", "last_error",
            "prof_read", "kernel_launches", "prof_enable", "prof_reset",
            "SignError", "SIGN_OK", "SIGN_EINVAL", "SIGN_ENOTCONV", "SIGN_EDIVERGED"]
 
@@ -269,3 +269,107 @@ class Batch:
     def close(self):
         for h in self.handles:
             h.close()
+
+
+class Server:
+    """A continuous-batching request loop on the GPU (sign_server_*).
+
+    submit() copies a matrix in and returns a ticket; the library's worker
+    thread admits it at a round boundary when its predicted footprint fits
+    the budget, solves it beside the requests already in flight, and poll()
+    reports it finished; take() reads its result.
+    """
+
+    def __init__(self, opts=None, mem_budget: float = 120e9, max_active: int = 1024,
+                 max_queue: int = 65536, **kw):
+        L = load()
+        so = N.sign_server_opts()
+        L.sign_server_default_opts(C.byref(so))
+        if opts is not None:
+            so.solve = opts
+        if kw:
+            so.solve = _opts(so.solve, {k: ({"none": 0, "exact": 1, "bound": 2}[v]
+                                             if k == "filter" and isinstance(v, str) else
+                                             {"fp64": 0, "mixed": 1}[v]
+                                             if k == "prec" and isinstance(v, str) else v)
+                                        for k, v in kw.items()})
+        so.mem_budget, so.max_active, so.max_queue = float(mem_budget), int(max_active), int(max_queue)
+        self.opts = so
+        self.h = C.c_void_p()
+        st = L.sign_server_create(C.byref(so), C.byref(self.h))
+        if st != SIGN_OK:
+            raise SignError(st, "sign_server_create")
+        self._n = {}
+
+    def submit(self, a) -> int:
+        """Queues matrix a (host numpy or CUDA torch CSR); raises SignError if refused."""
+        on_dev = _is_torch_cuda(a.val)
+        if on_dev:
+            keep = (a.rowptr.contiguous(), a.col.contiguous(), a.val.contiguous())
+        else:
+            keep = (np.ascontiguousarray(a.rowptr, dtype=np.int64),
+                    np.ascontiguousarray(a.col, dtype=np.int32),
+                    np.ascontiguousarray(a.val, dtype=np.float64))
+        rp, col, val = keep
+        t = C.c_uint64()
+        st = load().sign_server_submit(self.h, int(a.n), int(rp[-1]), _ptr(rp), _ptr(col), _ptr(val),
+                                       int(on_dev), C.byref(t))
+        if st != SIGN_OK:
+            raise SignError(st, "sign_server_submit")
+        self._n[t.value] = int(a.n)
+        return t.value
+
+    def poll(self, ticket: int, wait_ms: int = 0):
+        """None while pending; else a dict with the outcome and the request's times."""
+        info, times = N.sign_info(), N.sign_request_times()
+        st = load().sign_server_poll(self.h, ticket, int(wait_ms), C.byref(info), C.byref(times))
+        if st == SIGN_EAGAIN:
+            return None
+        if st != SIGN_OK:
+            raise SignError(st, "sign_server_poll")
+        return {"status": info.status, "iters": info.iters, "resid": info.resid,
+                "nnz_final": info.nnz_final, "t_submit": times.t_submit,
+                "t_admit": times.t_admit, "t_done": times.t_done, "footprint": times.footprint}
+
+    def take(self, ticket: int, device: bool = False):
+        """The finished request's result CSR (rowptr, col, val); forgets the ticket."""
+        h = N.sign_t()
+        stream = current_stream()
+        st = load().sign_server_take(self.h, ticket, stream, C.byref(h))
+        if st != SIGN_OK:
+            raise SignError(st, "sign_server_take")
+        hd = Handle.__new__(Handle)
+        hd.h, hd.n, hd.stream = h, self._n.pop(ticket), stream
+        try:
+            return hd.result(device=device)
+        finally:
+            hd.close()
+
+    def stats(self) -> dict:
+        s = N.sign_server_stats()
+        st = load().sign_server_get_stats(self.h, C.byref(s))
+        if st != SIGN_OK:
+            raise SignError(st, "sign_server_get_stats")
+        return {k: getattr(s, k) for k, _ in N.sign_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sign_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def footprint_bytes(n: int, nnz: int, delta: float, rho: float, bw: int) -> float:
+    """sign_footprint_bytes: the server's admission model (host arithmetic)."""
+    return float(load().sign_footprint_bytes(int(n), int(nnz), float(delta), float(rho), int(bw)))

@@ -12,11 +12,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsign_gb300.so")
 
 SIGN_OK, SIGN_EINVAL, SIGN_ENOMEM, SIGN_ENOTCONV, SIGN_EDIVERGED, SIGN_ECUDA, SIGN_ETIMEOUT, \
-    SIGN_ESTATE = range(8)
+    SIGN_ESTATE, SIGN_EAGAIN = range(9)
 SIGN_FILTER_NONE, SIGN_FILTER_EXACT, SIGN_FILTER_BOUND = 0, 1, 2
 SIGN_PREC_FP64, SIGN_PREC_MIXED = 0, 1
 STATUS_NAMES = ["SIGN_OK", "SIGN_EINVAL", "SIGN_ENOMEM", "SIGN_ENOTCONV", "SIGN_EDIVERGED",
-                "SIGN_ECUDA", "SIGN_ETIMEOUT", "SIGN_ESTATE"]
+                "SIGN_ECUDA", "SIGN_ETIMEOUT", "SIGN_ESTATE", "SIGN_EAGAIN"]
 
 
 class sign_opts(C.Structure):
@@ -35,6 +35,22 @@ class sign_info(C.Structure):
                 ("fnorm_k", C.POINTER(C.c_double)), ("nnz_bar", C.POINTER(C.c_int64)),
                 ("prec_k", C.POINTER(C.c_int)), ("mults_t", C.POINTER(C.c_double)),
                 ("mults_bar", C.POINTER(C.c_double))]
+
+
+class sign_server_opts(C.Structure):
+    _fields_ = [("solve", sign_opts), ("mem_budget", C.c_double), ("max_active", C.c_int),
+                ("max_queue", C.c_int)]
+
+
+class sign_request_times(C.Structure):
+    _fields_ = [("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("footprint", C.c_double)]
+
+
+class sign_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("refused", C.c_int64), ("admitted", C.c_int64),
+                ("completed", C.c_int64), ("queued", C.c_int64), ("active", C.c_int64),
+                ("max_active_seen", C.c_int64), ("rounds", C.c_int64), ("reserved", C.c_double)]
 
 
 class sign_prof_entry(C.Structure):
@@ -63,6 +79,17 @@ SIGNATURES = {
                                                C.POINTER(C.c_double)]),
     "sign_dense_product": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
                                      C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
+    "sign_footprint_bytes": (C.c_double, [C.c_int64, C.c_int64, C.c_double, C.c_double,
+                                          C.c_int64]),
+    "sign_server_default_opts": (None, [C.POINTER(sign_server_opts)]),
+    "sign_server_create": (C.c_int, [C.POINTER(sign_server_opts), C.POINTER(C.c_void_p)]),
+    "sign_server_submit": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_int, C.POINTER(C.c_uint64)]),
+    "sign_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.POINTER(sign_info),
+                                   C.POINTER(sign_request_times)]),
+    "sign_server_take": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(sign_t)]),
+    "sign_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(sign_server_stats)]),
+    "sign_server_destroy": (None, [C.c_void_p]),
     "sign_kernel_launches": (C.c_int64, []),
     "sign_prof_enable": (C.c_int, [C.c_int]),
     "sign_prof_read": (C.c_int, [C.c_void_p, C.c_int]),
@@ -95,7 +122,7 @@ def last_error() -> str:
 class SignError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
-        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 8 else status}: "
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 9 else status}: "
                          f"{last_error()}")
 
 

@@ -13,6 +13,19 @@ namespace sgn {
 void launch_validate(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col,
                      const double *val, int *flag, cudaStream_t s);
 
+// Matrix-wide statistics for the server's footprint model. Initialise
+// min_gap_bits to the bits of +inf and the rest to 0; then min_gap_bits holds
+// the bits of min over rows with a positive gap of |a_ii| - sum_{j!=i}|a_ij|,
+// nogap = 1 if any row has no positive gap, max_rowsum_bits the bits of
+// max_i sum_j |a_ij| and max_bw max |i - j| over the entries.
+struct GershStats {
+  unsigned long long min_gap_bits, max_rowsum_bits;
+  long long max_bw;
+  int nogap;
+};
+void launch_gersh(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                  GershStats *g, cudaStream_t s);
+
 // out[0] = 0, out[i+1] = sum_{r<=i} cnt[r] for i < n. tmp holds
 // scan_tmp_elems(n) int64 values.
 int64_t scan_tmp_elems(int64_t n);

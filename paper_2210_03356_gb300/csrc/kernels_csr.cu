@@ -50,6 +50,41 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t *rp, const int3
   });
 }
 
+// ------------------------------------------------------------ footprint statistics
+// Per row: diagonal magnitude, off-diagonal sum and farthest column, folded
+// into the matrix-wide Gershgorin gap, row-sum bound and half-bandwidth.
+__global__ void k_gersh(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                        GershStats *g) {
+  int lane = lane_id();
+  for_each_row_warp(n, [&](int64_t r) {
+    double diag = 0.0, off = 0.0;
+    long long bw = 0;
+    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) {
+      int64_t c = col[p];
+      double a = fabs(val[p]);
+      if (c == r) diag += a; else off += a;
+      long long d = c > r ? c - r : r - c;
+      bw = d > bw ? d : bw;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      diag += __shfl_xor_sync(0xffffffffu, diag, o);
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      long long b2 = __shfl_xor_sync(0xffffffffu, bw, o);
+      bw = b2 > bw ? b2 : bw;
+    }
+    if (lane == 0) {
+      double gap = diag - off, rowsum = diag + off;
+      if (gap > 0.0)
+        atomicMin(&g->min_gap_bits, (unsigned long long)__double_as_longlong(gap));
+      else
+        atomicOr(&g->nogap, 1);
+      atomicMax(&g->max_rowsum_bits, (unsigned long long)__double_as_longlong(rowsum));
+      atomicMax(&g->max_bw, bw);
+    }
+  });
+}
+
 // ------------------------------------------------------------ scan
 constexpr int SCAN_T = 1024;
 constexpr int SCAN_ITEMS = 4;
@@ -366,6 +401,12 @@ void launch_seg_count(int nb, const int64_t *moff, const int64_t *rs, const int6
 void launch_extract(int nblocks, const ExtractBlock *blocks, cudaStream_t s) {
   if (nblocks == 0) return;
   k_extract<<<nblocks, 512, 0, s>>>(blocks);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_gersh(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                  GershStats *g, cudaStream_t s) {
+  k_gersh<<<grid_for(n, 8), 256, 0, s>>>(n, rp, col, val, g);
   SGN_LAUNCH_CHECK();
 }
 

@@ -583,14 +583,14 @@ CUtensorMap operand_map(const float *base, int rows, int K, int ld, int box_rows
 void launch_dense_jobs(int njobs, const DenseJob *jobs_host, DenseJob *jobs_dev, void *scratch,
                        int *err, cudaStream_t s) {
   if (njobs <= 0) return;
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
+  static const int nsm = [] {  // once, thread-safe
+    int dev = 0, n = 0;
     SGN_CUDA(cudaGetDevice(&dev));
-    SGN_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    SGN_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
     SGN_CUDA(cudaFuncSetAttribute(k_gemm_nt, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   int(dense_gemm_smem())));
-  }
+    return n;
+  }();
   thread_local std::vector<CUtensorMap> host;  // 64-byte aligned elements
   host.resize(scratch_maps(njobs));
   CUtensorMap *maps = host.data();

@@ -590,13 +590,13 @@ static void num_launch(int64_t n, const Rows &A, const T *aval, const Rows &B, c
                             part, s);
   group_launch<T, MODE, 8>(n, A, aval, B, bval, lo, len, lists, ctr, RC_G8, cs, ce, ccol, cval,
                            part, s);
-  static bool attr = false;
   constexpr size_t sm = num_cta_smem<T>();
-  if (!attr) {
+  static const bool attr = [] {  // once, thread-safe
     SGN_CUDA(cudaFuncSetAttribute(k_num_cta<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   int(sm)));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   k_num_cta<T, MODE><<<grid_cap(n, 1, 2), CTA_THREADS, sm, s>>>(
       A.rs, A.re, A.col, aval, B.rs, B.re, B.col, bval, lo, len, lists + int64_t(RC_CTA) * n, ctr,
       cs, ce, ccol, cval, part);

@@ -1,781 +1,9 @@
-// C ABI and solve driver of the filtered Newton-Schulz sign solver.
-//
-// A solve (Alg. 3.2.1) is a loop of rounds. The matrices of a batch live in
-// stages, one per precision (FP32 for the first part of the mixed mode,
-// FP64 otherwise); a stage holds its matrices as one block-diagonal CSR with
-// global column indices, so every kernel launch serves all of them. Each
-// round, each non-empty stage:
-//   1. checks its iterates: T = X X and, per matrix, r = ||T - I||_F/sqrt(n),
-//      x = ||X||_F/sqrt(n) and the budget (steps a2, a4);
-//   2. per matrix: stops (r <= tol, step a7), diverges, runs out of updates,
-//      moves from FP32 to FP64 (r < fp32_until, step a8), or updates;
-//   3. for the updating matrices: Xbar = 1.5 X - 0.5 X T (step a3), the
-//      threshold (step a5) and the filter with CSR compaction (step a6).
-// A matrix that stops is copied out to its handle; the stage is rebuilt
-// without it at the next round. Per-matrix control flow is exactly that of a
-// lone solve, so every result is independent of the batch it ran in.
-#include <algorithm>
-#include <cmath>
-#include <cstdio>
-#include <cstring>
-#include <memory>
-#include <string>
-#include <vector>
-
-#include "../../include/sign.h"
-#include "common.cuh"
-#include "kernels.h"
-
-using namespace sgn;
+// C ABI of the filtered Newton-Schulz sign solver: handles, batch solves,
+// results. The round loop itself is in solver_core.cuh.
+#include "solver_core.cuh"
 
 namespace {
-
 thread_local std::string g_err;
-
-// ------------------------------------------------------------------ CSR
-template <typename T>
-struct Csr {
-  int64_t n = 0, nnz = 0;
-  DevBuf rp, col, val;
-  int64_t *d_rp() const { return rp.as<int64_t>(); }
-  int32_t *d_col() const { return col.as<int32_t>(); }
-  T *d_val() const { return val.as<T>(); }
-  void ensure(int64_t rows, int64_t nz, cudaStream_t s) {
-    n = rows;
-    nnz = nz;
-    rp.ensure(sizeof(int64_t) * size_t(rows + 1), s);
-    col.ensure(sizeof(int32_t) * size_t(nz > 0 ? nz : 1), s);
-    val.ensure(sizeof(T) * size_t(nz > 0 ? nz : 1), s);
-  }
-  void swap(Csr &o) {
-    std::swap(n, o.n);
-    std::swap(nnz, o.nnz);
-    std::swap(rp.p, o.rp.p);
-    std::swap(rp.cap, o.rp.cap);
-    std::swap(rp.s, o.rp.s);
-    std::swap(col.p, o.col.p);
-    std::swap(col.cap, o.col.cap);
-    std::swap(col.s, o.col.s);
-    std::swap(val.p, o.val.p);
-    std::swap(val.cap, o.val.cap);
-    std::swap(val.s, o.val.s);
-  }
-};
-
-}  // namespace
-
-struct sign_ctx {
-  int64_t n = 0, nnz = 0;
-  cudaStream_t stream = nullptr;
-  Csr<double> a;       // input copy
-  Csr<double> result;  // last result
-  bool has_result = false;
-};
-
-namespace {
-
-template <typename T> constexpr int is_f32() { return sizeof(T) == 4; }
-
-void sync(cudaStream_t s) { SGN_CUDA(cudaStreamSynchronize(s)); }
-
-template <typename T>
-void d2h(T *dst, const void *src, size_t count, cudaStream_t s) {
-  SGN_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * count, cudaMemcpyDeviceToHost, s));
-}
-template <typename T>
-void h2d(void *dst, const T *src, size_t count, cudaStream_t s) {
-  SGN_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, s));
-}
-
-// Per-matrix bookkeeping of one solve call.
-struct MatState {
-  sign_t h = nullptr;
-  sign_info *info = nullptr;
-  int k = 0;            // updates done
-  int status = -1;      // -1 running, else sign_status
-  double resid = NAN;
-  int trace_count = 0;
-};
-
-void trace_put(MatState &ms, int64_t nnz_x, int64_t nnz_t, double r, double x, int prec,
-               double mults_t) {
-  sign_info *in = ms.info;
-  if (!in) return;
-  int k = ms.trace_count;
-  if (k >= in->cap) return;
-  ms.trace_count++;
-  if (in->nnz_x) in->nnz_x[k] = nnz_x;
-  if (in->nnz_t) in->nnz_t[k] = nnz_t;
-  if (in->resid_k) in->resid_k[k] = r;
-  if (in->xnorm_k) in->xnorm_k[k] = x;
-  if (in->beta_k) in->beta_k[k] = 0.0;
-  if (in->tau_k) in->tau_k[k] = 0.0;
-  if (in->fnorm_k) in->fnorm_k[k] = 0.0;
-  if (in->nnz_bar) in->nnz_bar[k] = 0;
-  if (in->prec_k) in->prec_k[k] = prec;
-  if (in->mults_t) in->mults_t[k] = mults_t;
-  if (in->mults_bar) in->mults_bar[k] = 0.0;
-}
-
-void trace_filter(MatState &ms, double beta, double tau, double fnorm, int64_t nnz_bar,
-                  double mults_bar) {
-  sign_info *in = ms.info;
-  if (!in || ms.trace_count == 0 || ms.trace_count > in->cap) return;
-  int k = ms.trace_count - 1;
-  if (in->beta_k) in->beta_k[k] = beta;
-  if (in->tau_k) in->tau_k[k] = tau;
-  if (in->fnorm_k) in->fnorm_k[k] = fnorm;
-  if (in->nnz_bar) in->nnz_bar[k] = nnz_bar;
-  if (in->mults_bar) in->mults_bar[k] = mults_bar;
-}
-
-// A matrix's rows taken out of a stage (moving from FP32 to FP64).
-struct Parked {
-  int mat;
-  Csr<double> x;  // its rows, local column indices
-};
-
-// Output of a sparse product: row i occupies [rs[i], re[i]) of (col, val);
-// rs is the exclusive scan of the row slot sizes, so gaps may follow a row.
-template <typename T>
-struct Slotted {
-  int64_t n = 0, slots = 0;
-  DevBuf rs, re, col, val;
-  Rows rows() const { return Rows{rs.as<int64_t>(), re.as<int64_t>(), col.as<int32_t>()}; }
-  T *d_val() const { return val.as<T>(); }
-};
-
-template <typename T>
-Rows compact_rows(const Csr<T> &c) {
-  return Rows{c.d_rp(), c.d_rp() + 1, c.d_col()};
-}
-
-// Shared scratch of one solve call.
-struct Work {
-  DevBuf lo, len, ub, wlist, clist, counters, part, scan_tmp, eoff, sums, ms, active, sel,
-      asm_blocks, asm_off, asm_lens, dropped, norm_work, norm, work, mults, cnt, nnzc, xblocks,
-      dslot, dmem, dbufs, djobs, dscratch, dcount, derr;
-};
-
-// The matrices of one round on the dense path (FP32 stage): their slots,
-// dense blocks and the batched product jobs.
-struct DensePlan {
-  std::vector<int> slot;          // per matrix of the stage: dense index or -1
-  std::vector<DenseBuf> bufs;     // host copies of the device DenseBuf array
-  std::vector<int> mat;           // stage slot of each dense matrix
-  int nd = 0, max_ld = 0;
-  bool any() const { return nd > 0; }
-};
-
-// Page-locked host mirrors of the per-matrix values read back every round.
-// Kept per host thread and grown only (cudaFreeHost would synchronize the
-// device), so repeated solves reuse them.
-struct HostMirror {
-  void *p = nullptr;
-  size_t cap = 0;
-  MatScalars *ms = nullptr;
-  int64_t *ex = nullptr, *nnz_t = nullptr, *nnz_bar = nullptr, *tot = nullptr;
-  double *mults = nullptr, *dsum = nullptr;
-  ExtractBlock *xb = nullptr;
-  void alloc(int nb) {
-    size_t bytes = sizeof(MatScalars) * nb + sizeof(int64_t) * (4 * size_t(nb) + 8) +
-                   sizeof(double) * 2 * size_t(nb) + sizeof(ExtractBlock) * nb + 1024;
-    if (bytes > cap) {
-      if (p) cudaFreeHost(p);
-      p = nullptr;
-      SGN_CUDA(cudaMallocHost(&p, bytes));
-      cap = bytes;
-    }
-    char *c = static_cast<char *>(p);
-    auto take = [&](size_t b) {
-      char *r = c;
-      c += (b + 63) & ~size_t(63);
-      return r;
-    };
-    ms = reinterpret_cast<MatScalars *>(take(sizeof(MatScalars) * nb));
-    ex = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (nb + 1)));
-    nnz_t = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * nb));
-    nnz_bar = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * nb));
-    tot = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * 4));
-    mults = reinterpret_cast<double *>(take(sizeof(double) * nb));
-    dsum = reinterpret_cast<double *>(take(sizeof(double) * nb));
-    xb = reinterpret_cast<ExtractBlock *>(take(sizeof(ExtractBlock) * nb));
-  }
-  ~HostMirror() {
-    if (p) cudaFreeHost(p);
-  }
-};
-
-HostMirror &host_mirror() {
-  static thread_local HostMirror hm;
-  return hm;
-}
-
-template <typename T>
-struct Stage {
-  int prec = sizeof(T) == 4 ? 32 : 64;
-  std::vector<int> mats;          // matrix ids, in row order
-  std::vector<int> alive;         // 0 once a matrix has left (its rows are empty)
-  std::vector<int64_t> moff;      // row offsets (host), size mats+1
-  std::vector<int64_t> ex;        // entry offsets of X per matrix (host), size mats+1
-  DevBuf d_moff, d_seg;
-  Csr<T> X, Xh;                   // compact iterate and filtered update
-  Slotted<T> Tm, Xb;              // X X and 1.5 X - 0.5 X T
-  std::vector<Parked *> incoming; // matrices entering at the next round
-};
-
-struct Solver {
-  cudaStream_t s;
-  sign_opts o;
-  std::vector<MatState> m;
-  Work w;
-  HostMirror &hm = host_mirror();
-  std::vector<std::unique_ptr<Parked>> parked_store;
-
-  // ---------------------------------------------------------------- helpers
-  void set_layout(std::vector<int64_t> &moff, const std::vector<int> &mats, DevBuf &d_moff,
-                  DevBuf &d_seg) {
-    moff.assign(mats.size() + 1, 0);
-    for (size_t i = 0; i < mats.size(); ++i) moff[i + 1] = moff[i] + m[mats[i]].h->n;
-    int64_t N = moff.back();
-    d_moff.ensure(sizeof(int64_t) * moff.size(), s);
-    h2d(d_moff.p, moff.data(), moff.size(), s);
-    d_seg.ensure(sizeof(int32_t) * size_t(N > 0 ? N : 1), s);
-    launch_fill_seg(int(mats.size()), d_moff.as<int64_t>(), N, d_seg.as<int32_t>(), s);
-  }
-
-  // Assembles dst from blocks laid out one after another (block-diagonal).
-  template <typename TD>
-  void assemble(const std::vector<AsmBlock> &blocks, const std::vector<int64_t> &bnnz, Csr<TD> &dst) {
-    int nb = int(blocks.size());
-    std::vector<int64_t> boff(nb + 1, 0);
-    int64_t nnz = 0;
-    for (int b = 0; b < nb; ++b) {
-      boff[b + 1] = boff[b] + blocks[b].nrows;
-      nnz += bnnz[b];
-    }
-    int64_t N = boff[nb];
-    dst.ensure(N, nnz, s);
-    w.asm_blocks.ensure(sizeof(AsmBlock) * size_t(nb > 0 ? nb : 1), s);
-    w.asm_off.ensure(sizeof(int64_t) * size_t(nb + 1), s);
-    w.asm_lens.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
-    w.scan_tmp.ensure(sizeof(int64_t) * size_t(scan_tmp_elems(N)), s);
-    h2d(w.asm_blocks.p, blocks.data(), blocks.size(), s);
-    h2d(w.asm_off.p, boff.data(), boff.size(), s);
-    ProfScope ps(KC_ASSEMBLE, s, 0.0, double(nnz) * (8.0 + 4.0 + sizeof(TD)) + 16.0 * double(N));
-    launch_assemble_rows(nb, w.asm_blocks.as<AsmBlock>(), w.asm_off.as<int64_t>(), N,
-                         w.asm_lens.as<int64_t>(), dst.d_rp(), w.scan_tmp.as<int64_t>(), s);
-    launch_assemble_vals(nb, w.asm_blocks.as<AsmBlock>(), w.asm_off.as<int64_t>(), N, dst.d_rp(),
-                         dst.d_col(), dst.val.p, is_f32<TD>(), s);
-    // the block and offset arrays are pageable host copies: keep the stream in step
-    sync(s);
-  }
-
-  // ---------------------------------------------------------------- product
-  // C = A B for a stage. Enqueues everything; on return C is allocated and the
-  // product queued, hm.mults holds the per-matrix multiply-adds (synced) and
-  // w.nnzc the per-matrix nnz of C (device, read with the next sync).
-  template <typename T>
-  void product(Stage<T> &st, const Rows &A, const T *aval, int64_t nnzA, const Rows &B,
-               const T *bval, int64_t nnzB, int mode, Slotted<T> &C, const int *active,
-               const DensePlan *dp = nullptr) {
-    int64_t N = int64_t(st.moff.back());
-    int nb = int(st.mats.size());
-    w.lo.ensure(sizeof(int32_t) * size_t(N), s);
-    w.len.ensure(sizeof(int32_t) * size_t(N), s);
-    w.ub.ensure(sizeof(int64_t) * size_t(N), s);
-    w.wlist.ensure(sizeof(int32_t) * size_t(4 * N), s);
-    w.work.ensure(sizeof(double) * size_t(N), s);
-    w.mults.ensure(sizeof(double) * size_t(nb), s);
-    w.nnzc.ensure(sizeof(int64_t) * size_t(nb), s);
-    w.counters.ensure(sizeof(int) * 8, s);
-    w.scan_tmp.ensure(sizeof(int64_t) * size_t(scan_tmp_elems(N)), s);
-    SGN_CUDA(cudaMemsetAsync(w.counters.p, 0, sizeof(int) * 8, s));
-    {
-      ProfScope ps(KC_BOUNDS, s);
-      launch_bounds(N, A, B, st.d_seg.template as<int32_t>(), active, mode, sizeof(T) == 8 ? 1 : 0,
-                    dp && dp->any() ? w.dslot.as<int>() : nullptr,
-                    st.d_moff.template as<int64_t>(), w.lo.as<int32_t>(),
-                    w.len.as<int32_t>(), w.ub.as<int64_t>(), w.wlist.as<int32_t>(),
-                    w.counters.as<int>(), w.work.as<double>(), s);
-      launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.work.as<double>(), 1,
-                        w.mults.as<double>(), s);
-    }
-    C.n = N;
-    C.rs.ensure(sizeof(int64_t) * size_t(N + 1), s);
-    C.re.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
-    {
-      ProfScope ps(KC_SCAN, s);
-      launch_scan(N, w.ub.as<int64_t>(), C.rs.template as<int64_t>(), w.scan_tmp.as<int64_t>(), s);
-    }
-    d2h(hm.tot, C.rs.template as<int64_t>() + N, 1, s);
-    d2h(hm.mults, w.mults.p, size_t(nb), s);
-    sync(s);
-    int64_t slots = hm.tot[0];
-    C.slots = slots;
-    C.col.ensure(sizeof(int32_t) * size_t(slots > 0 ? slots : 1), s);
-    C.val.ensure(sizeof(T) * size_t(slots > 0 ? slots : 1), s);
-    if (mode == MODE_SQUARE) w.part.ensure(sizeof(double) * size_t(2 * N), s);
-    double fl = 0.0;
-    for (int i = 0; i < nb; ++i) fl += 2.0 * hm.mults[i];
-    double per = 4.0 + sizeof(T);
-    // algorithmic bytes: A and B read once, C written once (its size is known
-    // after the launch; the slot total bounds it and is used here)
-    double by = per * double(nnzA + (mode == MODE_UPDATE ? nnzB : 0) + slots) +
-                8.0 * double(N + 1) * (mode == MODE_UPDATE ? 3.0 : 2.0) +
-                (mode == MODE_SQUARE ? 16.0 * double(N) : 0.0);
-    int cls = mode == MODE_SQUARE ? (sizeof(T) == 8 ? KC_NUM_SQUARE_F64 : KC_NUM_SQUARE_F32)
-                                  : (sizeof(T) == 8 ? KC_NUM_UPDATE_F64 : KC_NUM_UPDATE_F32);
-    {
-      ProfScope ps(cls, s, fl, by);
-      launch_numeric<T>(N, A, aval, B, bval, mode, w.lo.as<int32_t>(), w.len.as<int32_t>(),
-                        w.wlist.as<int32_t>(), w.counters.as<int>(), C.rs.template as<int64_t>(),
-                        C.re.template as<int64_t>(), C.col.template as<int32_t>(), C.d_val(),
-                        mode == MODE_SQUARE ? w.part.as<double>() : nullptr, s);
-    }
-    if (dp && dp->any()) dense_step(st, mode, C, active, *dp);
-    launch_seg_count(nb, st.d_moff.template as<int64_t>(), C.rs.template as<int64_t>(),
-                     C.re.template as<int64_t>(), w.nnzc.as<int64_t>(), s);
-  }
-
-  // ---------------------------------------------------------------- dense path (a9)
-  // Chooses the FP32-stage matrices whose iterate has filled in (density >=
-  // dense_frac, n <= 4096) and lays out their dense blocks.
-  template <typename T>
-  DensePlan plan_dense(Stage<T> &st) {
-    DensePlan dp;
-    int nb = int(st.mats.size());
-    dp.slot.assign(nb, -1);
-    if (sizeof(T) != 4 || !(o.dense_frac <= 1.0) || o.filter == SIGN_FILTER_NONE) return dp;
-    size_t total = 0;
-    for (int i = 0; i < nb; ++i) {
-      if (!st.alive[i]) continue;
-      int64_t n = st.moff[i + 1] - st.moff[i];
-      int64_t nnz = st.ex[i + 1] - st.ex[i];
-      if (n > 4096 || double(nnz) < o.dense_frac * double(n) * double(n)) continue;
-      int ld = int((n + 3) / 4 * 4);
-      dp.slot[i] = dp.nd++;
-      dp.mat.push_back(i);
-      DenseBuf b = {};
-      b.n = int(n);
-      b.ld = ld;
-      dp.bufs.push_back(b);
-      dp.max_ld = std::max(dp.max_ld, ld);
-      total += 7 * size_t(ld) * size_t(ld);
-    }
-    if (!dp.nd) return dp;
-    float *mem = static_cast<float *>(w.dmem.ensure(sizeof(float) * total, s));
-    size_t off = 0;
-    for (DenseBuf &b : dp.bufs) {
-      size_t blk = size_t(b.ld) * size_t(b.ld);
-      float *base = mem + off;
-      b.X_hi = base;
-      b.X_lo = base + blk;
-      b.XT_hi = base + 2 * blk;
-      b.XT_lo = base + 3 * blk;
-      b.TT_hi = base + 4 * blk;
-      b.TT_lo = base + 5 * blk;
-      b.P = base + 6 * blk;
-      off += 7 * blk;
-    }
-    w.dslot.ensure(sizeof(int) * size_t(nb), s);
-    h2d(w.dslot.p, dp.slot.data(), size_t(nb), s);
-    w.dbufs.ensure(sizeof(DenseBuf) * size_t(dp.nd), s);
-    h2d(w.dbufs.p, dp.bufs.data(), size_t(dp.nd), s);
-    w.dcount.ensure(sizeof(unsigned long long) * size_t(dp.nd), s);
-    w.derr.ensure(sizeof(int), s);
-    SGN_CUDA(cudaMemsetAsync(w.derr.p, 0, sizeof(int), s));
-    sync(s);  // the host vectors above are pageable
-    return dp;
-  }
-
-  // The dense steps of a product: SQUARE densifies X and forms T = X X and the
-  // residual partials; UPDATE forms P = X T and emits 1.5 X - 0.5 P.
-  template <typename T>
-  void dense_step(Stage<T> &st, int mode, Slotted<T> &C, const int *active, const DensePlan &dp) {
-    if constexpr (sizeof(T) == 4) {
-      int64_t N = st.moff.back();
-      std::vector<DenseJob> jobs;
-      double fl = 0.0;
-      for (const DenseBuf &b : dp.bufs) {
-        if (mode == MODE_SQUARE)  // T^T = X^T X^T: C = A Bt^T with A = X^T, Bt = X
-          jobs.push_back(DenseJob{b.ld, b.ld, b.ld, b.XT_hi, b.XT_lo, b.ld, b.X_hi, b.X_lo, b.ld,
-                                  b.TT_hi, b.TT_lo, b.ld});
-        else  // P = X T as C = A Bt^T with A = X, Bt = T^T
-          jobs.push_back(DenseJob{b.ld, b.ld, b.ld, b.X_hi, b.X_lo, b.ld, b.TT_hi, b.TT_lo, b.ld,
-                                  b.P, nullptr, b.ld});
-        fl += 3.0 * 2.0 * double(b.ld) * double(b.ld) * double(b.ld);
-      }
-      w.djobs.ensure(sizeof(DenseJob) * jobs.size(), s);
-      w.dscratch.ensure(dense_jobs_scratch_bytes(int(jobs.size())), s);
-      const DenseBuf *bufs = w.dbufs.as<DenseBuf>();
-      if (mode == MODE_SQUARE) {
-        size_t total = 0;
-        for (const DenseBuf &b : dp.bufs) total += 7 * size_t(b.ld) * size_t(b.ld);
-        SGN_CUDA(cudaMemsetAsync(w.dmem.p, 0, sizeof(float) * total, s));
-        launch_densify(N, st.d_seg.template as<int32_t>(), w.dslot.as<int>(),
-                       st.d_moff.template as<int64_t>(), st.X.d_rp(), st.X.d_col(),
-                       reinterpret_cast<const float *>(st.X.val.p), bufs, s);
-      }
-      {
-        ProfScope ps(KC_DENSE, s, fl, 0.0);
-        launch_dense_jobs(int(jobs.size()), jobs.data(), w.djobs.as<DenseJob>(), w.dscratch.p,
-                          w.derr.as<int>(), s);
-      }
-      if (mode == MODE_SQUARE) {
-        SGN_CUDA(cudaMemsetAsync(w.dcount.p, 0, sizeof(unsigned long long) * size_t(dp.nd), s));
-        launch_dense_resid(N, st.d_seg.template as<int32_t>(), w.dslot.as<int>(),
-                           st.d_moff.template as<int64_t>(), bufs, w.part.as<double>(),
-                           w.dcount.as<unsigned long long>(), s);
-      } else {
-        launch_dense_emit(N, st.d_seg.template as<int32_t>(), w.dslot.as<int>(),
-                          st.d_moff.template as<int64_t>(), active, bufs,
-                          C.rs.template as<int64_t>(), C.re.template as<int64_t>(),
-                          C.col.template as<int32_t>(), reinterpret_cast<float *>(C.val.p), s);
-      }
-      sync(s);  // the job list is a pageable host vector
-    }
-  }
-
-  // ---------------------------------------------------------------- rounds
-  // Re-lays out a stage with its live matrices and the incoming ones.
-  template <typename T>
-  void rebuild(Stage<T> &st) {
-    HostScope hr(KH_REBUILD);
-    int nb = int(st.mats.size());
-    std::vector<int64_t> eoff(nb + 1, 0);
-    if (nb > 0) {
-      w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
-      launch_gather_offsets(nb, st.d_moff.template as<int64_t>(), st.X.d_rp(),
-                            w.eoff.as<int64_t>(), s);
-      d2h(eoff.data(), w.eoff.p, eoff.size(), s);
-      sync(s);
-    }
-    std::vector<int> mats;
-    std::vector<AsmBlock> blocks;
-    std::vector<int64_t> bnnz;
-    int64_t off = 0;
-    for (int i = 0; i < nb; ++i) {
-      if (!st.alive[i]) continue;
-      int id = st.mats[i];
-      blocks.push_back(AsmBlock{st.X.d_rp(), st.X.d_col(), st.X.val.p, st.moff[i],
-                                st.moff[i + 1] - st.moff[i], off - st.moff[i], is_f32<T>()});
-      bnnz.push_back(eoff[i + 1] - eoff[i]);
-      mats.push_back(id);
-      off += m[id].h->n;
-    }
-    for (Parked *p : st.incoming) {
-      blocks.push_back(AsmBlock{p->x.d_rp(), p->x.d_col(), p->x.val.p, 0, p->x.n, off, 0});
-      bnnz.push_back(p->x.nnz);
-      mats.push_back(p->mat);
-      off += p->x.n;
-    }
-    Csr<T> nx;
-    assemble<T>(blocks, bnnz, nx);
-    st.X.swap(nx);
-    st.mats = mats;
-    st.alive.assign(mats.size(), 1);
-    st.ex.assign(1, 0);
-    for (int64_t b : bnnz) st.ex.push_back(st.ex.back() + b);
-    set_layout(st.moff, st.mats, st.d_moff, st.d_seg);
-    st.incoming.clear();
-  }
-
-  template <typename T, typename TN>
-  void round(Stage<T> &st, Stage<TN> *next) {
-    if (!st.incoming.empty()) rebuild(st);
-    int nb = int(st.mats.size());
-    int live = 0;
-    for (int a : st.alive) live += a;
-    if (live == 0) return;
-    int64_t N = st.moff.back();
-    w.active.ensure(sizeof(int) * size_t(nb), s);
-    h2d(w.active.p, st.alive.data(), st.alive.size(), s);
-    const int *d_act = w.active.as<int>();
-    const std::vector<int64_t> ex = st.ex;  // entry offsets of the iterate per matrix
-    // ---- check: T = X X, r, x, budget (steps a2, a4)
-    Rows xr = compact_rows(st.X);
-    HostScope hcheck(KH_CHECK);
-    DensePlan dp = plan_dense(st);
-    product(st, xr, st.X.d_val(), st.X.nnz, xr, st.X.d_val(), st.X.nnz, MODE_SQUARE, st.Tm, d_act,
-            &dp);
-    std::vector<double> mt(hm.mults, hm.mults + nb);  // sparse multiply-adds of T
-    w.sums.ensure(sizeof(double) * size_t(2 * nb), s);
-    w.ms.ensure(sizeof(MatScalars) * size_t(nb), s);
-    double tol_stage = st.prec == 32 ? o.fp32_until : o.tol;
-    {
-      ProfScope ps(KC_REDUCE, s);
-      launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.part.as<double>(), 2,
-                        w.sums.as<double>(), s);
-      launch_matrix_scalars(nb, st.d_moff.template as<int64_t>(), w.sums.as<double>(), o.c4,
-                            tol_stage, o.switch_resid, w.ms.as<MatScalars>(), s);
-    }
-    d2h(hm.ms, w.ms.p, size_t(nb), s);
-    d2h(hm.nnz_t, w.nnzc.p, size_t(nb), s);
-    std::vector<unsigned long long> dcount(dp.nd);
-    if (dp.any()) d2h(dcount.data(), w.dcount.p, size_t(dp.nd), s);
-    sync(s);
-    for (int d = 0; d < dp.nd; ++d) {  // the dense path's T: its nonzeros and multiply-adds
-      int i = dp.mat[d];
-      hm.nnz_t[i] += int64_t(dcount[d]);
-      double n = double(st.moff[i + 1] - st.moff[i]);
-      mt[i] = n * n * n;
-    }
-    hcheck.stop();
-    std::vector<MatScalars> hms(hm.ms, hm.ms + nb);
-    // ---- per-matrix decisions (steps a7, a8); leavers copied out in one launch
-    HostScope hdecide(KH_DECIDE);
-    int nx = 0;
-    bool changed = false;
-    for (int i = 0; i < nb; ++i) {
-      if (!st.alive[i]) continue;
-      MatState &ms = m[st.mats[i]];
-      double r = hms[i].r;
-      trace_put(ms, ex[i + 1] - ex[i], hm.nnz_t[i], r, hms[i].x, st.prec, mt[i]);
-      ms.resid = r;
-      int decision = 0;  // 0 update, 1 retire, 2 move
-      if (st.prec == 64 && r <= o.tol) {
-        ms.status = SIGN_OK;
-        decision = 1;
-      } else if (!std::isfinite(r) || r > o.div_limit) {
-        ms.status = SIGN_EDIVERGED;
-        decision = 1;
-      } else if (st.prec == 32 && r < o.fp32_until) {
-        decision = 2;
-      } else if (ms.k >= o.max_iter) {
-        ms.status = SIGN_ENOTCONV;
-        decision = 1;
-      }
-      if (decision == 0) continue;
-      changed = true;
-      st.alive[i] = 0;
-      int64_t n_i = st.moff[i + 1] - st.moff[i], nnz_i = ex[i + 1] - ex[i];
-      Csr<double> *dst;
-      if (decision == 1) {
-        dst = &ms.h->result;
-        ms.h->has_result = true;
-      } else {
-        auto p = std::make_unique<Parked>();
-        p->mat = st.mats[i];
-        dst = &p->x;
-        if (next) next->incoming.push_back(p.get());
-        parked_store.push_back(std::move(p));
-      }
-      dst->ensure(n_i, nnz_i, s);
-      hm.xb[nx++] = ExtractBlock{st.X.d_rp(), st.X.d_col(), st.X.val.p, is_f32<T>(), st.moff[i],
-                                 n_i, -st.moff[i], dst->d_rp(), dst->d_col(), dst->d_val()};
-    }
-    if (nx > 0) {
-      w.xblocks.ensure(sizeof(ExtractBlock) * size_t(nx), s);
-      h2d(w.xblocks.p, hm.xb, size_t(nx), s);
-      ProfScope ps(KC_ASSEMBLE, s);
-      launch_extract(nx, w.xblocks.as<ExtractBlock>(), s);
-    }
-    live = 0;
-    for (int a : st.alive) live += a;
-    if (live == 0) {
-      sync(s);  // the extraction reads X and the pinned block list
-      return;
-    }
-    if (changed) h2d(w.active.p, st.alive.data(), st.alive.size(), s);
-    hdecide.stop();
-    // ---- update: Xbar = 1.5 X - 0.5 X T (step a3)
-    HostScope hupdate(KH_UPDATE);
-    int64_t nnz_t_all = 0;
-    for (int i = 0; i < nb; ++i) nnz_t_all += hm.nnz_t[i];
-    product(st, xr, st.X.d_val(), st.X.nnz, st.Tm.rows(), st.Tm.d_val(), nnz_t_all, MODE_UPDATE,
-            st.Xb, d_act, &dp);
-    std::vector<double> mb(hm.mults, hm.mults + nb);
-    for (int d = 0; d < dp.nd; ++d) {
-      double n = double(st.moff[dp.mat[d] + 1] - st.moff[dp.mat[d]]);
-      mb[dp.mat[d]] = n * n * n;
-    }
-    // per-matrix nnz(Xbar) straight into the device scalars (BOUND needs it)
-    launch_store_nnz_bar(nb, w.nnzc.as<int64_t>(), w.ms.as<MatScalars>(), s);
-    hupdate.stop();
-    HostScope hfilter(KH_FILTER);
-    if (o.filter == SIGN_FILTER_NONE) {
-      // keep every entry: compact the slotted rows as they are
-      hms_none(st, hms);
-    } else {
-      {
-        // ---- threshold (step a5)
-        if (o.filter == SIGN_FILTER_EXACT) {
-          w.sel.ensure(select_scratch_bytes(nb, st.Xb.slots), s);
-          SelRows R{N, st.d_seg.template as<int32_t>(), st.Xb.rs.template as<int64_t>(),
-                    st.Xb.re.template as<int64_t>(), 0};
-          launch_select_exact(nb, R, st.Xb.slots, d_act, st.Xb.val.p, is_f32<T>(),
-                              w.ms.as<MatScalars>(), w.sel.p, s);
-        } else {
-          ProfScope psel(KC_SELECT, s);
-          launch_select_bound(nb, d_act, w.ms.as<MatScalars>(), s);
-        }
-      }
-      filter(st, d_act, hms);
-    }
-    for (int i = 0; i < nb; ++i) {
-      if (!st.alive[i]) continue;
-      MatState &ms = m[st.mats[i]];
-      trace_filter(ms, hms[i].beta, o.filter == SIGN_FILTER_NONE ? 0.0 : hms[i].tau,
-                   o.filter == SIGN_FILTER_NONE ? 0.0 : hms[i].fnorm, hms[i].nnz_bar, mb[i]);
-      ms.k++;
-    }
-    st.X.swap(st.Xh);
-  }
-
-  // Filter + compaction (step a6): Xh = entries of Xb with |x| >= tau, x != 0.
-  template <typename T>
-  void filter(Stage<T> &st, const int *d_act, std::vector<MatScalars> &hms) {
-    int64_t N = st.moff.back();
-    int nb = int(st.mats.size());
-    w.dropped.ensure(sizeof(double) * size_t(N > 0 ? N : 1), s);
-    w.cnt.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
-    ProfScope pf(KC_FILTER, s, 0.0, double(st.Xb.slots) * (2.0 * sizeof(T) + 4.0) + 24.0 * double(N));
-    launch_filter_count(N, st.d_seg.template as<int32_t>(), d_act, st.Xb.rs.template as<int64_t>(),
-                        st.Xb.re.template as<int64_t>(), st.Xb.val.p, is_f32<T>(),
-                        w.ms.as<MatScalars>(), w.cnt.as<int64_t>(), w.dropped.as<double>(), s);
-    st.Xh.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
-    launch_scan(N, w.cnt.as<int64_t>(), st.Xh.d_rp(), w.scan_tmp.as<int64_t>(), s);
-    launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.dropped.as<double>(), 1,
-                      w.sums.as<double>(), s);
-    w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
-    launch_gather_offsets(nb, st.d_moff.template as<int64_t>(), st.Xh.d_rp(), w.eoff.as<int64_t>(), s);
-    d2h(hm.ex, w.eoff.p, size_t(nb + 1), s);
-    d2h(hm.tot, st.Xh.d_rp() + N, 1, s);
-    d2h(hm.ms, w.ms.p, size_t(nb), s);
-    d2h(hm.dsum, w.sums.p, size_t(nb), s);
-    sync(s);
-    int64_t nnz = hm.tot[0];
-    st.Xh.n = N;
-    st.Xh.nnz = nnz;
-    st.Xh.col.ensure(sizeof(int32_t) * size_t(nnz > 0 ? nnz : 1), s);
-    st.Xh.val.ensure(sizeof(T) * size_t(nnz > 0 ? nnz : 1), s);
-    launch_filter_write(N, st.d_seg.template as<int32_t>(), d_act, st.Xb.rs.template as<int64_t>(),
-                        st.Xb.re.template as<int64_t>(), st.Xb.col.template as<int32_t>(),
-                        st.Xb.val.p, is_f32<T>(), w.ms.as<MatScalars>(), st.Xh.d_rp(),
-                        st.Xh.d_col(), st.Xh.val.p, s);
-    for (int i = 0; i < nb; ++i) {
-      hms[i].tau = hm.ms[i].tau;
-      hms[i].nnz_bar = hm.ms[i].nnz_bar;
-      hms[i].fnorm = std::sqrt(hm.dsum[i]);
-    }
-    st.ex.assign(hm.ex, hm.ex + nb + 1);
-  }
-
-  // No filter: the update is compacted with every entry kept (exact zeros too).
-  template <typename T>
-  void hms_none(Stage<T> &st, std::vector<MatScalars> &hms) {
-    int64_t N = st.moff.back();
-    w.cnt.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
-    ProfScope pf(KC_FILTER, s, 0.0, double(st.Xb.slots) * (2.0 * sizeof(T) + 8.0));
-    launch_row_lengths(N, st.Xb.rs.template as<int64_t>(), st.Xb.re.template as<int64_t>(),
-                       w.cnt.as<int64_t>(), s);
-    st.Xh.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
-    launch_scan(N, w.cnt.as<int64_t>(), st.Xh.d_rp(), w.scan_tmp.as<int64_t>(), s);
-    int nbm = int(st.mats.size());
-    w.eoff.ensure(sizeof(int64_t) * size_t(nbm + 1), s);
-    launch_gather_offsets(nbm, st.d_moff.template as<int64_t>(), st.Xh.d_rp(), w.eoff.as<int64_t>(), s);
-    d2h(hm.ex, w.eoff.p, size_t(nbm + 1), s);
-    d2h(hm.tot, st.Xh.d_rp() + N, 1, s);
-    d2h(hm.ms, w.ms.p, size_t(nbm), s);
-    sync(s);
-    for (int i = 0; i < nbm; ++i) hms[i].nnz_bar = hm.ms[i].nnz_bar;
-    st.ex.assign(hm.ex, hm.ex + nbm + 1);
-    int64_t nnz = hm.tot[0];
-    st.Xh.n = N;
-    st.Xh.nnz = nnz;
-    st.Xh.col.ensure(sizeof(int32_t) * size_t(nnz > 0 ? nnz : 1), s);
-    st.Xh.val.ensure(sizeof(T) * size_t(nnz > 0 ? nnz : 1), s);
-    launch_compact_rows(N, st.Xb.rs.template as<int64_t>(), st.Xb.re.template as<int64_t>(),
-                        st.Xb.col.template as<int32_t>(), st.Xb.val.p, sizeof(T), st.Xh.d_rp(),
-                        st.Xh.d_col(), st.Xh.val.p, s);
-  }
-
-  // ---------------------------------------------------------------- solve
-  void run(sign_t *hs, int count, sign_info *infos) {
-    m.resize(count);
-    hm.alloc(count);
-    for (int i = 0; i < count; ++i) {
-      m[i].h = hs[i];
-      m[i].info = infos ? &infos[i] : nullptr;
-      hs[i]->has_result = false;
-    }
-    // block-diagonal input (FP64), scaled per matrix (step a1)
-    HostScope hsetup(KH_SETUP);
-    Stage<double> s64;
-    Stage<float> s32;
-    std::vector<int> all(count);
-    for (int i = 0; i < count; ++i) all[i] = i;
-    std::vector<AsmBlock> blocks;
-    std::vector<int64_t> bnnz;
-    int64_t off = 0;
-    for (int i = 0; i < count; ++i) {
-      blocks.push_back(AsmBlock{hs[i]->a.d_rp(), hs[i]->a.d_col(), hs[i]->a.val.p, 0, hs[i]->n, off, 0});
-      bnnz.push_back(hs[i]->nnz);
-      off += hs[i]->n;
-    }
-    s64.mats = all;
-    s64.alive.assign(count, 1);
-    set_layout(s64.moff, s64.mats, s64.d_moff, s64.d_seg);
-    assemble<double>(blocks, bnnz, s64.X);
-    s64.ex.assign(1, 0);
-    for (int64_t b : bnnz) s64.ex.push_back(s64.ex.back() + b);
-    int64_t N = off;
-    if (o.scale_1norm) {
-      w.norm_work.ensure(sizeof(unsigned long long) * size_t(2 * N + 4 * count), s);
-      w.norm.ensure(sizeof(double) * size_t(count), s);
-      std::vector<double> nrm(count);
-      {
-        ProfScope ps(KC_NORM, s);
-        launch_onenorm(count, s64.d_moff.as<int64_t>(), s64.d_seg.as<int32_t>(), N, s64.X.d_rp(),
-                       s64.X.d_col(), s64.X.d_val(), w.norm_work.as<unsigned long long>(),
-                       w.norm.as<double>(), s);
-      }
-      d2h(nrm.data(), w.norm.p, size_t(count), s);
-      sync(s);
-      for (int i = 0; i < count; ++i)
-        if (!(nrm[i] > 0.0) || !std::isfinite(nrm[i]))
-          throw Error(SIGN_EINVAL, "matrix " + std::to_string(i) + " has no finite nonzero 1-norm");
-      launch_scale(N, s64.d_seg.as<int32_t>(), s64.X.d_rp(), s64.X.d_val(), w.norm.as<double>(), s);
-    }
-    if (o.prec == SIGN_PREC_MIXED) {
-      int64_t nnz = 0;
-      for (int64_t b : bnnz) nnz += b;
-      std::vector<AsmBlock> b1{AsmBlock{s64.X.d_rp(), s64.X.d_col(), s64.X.val.p, 0, N, 0, 0}};
-      assemble<float>(b1, {nnz}, s32.X);
-      s32.mats = all;
-      s32.alive.assign(count, 1);
-      s32.ex = s64.ex;
-      set_layout(s32.moff, s32.mats, s32.d_moff, s32.d_seg);
-      s64.mats.clear();
-      s64.alive.clear();
-      s64.moff.assign(1, 0);
-      s64.ex.assign(1, 0);
-    }
-    hsetup.stop();
-    for (int guard = 0; guard < 4 * o.max_iter + 16; ++guard) {
-      round<float, double>(s32, &s64);
-      round<double, double>(s64, nullptr);
-      bool any = !s64.incoming.empty();
-      for (int a : s32.alive) any |= a != 0;
-      for (int a : s64.alive) any |= a != 0;
-      if (!any) break;
-    }
-    sync(s);
-    for (int i = 0; i < count; ++i) {
-      MatState &ms = m[i];
-      if (ms.status < 0) throw Error(SIGN_ESTATE, "solve loop ended with a running matrix");
-      if (ms.info) {
-        ms.info->iters = ms.k;
-        ms.info->status = ms.status;
-        ms.info->resid = ms.resid;
-        ms.info->nnz_final = hs[i]->result.nnz;
-        ms.info->count = ms.trace_count;
-      }
-    }
-  }
-};
-
 }  // namespace
 
 namespace sgn {
@@ -803,6 +31,10 @@ bool valid_opts(const sign_opts *o, std::string &why) {
 }
 
 }  // namespace
+
+namespace sgn {
+bool check_opts(const sign_opts *o, std::string &why) { return valid_opts(o, why); }
+}  // namespace sgn
 
 extern "C" {
 
