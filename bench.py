@@ -188,7 +188,7 @@ def serve_leg(sg, rates, seconds: float, seed: int = 7):
                     if e.status != sg.SIGN_ENOMEM:
                         raise
                     refused += 1
-            lat, done, bad = [], [], 0
+            lat, done, lanes, bad = [], [], [], 0
             for t, ta in zip(tickets, t_arr):
                 r = None
                 while r is None:
@@ -196,17 +196,27 @@ def serve_leg(sg, rates, seconds: float, seed: int = 7):
                 bad += r["status"] != sg.SIGN_OK
                 lat.append(r["t_done"] - ta)
                 done.append(r["t_done"])
+                lanes.append(r["lane"])
             st = srv.stats()
-        lat_ms = np.array(lat) * 1e3
+        lat_ms, lanes = np.array(lat) * 1e3, np.array(lanes)
         span = (max(done) - t0) if done else float("nan")
-        out.append({"rate_req_per_s": rate, "requests": k, "refused": refused,
-                    "completed": len(tickets), "not_converged": int(bad),
-                    "p50_ms": float(np.percentile(lat_ms, 50)) if lat else None,
-                    "p99_ms": float(np.percentile(lat_ms, 99)) if lat else None,
-                    "mean_ms": float(lat_ms.mean()) if lat else None,
-                    "solves_per_s": len(tickets) / span if done else 0.0,
-                    "max_active_seen": st["max_active_seen"], "rounds": st["rounds"]})
+
+        def pct(x):
+            if not len(x):
+                return None
+            return {"count": int(len(x)), "p50_ms": float(np.percentile(x, 50)),
+                    "p99_ms": float(np.percentile(x, 99)), "mean_ms": float(x.mean())}
+
+        row = {"rate_req_per_s": rate, "requests": k, "refused": refused,
+               "completed": len(tickets), "not_converged": int(bad),
+               "solves_per_s": len(tickets) / span if done else 0.0,
+               "max_active_seen": st["max_active_seen"], "rounds": st["rounds"]}
+        row.update(pct(lat_ms) or {})
+        row["sparse_lane"] = pct(lat_ms[lanes == 0])
+        row["fill_in_lane"] = pct(lat_ms[lanes == 1])
+        out.append(row)
     return {"mix": SERVE_MIX, "seconds_per_rate": seconds, "mem_budget_bytes": 120e9,
+            "lanes": "2: requests predicted to fill in (no Gershgorin gap) on a lane of their own",
             "latency": "completion minus scheduled arrival, both on CLOCK_MONOTONIC",
             "rates": out}
 

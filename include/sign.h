@@ -192,13 +192,14 @@ sign_status sign_dense_product(int M, int N, int K, const float *A, int lda, con
 
 /* ---- serving (not part of the paper's method) ---------------------------
  *
- * A server owns a worker thread and two CUDA streams of its own, on the
- * device current at creation. Requests are submitted from any thread;
- * the worker runs the solver's rounds continuously and admits waiting
- * requests at each round boundary, first come first served, while the sum of
- * the admitted requests' predicted footprints stays within mem_budget and
- * fewer than max_active are on the GPU. An admitted request joins the next
- * round of the entry stage beside the requests already in flight; each
+ * A server owns worker threads (one per lane) and CUDA streams of its own, on
+ * the device current at creation. Requests are submitted from any thread;
+ * each lane's worker runs its solver's rounds continuously and admits the
+ * lane's waiting requests at each round boundary, first come first served,
+ * while the sum of the admitted requests' predicted footprints stays within
+ * mem_budget and fewer than max_active are on the GPU (both shared by the
+ * lanes). An admitted request joins the next round of its lane's entry
+ * stage beside the requests already in flight; each
  * request's arithmetic is that of a lone sign_solve with the server's
  * options, so its result is the same alone or in any mix. A request whose
  * predicted footprint alone exceeds mem_budget is refused at submission.
@@ -223,11 +224,16 @@ typedef struct {
   double mem_budget; /* bytes of predicted footprints in flight (120e9)  */
   int max_active;    /* requests on the GPU at once (1024)               */
   int max_queue;     /* requests waiting for admission (65536)           */
+  int lanes;         /* 1, or 2 to give requests predicted to fill in (no
+                        Gershgorin gap, or w >= n/4 in the model above) a
+                        worker, solver and stream of their own, the other
+                        lane's stream having the higher priority (2)      */
 } sign_server_opts;
 
 typedef struct {
   double t_submit, t_admit, t_done; /* seconds on the server's steady clock */
   double footprint;                 /* predicted bytes, reserved while on the GPU */
+  int lane;                         /* lane the request ran on */
 } sign_request_times;
 
 typedef struct {
@@ -244,7 +250,7 @@ typedef struct {
 double sign_footprint_bytes(int64_t n, int64_t nnz, double delta, double rho, int64_t bw);
 
 /* Defaults: sign_default_opts with SIGN_PREC_MIXED, mem_budget 120e9,
- * max_active 1024, max_queue 65536. */
+ * max_active 1024, max_queue 65536, lanes 2. */
 void sign_server_default_opts(sign_server_opts *o);
 
 /* Starts a server. SIGN_EINVAL for bad options. */

@@ -281,7 +281,7 @@ class Server:
     """
 
     def __init__(self, opts=None, mem_budget: float = 120e9, max_active: int = 1024,
-                 max_queue: int = 65536, **kw):
+                 max_queue: int = 65536, lanes: int = 2, **kw):
         L = load()
         so = N.sign_server_opts()
         L.sign_server_default_opts(C.byref(so))
@@ -294,6 +294,7 @@ class Server:
                                              if k == "prec" and isinstance(v, str) else v)
                                         for k, v in kw.items()})
         so.mem_budget, so.max_active, so.max_queue = float(mem_budget), int(max_active), int(max_queue)
+        so.lanes = int(lanes)
         self.opts = so
         self.h = C.c_void_p()
         st = L.sign_server_create(C.byref(so), C.byref(self.h))
@@ -329,7 +330,8 @@ class Server:
             raise SignError(st, "sign_server_poll")
         return {"status": info.status, "iters": info.iters, "resid": info.resid,
                 "nnz_final": info.nnz_final, "t_submit": times.t_submit,
-                "t_admit": times.t_admit, "t_done": times.t_done, "footprint": times.footprint}
+                "t_admit": times.t_admit, "t_done": times.t_done, "footprint": times.footprint,
+                "lane": times.lane}
 
     def take(self, ticket: int, device: bool = False):
         """The finished request's result CSR (rowptr, col, val); forgets the ticket."""

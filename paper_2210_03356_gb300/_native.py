@@ -39,12 +39,12 @@ class sign_info(C.Structure):
 
 class sign_server_opts(C.Structure):
     _fields_ = [("solve", sign_opts), ("mem_budget", C.c_double), ("max_active", C.c_int),
-                ("max_queue", C.c_int)]
+                ("max_queue", C.c_int), ("lanes", C.c_int)]
 
 
 class sign_request_times(C.Structure):
     _fields_ = [("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
-                ("footprint", C.c_double)]
+                ("footprint", C.c_double), ("lane", C.c_int)]
 
 
 class sign_server_stats(C.Structure):

@@ -1,14 +1,20 @@
 // Serving: continuous batching of sign solves on one GPU.
 //
-// A worker thread owns one Solver and runs its rounds back to back. Between
-// rounds it admits queued requests (first come first served) while their
-// predicted footprints fit the memory budget and the number on the GPU stays
-// below max_active; an admitted request joins the next round of the entry
-// stage beside those already in flight, and leaves the round it stops in.
-// Submission (copy, validation, footprint statistics) runs on the
-// submitting thread with the server's upload stream, so the worker never
-// waits for it. Per-matrix arithmetic is that of a lone solve, so a result
-// does not depend on the requests it shared rounds with.
+// The server has one or two lanes. Each lane is a worker thread that owns a
+// Solver and a CUDA stream and runs the solver's rounds back to back; between
+// rounds it admits requests from its own queue (first come first served)
+// while the predicted footprints of everything on the GPU fit the memory
+// budget and fewer than max_active requests are in flight. An admitted
+// request joins the next round of the entry stage beside those already in
+// flight, and leaves the round it stops in. With two lanes, requests whose
+// iterate is predicted to fill in (no Gershgorin gap, or a predicted quarter
+// of the row or more) go to the second lane: their rounds are long (dense
+// products, FP64 finish), and on a lane of their own they do not hold up the
+// rounds of sparse requests; the two streams overlap on the device.
+// Submission (copy, validation, footprint statistics) runs on the submitting
+// thread with the server's upload stream, so the workers never wait for it.
+// Per-matrix arithmetic is that of a lone solve, so a result does not depend
+// on the requests it shared rounds with.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -34,8 +40,24 @@ struct Request {
   int state = RQ_QUEUED;
 };
 
+struct Lane {
+  int idx = 0;
+  cudaStream_t stream = nullptr;
+  std::thread worker;
+  std::deque<Request *> queue;
+  std::unordered_map<int, Request *> by_mat;  // solver id -> request on the GPU
+  int64_t active = 0;
+};
+
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Predicted entries per row of the filtered iterate (the footprint model).
+double predicted_width(int64_t n, double delta, double rho, int64_t bw) {
+  if (!(delta > 0.0) || !std::isfinite(delta) || !std::isfinite(rho)) return double(n);
+  double band = std::ceil(1.5 * (rho / delta) * (2.0 * double(bw) + 1.0));
+  return std::min(double(n), std::max(32.0, band));
 }
 
 }  // namespace
@@ -43,23 +65,26 @@ double now_s() {
 struct sign_server_s {
   sign_server_opts o;
   int device = 0;
-  cudaStream_t stream = nullptr, upload = nullptr;
-  std::thread worker;
+  cudaStream_t upload = nullptr;
+  std::vector<std::unique_ptr<Lane>> lanes;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<Request *> queue;
   std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;  // every ticket not yet taken
-  std::unordered_map<int, Request *> by_mat;                    // solver id -> request on the GPU
   uint64_t next_ticket = 1;
   bool stop = false;
   sign_server_stats st{};
 
-  void serve();
-  void finish(Request *r, const MatState *ms, int status);
+  void serve(Lane &L);
+  void finish(Lane &L, Request *r, const MatState *ms, int status);
+  int64_t queued() const {
+    int64_t q = 0;
+    for (const auto &l : lanes) q += int64_t(l->queue.size());
+    return q;
+  }
 };
 
 // Marks a request done (caller holds mu) and releases its reservation.
-void sign_server_s::finish(Request *r, const MatState *ms, int status) {
+void sign_server_s::finish(Lane &L, Request *r, const MatState *ms, int status) {
   r->info.status = status;
   if (ms) {
     r->info.iters = ms->k;
@@ -69,16 +94,17 @@ void sign_server_s::finish(Request *r, const MatState *ms, int status) {
   r->info.nnz_final = r->h->has_result ? r->h->result.nnz : 0;
   r->t.t_done = now_s();
   r->state = RQ_DONE;
+  L.active--;
   st.active--;
   st.completed++;
   st.reserved = st.active > 0 ? std::max(0.0, st.reserved - r->t.footprint) : 0.0;
 }
 
-void sign_server_s::serve() {
+void sign_server_s::serve(Lane &L) {
   cudaSetDevice(device);
   auto fresh = [&] {
     auto sv = std::make_unique<Solver>();
-    sv->s = stream;
+    sv->s = L.stream;
     sv->o = o.solve;
     return sv;
   };
@@ -87,21 +113,27 @@ void sign_server_s::serve() {
     std::vector<Request *> adm;
     {
       std::unique_lock<std::mutex> lk(mu);
-      cv_work.wait(lk, [&] { return stop || !queue.empty() || st.active > 0; });
-      if (stop && st.active == 0) break;
-      while (!stop && !queue.empty()) {
-        Request *r = queue.front();
-        if (st.active >= o.max_active || st.reserved + r->t.footprint > o.mem_budget) break;
-        queue.pop_front();
-        r->state = RQ_ACTIVE;
-        r->t.t_admit = now_s();
-        st.reserved += r->t.footprint;
-        st.active++;
-        st.admitted++;
-        adm.push_back(r);
+      for (;;) {
+        if (stop && L.active == 0) break;
+        while (!stop && !L.queue.empty()) {
+          Request *r = L.queue.front();
+          if (st.active >= o.max_active || st.reserved + r->t.footprint > o.mem_budget) break;
+          L.queue.pop_front();
+          r->state = RQ_ACTIVE;
+          r->t.t_admit = now_s();
+          st.reserved += r->t.footprint;
+          st.active++;
+          L.active++;
+          st.admitted++;
+          adm.push_back(r);
+        }
+        st.queued = queued();
+        if (st.active > st.max_active_seen) st.max_active_seen = st.active;
+        if (!adm.empty() || L.active > 0) break;
+        // nothing to run: wait for a submission, freed budget or the stop
+        cv_work.wait(lk);
       }
-      st.queued = int64_t(queue.size());
-      if (st.active > st.max_active_seen) st.max_active_seen = st.active;
+      if (adm.empty() && L.active == 0) break;  // stopping
     }
     try {
       if (!adm.empty()) {
@@ -112,46 +144,57 @@ void sign_server_s::serve() {
           infos.push_back(&r->info);
         }
         std::vector<int> ids = sv->admit(hs, infos, false);
-        for (size_t i = 0; i < ids.size(); ++i) by_mat[ids[i]] = adm[i];
+        for (size_t i = 0; i < ids.size(); ++i) L.by_mat[ids[i]] = adm[i];
         adm.clear();
       }
-      if (sv->busy()) {
+      const bool ran = sv->busy();
+      if (ran) {
         sv->step();
       } else if (sv->retired.empty()) {
         std::lock_guard<std::mutex> lk(mu);
-        if (!by_mat.empty()) throw Error(SIGN_ESTATE, "requests on the GPU but nothing to run");
+        if (!L.by_mat.empty()) throw Error(SIGN_ESTATE, "requests on the GPU but nothing to run");
       }
       std::vector<int> fin = sv->collect();
-      if (!fin.empty()) SGN_CUDA(cudaStreamSynchronize(stream));  // results complete
-      std::lock_guard<std::mutex> lk(mu);
-      st.rounds++;
-      for (int id : fin) {
-        auto it = by_mat.find(id);
-        if (it == by_mat.end()) continue;
-        Request *r = it->second;
-        by_mat.erase(it);
-        r->h->a.rp.release();  // the input is no longer needed
-        r->h->a.col.release();
-        r->h->a.val.release();
-        finish(r, &sv->m[id], sv->m[id].status);
+      if (!fin.empty()) SGN_CUDA(cudaStreamSynchronize(L.stream));  // results complete
+      bool freed = false;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        st.rounds += ran;
+        for (int id : fin) {
+          auto it = L.by_mat.find(id);
+          if (it == L.by_mat.end()) continue;
+          Request *r = it->second;
+          L.by_mat.erase(it);
+          r->h->a.rp.release();  // the input is no longer needed
+          r->h->a.col.release();
+          r->h->a.val.release();
+          finish(L, r, &sv->m[id], sv->m[id].status);
+          freed = true;
+        }
       }
-      if (!fin.empty()) cv_done.notify_all();
+      if (freed) {
+        cv_done.notify_all();
+        cv_work.notify_all();  // budget and slots freed: the other lane may admit
+      }
     } catch (const std::exception &e) {
-      // the round failed: every request on the GPU fails with it, and the
-      // solver starts over empty
+      // the round failed: every request of this lane on the GPU fails with it,
+      // and the lane's solver starts over empty
       int status = SIGN_ECUDA;
       if (const Error *er = dynamic_cast<const Error *>(&e)) status = er->status;
-      cudaStreamSynchronize(stream);
+      cudaStreamSynchronize(L.stream);
       cudaGetLastError();
-      std::lock_guard<std::mutex> lk(mu);
-      for (auto &kv : by_mat) adm.push_back(kv.second);
-      for (Request *r : adm) {  // by_mat, and admitted requests the solver never took
-        r->h->has_result = false;
-        finish(r, nullptr, status);
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto &kv : L.by_mat) adm.push_back(kv.second);
+        for (Request *r : adm) {  // by_mat, and admitted requests the solver never took
+          r->h->has_result = false;
+          finish(L, r, nullptr, status);
+        }
+        L.by_mat.clear();
       }
-      by_mat.clear();
       sv = fresh();
       cv_done.notify_all();
+      cv_work.notify_all();
     }
   }
 }
@@ -159,12 +202,7 @@ void sign_server_s::serve() {
 extern "C" {
 
 double sign_footprint_bytes(int64_t n, int64_t nnz, double delta, double rho, int64_t bw) {
-  double w = double(n);
-  if (delta > 0.0 && std::isfinite(delta) && std::isfinite(rho)) {
-    double band = std::ceil(1.5 * (rho / delta) * (2.0 * double(bw) + 1.0));
-    w = std::min(double(n), std::max(32.0, band));
-  }
-  return 96.0 * double(n) * w + 24.0 * double(nnz);
+  return 96.0 * double(n) * predicted_width(n, delta, rho, bw) + 24.0 * double(nnz);
 }
 
 void sign_server_default_opts(sign_server_opts *o) {
@@ -174,6 +212,7 @@ void sign_server_default_opts(sign_server_opts *o) {
   o->mem_budget = 120e9;
   o->max_active = 1024;
   o->max_queue = 65536;
+  o->lanes = 2;
 }
 
 sign_status sign_server_create(const sign_server_opts *o, sign_server_t *out) {
@@ -183,21 +222,46 @@ sign_status sign_server_create(const sign_server_opts *o, sign_server_t *out) {
   std::string why;
   if (!o) return set_last_error("opts is NULL"), SIGN_EINVAL;
   if (!check_opts(&o->solve, why)) return set_last_error(why), SIGN_EINVAL;
-  if (!(o->mem_budget > 0.0) || o->max_active < 1 || o->max_queue < 1)
-    return set_last_error("need mem_budget > 0, max_active >= 1, max_queue >= 1"), SIGN_EINVAL;
+  if (!(o->mem_budget > 0.0) || o->max_active < 1 || o->max_queue < 1 || o->lanes < 1 ||
+      o->lanes > 2)
+    return set_last_error("need mem_budget > 0, max_active >= 1, max_queue >= 1, lanes 1 or 2"),
+           SIGN_EINVAL;
   auto S = std::make_unique<sign_server_s>();
   S->o = *o;
-  if (cudaGetDevice(&S->device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&S->upload, cudaStreamNonBlocking) != cudaSuccess) {
-    if (S->stream) cudaStreamDestroy(S->stream);
+  // the sparse lane (and submission) at the highest stream priority: when
+  // both lanes have work, the block scheduler serves the short rounds first
+  // and the fill-in lane takes the rest of the device
+  int least = 0, greatest = 0;
+  bool ok = cudaGetDevice(&S->device) == cudaSuccess &&
+            cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+            cudaStreamCreateWithPriority(&S->upload, cudaStreamNonBlocking, greatest) ==
+                cudaSuccess;
+  for (int i = 0; ok && i < o->lanes; ++i) {
+    auto L = std::make_unique<Lane>();
+    L->idx = i;
+    ok = cudaStreamCreateWithPriority(&L->stream, cudaStreamNonBlocking,
+                                      i == 0 ? greatest : least) == cudaSuccess;
+    if (ok) S->lanes.push_back(std::move(L));
+  }
+  auto drop_streams = [&] {
+    for (auto &L : S->lanes) cudaStreamDestroy(L->stream);
+    if (S->upload) cudaStreamDestroy(S->upload);
+  };
+  if (!ok) {
+    drop_streams();
     return set_last_error("stream creation failed"), SIGN_ECUDA;
   }
   try {
-    S->worker = std::thread([p = S.get()] { p->serve(); });
+    for (auto &L : S->lanes) L->worker = std::thread([p = S.get(), l = L.get()] { p->serve(*l); });
   } catch (const std::exception &e) {
-    cudaStreamDestroy(S->stream);
-    cudaStreamDestroy(S->upload);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->stop = true;
+    }
+    S->cv_work.notify_all();
+    for (auto &L : S->lanes)
+      if (L->worker.joinable()) L->worker.join();
+    drop_streams();
     return set_last_error(e.what()), SIGN_ENOMEM;
   }
   *out = S.release();
@@ -211,7 +275,7 @@ sign_status sign_server_submit(sign_server_t S, int64_t n, int64_t nnz, const in
   sign_t h = nullptr;
   sign_status st = sign_create(n, nnz, rowptr, col, val, on_device, S->upload, &h);
   if (st != SIGN_OK) return st;  // sign_create has set the message
-  double fp = 0.0;
+  double fp = 0.0, width = 0.0;
   try {
     DevBuf g;
     GershStats init{0x7FF0000000000000ull, 0ull, 0, 0}, res;
@@ -220,18 +284,20 @@ sign_status sign_server_submit(sign_server_t S, int64_t n, int64_t nnz, const in
     launch_gersh(n, h->a.d_rp(), h->a.d_col(), h->a.d_val(), g.as<GershStats>(), S->upload);
     SGN_CUDA(cudaMemcpyAsync(&res, g.p, sizeof(res), cudaMemcpyDeviceToHost, S->upload));
     SGN_CUDA(cudaStreamSynchronize(S->upload));
-    double delta;
+    double delta, rho;
     std::memcpy(&delta, &res.min_gap_bits, sizeof(double));
-    double rho;
     std::memcpy(&rho, &res.max_rowsum_bits, sizeof(double));
-    fp = sign_footprint_bytes(n, nnz, res.nogap ? 0.0 : delta, rho, res.max_bw);
+    if (res.nogap) delta = 0.0;
+    width = predicted_width(n, delta, rho, res.max_bw);
+    fp = sign_footprint_bytes(n, nnz, delta, rho, res.max_bw);
   } catch (const Error &e) {
     sign_destroy(h);
     return set_last_error(e.what()), sign_status(e.status);
   }
+  const int lane = (S->lanes.size() > 1 && 4.0 * width >= double(n)) ? 1 : 0;
   std::lock_guard<std::mutex> lk(S->mu);
   S->st.submitted++;
-  if (S->stop || fp > S->o.mem_budget || int64_t(S->queue.size()) >= S->o.max_queue) {
+  if (S->stop || fp > S->o.mem_budget || S->queued() >= S->o.max_queue) {
     S->st.refused++;
     char msg[160];
     if (S->stop)
@@ -249,11 +315,12 @@ sign_status sign_server_submit(sign_server_t S, int64_t n, int64_t nnz, const in
   r->h = h;
   r->t.t_submit = now_s();
   r->t.footprint = fp;
+  r->t.lane = lane;
   *ticket = S->next_ticket++;
-  S->queue.push_back(r.get());
-  S->st.queued = int64_t(S->queue.size());
+  S->lanes[lane]->queue.push_back(r.get());
+  S->st.queued = S->queued();
   S->reqs[*ticket] = std::move(r);
-  S->cv_work.notify_one();
+  S->cv_work.notify_all();
   return SIGN_OK;
 }
 
@@ -287,7 +354,7 @@ sign_status sign_server_take(sign_server_t S, uint64_t ticket, void *cuda_stream
   if (it == S->reqs.end()) return set_last_error("unknown ticket"), SIGN_EINVAL;
   if (it->second->state != RQ_DONE) return SIGN_EAGAIN;
   sign_ctx *h = it->second->h;
-  // the worker synchronized its stream before marking the request done, so the
+  // the lane synchronized its stream before marking the request done, so the
   // buffers may move to the caller's stream (which also frees them later)
   cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
   h->stream = cs;
@@ -312,8 +379,9 @@ void sign_server_destroy(sign_server_t S) {
     S->stop = true;
   }
   S->cv_work.notify_all();
-  if (S->worker.joinable()) S->worker.join();
-  cudaStreamSynchronize(S->stream);
+  for (auto &L : S->lanes)
+    if (L->worker.joinable()) L->worker.join();
+  for (auto &L : S->lanes) cudaStreamSynchronize(L->stream);
   cudaStreamSynchronize(S->upload);
   for (auto &kv : S->reqs) {  // queued or finished, not taken
     sign_ctx *h = kv.second->h;
@@ -324,7 +392,7 @@ void sign_server_destroy(sign_server_t S) {
   }
   S->reqs.clear();
   cudaStreamSynchronize(S->upload);
-  cudaStreamDestroy(S->stream);
+  for (auto &L : S->lanes) cudaStreamDestroy(L->stream);
   cudaStreamDestroy(S->upload);
   delete S;
 }

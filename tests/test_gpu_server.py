@@ -48,9 +48,10 @@ def _same(res, rp, col, val):
     assert np.array_equal(res.val, val)
 
 
-def test_results_in_the_mix_equal_lone_solves(sg):
+@pytest.mark.parametrize("lanes", [1, 2])
+def test_results_in_the_mix_equal_lone_solves(sg, lanes):
     mats = _mix(3, 16)
-    with sg.Server(tol=1e-8, filter="exact", prec="mixed") as srv:
+    with sg.Server(tol=1e-8, filter="exact", prec="mixed", lanes=lanes) as srv:
         tickets = []
 
         def feed():  # arrivals spread over the first rounds of the earlier requests
@@ -78,6 +79,8 @@ def test_results_in_the_mix_equal_lone_solves(sg):
         _same(lone, *outs[t])
         tm = done[t]
         assert tm["t_submit"] <= tm["t_admit"] <= tm["t_done"]
+        # shifted Laplacians have no Gershgorin gap: predicted dense, second lane
+        assert tm["lane"] == (1 if lanes == 2 and a.name.startswith("laplacian") else 0)
 
 
 def test_budget_admits_one_request_at_a_time(sg):
