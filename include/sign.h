@@ -190,6 +190,21 @@ sign_status sign_threshold_exact_noalloc(const double *val, int64_t nnz, double 
 sign_status sign_dense_product(int M, int N, int K, const float *A, int lda, const float *B,
                                int ldb, float *C, int ldc, void *cuda_stream);
 
+/* Dense product C = A B to about FP64 accuracy on the BF16 tensor cores: the
+ * dense path (a9) of the FP64 stage. A (M x K), B (K x N) and C (M x N) are
+ * row-major FP64 device arrays with leading dimensions lda, ldb, ldc
+ * (elements). Each row of A and each column of B is scaled by a power of
+ * two and cut into eight 7-bit integer digits (56 bits below its largest
+ * entry); the 36 digit pairs of highest weight are multiplied exactly (BF16
+ * digits, FP32 sums that stay integers below 2^24) and summed in FP64. The
+ * error of an entry stays below about 2^-41 (K/4096) 2^(e_i + f_j), with
+ * 2^e_i, 2^f_j bounding row i of A and column j of B (an FP64 dot product's
+ * bound). Needs K <= 4096, N and ldc even and C 16-byte aligned, else
+ * SIGN_EINVAL; SIGN_ETIMEOUT if a bounded wait on the tensor cores gave up.
+ * Returns after cuda_stream has finished. */
+sign_status sign_dense_product_f64(int M, int N, int K, const double *A, int lda, const double *B,
+                                   int ldb, double *C, int ldc, void *cuda_stream);
+
 /* ---- serving (not part of the paper's method) ---------------------------
  *
  * A server owns worker threads (one per lane) and CUDA streams of its own, on

@@ -226,6 +226,22 @@ def dense_product(a, b, out=None, stream=None):
     return out
 
 
+def dense_product_f64(a, b, out=None, stream=None):
+    """sign_dense_product_f64 for CUDA torch float64 matrices (row-major)."""
+    import torch
+    M, K = a.shape
+    K2, N = b.shape
+    assert K == K2 and a.dtype == b.dtype == torch.float64 and a.is_cuda and b.is_cuda
+    if out is None:
+        out = torch.empty(M, N, dtype=torch.float64, device=a.device)
+    st = load().sign_dense_product_f64(M, N, K, _ptr(a), a.stride(0), _ptr(b), b.stride(0),
+                                       _ptr(out), out.stride(0),
+                                       stream if stream is not None else current_stream())
+    if st != SIGN_OK:
+        raise SignError(st, "sign_dense_product_f64")
+    return out
+
+
 def kernel_launches() -> int:
     return int(load().sign_kernel_launches())
 

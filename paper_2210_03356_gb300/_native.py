@@ -79,6 +79,8 @@ SIGNATURES = {
                                                C.POINTER(C.c_double)]),
     "sign_dense_product": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
                                      C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
+    "sign_dense_product_f64": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                         C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     "sign_footprint_bytes": (C.c_double, [C.c_int64, C.c_int64, C.c_double, C.c_double,
                                           C.c_int64]),
     "sign_server_default_opts": (None, [C.POINTER(sign_server_opts)]),

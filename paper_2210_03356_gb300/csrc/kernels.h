@@ -221,6 +221,35 @@ void launch_dense_jobs(int njobs, const DenseJob *jobs_host, DenseJob *jobs_dev,
 void launch_split(int rows, int cols, const float *in, int ldi, int transpose, float *hi,
                   float *lo, int ldo, cudaStream_t s);
 
+// ---------------------------------------------------------------- dense FP64 (a9)
+// C = A Bt^T to about FP64 accuracy on the BF16 tensor cores from exact
+// integer digits (see kernels_f64x.cu). The rows of A and of Bt are given as
+// F64X_DIGITS digit planes, each rows x ld BF16 (plane s - 1 of an array of
+// `rows` rows starts at row (s - 1) rows), with per-row scale exponents ea,
+// eb (a_ik ~= 2^ea_i sum_s d_ik^(s) 2^(-7 s)). C is FP64, written (not
+// accumulated), K <= F64X_MAX_K, lda and ldb multiples of 8, N and ldc even,
+// C 16-byte and eb 8-byte aligned.
+constexpr int F64X_DIGITS = 8;
+constexpr int F64X_MAX_K = 4096;
+struct SliceJob {
+  int M, N, K;
+  const uint16_t *A;
+  int lda;
+  const uint16_t *B;
+  int ldb;
+  const int *ea, *eb;
+  double *C;
+  int ldc;
+};
+size_t f64x_digits_bytes(int rows, int ld);
+size_t slice_jobs_scratch_bytes(int njobs);
+// Digit planes and scales of the rows of x (rows x K, leading dimension ldx),
+// or of its columns when transpose; digits zero for K <= k < ld.
+void launch_slices(int rows, int K, const double *x, int ldx, int transpose, uint16_t *digits,
+                   int ld, int *w, cudaStream_t s);
+void launch_slice_jobs(int njobs, const SliceJob *jobs_host, SliceJob *jobs_dev, void *scratch,
+                       int *err, cudaStream_t s);
+
 // The dense blocks of one matrix on the dense path, n x n with leading
 // dimension ld (a multiple of 4): X and X^T split, T^T = (X X)^T split, and
 // P = X T.

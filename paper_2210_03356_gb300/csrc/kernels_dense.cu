@@ -35,11 +35,14 @@
 
 #include "../../include/sign.h"
 #include "common.cuh"
+#include "tc.cuh"
 #include "kernels.h"
 
 namespace sgn {
 
 namespace {
+
+using namespace tc;
 
 constexpr int DM = 128;   // tile rows (UMMA M)
 constexpr int DN = 256;   // tile columns (UMMA N)
@@ -51,142 +54,7 @@ constexpr int B_BYTES = DN * DK * 4;  // one 256 x 16 operand slice (16 KB)
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int DTHREADS = 192;          // producer, MMA, four epilogue warps
 constexpr uint32_t TMEM_COLS = 2 * DN; // two FP32 accumulators of 128 lanes x 256 columns
-constexpr long long WAIT_BUDGET = 4000000000LL;  // clock cycles (~2 s) per wait
 static_assert(SWIZZLE_BYTES == 64 || SWIZZLE_BYTES == 128, "one swizzle span per slice");
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
-  uint32_t ok;
-  asm volatile(
-      "{\n"
-      ".reg .pred p;\n"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                   smem_u32(dst)),
-               "r"(ncols)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-
-// D[tmem] (+)= A[smem desc] * B[smem desc]^T, kind::tf32
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n"
-      ".reg .pred p;\n"
-      "setp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
-      "}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-// 32 TMEM lanes x 32 consecutive 32-bit columns; thread t of the warp gets lane
-// (base lane + t).
-__device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major operand slice whose rows are
-// one swizzle span wide (64 or 128 bytes, the pattern TMA writes): start
-// address, stride byte offset between 8-row groups (8 x span), version 1
-// (tcgen05), swizzle mode (4 = 64 B, 2 = 128 B). The leading byte offset is
-// unused when the K extent of one MMA (8 x 4 bytes) lies inside the span; a
-// K step inside the span advances the start address by 32 bytes.
-__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t saddr) {
-  constexpr uint64_t mode = SWIZZLE_BYTES == 128 ? 2u : 4u;
-  uint64_t d = 0;
-  d |= uint64_t((saddr >> 4) & 0x3FFFu);
-  d |= uint64_t(1) << 16;
-  d |= uint64_t(((8 * SWIZZLE_BYTES) >> 4) & 0x3FFFu) << 32;
-  d |= uint64_t(1) << 46;
-  d |= mode << 61;
-  return d;
-}
-
-// Instruction descriptor of kind::tf32: FP32 accumulator, A and B TF32, both
-// K-major, N >> 3 and M >> 4.
-__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// 2-D TMA load of the box at (x = k, y = row) into shared memory, completing
-// on bar by transaction bytes. Out-of-range elements are filled with zeros.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
-                                            uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
 
 // hi = x rounded to nearest TF32 (10 explicit mantissa bits), lo = x - hi
 // (exact, so hi + lo == x).
@@ -196,30 +64,6 @@ __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
   hi = __uint_as_float(r);
   if (!isfinite(hi)) hi = x;
   lo = __fsub_rn(x, hi);
-}
-
-// Waits for phase parity `ph` of `bar`. Gives up, raising *abort, when the
-// clock budget runs out, and returns false at once when another role has
-// raised *abort.
-__device__ __forceinline__ bool bounded_wait(uint64_t *bar, uint32_t ph, volatile int *abort) {
-  long long t0 = clock64();
-  while (!mbar_try_wait(bar, ph)) {
-    if (*abort) return false;
-    if (clock64() - t0 > WAIT_BUDGET) {
-      *abort = 1;
-      return false;
-    }
-  }
-  return true;
-}
-
-// Waits for phase parity `ph` of `bar` for at most `budget` clock cycles,
-// whatever the abort flag says (draining work already issued).
-__device__ __forceinline__ bool drain_wait(uint64_t *bar, uint32_t ph, long long budget) {
-  long long t0 = clock64();
-  while (!mbar_try_wait(bar, ph))
-    if (clock64() - t0 > budget) return false;
-  return true;
 }
 
 // Tile t of the launch -> job and tile origin (m0, n0); M blocks run fastest.
@@ -318,9 +162,9 @@ __global__ void __launch_bounds__(DTHREADS, 1)
 #pragma unroll
           for (int s = 0; s < DK / 8; ++s) {
             const uint32_t ko = uint32_t(s) * 32u;
-            const uint64_t ah = smem_desc_sw(d + ko), al = smem_desc_sw(d + A_BYTES + ko);
-            const uint64_t bh = smem_desc_sw(d + 2 * A_BYTES + ko);
-            const uint64_t bl = smem_desc_sw(d + 2 * A_BYTES + B_BYTES + ko);
+            const uint64_t ah = smem_desc_sw<SWIZZLE_BYTES>(d + ko), al = smem_desc_sw<SWIZZLE_BYTES>(d + A_BYTES + ko);
+            const uint64_t bh = smem_desc_sw<SWIZZLE_BYTES>(d + 2 * A_BYTES + ko);
+            const uint64_t bl = smem_desc_sw<SWIZZLE_BYTES>(d + 2 * A_BYTES + B_BYTES + ko);
             mma_tf32(acc, ah, bh, idesc, (kb | s) != 0 ? 1u : 0u);
             mma_tf32(acc, ah, bl, idesc, 1u);
             mma_tf32(acc, al, bh, idesc, 1u);
@@ -542,44 +386,6 @@ static size_t scratch_maps(int njobs) {
 
 size_t dense_jobs_scratch_bytes(int njobs) { return scratch_maps(njobs) * sizeof(CUtensorMap); }
 
-namespace {
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiled encode_tiled() {
-  static EncodeTiled fn = [] {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    SGN_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                              cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !p)
-      throw Error(SIGN_ECUDA, "cuTensorMapEncodeTiled is not available");
-    return reinterpret_cast<EncodeTiled>(p);
-  }();
-  return fn;
-}
-
-// Row-major rows x K FP32 array with leading dimension ld, read in boxes of
-// DK x box_rows with the swizzle of one span.
-CUtensorMap operand_map(const float *base, int rows, int K, int ld, int box_rows) {
-  CUtensorMap m;
-  cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(rows)};
-  cuuint64_t strides[1] = {cuuint64_t(ld) * sizeof(float)};
-  cuuint32_t box[2] = {cuuint32_t(DK), cuuint32_t(box_rows)};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode_tiled()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base),
-                              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              SWIZZLE_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
-                                                   : CU_TENSOR_MAP_SWIZZLE_64B,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) throw Error(SIGN_ECUDA, "cuTensorMapEncodeTiled failed");
-  return m;
-}
-}  // namespace
-
 void launch_dense_jobs(int njobs, const DenseJob *jobs_host, DenseJob *jobs_dev, void *scratch,
                        int *err, cudaStream_t s) {
   if (njobs <= 0) return;
@@ -600,10 +406,11 @@ void launch_dense_jobs(int njobs, const DenseJob *jobs_host, DenseJob *jobs_dev,
     const DenseJob &J = jobs_host[j];
     if (J.M <= 0 || J.N <= 0 || J.K <= 0 || J.lda % 4 || J.ldb % 4 || J.ldc % 4 || J.N % 4)
       throw Error(SIGN_EINVAL, "dense job with bad shape");
-    maps[4 * j + 0] = operand_map(J.A_hi, J.M, J.K, J.lda, DM);
-    maps[4 * j + 1] = operand_map(J.A_lo, J.M, J.K, J.lda, DM);
-    maps[4 * j + 2] = operand_map(J.B_hi, J.N, J.K, J.ldb, DN);
-    maps[4 * j + 3] = operand_map(J.B_lo, J.N, J.K, J.ldb, DN);
+    const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    maps[4 * j + 0] = tc::operand_map(J.A_hi, f32, 4, J.M, J.K, J.lda, DK, DM);
+    maps[4 * j + 1] = tc::operand_map(J.A_lo, f32, 4, J.M, J.K, J.lda, DK, DM);
+    maps[4 * j + 2] = tc::operand_map(J.B_hi, f32, 4, J.N, J.K, J.ldb, DK, DN);
+    maps[4 * j + 3] = tc::operand_map(J.B_lo, f32, 4, J.N, J.K, J.ldb, DK, DN);
     tile_start[j] = ntiles;
     ntiles += ((J.M + DM - 1) / DM) * ((J.N + DN - 1) / DN);
   }

@@ -34,6 +34,7 @@ const char *kNames[KC_COUNT] = {"numeric_square_f64", "numeric_update_f64", "num
                                 "select_hist",        "select_extract",     "select_digits",
                                 "select_bound",       "filter",             "reduce",
                                 "assemble",           "onenorm",            "dense_tf32x3",
+                                "dense_f64_slices",
                                 "host_setup",
                                 "host_check",         "host_decide",        "host_update",
                                 "host_filter",        "host_rebuild"};
