@@ -53,7 +53,7 @@ typedef enum {
   SIGN_EDIVERGED = 4, /* residual non-finite or above div_limit (Sec. 2:
                          convergence needs ||I - X_1^2|| < 1)                 */
   SIGN_ECUDA = 5,     /* a CUDA runtime call failed                          */
-  SIGN_ETIMEOUT = 6,  /* reserved: a bounded device wait gave up             */
+  SIGN_ETIMEOUT = 6,  /* a bounded wait of a tensor-core kernel gave up     */
   SIGN_ESTATE = 7,    /* call out of order (e.g. sign_get_csr before solve)  */
   SIGN_EAGAIN = 8     /* server: the request has not finished yet            */
 } sign_status;

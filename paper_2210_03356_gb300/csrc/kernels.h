@@ -250,6 +250,33 @@ void launch_slices(int rows, int K, const double *x, int ldx, int transpose, uin
 void launch_slice_jobs(int njobs, const SliceJob *jobs_host, SliceJob *jobs_dev, void *scratch,
                        int *err, cudaStream_t s);
 
+int f64x_pairs();  // digit pairs one product multiplies
+
+// The dense blocks of one matrix on the dense path of the FP64 stage, n x n
+// with leading dimension ld (a multiple of 8): X, X^T, T^T = (X X)^T and
+// P = X T in FP64, and the digit planes and scale exponents of X, X^T, T^T.
+struct DenseBuf64 {
+  double *X, *XT, *TT, *P;
+  uint16_t *dX, *dXT, *dTT;
+  int *eX, *eXT, *eTT;
+  int n, ld;
+};
+// The FP64 stage's CSR rows of the dense-path matrices into their zeroed X
+// and X^T blocks.
+void launch_densify64(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                      const int64_t *rp, const int32_t *col, const double *val,
+                      const DenseBuf64 *bufs, cudaStream_t s);
+// part[2r] = sum_j (t_rj - delta_rj)^2 over row r of T^T, part[2r+1] =
+// sum_j x_rj^2 (FP64, fixed order); tcount[d] += nonzeros of T.
+void launch_dense_resid64(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                          const DenseBuf64 *bufs, double *part, unsigned long long *tcount,
+                          cudaStream_t s);
+// Xbar = 1.5 X - 0.5 P (each product and the difference rounded once), its
+// nonzeros in column order into the row slots [cs[r], ce[r]).
+void launch_dense_emit64(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                         const int *active, const DenseBuf64 *bufs, const int64_t *cs,
+                         int64_t *ce, int32_t *ccol, double *cval, cudaStream_t s);
+
 // The dense blocks of one matrix on the dense path, n x n with leading
 // dimension ld (a multiple of 4): X and X^T split, T^T = (X X)^T split, and
 // P = X T.

@@ -339,12 +339,130 @@ __global__ void k_slices(int rows, int K, const double *x, int ldx, int transpos
   }
 }
 
+// Warp-per-row helpers of the FP64 dense path (same row loop as the FP32 one).
+template <typename F>
+__device__ __forceinline__ void dense_rows(int64_t n, F f) {
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nwarps) f(r);
+}
+
+__global__ void k_densify64(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                            const int64_t *rp, const int32_t *col, const double *val,
+                            const DenseBuf64 *bufs) {
+  const int lane = threadIdx.x & 31;
+  dense_rows(n, [&](int64_t r) {
+    const int m = seg[r], d = dslot[m];
+    if (d < 0) return;
+    const DenseBuf64 B = bufs[d];
+    const int64_t r0 = moff[m], i = r - r0;
+    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) {
+      const int64_t j = col[p] - r0;
+      B.X[i * B.ld + j] = val[p];
+      B.XT[j * B.ld + i] = val[p];
+    }
+  });
+}
+
+__global__ void k_dense_resid64(int64_t n, const int32_t *seg, const int *dslot,
+                                const int64_t *moff, const DenseBuf64 *bufs, double *part,
+                                unsigned long long *tcount) {
+  const int lane = threadIdx.x & 31;
+  dense_rows(n, [&](int64_t r) {
+    const int m = seg[r], d = dslot[m];
+    if (d < 0) return;
+    const DenseBuf64 B = bufs[d];
+    const int64_t i = r - moff[m];
+    double rs = 0.0, xs = 0.0;
+    unsigned cnt = 0;
+    for (int j = lane; j < B.n; j += 32) {
+      const double t = B.TT[i * B.ld + j], x = B.X[i * B.ld + j];
+      const double e = j == i ? t - 1.0 : t;
+      rs = fma(e, e, rs);
+      xs = fma(x, x, xs);
+      cnt += t != 0.0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rs += __shfl_xor_sync(0xffffffffu, rs, o);
+      xs += __shfl_xor_sync(0xffffffffu, xs, o);
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) {
+      part[2 * r] = rs;
+      part[2 * r + 1] = xs;
+      atomicAdd(&tcount[d], (unsigned long long)cnt);
+    }
+  });
+}
+
+__global__ void k_dense_emit64(int64_t n, const int32_t *seg, const int *dslot,
+                               const int64_t *moff, const int *active, const DenseBuf64 *bufs,
+                               const int64_t *cs, int64_t *ce, int32_t *ccol, double *cval) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  dense_rows(n, [&](int64_t r) {
+    const int m = seg[r], d = dslot[m];
+    if (d < 0 || !active[m]) return;
+    const DenseBuf64 B = bufs[d];
+    const int64_t r0 = moff[m], i = r - r0;
+    int64_t out = cs[r];
+    for (int j0 = 0; j0 < B.n; j0 += 32) {
+      const int j = j0 + lane;
+      double v = 0.0;
+      if (j < B.n)
+        v = __dsub_rn(__dmul_rn(1.5, B.X[i * B.ld + j]), __dmul_rn(0.5, B.P[i * B.ld + j]));
+      const bool keep = v != 0.0;
+      const unsigned mk = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const int64_t pos = out + __popc(mk & lt);
+        ccol[pos] = int32_t(r0 + j);
+        cval[pos] = v;
+      }
+      out += __popc(mk);
+    }
+    if (lane == 0) ce[r] = out;
+  });
+}
+
+int rows_grid(int64_t n) {
+  int64_t g = (n + 7) / 8;
+  return int(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
+}
+
 size_t scratch_maps_x(int njobs) {
   return size_t(njobs) * 2 + (size_t(njobs + 1) * sizeof(int) + sizeof(CUtensorMap) - 1) /
                                  sizeof(CUtensorMap);
 }
 
 }  // namespace
+
+int f64x_pairs() { return kPairs.n; }
+
+void launch_densify64(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                      const int64_t *rp, const int32_t *col, const double *val,
+                      const DenseBuf64 *bufs, cudaStream_t s) {
+  if (n == 0) return;
+  k_densify64<<<rows_grid(n), 256, 0, s>>>(n, seg, dslot, moff, rp, col, val, bufs);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_dense_resid64(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                          const DenseBuf64 *bufs, double *part, unsigned long long *tcount,
+                          cudaStream_t s) {
+  if (n == 0) return;
+  k_dense_resid64<<<rows_grid(n), 256, 0, s>>>(n, seg, dslot, moff, bufs, part, tcount);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_dense_emit64(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
+                         const int *active, const DenseBuf64 *bufs, const int64_t *cs,
+                         int64_t *ce, int32_t *ccol, double *cval, cudaStream_t s) {
+  if (n == 0) return;
+  k_dense_emit64<<<rows_grid(n), 256, 0, s>>>(n, seg, dslot, moff, active, bufs, cs, ce, ccol,
+                                              cval);
+  SGN_LAUNCH_CHECK();
+}
 
 size_t f64x_digits_bytes(int rows, int ld) {
   return size_t(F64X_DIGITS) * size_t(rows) * size_t(ld) * sizeof(uint16_t);

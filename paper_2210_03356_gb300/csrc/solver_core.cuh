@@ -168,7 +168,8 @@ struct Work {
 // dense blocks and the batched product jobs.
 struct DensePlan {
   std::vector<int> slot;          // per matrix of the stage: dense index or -1
-  std::vector<DenseBuf> bufs;     // host copies of the device DenseBuf array
+  std::vector<DenseBuf> bufs;     // host copies of the device DenseBuf array (FP32 stage)
+  std::vector<DenseBuf64> bufs64; // ... or of the DenseBuf64 array (FP64 stage)
   std::vector<int> mat;           // stage slot of each dense matrix
   int nd = 0, max_ld = 0;
   bool any() const { return nd > 0; }
@@ -356,42 +357,84 @@ struct Solver {
     DensePlan dp;
     int nb = int(st.mats.size());
     dp.slot.assign(nb, -1);
-    if (sizeof(T) != 4 || !(o.dense_frac <= 1.0) || o.filter == SIGN_FILTER_NONE) return dp;
-    size_t total = 0;
+    if (!(o.dense_frac <= 1.0) || o.filter == SIGN_FILTER_NONE) return dp;
+    constexpr bool f32 = sizeof(T) == 4;
+    size_t total = 0;  // bytes
+    auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+    // FP32: X, X^T, T^T split hi/lo and P; FP64: X, X^T, T^T, P, the digit
+    // planes of X, X^T, T^T and their row exponents
+    auto bytes_of = [&](size_t ld) {
+      return f32 ? 7 * 4 * ld * ld
+                 : 4 * r256(8 * ld * ld) + 3 * r256(f64x_digits_bytes(int(ld), int(ld))) +
+                       3 * r256(4 * ld);
+    };
     for (int i = 0; i < nb; ++i) {
       if (!st.alive[i]) continue;
       int64_t n = st.moff[i + 1] - st.moff[i];
       int64_t nnz = st.ex[i + 1] - st.ex[i];
       if (n > 4096 || double(nnz) < o.dense_frac * double(n) * double(n)) continue;
-      int ld = int((n + 3) / 4 * 4);
+      int ld = f32 ? int((n + 3) / 4 * 4) : int((n + 7) / 8 * 8);
       dp.slot[i] = dp.nd++;
       dp.mat.push_back(i);
-      DenseBuf b = {};
-      b.n = int(n);
-      b.ld = ld;
-      dp.bufs.push_back(b);
+      if (f32) {
+        DenseBuf b = {};
+        b.n = int(n);
+        b.ld = ld;
+        dp.bufs.push_back(b);
+      } else {
+        DenseBuf64 b = {};
+        b.n = int(n);
+        b.ld = ld;
+        dp.bufs64.push_back(b);
+      }
       dp.max_ld = std::max(dp.max_ld, ld);
-      total += 7 * size_t(ld) * size_t(ld);
+      total += bytes_of(size_t(ld));
     }
     if (!dp.nd) return dp;
-    float *mem = static_cast<float *>(w.dmem.ensure(sizeof(float) * total, s));
+    unsigned char *mem = static_cast<unsigned char *>(w.dmem.ensure(total, s));
     size_t off = 0;
-    for (DenseBuf &b : dp.bufs) {
-      size_t blk = size_t(b.ld) * size_t(b.ld);
-      float *base = mem + off;
-      b.X_hi = base;
-      b.X_lo = base + blk;
-      b.XT_hi = base + 2 * blk;
-      b.XT_lo = base + 3 * blk;
-      b.TT_hi = base + 4 * blk;
-      b.TT_lo = base + 5 * blk;
-      b.P = base + 6 * blk;
-      off += 7 * blk;
+    if (f32) {
+      for (DenseBuf &b : dp.bufs) {
+        size_t blk = size_t(b.ld) * size_t(b.ld);
+        float *base = reinterpret_cast<float *>(mem + off);
+        b.X_hi = base;
+        b.X_lo = base + blk;
+        b.XT_hi = base + 2 * blk;
+        b.XT_lo = base + 3 * blk;
+        b.TT_hi = base + 4 * blk;
+        b.TT_lo = base + 5 * blk;
+        b.P = base + 6 * blk;
+        off += bytes_of(size_t(b.ld));
+      }
+    } else {
+      for (DenseBuf64 &b : dp.bufs64) {
+        const size_t ld = size_t(b.ld), fb = r256(8 * ld * ld);
+        const size_t db = r256(f64x_digits_bytes(b.ld, b.ld)), eb = r256(4 * ld);
+        unsigned char *p = mem + off;
+        b.X = reinterpret_cast<double *>(p);  // X and X^T adjacent: zeroed together
+        b.XT = reinterpret_cast<double *>(p + fb);
+        b.TT = reinterpret_cast<double *>(p + 2 * fb);
+        b.P = reinterpret_cast<double *>(p + 3 * fb);
+        p += 4 * fb;
+        b.dX = reinterpret_cast<uint16_t *>(p);
+        b.dXT = reinterpret_cast<uint16_t *>(p + db);
+        b.dTT = reinterpret_cast<uint16_t *>(p + 2 * db);
+        p += 3 * db;
+        b.eX = reinterpret_cast<int *>(p);
+        b.eXT = reinterpret_cast<int *>(p + eb);
+        b.eTT = reinterpret_cast<int *>(p + 2 * eb);
+        off += bytes_of(ld);
+      }
     }
     w.dslot.ensure(sizeof(int) * size_t(nb), s);
     h2d(w.dslot.p, dp.slot.data(), size_t(nb), s);
-    w.dbufs.ensure(sizeof(DenseBuf) * size_t(dp.nd), s);
-    h2d(w.dbufs.p, dp.bufs.data(), size_t(dp.nd), s);
+    if (f32) {
+      w.dbufs.ensure(sizeof(DenseBuf) * size_t(dp.nd), s);
+      h2d(w.dbufs.p, dp.bufs.data(), size_t(dp.nd), s);
+    } else {
+      w.dbufs.ensure(sizeof(DenseBuf64) * size_t(dp.nd), s);
+      h2d(w.dbufs.p, dp.bufs64.data(), size_t(dp.nd), s);
+    }
     w.dcount.ensure(sizeof(unsigned long long) * size_t(dp.nd), s);
     w.derr.ensure(sizeof(int), s);
     SGN_CUDA(cudaMemsetAsync(w.derr.p, 0, sizeof(int), s));
@@ -443,8 +486,57 @@ struct Solver {
                           C.rs.template as<int64_t>(), C.re.template as<int64_t>(),
                           C.col.template as<int32_t>(), reinterpret_cast<float *>(C.val.p), s);
       }
-      sync(s);  // the job list is a pageable host vector
+    } else {
+      int64_t N = st.moff.back();
+      std::vector<SliceJob> jobs;
+      double fl = 0.0;
+      const DenseBuf64 *bufs = w.dbufs.as<DenseBuf64>();
+      if (mode == MODE_SQUARE) {
+        // X and X^T are adjacent in each matrix's block
+        for (const DenseBuf64 &b : dp.bufs64)
+          SGN_CUDA(cudaMemsetAsync(b.X, 0, sizeof(double) * (size_t(b.XT - b.X) +
+                                                             size_t(b.ld) * size_t(b.ld)), s));
+        launch_densify64(N, st.d_seg.template as<int32_t>(), w.dslot.as<int>(),
+                         st.d_moff.template as<int64_t>(), st.X.d_rp(), st.X.d_col(),
+                         reinterpret_cast<const double *>(st.X.val.p), bufs, s);
+      }
+      for (const DenseBuf64 &b : dp.bufs64) {
+        if (mode == MODE_SQUARE) {  // T^T = X^T X^T: C = A Bt^T with A = X^T, Bt = X
+          launch_slices(b.ld, b.ld, b.X, b.ld, 0, b.dX, b.ld, b.eX, s);
+          launch_slices(b.ld, b.ld, b.XT, b.ld, 0, b.dXT, b.ld, b.eXT, s);
+          jobs.push_back(SliceJob{b.ld, b.ld, b.ld, b.dXT, b.ld, b.dX, b.ld, b.eXT, b.eX, b.TT,
+                                  b.ld});
+        } else {  // P = X T as C = A Bt^T with A = X, Bt = T^T
+          launch_slices(b.ld, b.ld, b.TT, b.ld, 0, b.dTT, b.ld, b.eTT, s);
+          jobs.push_back(SliceJob{b.ld, b.ld, b.ld, b.dX, b.ld, b.dTT, b.ld, b.eX, b.eTT, b.P,
+                                  b.ld});
+        }
+        fl += 2.0 * f64x_pairs() * double(b.ld) * double(b.ld) * double(b.ld);
+      }
+      w.djobs.ensure(sizeof(SliceJob) * jobs.size(), s);
+      w.dscratch.ensure(slice_jobs_scratch_bytes(int(jobs.size())), s);
+      {
+        ProfScope ps(KC_DENSE64, s, fl, 0.0);
+        launch_slice_jobs(int(jobs.size()), jobs.data(), w.djobs.as<SliceJob>(), w.dscratch.p,
+                          w.derr.as<int>(), s);
+      }
+      if (mode == MODE_SQUARE) {
+        SGN_CUDA(cudaMemsetAsync(w.dcount.p, 0, sizeof(unsigned long long) * size_t(dp.nd), s));
+        launch_dense_resid64(N, st.d_seg.template as<int32_t>(), w.dslot.as<int>(),
+                             st.d_moff.template as<int64_t>(), bufs, w.part.as<double>(),
+                             w.dcount.as<unsigned long long>(), s);
+      } else {
+        launch_dense_emit64(N, st.d_seg.template as<int32_t>(), w.dslot.as<int>(),
+                            st.d_moff.template as<int64_t>(), active, bufs,
+                            C.rs.template as<int64_t>(), C.re.template as<int64_t>(),
+                            C.col.template as<int32_t>(), reinterpret_cast<double *>(C.val.p), s);
+      }
     }
+    // a tensor-core wait that gave up leaves the products undefined
+    int herr = 0;
+    d2h(&herr, w.derr.p, 1, s);
+    sync(s);
+    if (herr) throw Error(SIGN_ETIMEOUT, "a bounded wait of the dense tensor-core path gave up");
   }
 
   // ---------------------------------------------------------------- rounds

@@ -112,3 +112,51 @@ def test_solver_dense_and_sparse_in_one_batch(sg, orc):
     # the sparse members are untouched by the dense path: bit for bit
     ref = orc.nsf(mats[1], tol=1e-8, filter="exact", mixed=True)
     assert np.array_equal(out[1].val, ref.val)
+
+
+# ---------------------------------------------------------------- the dense path of the FP64 stage
+def _f64_launches(sg):
+    return sg.prof_read().get("dense_f64_slices", {}).get("launches", 0)
+
+
+def _rel(S, R):
+    import numpy as np
+    return np.linalg.norm(S - R) / np.linalg.norm(R)
+
+
+@pytest.mark.parametrize("case", ["banded", "laplacian2d", "laplacian3d"])
+def test_fp64_dense_path_within_fp64_tolerance(sg, orc, case):
+    """FP64 solves whose iterate fills in run both products as exact-slice
+    tensor-core GEMMs; the result stays within the FP64 bound 1e-10 of the
+    oracle's FP64 run, at the same iteration count."""
+    import workloads as w
+    a = {"banded": w.banded(300, 10, 1234), "laplacian2d": w.laplacian(18, 2),
+         "laplacian3d": w.laplacian(7, 3)}[case]
+    tol = 1e-8
+    sg.prof_reset()
+    sg.prof_enable(True)
+    res = sg.solve(a, tol=tol, filter="exact", dense_frac=0.25, max_iter=200)
+    sg.prof_enable(False)
+    assert _f64_launches(sg) > 0
+    ref = orc.nsf(a, tol=tol, filter="exact", max_iter=200)
+    assert res.status == ref.status == sg.SIGN_OK
+    assert res.iters == ref.iters
+    assert _rel(_dense(res, a.n), ref.to_dense(a.n)) <= 1e-10
+
+
+def test_fp64_dense_and_sparse_in_one_batch_equal_lone_solves(sg, orc):
+    """Dense-path results do not depend on the batch: each equals its lone
+    solve bit for bit, and stays within 1e-10 of the oracle."""
+    import numpy as np
+    import workloads as w
+    mats = [w.banded(260, 9, 77), w.tridiagonal(900), w.laplacian(16, 2), w.banded(220, 8, 79)]
+    out = sg.solve_batch(mats, tol=1e-8, filter="exact", dense_frac=0.25)
+    for a, res in zip(mats, out):
+        alone = sg.solve(a, tol=1e-8, filter="exact", dense_frac=0.25)
+        assert np.array_equal(res.val, alone.val) and np.array_equal(res.col, alone.col)
+        ref = orc.nsf(a, tol=1e-8, filter="exact")
+        assert res.iters == ref.iters
+        assert _rel(_dense(res, a.n), ref.to_dense(a.n)) <= 1e-10
+    # the sparse member is untouched by the dense path: bit for bit with the oracle
+    ref = orc.nsf(mats[1], tol=1e-8, filter="exact")
+    assert np.array_equal(out[1].val, ref.val)
