@@ -81,9 +81,14 @@ typedef struct {
   int max_iter;        /* maximum Newton-Schulz updates; 100                 */
   int prec;            /* sign_prec; SIGN_PREC_FP64                          */
   double fp32_until;   /* FP32 stage ends below this residual; 1e-4          */
-  double dense_frac;   /* reserved for the dense path; 0.25                  */
+  double dense_frac;   /* a matrix whose iterate holds at least
+                          dense_frac n^2 entries (n <= 4096, a filter on)
+                          runs its products on the dense tensor-core path
+                          in that round; > 1 turns the path off; 0.25      */
   int scale_1norm;     /* 1: X_1 = A/||A||_1 (default); 0: X_1 = A (paper)   */
   double div_limit;    /* residual above this = diverged; 1e6                */
+  int dense64_min_n;   /* the FP64 stage's dense path (36 exact digit-pair
+                          products per tile) only for n >= this; 1024      */
 } sign_opts;
 
 /* Per-iteration record, filled by sign_solve when non-NULL. The arrays are

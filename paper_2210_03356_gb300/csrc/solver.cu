@@ -27,6 +27,7 @@ bool valid_opts(const sign_opts *o, std::string &why) {
   if (!(o->c4 >= 0.0) || !(o->switch_resid >= 0.0) || !(o->fp32_until > 0.0))
     return why = "c4, switch_resid must be >= 0 and fp32_until > 0", false;
   if (!(o->div_limit > 0.0)) return why = "div_limit must be > 0", false;
+  if (o->dense64_min_n < 0) return why = "dense64_min_n < 0", false;
   return true;
 }
 
@@ -50,6 +51,7 @@ void sign_default_opts(sign_opts *o) {
   o->dense_frac = 0.25;
   o->scale_1norm = 1;
   o->div_limit = 1e6;
+  o->dense64_min_n = 1024;
 }
 
 const char *sign_last_error(void) { return g_err.c_str(); }

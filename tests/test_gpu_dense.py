@@ -135,7 +135,7 @@ def test_fp64_dense_path_within_fp64_tolerance(sg, orc, case):
     tol = 1e-8
     sg.prof_reset()
     sg.prof_enable(True)
-    res = sg.solve(a, tol=tol, filter="exact", dense_frac=0.25, max_iter=200)
+    res = sg.solve(a, tol=tol, filter="exact", dense_frac=0.25, dense64_min_n=1, max_iter=200)
     sg.prof_enable(False)
     assert _f64_launches(sg) > 0
     ref = orc.nsf(a, tol=tol, filter="exact", max_iter=200)
@@ -150,9 +150,9 @@ def test_fp64_dense_and_sparse_in_one_batch_equal_lone_solves(sg, orc):
     import numpy as np
     import workloads as w
     mats = [w.banded(260, 9, 77), w.tridiagonal(900), w.laplacian(16, 2), w.banded(220, 8, 79)]
-    out = sg.solve_batch(mats, tol=1e-8, filter="exact", dense_frac=0.25)
+    out = sg.solve_batch(mats, tol=1e-8, filter="exact", dense_frac=0.25, dense64_min_n=1)
     for a, res in zip(mats, out):
-        alone = sg.solve(a, tol=1e-8, filter="exact", dense_frac=0.25)
+        alone = sg.solve(a, tol=1e-8, filter="exact", dense_frac=0.25, dense64_min_n=1)
         assert np.array_equal(res.val, alone.val) and np.array_equal(res.col, alone.col)
         ref = orc.nsf(a, tol=1e-8, filter="exact")
         assert res.iters == ref.iters
