@@ -221,6 +221,33 @@ def serve_leg(sg, rates, seconds: float, seed: int = 7):
             "rates": out}
 
 
+# ---------------------------------------------------------------------- fill tracking
+def fill_leg(sg, iters: int):
+    """The 2-D shifted Laplacian at m = 256 (n = 65,536) for a bounded number
+    of updates: nnz(X), nnz(T), residual and wall time per iteration, filtered
+    (EXACT, FP64 and mixed) against unfiltered FP64."""
+    import torch
+    a = w.laplacian(256, 2)
+    # unfiltered NS fills in fastest; its FP64 products are capped at 4 updates
+    runs = {"filtered_fp64": (dict(filter="exact", prec="fp64"), iters),
+            "filtered_mixed": (dict(filter="exact", prec="mixed"), iters),
+            "unfiltered_fp64": (dict(filter="none", prec="fp64"), min(iters, 4))}
+    out = {"workload": "laplacian2d m=256 (n=65,536), sigma mid-gap, tol 1e-8",
+           "max_updates": iters}
+    for name, (kw, k) in runs.items():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = sg.solve(a, tol=TOL, max_iter=k, **kw)
+        torch.cuda.synchronize()
+        tr = r.trace
+        out[name] = {"status": int(r.status), "updates": int(r.iters),
+                     "seconds": time.perf_counter() - t0,
+                     "nnz_x": [int(x) for x in tr["nnz_x"]], "nnz_t": [int(x) for x in tr["nnz_t"]],
+                     "resid": [float(x) for x in tr["resid_k"]],
+                     "prec": [int(x) for x in tr["prec_k"]]}
+    return out
+
+
 # ---------------------------------------------------------------------- clocks
 class Clocks:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -283,6 +310,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="length of the Poisson stream at each serving rate (0: skip)")
     ap.add_argument("--serve-rates", default="50,200,800")
+    ap.add_argument("--fill-iters", type=int, default=0,
+                    help="also track fill on the n=65,536 2-D Laplacian for this many updates")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -458,6 +487,8 @@ def main():
     if args.legs == "all" and args.serve_seconds > 0 and rank == 0:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
         line["serving"] = serve_leg(sg, rates, args.serve_seconds)
+    if args.fill_iters > 0 and rank == 0:
+        line["laplacian2d_fill"] = fill_leg(sg, args.fill_iters)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
