@@ -248,6 +248,41 @@ def fill_leg(sg, iters: int):
     return out
 
 
+# ---------------------------------------------------------------------- 3-D Laplacian (scaled)
+def laplacian3d_leg(sg, m: int, samples: int = 4000):
+    """The 3-D shifted Laplacian on m^3 points (scaled variants of the 64^3
+    workload): mixed and FP64 solves with their fill per iteration, and the
+    error of each against the closed-form sign at seeded sampled entries."""
+    import torch
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from test_gpu_laplacian import _closed_form_entries, _entries
+    a = w.laplacian(m, 3)
+    rng = np.random.default_rng(m)
+    p = rng.integers(0, a.n, samples)
+    pp = np.where(rng.random(samples) < 0.5, p + rng.integers(-3 * m * m, 3 * m * m, samples),
+                  rng.integers(0, a.n, samples)) % a.n
+    ref = _closed_form_entries(m, 3, p, pp)
+    out = {"workload": f"laplacian3d m={m} (n={a.n}), sigma = 6, EXACT, tol 1e-8",
+           "samples": samples}
+    # FP64 throughout only up to n = 16384: before the iterate reaches the dense
+    # path's quarter, every FP64 iteration is a sparse product on filling rows
+    modes = (("mixed", "mixed"), ("fp64", "fp64")) if a.n <= 16384 else (("mixed", "mixed"),)
+    for name, prec in modes:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = sg.solve(a, tol=TOL, filter="exact", prec=prec, max_iter=200)
+        torch.cuda.synchronize()
+        got = _entries(r, a.n, p, pp)
+        tr = r.trace
+        out[name] = {"status": int(r.status), "updates": int(r.iters), "resid": float(r.resid),
+                     "seconds": time.perf_counter() - t0,
+                     "err_vs_closed_form": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                     "nnz_x": [int(x) for x in tr["nnz_x"]], "prec": [int(x) for x in tr["prec_k"]]}
+        print(f"laplacian3d m={m} {name}: {out[name]['seconds']:.1f} s, "
+              f"error {out[name]['err_vs_closed_form']:.3g}", file=sys.stderr, flush=True)
+    return out
+
+
 # ---------------------------------------------------------------------- clocks
 class Clocks:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -310,6 +345,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="length of the Poisson stream at each serving rate (0: skip)")
     ap.add_argument("--serve-rates", default="50,200,800")
+    ap.add_argument("--laplacian3d", default="",
+                    help="comma-separated m: also solve the m^3 3-D Laplacian against its closed form")
     ap.add_argument("--fill-iters", type=int, default=0,
                     help="also track fill on the n=65,536 2-D Laplacian for this many updates")
     args = ap.parse_args()
@@ -489,6 +526,8 @@ def main():
         line["serving"] = serve_leg(sg, rates, args.serve_seconds)
     if args.fill_iters > 0 and rank == 0:
         line["laplacian2d_fill"] = fill_leg(sg, args.fill_iters)
+    if args.laplacian3d and rank == 0:
+        line["laplacian3d"] = [laplacian3d_leg(sg, int(m)) for m in args.laplacian3d.split(",")]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -82,7 +82,7 @@ typedef struct {
   int prec;            /* sign_prec; SIGN_PREC_FP64                          */
   double fp32_until;   /* FP32 stage ends below this residual; 1e-4          */
   double dense_frac;   /* a matrix whose iterate holds at least
-                          dense_frac n^2 entries (n <= 4096, a filter on)
+                          dense_frac n^2 entries (n <= 32768, a filter on)
                           runs its products on the dense tensor-core path
                           in that round; > 1 turns the path off; 0.25      */
   int scale_1norm;     /* 1: X_1 = A/||A||_1 (default); 0: X_1 = A (paper)   */
@@ -204,7 +204,8 @@ sign_status sign_dense_product(int M, int N, int K, const float *A, int lda, con
  * digits, FP32 sums that stay integers below 2^24) and summed in FP64. The
  * error of an entry stays below about 2^-41 (K/4096) 2^(e_i + f_j), with
  * 2^e_i, 2^f_j bounding row i of A and column j of B (an FP64 dot product's
- * bound). Needs K <= 4096, N and ldc even and C 16-byte aligned, else
+ * bound); K is taken in blocks of 4096, each summed exactly, the blocks
+ * added in FP64. Needs N and ldc even and C 16-byte aligned, else
  * SIGN_EINVAL; SIGN_ETIMEOUT if a bounded wait on the tensor cores gave up.
  * Returns after cuda_stream has finished. */
 sign_status sign_dense_product_f64(int M, int N, int K, const double *A, int lda, const double *B,
@@ -229,13 +230,15 @@ sign_status sign_dense_product_f64(int M, int N, int K, const double *A, int lda
  * rho = max_i sum_j |a_ij| and half-bandwidth bw = max |i - j|:
  *   w = n                                          if delta <= 0,
  *   w = min(n, max(32, ceil(1.5 (rho/delta) (2 bw + 1))))  otherwise,
- *   bytes = 96 n w + 24 nnz.
+ *   bytes = 96 n w + 80 n^2 [if 4 w >= n] + 24 nnz.
  * w predicts the filtered iterate's entries per row: the sign of a matrix
  * whose spectrum avoids (-delta, delta) decays away from the band at a rate
  * set by rho/delta; without a Gershgorin gap no decay is assumed (dense).
  * 96 bytes per predicted entry covers the iterate, its square, the update
  * slots and the filtered copy in FP64 (12 bytes per entry each, with the
- * products' upper-bound slots counted twice); 24 bytes per input entry the
+ * products' upper-bound slots counted twice); 80 bytes per n^2 entry the
+ * dense path's FP64 blocks and digit planes, taken when the fill is
+ * predicted to reach a quarter of the row; 24 bytes per input entry the
  * input and its scaled copy. */
 typedef struct sign_server_s *sign_server_t;
 

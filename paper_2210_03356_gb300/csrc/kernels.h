@@ -227,8 +227,8 @@ void launch_split(int rows, int cols, const float *in, int ldi, int transpose, f
 // F64X_DIGITS digit planes, each rows x ld BF16 (plane s - 1 of an array of
 // `rows` rows starts at row (s - 1) rows), with per-row scale exponents ea,
 // eb (a_ik ~= 2^ea_i sum_s d_ik^(s) 2^(-7 s)). C is FP64, written (not
-// accumulated), K <= F64X_MAX_K, lda and ldb multiples of 8, N and ldc even,
-// C 16-byte and eb 8-byte aligned.
+// accumulated); K is taken in exact blocks of F64X_MAX_K; lda and ldb
+// multiples of 8, N and ldc even, C 16-byte and eb 8-byte aligned.
 constexpr int F64X_DIGITS = 8;
 constexpr int F64X_MAX_K = 4096;
 struct SliceJob {

@@ -13,22 +13,26 @@
 //
 // Products. For a digit pair (s, t) the tensor cores form the integer matrix
 // D_s E_t^T with FP32 accumulation: each product is at most 64 * 64 = 2^12 in
-// magnitude and K <= 4096, so every partial sum is an integer of magnitude at
-// most 2^24 and the accumulation is exact in any order. The epilogue adds
+// magnitude and K is taken in blocks of at most 4096, so every partial sum of
+// a block is an integer of magnitude at most 2^24 and its accumulation is
+// exact in any order. The epilogue adds, block by block,
 //   C_ij += (D_s E_t^T)_ij * 2^(e_i + 1) 2^(f_j + 1) 2^(-7 (s + t))
 // in FP64: the scale is a power of two, so each term is exact and is built
-// from the FP32 bits with integer operations; one FP64 addition per term. The pairs with s + t <= 9 (36 of the 64) are kept, in the
-// order of increasing weight; the dropped ones and the rounding of the inputs
-// to the 2^-55 grid stay below 2^-41 * 2^(e_i + f_j) * K / 4096 in the worst
-// case (digits of equal sign), about the error bound of an FP64 dot product.
+// from the FP32 bits with integer operations; one FP64 addition per term.
+// The pairs with s + t <= 9 (36 of the 64) are kept, in the order of
+// increasing weight; the dropped ones and the rounding of the inputs to the
+// 2^-55 grid stay below 2^-41 * 2^(e_i + f_j) * K / 4096 in the worst case
+// (digits of equal sign), about the error bound of an FP64 dot product; the
+// FP64 sums of the blocks add their own rounding.
 //
 // Kernel: persistent, one CTA per SM, 320 threads, laid out as the
 // split-TF32 kernel but with eight epilogue warps (two per 32 TMEM lanes,
 // one per half of the columns). A work unit is one 128 x 256 tile of C; its
-// CTA runs the digit pairs one after another, each a K loop into one of two
-// 256-column TMEM accumulators, so that the epilogue warps add pair p into C
-// while the MMAs of pair p + 1 run. A thread's loads of C for a 32-column
-// chunk are all issued before its stores, to keep them in flight together. The producer thread streams 32-wide K slices of the pair's A and
+// CTA runs the (digit pair, K block) steps one after another, each a K loop
+// into one of two 256-column TMEM accumulators, so that the epilogue warps add
+// step u into C while the MMAs of step u + 1 run. A thread's loads of C for a
+// 32-column chunk are all issued before its stores, to keep them in flight
+// together. The producer thread streams 32-wide K slices of the pair's A and
 // Bt digits with TMA into an eight-stage ring (64-byte swizzle); the MMA
 // thread issues two kind::f16 (BF16) MMAs per stage. Every wait has a clock
 // budget, as in the split-TF32 kernel.
@@ -61,6 +65,7 @@ constexpr uint32_t XTMEM_COLS = 2 * XN;
 constexpr int XSMEM = XSTAGE * XSTAGE_BYTES + 1024;  // ring and alignment slack
 constexpr int DIGIT_BITS = 7;
 constexpr int MAX_LEVEL = F64X_DIGITS + 1;  // pairs with s + t <= MAX_LEVEL
+constexpr int KBLK = F64X_MAX_K / XK;       // K stages per exact block (integer sums <= 2^24)
 
 // The kept digit pairs, smallest weight first: s + t from MAX_LEVEL down to 2.
 struct PairList {
@@ -155,10 +160,11 @@ __global__ void __launch_bounds__(XTHREADS, 1)
         xtile_of(t, jobs, tile_start, njobs, j, m0, n0);
         const SliceJob &J = jobs[j];
         const CUtensorMap *mp = maps + 2 * j;
-        const int nk = (J.K + XK - 1) / XK;
-        for (int p = 0; p < npairs && !*abort; ++p) {
+        const int nk = (J.K + XK - 1) / XK, nblk = (nk + KBLK - 1) / KBLK;
+        for (int u = 0; u < npairs * nblk && !*abort; ++u) {
+          const int p = u / nblk, k0 = (u % nblk) * KBLK, k1 = min(nk, k0 + KBLK);
           const int ya = (c_pairs.s[p] - 1) * J.M + m0, yb = (c_pairs.t[p] - 1) * J.N + n0;
-          for (int kb = 0; kb < nk; ++kb, ++issued) {
+          for (int kb = k0; kb < k1; ++kb, ++issued) {
             const int st = issued % XSTAGE;
             if (!bounded_wait(&empty[st], ((issued / XSTAGE) & 1) ^ 1, abort)) break;
             const uint32_t d = sbase + uint32_t(st * XSTAGE_BYTES);
@@ -177,8 +183,9 @@ __global__ void __launch_bounds__(XTHREADS, 1)
       for (int t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x) {
         int j, m0, n0;
         xtile_of(t, jobs, tile_start, njobs, j, m0, n0);
-        const int nk = (jobs[j].K + XK - 1) / XK;
-        for (int p = 0; p < npairs && ok; ++p, ++uc) {
+        const int nk = (jobs[j].K + XK - 1) / XK, nblk = (nk + KBLK - 1) / KBLK;
+        for (int u = 0; u < npairs * nblk && ok; ++u, ++uc) {
+          const int k0 = (u % nblk) * KBLK, k1 = min(nk, k0 + KBLK);
           const int a = uc & 1;
           if (!bounded_wait(&tempty[a], ((uc >> 1) & 1) ^ 1, abort)) {
             ok = false;
@@ -186,7 +193,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
           }
           tc_fence_after();
           const uint32_t acc = tmem + uint32_t(a * XN);
-          for (int kb = 0; kb < nk; ++kb, ++it) {
+          for (int kb = k0; kb < k1; ++kb, ++it) {
             const int st = it % XSTAGE;
             if (!bounded_wait(&full[st], (it / XSTAGE) & 1, abort)) {
               ok = false;
@@ -198,7 +205,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
             for (int s = 0; s < XK / 16; ++s) {
               const uint32_t ko = uint32_t(s) * 32u;
               mma_bf16(acc, smem_desc_sw<XSPAN>(d + ko), smem_desc_sw<XSPAN>(d + XA_BYTES + ko),
-                       idesc, (kb | s) != 0 ? 1u : 0u);
+                       idesc, ((kb - k0) | s) != 0 ? 1u : 0u);
             }
             any = true;
             mma_commit(&empty[st]);
@@ -223,8 +230,10 @@ __global__ void __launch_bounds__(XTHREADS, 1)
       const SliceJob J = jobs[j];
       const int gr = m0 + q * 32 + lane;
       const int ea = gr < J.M ? J.ea[gr] : 0;
+      const int nk = (J.K + XK - 1) / XK, nblk = (nk + KBLK - 1) / KBLK;
       bool stop = false;
-      for (int p = 0; p < npairs; ++p, ++uc) {
+      for (int u = 0; u < npairs * nblk; ++u, ++uc) {
+        const int p = u / nblk;
         const int a = uc & 1;
         if (!bounded_wait(&tfull[a], (uc >> 1) & 1, abort)) {
           stop = true;
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
           if (gc + 32 <= J.N) {
             // all sixteen loads of the row's chunk in flight before any store
             double2 c2[16];
-            if (p != 0) {
+            if (u != 0) {
 #pragma unroll
               for (int i = 0; i < 16; ++i) c2[i] = reinterpret_cast<const double2 *>(crow)[i];
             }
@@ -255,7 +264,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
               const int2 eb = reinterpret_cast<const int2 *>(J.eb + gc)[i];
               double2 t2 = make_double2(exact_scaled(__uint_as_float(v[2 * i]), er + eb.x),
                                         exact_scaled(__uint_as_float(v[2 * i + 1]), er + eb.y));
-              if (p != 0) {
+              if (u != 0) {
                 t2.x = c2[i].x + t2.x;
                 t2.y = c2[i].y + t2.y;
               }
@@ -270,7 +279,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
               double2 t2 = make_double2(exact_scaled(__uint_as_float(v[k]), er + eb.x),
                                         exact_scaled(__uint_as_float(v[k + 1]), er + eb.y));
               double2 *cp = reinterpret_cast<double2 *>(crow + k);
-              if (p != 0) {
+              if (u != 0) {
                 const double2 c2 = *cp;
                 t2.x = c2.x + t2.x;
                 t2.y = c2.y + t2.y;
@@ -497,7 +506,7 @@ void launch_slice_jobs(int njobs, const SliceJob *jobs_host, SliceJob *jobs_dev,
   int ntiles = 0;
   for (int j = 0; j < njobs; ++j) {
     const SliceJob &J = jobs_host[j];
-    if (J.M <= 0 || J.N <= 0 || J.K <= 0 || J.K > F64X_MAX_K || J.lda % 8 || J.ldb % 8 ||
+    if (J.M <= 0 || J.N <= 0 || J.K <= 0 || J.lda % 8 || J.ldb % 8 ||
         J.ldc % 2 || J.N % 2)
       throw Error(SIGN_EINVAL, "slice job with bad shape");
     const CUtensorMapDataType bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
@@ -533,8 +542,8 @@ extern "C" sign_status sign_dense_product_f64(int M, int N, int K, const double 
   set_last_error("");
   if (M < 0 || N < 0 || K < 0 || !A || !B || !C || lda < K || ldb < N || ldc < N)
     return set_last_error("bad dimensions or NULL pointer"), SIGN_EINVAL;
-  if (K > F64X_MAX_K || N % 2 || ldc % 2 || (reinterpret_cast<uintptr_t>(C) & 15u))
-    return set_last_error("need K <= 4096, N and ldc even, C 16-byte aligned"), SIGN_EINVAL;
+  if (N % 2 || ldc % 2 || (reinterpret_cast<uintptr_t>(C) & 15u))
+    return set_last_error("need N and ldc even, C 16-byte aligned"), SIGN_EINVAL;
   if (M == 0 || N == 0) return SIGN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   try {
@@ -559,7 +568,7 @@ extern "C" sign_status sign_dense_product_f64(int M, int N, int K, const double 
     err.ensure(sizeof(int), s);
     SGN_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     {
-      ProfScope ps(KC_DENSE64, s, 2.0 * kPairs.n * double(M) * double(N) * double(K), 0.0);
+      ProfScope ps(KC_DENSE64, s, 2.0 * kPairs.n * double(M) * double(N) * double(kp), 0.0);
       launch_slice_jobs(1, &J, job.as<SliceJob>(), scratch.p, err.as<int>(), s);
     }
     int herr = 0;

@@ -202,7 +202,11 @@ void sign_server_s::serve(Lane &L) {
 extern "C" {
 
 double sign_footprint_bytes(int64_t n, int64_t nnz, double delta, double rho, int64_t bw) {
-  return 96.0 * double(n) * predicted_width(n, delta, rho, bw) + 24.0 * double(nnz);
+  const double w = predicted_width(n, delta, rho, bw);
+  // a predicted fill of a quarter or more takes the dense path: FP64 blocks and
+  // digit planes (80 bytes per n^2 entry, the FP32 stage's 28 reuse them)
+  const double dense = 4.0 * w >= double(n) ? 80.0 * double(n) * double(n) : 0.0;
+  return 96.0 * double(n) * w + dense + 24.0 * double(nnz);
 }
 
 void sign_server_default_opts(sign_server_opts *o) {

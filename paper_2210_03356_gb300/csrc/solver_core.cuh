@@ -372,7 +372,9 @@ struct Solver {
       if (!st.alive[i]) continue;
       int64_t n = st.moff[i + 1] - st.moff[i];
       int64_t nnz = st.ex[i + 1] - st.ex[i];
-      if (n > 4096 || double(nnz) < o.dense_frac * double(n) * double(n)) continue;
+      // up to n = 32768: seven FP32 blocks (30 GB) in the FP32 stage; four
+      // FP64 blocks and 24 BF16 digit planes (86 GB) in the FP64 stage
+      if (n > 32768 || double(nnz) < o.dense_frac * double(n) * double(n)) continue;
       if (!f32 && n < o.dense64_min_n) continue;  // too small to repay 36 passes per tile
       int ld = f32 ? int((n + 3) / 4 * 4) : int((n + 7) / 8 * 8);
       dp.slot[i] = dp.nd++;

@@ -82,11 +82,23 @@ def test_digit_sums_at_the_fp32_limit_are_exact(sg):
     assert np.all(c[:, 0::2] == exact) and np.all(c[:, 1::2] == -exact)
 
 
+def test_k_beyond_one_exact_block(sg):
+    """K = 9000 runs as three exact blocks of at most 4096, added in FP64."""
+    import torch
+    rng = np.random.default_rng(9)
+    m, n, k = 200, 300, 9000
+    a = rng.uniform(-1, 1, (m, k))
+    b = rng.uniform(-1, 1, (k, n))
+    c = sg.dense_product_f64(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()).cpu().numpy()
+    sc = _scales(a, b)
+    for i, j in zip(rng.integers(0, m, 12), rng.integers(0, n, 12)):
+        exact = sum(Fraction(x) * Fraction(y) for x, y in zip(a[i], b[:, j]))
+        assert abs(Fraction(c[i, j]) - exact) <= Fraction(2.0 ** -41 * k / 4096) * Fraction(sc[i, j])
+
+
 def test_rejects_bad_shapes(sg):
     import torch
-    a = torch.zeros(8, 5000, dtype=torch.float64, device="cuda")
-    b = torch.zeros(5000, 8, dtype=torch.float64, device="cuda")
+    a = torch.zeros(8, 16, dtype=torch.float64, device="cuda")
+    b = torch.zeros(16, 7, dtype=torch.float64, device="cuda")
     with pytest.raises(sg.SignError):
-        sg.dense_product_f64(a, b)  # K > 4096
-    with pytest.raises(sg.SignError):
-        sg.dense_product_f64(a[:, :16], b[:16, :7])  # N odd
+        sg.dense_product_f64(a, b)  # N odd

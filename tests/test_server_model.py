@@ -30,15 +30,17 @@ def _stats(a):
 
 
 def test_footprint_closed_form(sg):
-    # no Gershgorin gap: the dense bound
-    assert sg.footprint_bytes(65536, 326656, 0.0, 8.0, 256) == 96.0 * 65536 ** 2 + 24 * 326656
-    assert sg.footprint_bytes(100, 400, -1.0, 8.0, 3) == 96.0 * 100 * 100 + 24 * 400
+    # no Gershgorin gap: the dense bound, with the dense path's blocks
+    assert sg.footprint_bytes(65536, 326656, 0.0, 8.0, 256) == 176.0 * 65536 ** 2 + 24 * 326656
+    assert sg.footprint_bytes(100, 400, -1.0, 8.0, 3) == 176.0 * 100 * 100 + 24 * 400
     # 1.5 (rho/delta)(2 bw + 1) = 1.5 * 12 * 21 = 378 entries per row
     assert sg.footprint_bytes(8000, 160000, 0.25, 3.0, 10) == 96.0 * 8000 * 378 + 24 * 160000
     # at least 32 per row: 1.5 * 5 * 3 = 22.5 -> 32
     assert sg.footprint_bytes(2000, 5998, 0.5, 2.5, 1) == 96.0 * 2000 * 32 + 24 * 5998
-    # at most n per row
-    assert sg.footprint_bytes(100, 300, 0.01, 2.0, 10) == 96.0 * 100 * 100 + 24 * 300
+    # at most n per row (and then dense)
+    assert sg.footprint_bytes(100, 300, 0.01, 2.0, 10) == 176.0 * 100 * 100 + 24 * 300
+    # a predicted quarter of the row already takes the dense path: 1.5 * 4 * 21 = 126 >= 500/4
+    assert sg.footprint_bytes(500, 1000, 0.5, 2.0, 10) == 96.0 * 500 * 126 + 80.0 * 500 ** 2 + 24 * 1000
 
 
 def test_budget_admits_the_sparse_workloads_and_refuses_the_3d_laplacian(sg):
