@@ -86,7 +86,8 @@ struct ExtractBlock {
   int32_t *dcol;
   double *dval;
 };
-void launch_extract(int nblocks, const ExtractBlock *blocks, cudaStream_t s);
+// max_entries: the most entries of one block (sizes the grid).
+void launch_extract(int nblocks, const ExtractBlock *blocks, int64_t max_entries, cudaStream_t s);
 
 // out[m] = rp[moff[m]] for m = 0..nb (entry offsets of the matrices).
 void launch_gather_offsets(int nb, const int64_t *moff, const int64_t *rp, int64_t *out,

@@ -340,15 +340,21 @@ __global__ void __launch_bounds__(RED_T) k_seg_count(const int64_t *moff, const 
 
 // One CTA per extracted matrix: rebased row pointers, shifted columns,
 // values widened to FP64.
-__global__ void k_extract(const ExtractBlock *blocks) {
-  const ExtractBlock B = blocks[blockIdx.x];
-  int64_t e0 = B.rp[B.row0];
-  for (int64_t i = threadIdx.x; i <= B.nrows; i += blockDim.x) B.drp[i] = B.rp[B.row0 + i] - e0;
-  int64_t ne = B.rp[B.row0 + B.nrows] - e0;
-  for (int64_t p = threadIdx.x; p < ne; p += blockDim.x) {
-    B.dcol[p] = int32_t(B.col[e0 + p] + B.col_shift);
-    B.dval[p] = B.val_f32 ? double(static_cast<const float *>(B.val)[e0 + p])
-                          : static_cast<const double *>(B.val)[e0 + p];
+// blockIdx.y walks the blocks; the gridDim.x CTAs of a block share its rows
+// and entries, so that a large matrix is copied by many SMs.
+__global__ void k_extract(int nblocks, const ExtractBlock *blocks) {
+  for (int b = blockIdx.y; b < nblocks; b += gridDim.y) {
+    const ExtractBlock B = blocks[b];
+    const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t step = int64_t(gridDim.x) * blockDim.x;
+    const int64_t e0 = B.rp[B.row0];
+    for (int64_t i = t0; i <= B.nrows; i += step) B.drp[i] = B.rp[B.row0 + i] - e0;
+    const int64_t ne = B.rp[B.row0 + B.nrows] - e0;
+    for (int64_t p = t0; p < ne; p += step) {
+      B.dcol[p] = int32_t(B.col[e0 + p] + B.col_shift);
+      B.dval[p] = B.val_f32 ? double(static_cast<const float *>(B.val)[e0 + p])
+                            : static_cast<const double *>(B.val)[e0 + p];
+    }
   }
 }
 
@@ -398,9 +404,12 @@ void launch_seg_count(int nb, const int64_t *moff, const int64_t *rs, const int6
   SGN_LAUNCH_CHECK();
 }
 
-void launch_extract(int nblocks, const ExtractBlock *blocks, cudaStream_t s) {
+void launch_extract(int nblocks, const ExtractBlock *blocks, int64_t max_entries, cudaStream_t s) {
   if (nblocks == 0) return;
-  k_extract<<<nblocks, 512, 0, s>>>(blocks);
+  // about 8 entries per thread of a 512-thread CTA, at most 152 CTAs per block
+  const int64_t per = (max_entries + 4095) / 4096;
+  dim3 grid(unsigned(per < 1 ? 1 : (per > 152 ? 152 : per)), unsigned(nblocks < 65535 ? nblocks : 65535));
+  k_extract<<<grid, 512, 0, s>>>(nblocks, blocks);
   SGN_LAUNCH_CHECK();
 }
 

@@ -118,9 +118,21 @@ __device__ __forceinline__ void row_range(const SelRows &R, int64_t r, int64_t &
   }
 }
 
+// Bit pattern of |x| as an FP64 number. For FP32 values of the normal range
+// it is built with integer operations (exponent rebiased by 1023 - 127 = 896,
+// mantissa widened by 29 bits): the same bits as the exact conversion, with
+// no work for the FP64 pipe, which this GPU runs at 1/64 of its FP32 rate.
 __device__ __forceinline__ unsigned long long key_of(const void *val, int f32, int64_t p) {
-  double x = f32 ? double(static_cast<const float *>(val)[p]) : static_cast<const double *>(val)[p];
-  return (unsigned long long)__double_as_longlong(fabs(x));
+  if (f32) {
+    const float x = static_cast<const float *>(val)[p];
+    const uint32_t b = __float_as_uint(x) & 0x7FFFFFFFu, e = b >> 23;
+    if (e != 0u && e != 0xFFu)
+      return ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29);
+    if (b == 0u) return 0ULL;
+    return (unsigned long long)__double_as_longlong(fabs(double(x)));  // subnormal, inf, NaN
+  }
+  return (unsigned long long)__double_as_longlong(static_cast<const double *>(val)[p]) &
+         0x7FFFFFFFFFFFFFFFULL;
 }
 
 // q = round((x * s)^2) with s = 2^31 / b, i.e. (x/b)^2 in units of 2^-62 of
@@ -369,6 +381,25 @@ __global__ void k_sel_final(int nb, const int *active, SelScratch sc, MatScalars
 }
 
 // ------------------------------------------------------------ filter
+// (hi, lo) += x^2 for FP32 x, exactly: the square's rounding error comes from
+// an FMA and the sum's from TwoSum; all in FP32, which this GPU runs at 64x
+// its FP64 rate. Inputs are scaled by 2^48 (exact), so that squares of
+// entries from 2^-111 to 2^16 stay normal FP32 numbers.
+__device__ __forceinline__ void ff_add_sq48(float x, float &hi, float &lo) {
+  const float y = __fmul_rn(x, 281474976710656.0f);  // 2^48
+  const float p = __fmul_rn(y, y), e = __fmaf_rn(y, y, -p);
+  const float s = __fadd_rn(hi, p), bb = __fsub_rn(s, hi);
+  lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb)), e));
+  hi = s;
+}
+
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float h2, float l2) {
+  const float s = __fadd_rn(hi, h2), bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+  lo = __fadd_rn(__fadd_rn(lo, l2), err);
+  hi = s;
+}
+
 __global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
                                const int64_t *rs, const int64_t *re, const void *val, int f32,
                                const MatScalars *ms, int64_t *cnt, double *dropped) {
@@ -380,35 +411,42 @@ __global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
     double tau = ms[m].tau;
     int c = 0;
     double d2 = 0.0;
-    if (active[m]) {
-      if (f32) {
-        // the smallest float >= tau: for a float x, |x| >= tf exactly when |x| >= tau
-        float tf = __double2float_ru(tau);
-        const float *v = static_cast<const float *>(val);
-        for (int64_t p = rs[r] + lane; p < re[r]; p += 32) {
-          float x = v[p];
-          if (fabsf(x) >= tf && x != 0.0f) {
-            ++c;
-          } else {
-            double xd = double(x);
-            d2 = __fma_rn(xd, xd, d2);
-          }
-        }
-      } else {
-        const double *v = static_cast<const double *>(val);
-        for (int64_t p = rs[r] + lane; p < re[r]; p += 32) {
-          double x = v[p];
-          if (fabs(x) >= tau && x != 0.0)
-            ++c;
-          else
-            d2 = __fma_rn(x, x, d2);
-        }
+    if (active[m] && f32) {
+      // the smallest float >= tau: for a float x, |x| >= tf exactly when |x| >= tau
+      const float tf = __double2float_ru(tau);
+      const float *v = static_cast<const float *>(val);
+      float hi = 0.0f, lo = 0.0f;  // dropped squares, scaled by 2^96
+      for (int64_t p = rs[r] + lane; p < re[r]; p += 32) {
+        const float x = v[p];
+        if (fabsf(x) >= tf && x != 0.0f)
+          ++c;
+        else if (x != 0.0f)
+          ff_add_sq48(x, hi, lo);
       }
-    }
+      c = __reduce_add_sync(0xffffffffu, c);
+      if (__any_sync(0xffffffffu, hi != 0.0f)) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      c += __shfl_xor_sync(0xffffffffu, c, o);
-      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        for (int o = 16; o > 0; o >>= 1) {
+          const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+          const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+          ff_add(hi, lo, h2, l2);
+        }
+        if (lane == 0) d2 = ldexp(double(hi) + double(lo), -96);
+      }
+    } else if (active[m]) {
+      const double *v = static_cast<const double *>(val);
+      for (int64_t p = rs[r] + lane; p < re[r]; p += 32) {
+        double x = v[p];
+        if (fabs(x) >= tau && x != 0.0)
+          ++c;
+        else
+          d2 = __fma_rn(x, x, d2);
+      }
+      c = __reduce_add_sync(0xffffffffu, c);
+      if (__any_sync(0xffffffffu, d2 != 0.0)) {  // FP64 adds only for rows that drop
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+      }
     }
     if (lane == 0) {
       cnt[r] = c;

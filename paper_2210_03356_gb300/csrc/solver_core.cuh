@@ -632,6 +632,7 @@ struct Solver {
     // ---- per-matrix decisions (steps a7, a8); leavers copied out in one launch
     HostScope hdecide(KH_DECIDE);
     int nx = 0;
+    int64_t xmax = 0;  // most entries (or rows + 1) of one extracted block
     bool changed = false;
     std::vector<int> movers;
     for (int i = 0; i < nb; ++i) {
@@ -665,6 +666,7 @@ struct Solver {
       ms.h->has_result = true;
       retired.push_back(st.mats[i]);
       dst->ensure(n_i, nnz_i, s);
+      xmax = std::max(xmax, std::max(nnz_i, n_i + 1));
       hm.xb[nx++] = ExtractBlock{st.X.d_rp(), st.X.d_col(), st.X.val.p, is_f32<T>(), st.moff[i],
                                  n_i, -st.moff[i], dst->d_rp(), dst->d_col(), dst->d_val()};
     }
@@ -696,6 +698,7 @@ struct Solver {
         p->n = n_i;
         p->col0 = 0;
         p->nnz = nnz_i;
+        xmax = std::max(xmax, std::max(nnz_i, n_i + 1));
         hm.xb[nx++] = ExtractBlock{st.X.d_rp(), st.X.d_col(), st.X.val.p, is_f32<T>(), st.moff[i],
                                    n_i, -st.moff[i], rp, col, val};
         next->incoming.push_back(std::move(p));
@@ -707,7 +710,7 @@ struct Solver {
       w.xblocks.ensure(sizeof(ExtractBlock) * size_t(nx), s);
       h2d(w.xblocks.p, hm.xb, size_t(nx), s);
       ProfScope ps(KC_ASSEMBLE, s);
-      launch_extract(nx, w.xblocks.as<ExtractBlock>(), s);
+      launch_extract(nx, w.xblocks.as<ExtractBlock>(), xmax, s);
     }
     live = 0;
     for (int a : st.alive) live += a;
