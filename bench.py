@@ -52,9 +52,27 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 
 
+def rank_seed0(rank: int, count: int = BATCH) -> int:
+    """First seed of rank `rank`'s batch: the ranks' batches never share a seed."""
+    return w.BASE_SEED + 3000 + rank * count
+
+
 def batch_mats(rank: int, count: int = BATCH):
-    seed0 = w.BASE_SEED + 3000 + rank * count
-    return [w.banded(n, b, s) for n, b, s in w.banded_batch_shapes(count, seed0)]
+    return [w.banded(n, b, s) for n, b, s in w.banded_batch_shapes(count, rank_seed0(rank, count))]
+
+
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """The slowest rank's timed milliseconds (every rank gets the same value)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(per_rank: int, world: int, steps: int, ms_max: float) -> float:
+    """Whole-job solves/s: every rank's matrices over the slowest rank's time."""
+    return per_rank * world * steps / (ms_max / 1000.0)
 
 
 def measured_peaks():
@@ -416,11 +434,8 @@ def main():
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
     assert all(s == sg.SIGN_OK and r <= TOL for s, _, r in out)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = len(mats) * world * args.steps / (ms_max / 1000.0)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = job_throughput(len(mats), world, args.steps, ms_max)
 
     # roofline of the dominant kernel class
     peaks, peak_kind = measured_peaks()
