@@ -535,14 +535,14 @@ __global__ void k_rows_empty(int64_t n, const int64_t *ars, const int64_t *are, 
   }
 }
 
-int g_sms = 0;
 int sm_count() {
-  if (!g_sms) {
-    int dev = 0;
+  static const int n = [] {  // once, thread-safe (server lanes launch from several threads)
+    int dev = 0, v = 0;
     SGN_CUDA(cudaGetDevice(&dev));
-    SGN_CUDA(cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev));
-  }
-  return g_sms;
+    SGN_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    return v;
+  }();
+  return n;
 }
 
 int grid_cap(int64_t items, int per_block, int per_sm) {
