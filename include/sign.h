@@ -304,7 +304,8 @@ sign_status sign_server_take(sign_server_t srv, uint64_t ticket, void *cuda_stre
 sign_status sign_server_get_stats(sign_server_t srv, sign_server_stats *out);
 
 /* Stops admitting, lets the requests on the GPU finish, and frees the server
- * with every request not yet taken. */
+ * with every request not yet taken. The other sign_server_* calls may come
+ * from any threads at once; this one must not overlap any of them. */
 void sign_server_destroy(sign_server_t srv);
 
 /* ---- observability (not part of the paper's method) -------------------- */

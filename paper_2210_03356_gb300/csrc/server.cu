@@ -219,7 +219,35 @@ void sign_server_default_opts(sign_server_opts *o) {
   o->lanes = 2;
 }
 
+static sign_status server_create(const sign_server_opts *o, sign_server_t *out);
+static sign_status server_submit(sign_server_t S, int64_t n, int64_t nnz, const int64_t *rowptr,
+                                 const int32_t *col, const double *val, int on_device,
+                                 uint64_t *ticket);
+
+// No C++ exception crosses the C ABI: allocation failures become SIGN_ENOMEM.
 sign_status sign_server_create(const sign_server_opts *o, sign_server_t *out) {
+  try {
+    return server_create(o, out);
+  } catch (const std::bad_alloc &) {
+    return set_last_error("host allocation failed"), SIGN_ENOMEM;
+  } catch (const std::exception &e) {
+    return set_last_error(e.what()), SIGN_ECUDA;
+  }
+}
+
+sign_status sign_server_submit(sign_server_t S, int64_t n, int64_t nnz, const int64_t *rowptr,
+                               const int32_t *col, const double *val, int on_device,
+                               uint64_t *ticket) {
+  try {
+    return server_submit(S, n, nnz, rowptr, col, val, on_device, ticket);
+  } catch (const std::bad_alloc &) {
+    return set_last_error("host allocation failed"), SIGN_ENOMEM;
+  } catch (const std::exception &e) {
+    return set_last_error(e.what()), SIGN_ECUDA;
+  }
+}
+
+static sign_status server_create(const sign_server_opts *o, sign_server_t *out) {
   set_last_error("");
   if (!out) return set_last_error("out is NULL"), SIGN_EINVAL;
   *out = nullptr;
@@ -272,10 +300,11 @@ sign_status sign_server_create(const sign_server_opts *o, sign_server_t *out) {
   return SIGN_OK;
 }
 
-sign_status sign_server_submit(sign_server_t S, int64_t n, int64_t nnz, const int64_t *rowptr,
-                               const int32_t *col, const double *val, int on_device,
-                               uint64_t *ticket) {
+static sign_status server_submit(sign_server_t S, int64_t n, int64_t nnz, const int64_t *rowptr,
+                                 const int32_t *col, const double *val, int on_device,
+                                 uint64_t *ticket) {
   if (!S || !ticket) return set_last_error("NULL server or ticket"), SIGN_EINVAL;
+  auto r = std::make_unique<Request>();  // before the copy: nothing to undo if this fails
   sign_t h = nullptr;
   sign_status st = sign_create(n, nnz, rowptr, col, val, on_device, S->upload, &h);
   if (st != SIGN_OK) return st;  // sign_create has set the message
@@ -299,31 +328,47 @@ sign_status sign_server_submit(sign_server_t S, int64_t n, int64_t nnz, const in
     return set_last_error(e.what()), sign_status(e.status);
   }
   const int lane = (S->lanes.size() > 1 && 4.0 * width >= double(n)) ? 1 : 0;
-  std::lock_guard<std::mutex> lk(S->mu);
-  S->st.submitted++;
-  if (S->stop || fp > S->o.mem_budget || S->queued() >= S->o.max_queue) {
-    S->st.refused++;
-    char msg[160];
-    if (S->stop)
-      std::snprintf(msg, sizeof msg, "server is stopping");
-    else if (fp > S->o.mem_budget)
-      std::snprintf(msg, sizeof msg, "predicted footprint %.3g bytes exceeds mem_budget %.3g",
-                    fp, S->o.mem_budget);
-    else
-      std::snprintf(msg, sizeof msg, "%d requests already waiting (max_queue)", S->o.max_queue);
-    sign_destroy(h);
-    set_last_error(msg);
-    return S->stop ? SIGN_ESTATE : SIGN_ENOMEM;
+  char msg[160] = "";
+  sign_status refused = SIGN_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->st.submitted++;
+    if (S->stop || fp > S->o.mem_budget || S->queued() >= S->o.max_queue) {
+      S->st.refused++;
+      if (S->stop)
+        std::snprintf(msg, sizeof msg, "server is stopping");
+      else if (fp > S->o.mem_budget)
+        std::snprintf(msg, sizeof msg, "predicted footprint %.3g bytes exceeds mem_budget %.3g",
+                      fp, S->o.mem_budget);
+      else
+        std::snprintf(msg, sizeof msg, "%d requests already waiting (max_queue)",
+                      S->o.max_queue);
+      refused = S->stop ? SIGN_ESTATE : SIGN_ENOMEM;
+    } else {
+      r->h = h;
+      r->t.t_submit = now_s();
+      r->t.footprint = fp;
+      r->t.lane = lane;
+      const uint64_t t = S->next_ticket++;
+      Request *rp = r.get();
+      S->reqs[t] = std::move(r);  // owned by the ticket map first, then queued
+      try {
+        S->lanes[lane]->queue.push_back(rp);
+        *ticket = t;
+        S->st.queued = S->queued();
+      } catch (const std::bad_alloc &) {  // not queued: refused, the copy is freed below
+        S->reqs.erase(t);
+        S->st.refused++;
+        std::snprintf(msg, sizeof msg, "host allocation failed");
+        refused = SIGN_ENOMEM;
+      }
+    }
   }
-  auto r = std::make_unique<Request>();
-  r->h = h;
-  r->t.t_submit = now_s();
-  r->t.footprint = fp;
-  r->t.lane = lane;
-  *ticket = S->next_ticket++;
-  S->lanes[lane]->queue.push_back(r.get());
-  S->st.queued = S->queued();
-  S->reqs[*ticket] = std::move(r);
+  if (refused != SIGN_OK) {
+    sign_destroy(h);  // synchronizes the upload stream: outside the lock
+    set_last_error(msg);
+    return refused;
+  }
   S->cv_work.notify_all();
   return SIGN_OK;
 }
