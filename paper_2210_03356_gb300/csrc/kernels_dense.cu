@@ -515,6 +515,12 @@ extern "C" sign_status sign_dense_product(int M, int N, int K, const float *A, i
   } catch (const Error &e) {
     set_last_error(e.what());
     return sign_status(e.status);
+  } catch (const std::bad_alloc &) {
+    set_last_error("host allocation failed");
+    return SIGN_ENOMEM;
+  } catch (const std::exception &e) {
+    set_last_error(e.what());
+    return SIGN_ECUDA;
   }
   return SIGN_OK;
 }

@@ -91,6 +91,9 @@ sign_status sign_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int
   } catch (const Error &e) {
     delete h;
     return fail(e.status, e.what());
+  } catch (const std::bad_alloc &) {
+    delete h;
+    return fail(SIGN_ENOMEM, "host allocation failed");
   } catch (const std::exception &e) {
     delete h;
     return fail(SIGN_ECUDA, e.what());
@@ -150,6 +153,10 @@ sign_status sign_get_csr(sign_t h, int64_t *nnz_out, int64_t *row_ptr, int32_t *
     SGN_CUDA(cudaStreamSynchronize(s));
   } catch (const Error &e) {
     return fail(e.status, e.what());
+  } catch (const std::bad_alloc &) {
+    return fail(SIGN_ENOMEM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(SIGN_ECUDA, e.what());
   }
   return SIGN_OK;
 }
