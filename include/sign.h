@@ -126,6 +126,15 @@ void sign_default_opts(sign_opts *o);
 sign_status sign_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col,
                         const double *val, int on_device, void *cuda_stream, sign_t *out);
 
+/* sign_create for `count` matrices at once (arrays of their arguments):
+ * the copies and checks of all of them are queued back to back on
+ * cuda_stream, which is waited for once. On any error no handle is created,
+ * every out[i] is NULL, and sign_last_error names the first bad matrix. */
+sign_status sign_create_batch(int count, const int64_t *n, const int64_t *nnz,
+                              const int64_t *const *rowptr, const int32_t *const *col,
+                              const double *const *val, int on_device, void *cuda_stream,
+                              sign_t *out);
+
 /* Runs the solve (Alg. 3.2.1). Returns the matrix's status (SIGN_OK,
  * SIGN_ENOTCONV or SIGN_EDIVERGED leave a result to read) or an error. */
 sign_status sign_solve(sign_t h, const sign_opts *o, sign_info *info);

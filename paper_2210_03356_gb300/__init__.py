@@ -111,6 +111,13 @@ class Handle:
         self.h = h
         self._keep = None
 
+    @classmethod
+    def _adopt(cls, h, n, stream):
+        """Wraps a handle that sign_create_batch made."""
+        self = cls.__new__(cls)
+        self.n, self.stream, self.h, self._keep = int(n), stream, h, None
+        return self
+
     def close(self):
         if getattr(self, "h", None):
             load().sign_destroy(self.h)
@@ -128,13 +135,38 @@ class Handle:
     def __exit__(self, *a):
         self.close()
 
-    def result(self, device=False):
-        """sign_get_csr: host numpy arrays, or CUDA torch tensors if device=True."""
+    def result_nnz(self) -> int:
+        """Stored entries of the result (sign_get_csr with no arrays)."""
+        nnz = C.c_int64()
+        st = load().sign_get_csr(self.h, C.byref(nnz), None, None, None, 0)
+        if st != SIGN_OK:
+            raise SignError(st, "sign_get_csr")
+        return nnz.value
+
+    def result(self, device=False, out=None):
+        """sign_get_csr: host numpy arrays, or CUDA torch tensors if device=True.
+
+        out = (rowptr, col, val) reads into caller-owned host arrays instead
+        (numpy views, e.g. of pinned memory, reused across solves); they must
+        hold n + 1 and result_nnz() entries. Returns views of them.
+        """
         L = load()
         nnz = C.c_int64()
         st = L.sign_get_csr(self.h, C.byref(nnz), None, None, None, 0)
         if st != SIGN_OK:
             raise SignError(st, "sign_get_csr")
+        if out is not None:
+            rp, col, val = out
+            if (rp.dtype != np.int64 or col.dtype != np.int32 or val.dtype != np.float64 or
+                    rp.size < self.n + 1 or col.size < nnz.value or val.size < nnz.value or
+                    not (rp.flags.c_contiguous and col.flags.c_contiguous and
+                         val.flags.c_contiguous)):
+                raise ValueError("out arrays: need contiguous int64[n+1], int32[nnz], "
+                                 "float64[nnz]")
+            st = L.sign_get_csr(self.h, C.byref(nnz), _ptr(rp), _ptr(col), _ptr(val), 0)
+            if st != SIGN_OK:
+                raise SignError(st, "sign_get_csr")
+            return rp[:self.n + 1], col[:nnz.value], val[:nnz.value]
         if device:
             import torch
             rp = torch.empty(self.n + 1, dtype=torch.int64, device="cuda")
@@ -178,7 +210,7 @@ def solve_batch(mats, opts=None, trace_cap: int = 256, device_out: bool = False,
                 **kw) -> list[Result]:
     """sign_solve_batch: all matrices in the same kernel launches, one result each."""
     o = _opts(opts, kw)
-    hs = [Handle(a, stream) for a in mats]
+    hs = Batch(mats, stream).handles
     try:
         arr = (N.sign_t * len(hs))(*[h.h for h in hs])
         infos = [_Info(trace_cap) for _ in hs]
@@ -262,8 +294,32 @@ class Batch:
     """
 
     def __init__(self, mats, stream=None):
-        self.handles = [Handle(a, stream) for a in mats]
-        self.arr = (N.sign_t * len(self.handles))(*[h.h for h in self.handles])
+        mats = list(mats)
+        if not mats:
+            raise ValueError("empty batch")
+        L = load()
+        stream = stream if stream is not None else current_stream()
+        on_dev = [_is_torch_cuda(a.val) for a in mats]
+        if any(on_dev) and not all(on_dev):
+            raise ValueError("a batch is all on the host or all on the device")
+        if on_dev[0]:
+            keep = [(a.rowptr.contiguous(), a.col.contiguous(), a.val.contiguous()) for a in mats]
+        else:
+            keep = [(np.ascontiguousarray(a.rowptr, dtype=np.int64),
+                     np.ascontiguousarray(a.col, dtype=np.int32),
+                     np.ascontiguousarray(a.val, dtype=np.float64)) for a in mats]
+        k = len(mats)
+        ns = (C.c_int64 * k)(*[int(a.n) for a in mats])
+        nnzs = (C.c_int64 * k)(*[int(rp[-1]) for rp, _, _ in keep])
+        rps = (C.c_void_p * k)(*[_ptr(t[0]) for t in keep])
+        cols = (C.c_void_p * k)(*[_ptr(t[1]) for t in keep])
+        vals = (C.c_void_p * k)(*[_ptr(t[2]) for t in keep])
+        out = (N.sign_t * k)()
+        st = L.sign_create_batch(k, ns, nnzs, rps, cols, vals, int(on_dev[0]), stream, out)
+        if st != SIGN_OK:
+            raise SignError(st, "sign_create_batch")
+        self.handles = [Handle._adopt(out[i], ns[i], stream) for i in range(k)]
+        self.arr = (N.sign_t * k)(*[h.h for h in self.handles])
         self.infos = None
 
     def solve(self, opts, trace_cap: int = 0) -> list:

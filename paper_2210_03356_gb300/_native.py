@@ -66,6 +66,10 @@ SIGNATURES = {
     "sign_default_opts": (None, [C.POINTER(sign_opts)]),
     "sign_create": (C.c_int, [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                               C.c_void_p, C.POINTER(sign_t)]),
+    "sign_create_batch": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                    C.POINTER(C.c_void_p), C.c_int, C.c_void_p,
+                                    C.POINTER(sign_t)]),
     "sign_solve": (C.c_int, [sign_t, C.POINTER(sign_opts), C.POINTER(sign_info)]),
     "sign_solve_batch": (C.c_int, [C.POINTER(sign_t), C.c_int, C.POINTER(sign_opts),
                                    C.POINTER(sign_info)]),

@@ -102,6 +102,62 @@ sign_status sign_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int
   return SIGN_OK;
 }
 
+sign_status sign_create_batch(int count, const int64_t *n, const int64_t *nnz,
+                              const int64_t *const *rowptr, const int32_t *const *col,
+                              const double *const *val, int on_device, void *cuda_stream,
+                              sign_t *out) {
+  g_err.clear();
+  if (count < 1 || !n || !nnz || !rowptr || !col || !val || !out)
+    return fail(SIGN_EINVAL, "need count >= 1 and non-NULL arrays");
+  for (int i = 0; i < count; ++i) out[i] = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 1 || n[i] > INT32_MAX || nnz[i] < 0)
+      return fail(SIGN_EINVAL, "matrix " + std::to_string(i) + ": need 1 <= n < 2^31, nnz >= 0");
+    if (!rowptr[i] || (nnz[i] > 0 && (!col[i] || !val[i])))
+      return fail(SIGN_EINVAL, "matrix " + std::to_string(i) + ": NULL array");
+  }
+  std::vector<std::unique_ptr<sign_ctx>> hs;
+  try {
+    hs.reserve(size_t(count));
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    DevBuf flags;
+    flags.ensure(sizeof(int) * size_t(count), s);
+    SGN_CUDA(cudaMemsetAsync(flags.p, 0, sizeof(int) * size_t(count), s));
+    for (int i = 0; i < count; ++i) {  // copies and checks queued back to back, one wait
+      hs.emplace_back(new sign_ctx);
+      sign_ctx *h = hs.back().get();
+      h->n = n[i];
+      h->nnz = nnz[i];
+      h->stream = s;
+      h->a.ensure(n[i], nnz[i], s);
+      SGN_CUDA(cudaMemcpyAsync(h->a.rp.p, rowptr[i], sizeof(int64_t) * size_t(n[i] + 1), kind, s));
+      if (nnz[i] > 0) {
+        SGN_CUDA(cudaMemcpyAsync(h->a.col.p, col[i], sizeof(int32_t) * size_t(nnz[i]), kind, s));
+        SGN_CUDA(cudaMemcpyAsync(h->a.val.p, val[i], sizeof(double) * size_t(nnz[i]), kind, s));
+      }
+      launch_validate(n[i], nnz[i], h->a.d_rp(), h->a.d_col(), h->a.d_val(), flags.as<int>() + i,
+                      s);
+    }
+    std::vector<int> hf(size_t(count), 0);
+    SGN_CUDA(cudaMemcpyAsync(hf.data(), flags.p, sizeof(int) * size_t(count),
+                             cudaMemcpyDeviceToHost, s));
+    SGN_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < count; ++i)
+      if (hf[size_t(i)])
+        return fail(SIGN_EINVAL, "matrix " + std::to_string(i) +
+                                     ": malformed CSR (rowptr, column order/range or non-finite value)");
+  } catch (const Error &e) {
+    return fail(e.status, e.what());
+  } catch (const std::bad_alloc &) {
+    return fail(SIGN_ENOMEM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(SIGN_ECUDA, e.what());
+  }
+  for (int i = 0; i < count; ++i) out[i] = hs[size_t(i)].release();
+  return SIGN_OK;
+}
+
 sign_status sign_solve_batch(sign_t *hs, int count, const sign_opts *o, sign_info *infos) {
   g_err.clear();
   if (!hs || count < 1) return fail(SIGN_EINVAL, "need at least one handle");

@@ -262,6 +262,42 @@ def test_invalid_inputs_rejected(sg):
         sg.solve(w.tridiagonal(10), filter=7)
 
 
+def test_create_batch_names_the_bad_matrix_and_reads_into_caller_buffers(sg):
+    import torch
+    from paper_2210_03356_gb300 import Batch, SignError
+    good = [w.tridiagonal(300), w.banded(500, 3, 11)]
+    bad = w.CSR(2, np.array([0, 2, 3], np.int64), np.array([1, 0, 1], np.int32), np.ones(3))
+    with pytest.raises(SignError) as e:
+        Batch(good + [bad] + good)
+    assert e.value.status == sg.SIGN_EINVAL and "matrix 2" in str(e.value)
+    class T:  # the same CSR as CUDA tensors
+        n = good[0].n
+        rowptr = torch.from_numpy(good[0].rowptr).cuda()
+        col = torch.from_numpy(good[0].col).cuda()
+        val = torch.from_numpy(good[0].val).cuda()
+    with pytest.raises(ValueError):
+        Batch([good[0], T])
+    opts = sg.default_opts(tol=1e-8, dense_frac=2.0)
+    for mats in (good, [T, T]):
+        b = Batch(mats)
+        try:
+            b.solve(opts)
+            h = b.handles[0]
+            rp, col, val = h.result()
+            nnz = h.result_nnz()
+            assert nnz == col.size
+            pin = (torch.empty(h.n + 1, dtype=torch.int64, pin_memory=True).numpy(),
+                   torch.empty(nnz + 5, dtype=torch.int32, pin_memory=True).numpy(),
+                   torch.empty(nnz + 5, dtype=torch.float64, pin_memory=True).numpy())
+            rp2, col2, val2 = h.result(out=pin)
+            assert np.array_equal(rp, rp2) and np.array_equal(col, col2)
+            assert np.array_equal(val, val2)
+            with pytest.raises(ValueError):
+                h.result(out=(pin[0], pin[1][:nnz - 1], pin[2]))
+        finally:
+            b.close()
+
+
 # ---------------------------------------------------------------- threshold select (step a5)
 def _tau_ref(orc, vals, b):
     """tau of the oracle's EXACT filter for an array (laid out as one CSR row per value)."""
