@@ -117,8 +117,11 @@ struct Rows {
 // them: lists holds 4 lists of n entries (32-, 16- or 8-lane groups, or one
 // CTA per row); counters[0..3] are their lengths and counters[4..7] the
 // work-queue heads of the numeric kernels (all zeroed by the caller).
-// groups = 0 keeps every warp-sized row on 32 lanes (the FP32 products are
-// latency-bound; narrower groups pay off only for the FP64 pipe).
+// groups: 0 keeps every warp-sized row on 32 lanes; 1 (FP64 products, bound
+// by the FP64 pipe) picks 32, 16 or 8 lanes by lane utilisation; 2 (FP32
+// products, bound by gather latency) gives 16 lanes to rows of extent <= 512
+// whose B rows average <= 128 entries, so that a warp has two rows' gathers
+// in flight.
 // dslot (nullable, per matrix): matrices with dslot[m] >= 0 take the dense
 // path; their rows get no sparse work, and in MODE_UPDATE a whole row of
 // slots (moff gives the matrix sizes).

@@ -94,6 +94,16 @@ __device__ __forceinline__ int64_t lower_bound(const int32_t *a, int64_t lo, int
 enum RowClass { RC_G32 = 0, RC_CTA = 1, RC_G16 = 2, RC_G8 = 3, RC_NONE = 4, RC_N = 4 };
 constexpr int BOUNDS_TILE = 256;  // rows per CTA of k_bounds; lists keep this order
 
+// Row grouping of k_bounds: GROUPS_NONE keeps every row on 32 lanes.
+// GROUPS_THROUGHPUT (FP64 products, bound by the FP64 pipe) picks the group
+// size that leaves the fewest lanes idle in a k-step. GROUPS_LATENCY (FP32
+// products, bound by the latency of the B-row gathers) puts two rows in a
+// warp when a 32-lane pass over their B rows would give each lane at most one
+// unrolled batch of four products (an average B row of <= G16_MAX_AVG
+// entries): the warp then has twice the independent gathers in flight.
+enum { GROUPS_NONE = 0, GROUPS_THROUGHPUT = 1, GROUPS_LATENCY = 2 };
+constexpr float G16_MAX_AVG = 128.0f;
+
 // Lane utilization of one k-step with g lanes and a B row of avg entries.
 __device__ __forceinline__ float lane_use(float avg, int g) {
   float rounds = ceilf(avg / float(g));
@@ -167,6 +177,10 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
               cls = RC_CTA;
             } else if (!groups) {
               cls = RC_G32;
+            } else if (groups == GROUPS_LATENCY) {
+              float avg = float(wk) / float(a1 > a0 ? a1 - a0 : 1);
+              cls = RC_G32;
+              if (L <= WARP_W / 2 && avg <= G16_MAX_AVG) cls = RC_G16;
             } else {
               float avg = float(wk) / float(a1 > a0 ? a1 - a0 : 1);
               float u32 = lane_use(avg, 32), u16 = lane_use(avg, 16), u8 = lane_use(avg, 8);
@@ -265,15 +279,19 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, WarpOcc<T>::value)
                 int cls, const int64_t *cs, int64_t *ce, int32_t *ccol, T *cval, double *part) {
   constexpr int NG = 32 / G;
   constexpr int SLOTS = WARP_W / NG;
-  __shared__ T acc_all[WARPS_PER_CTA][WARP_W];
-  __shared__ unsigned char flags[WARPS_PER_CTA][WARP_W];
+  // group bases staggered across shared-memory banks: without it the groups of
+  // a warp (or of a half-warp, for 8-byte values) start on the same bank and
+  // their lanes, which touch neighbouring slots, collide
+  constexpr int PAD = G == 32 ? 0 : (sizeof(T) == 4 ? G : (G == 8 ? 8 : 0));
+  __shared__ T acc_all[WARPS_PER_CTA][WARP_W + 3 * PAD];
+  __shared__ unsigned char flags[WARPS_PER_CTA][WARP_W + 3 * PAD];
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int g = lane / G, gl = lane % G;
   const unsigned gbits = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
   const unsigned gmask = gbits << (g * G);
   const unsigned lt = (1u << gl) - 1u;
-  T *acc = acc_all[w] + g * SLOTS;
-  unsigned char *f = flags[w] + g * SLOTS;
+  T *acc = acc_all[w] + g * (SLOTS + PAD);
+  unsigned char *f = flags[w] + g * (SLOTS + PAD);
   const int total = counters[cls];
   for (;;) {
     int base = 0;

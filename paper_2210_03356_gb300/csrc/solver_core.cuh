@@ -304,7 +304,7 @@ struct Solver {
     SGN_CUDA(cudaMemsetAsync(w.counters.p, 0, sizeof(int) * 8, s));
     {
       ProfScope ps(KC_BOUNDS, s);
-      launch_bounds(N, A, B, st.d_seg.template as<int32_t>(), active, mode, sizeof(T) == 8 ? 1 : 0,
+      launch_bounds(N, A, B, st.d_seg.template as<int32_t>(), active, mode, sizeof(T) == 8 ? 1 : 2,
                     dp && dp->any() ? w.dslot.as<int>() : nullptr,
                     st.d_moff.template as<int64_t>(), w.lo.as<int32_t>(),
                     w.len.as<int32_t>(), w.ub.as<int64_t>(), w.wlist.as<int32_t>(),
