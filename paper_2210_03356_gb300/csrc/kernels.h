@@ -119,9 +119,8 @@ struct Rows {
 // work-queue heads of the numeric kernels (all zeroed by the caller).
 // groups: 0 keeps every warp-sized row on 32 lanes; 1 (FP64 products, bound
 // by the FP64 pipe) picks 32, 16 or 8 lanes by lane utilisation; 2 (FP32
-// products, bound by gather latency) gives 16 lanes to rows of extent <= 512
-// whose B rows average <= 128 entries, so that a warp has two rows' gathers
-// in flight.
+// products) lists every row of extent <= 512 in the 16-lane class, whose FP32
+// kernel runs the rows two per warp with shared passes over B.
 // dslot (nullable, per matrix): matrices with dslot[m] >= 0 take the dense
 // path; their rows get no sparse work, and in MODE_UPDATE a whole row of
 // slots (moff gives the matrix sizes).

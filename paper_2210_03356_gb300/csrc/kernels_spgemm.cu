@@ -96,13 +96,11 @@ constexpr int BOUNDS_TILE = 256;  // rows per CTA of k_bounds; lists keep this o
 
 // Row grouping of k_bounds: GROUPS_NONE keeps every row on 32 lanes.
 // GROUPS_THROUGHPUT (FP64 products, bound by the FP64 pipe) picks the group
-// size that leaves the fewest lanes idle in a k-step. GROUPS_LATENCY (FP32
-// products, bound by the latency of the B-row gathers) puts two rows in a
-// warp when a 32-lane pass over their B rows would give each lane at most one
-// unrolled batch of four products (an average B row of <= G16_MAX_AVG
-// entries): the warp then has twice the independent gathers in flight.
-enum { GROUPS_NONE = 0, GROUPS_THROUGHPUT = 1, GROUPS_LATENCY = 2 };
-constexpr float G16_MAX_AVG = 128.0f;
+// size that leaves the fewest lanes idle in a k-step. GROUPS_PAIRS (FP32
+// products, bound by instruction issue and gather latency) sends every row
+// that fits half a warp's accumulator to the pair kernel, where neighbouring
+// rows share their passes over B (pair_rows).
+enum { GROUPS_NONE = 0, GROUPS_THROUGHPUT = 1, GROUPS_PAIRS = 2 };
 
 // Lane utilization of one k-step with g lanes and a B row of avg entries.
 __device__ __forceinline__ float lane_use(float avg, int g) {
@@ -177,10 +175,8 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
               cls = RC_CTA;
             } else if (!groups) {
               cls = RC_G32;
-            } else if (groups == GROUPS_LATENCY) {
-              float avg = float(wk) / float(a1 > a0 ? a1 - a0 : 1);
-              cls = RC_G32;
-              if (L <= WARP_W / 2 && avg <= G16_MAX_AVG) cls = RC_G16;
+            } else if (groups == GROUPS_PAIRS) {
+              cls = L <= WARP_W / 2 ? RC_G16 : RC_G32;
             } else {
               float avg = float(wk) / float(a1 > a0 ? a1 - a0 : 1);
               float u32 = lane_use(avg, 32), u16 = lane_use(avg, 16), u8 = lane_use(avg, 8);
@@ -225,11 +221,35 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
   }
 }
 
+// Touched slots. With MARK = false every product sets the slot's byte flag
+// f[j] = 1. With MARK = true (FP32 accumulators) an untouched slot holds -0.0
+// and no flag is written: each product is fma(a, b, acc) + 0, and adding +0
+// turns a -0 result into +0 and leaves every other value as it is. A slot
+// reads -0 only until its first product, and its values are those of an
+// accumulation from +0 (which can never produce -0) bit for bit.
+template <typename T, bool MARK>
+__device__ __forceinline__ bool untouched(T v) {
+  if constexpr (MARK)
+    return __float_as_uint(v) == 0x80000000u;
+  else
+    return false;
+}
+template <typename T, bool MARK>
+__device__ __forceinline__ void mac(T *acc, unsigned char *f, int j, T a, T v) {
+  static_assert(!MARK || sizeof(T) == 4, "the -0 marker is used for FP32 accumulators");
+  if constexpr (MARK) {
+    acc[j] = __fadd_rn(fma_rn(a, v, acc[j]), 0.0f);
+  } else {
+    acc[j] = fma_rn(a, v, acc[j]);
+    f[j] = 1;
+  }
+}
+
 // One k of the accumulation: lanes stride over B_k = [q0, q1) and add
 // a * b_kj into acc[col - c0], up to four independent products per lane in
 // flight. The columns of B_k are distinct, so the slots of one call never
 // collide.
-template <typename T, int STRIDE>
+template <typename T, int STRIDE, bool MARK = false>
 __device__ __forceinline__ void accumulate_k(T a, int64_t q0, int64_t q1, const int32_t *bcol,
                                              const T *bval, int64_t c0, T *acc,
                                              unsigned char *f, int tid) {
@@ -238,31 +258,139 @@ __device__ __forceinline__ void accumulate_k(T a, int64_t q0, int64_t q1, const 
     int j0 = int(bcol[q] - c0), j1 = int(bcol[q + STRIDE] - c0);
     int j2 = int(bcol[q + 2 * STRIDE] - c0), j3 = int(bcol[q + 3 * STRIDE] - c0);
     T v0 = bval[q], v1 = bval[q + STRIDE], v2 = bval[q + 2 * STRIDE], v3 = bval[q + 3 * STRIDE];
-    acc[j0] = fma_rn(a, v0, acc[j0]);
-    acc[j1] = fma_rn(a, v1, acc[j1]);
-    acc[j2] = fma_rn(a, v2, acc[j2]);
-    acc[j3] = fma_rn(a, v3, acc[j3]);
-    f[j0] = 1;
-    f[j1] = 1;
-    f[j2] = 1;
-    f[j3] = 1;
+    mac<T, MARK>(acc, f, j0, a, v0);
+    mac<T, MARK>(acc, f, j1, a, v1);
+    mac<T, MARK>(acc, f, j2, a, v2);
+    mac<T, MARK>(acc, f, j3, a, v3);
   }
   if (q + STRIDE < q1) {
     int j0 = int(bcol[q] - c0), j1 = int(bcol[q + STRIDE] - c0);
     T v0 = bval[q], v1 = bval[q + STRIDE];
-    acc[j0] = fma_rn(a, v0, acc[j0]);
-    acc[j1] = fma_rn(a, v1, acc[j1]);
-    f[j0] = 1;
-    f[j1] = 1;
+    mac<T, MARK>(acc, f, j0, a, v0);
+    mac<T, MARK>(acc, f, j1, a, v1);
     q += 2 * STRIDE;
   }
-  if (q < q1) {
-    int j = int(bcol[q] - c0);
-    acc[j] = fma_rn(a, bval[q], acc[j]);
-    f[j] = 1;
+  if (q < q1) mac<T, MARK>(acc, f, int(bcol[q] - c0), a, bval[q]);
+}
+
+// accumulate_k for one k shared by two rows (a_ik and a_i'k): every entry of
+// B_k is loaded once and added into both rows' accumulators.
+template <typename T, bool MARK>
+__device__ __forceinline__ void accumulate_k2(T a, T b, int64_t q0, int64_t q1,
+                                              const int32_t *bcol, const T *bval, int32_t ca,
+                                              T *acca, unsigned char *fa, int32_t cb, T *accb,
+                                              unsigned char *fb, int tid) {
+  int64_t q = q0 + tid;
+  for (; q + 96 < q1; q += 128) {
+    int32_t c0 = bcol[q], c1 = bcol[q + 32], c2 = bcol[q + 64], c3 = bcol[q + 96];
+    T v0 = bval[q], v1 = bval[q + 32], v2 = bval[q + 64], v3 = bval[q + 96];
+    mac<T, MARK>(acca, fa, c0 - ca, a, v0);
+    mac<T, MARK>(acca, fa, c1 - ca, a, v1);
+    mac<T, MARK>(acca, fa, c2 - ca, a, v2);
+    mac<T, MARK>(acca, fa, c3 - ca, a, v3);
+    mac<T, MARK>(accb, fb, c0 - cb, b, v0);
+    mac<T, MARK>(accb, fb, c1 - cb, b, v1);
+    mac<T, MARK>(accb, fb, c2 - cb, b, v2);
+    mac<T, MARK>(accb, fb, c3 - cb, b, v3);
+  }
+  for (; q < q1; q += 32) {
+    int32_t c = bcol[q];
+    T v = bval[q];
+    mac<T, MARK>(acca, fa, c - ca, a, v);
+    mac<T, MARK>(accb, fb, c - cb, b, v);
   }
 }
 
+// The k-loop of two rows run by one warp (rows of the 16-lane pair class).
+// Their k lists, each ascending, are merged: a k found in both rows is one
+// step that feeds both accumulators from a single pass over B_k, a k of one
+// row only is a step of that row alone. Each row thus still receives its k in
+// ascending order, one FMA per slot per k, exactly as with a warp of its own.
+// Rows of a banded iterate that are neighbours share almost all of their k,
+// so the pair gathers B about half as often as two warps would.
+// Row x has k entries [pa, ea) and accumulator (acca, fa) for columns from
+// ca; row y likewise (an absent row has pb == eb).
+template <typename T, bool MARK>
+__device__ __forceinline__ void pair_rows(int64_t pa, int64_t ea, int64_t pb, int64_t eb,
+                                          const int32_t *acol, const T *aval,
+                                          const int64_t *brs, const int64_t *bre,
+                                          const int32_t *bcol, const T *bval, int32_t ca,
+                                          T *acca, unsigned char *fa, int32_t cb, T *accb,
+                                          unsigned char *fb, int lane) {
+  constexpr unsigned FULL = 0xffffffffu;
+  // lane l holds the (k, a_k, start, length) of the l-th k of each row's window
+  int ka = INT_MAX, kb = INT_MAX, na = 0, nb = 0;
+  T va = T(0), vb = T(0);
+  int64_t qa = 0, qb = 0;
+  {
+    int64_t p = pa + lane;
+    if (p < ea) {
+      ka = acol[p];
+      va = aval[p];
+      qa = brs[ka];
+      na = int(bre[ka] - qa);
+    }
+    p = pb + lane;
+    if (p < eb) {
+      kb = acol[p];
+      vb = aval[p];
+      qb = brs[kb];
+      nb = int(bre[kb] - qb);
+    }
+  }
+  int ia = 0, ib = 0;
+  for (;;) {
+    if (ia == 32) {  // window of row x used up: the next 32 k
+      pa += 32;
+      ia = 0;
+      int64_t p = pa + lane;
+      ka = INT_MAX;
+      if (p < ea) {
+        ka = acol[p];
+        va = aval[p];
+        qa = brs[ka];
+        na = int(bre[ka] - qa);
+      }
+    }
+    if (ib == 32) {
+      pb += 32;
+      ib = 0;
+      int64_t p = pb + lane;
+      kb = INT_MAX;
+      if (p < eb) {
+        kb = acol[p];
+        vb = aval[p];
+        qb = brs[kb];
+        nb = int(bre[kb] - qb);
+      }
+    }
+    const int ha = __shfl_sync(FULL, ka, ia), hb = __shfl_sync(FULL, kb, ib);
+    if (ha == INT_MAX && hb == INT_MAX) break;
+    if (ha == hb) {
+      const T a = __shfl_sync(FULL, va, ia), b = __shfl_sync(FULL, vb, ib);
+      const int64_t q0 = __shfl_sync(FULL, qa, ia);
+      const int n = __shfl_sync(FULL, na, ia);
+      accumulate_k2<T, MARK>(a, b, q0, q0 + n, bcol, bval, ca, acca, fa, cb, accb, fb, lane);
+      ++ia;
+      ++ib;
+    } else if (ha < hb) {
+      const T a = __shfl_sync(FULL, va, ia);
+      const int64_t q0 = __shfl_sync(FULL, qa, ia);
+      const int n = __shfl_sync(FULL, na, ia);
+      accumulate_k<T, 32, MARK>(a, q0, q0 + n, bcol, bval, ca, acca, fa, lane);
+      ++ia;
+    } else {
+      const T b = __shfl_sync(FULL, vb, ib);
+      const int64_t q0 = __shfl_sync(FULL, qb, ib);
+      const int n = __shfl_sync(FULL, nb, ib);
+      accumulate_k<T, 32, MARK>(b, q0, q0 + n, bcol, bval, cb, accb, fb, lane);
+      ++ib;
+    }
+    __syncwarp();
+  }
+}
+
+constexpr int PAIR_OCC = 8;  // CTAs per SM of the pair kernel: 64 registers, no spills
 template <typename T>
 struct WarpOcc;  // CTAs per SM of the warp kernel (shared memory and registers)
 template <> struct WarpOcc<double> { static constexpr int value = 6; };
@@ -271,12 +399,16 @@ template <> struct WarpOcc<float> { static constexpr int value = 10; };
 // G lanes per row, 32/G rows per warp; each group owns WARP_W*G/32 slots of
 // its warp's accumulator and runs the ascending-k accumulation of its own row
 // with group-wide barriers, so the result is the same as with a whole warp.
-template <typename T, int MODE, int G>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32, WarpOcc<T>::value)
+// PAIR (with G = 16): the two rows of a warp share its k-loop (pair_rows);
+// the rest of the kernel is that of 16-lane groups.
+template <typename T, int MODE, int G, bool PAIR = false>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, PAIR ? PAIR_OCC : WarpOcc<T>::value)
     k_num_group(const int64_t *ars, const int64_t *are, const int32_t *acol, const T *aval,
                 const int64_t *brs, const int64_t *bre, const int32_t *bcol, const T *bval,
                 const int32_t *lo, const int32_t *len, const int32_t *list, int *counters,
                 int cls, const int64_t *cs, int64_t *ce, int32_t *ccol, T *cval, double *part) {
+  static_assert(!PAIR || G == 16, "pairs are two 16-lane groups");
+  constexpr bool MARK = sizeof(T) == 4;  // untouched FP32 slots hold -0 (see mac)
   constexpr int NG = 32 / G;
   constexpr int SLOTS = WARP_W / NG;
   // group bases staggered across shared-memory banks: without it the groups of
@@ -299,88 +431,111 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, WarpOcc<T>::value)
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= total) break;
     const int idx = base + g;
-    if (idx < total) {
-      const int32_t r = list[idx];
-      const int L = len[r];
-      const int32_t c0 = lo[r];
+    if (PAIR || idx < total) {
+      const bool has = idx < total;  // the second row of the last pair may be absent
+      const int32_t r = has ? list[idx] : 0;
+      const int L = has ? len[r] : 0;
+      const int32_t c0 = has ? lo[r] : 0;
       for (int s = gl; s < L; s += G) {
-        acc[s] = T(0);
-        f[s] = 0;
+        acc[s] = MARK ? T(-0.0) : T(0);
+        if (!MARK || MODE == MODE_UPDATE) f[s] = 0;
       }
-      __syncwarp(gmask);
-      const int64_t a0 = ars[r], a1 = are[r];
-      // ascending k; the (a_ik, start, end) of G k at a time are fetched by the
-      // group's lanes together and broadcast inside the group
-      for (int64_t pb = a0; pb < a1; pb += G) {
-        const int nk = int(min(int64_t(G), a1 - pb));
-        T av = T(0);
-        int64_t qs = 0, qe = 0;
-        if (gl < nk) {
-          int32_t k = acol[pb + gl];
-          av = aval[pb + gl];
-          qs = brs[k];
-          qe = bre[k];
+      const int64_t a0 = has ? ars[r] : 0, a1 = has ? are[r] : 0;
+      if (PAIR) {
+        __syncwarp();
+        constexpr unsigned FULL = 0xffffffffu;
+        pair_rows<T, MARK>(__shfl_sync(FULL, a0, 0), __shfl_sync(FULL, a1, 0),
+                     __shfl_sync(FULL, a0, G), __shfl_sync(FULL, a1, G), acol, aval, brs, bre,
+                     bcol, bval, __shfl_sync(FULL, c0, 0), acc_all[w], flags[w],
+                     __shfl_sync(FULL, c0, G), acc_all[w] + (SLOTS + PAD),
+                     flags[w] + (SLOTS + PAD), lane);
+      } else {
+        __syncwarp(gmask);
+        // ascending k; the (a_ik, start, end) of G k at a time are fetched by
+        // the group's lanes together and broadcast inside the group
+        for (int64_t pb = a0; pb < a1; pb += G) {
+          const int nk = int(min(int64_t(G), a1 - pb));
+          T av = T(0);
+          int64_t qs = 0, qe = 0;
+          if (gl < nk) {
+            int32_t k = acol[pb + gl];
+            av = aval[pb + gl];
+            qs = brs[k];
+            qe = bre[k];
+          }
+          for (int t = 0; t < nk; ++t) {
+            T a = __shfl_sync(gmask, av, t, G);
+            int64_t q0 = __shfl_sync(gmask, qs, t, G);
+            int64_t q1 = __shfl_sync(gmask, qe, t, G);
+            accumulate_k<T, G, MARK>(a, q0, q1, bcol, bval, c0, acc, f, gl);
+            __syncwarp(gmask);
+          }
         }
-        for (int t = 0; t < nk; ++t) {
-          T a = __shfl_sync(gmask, av, t, G);
-          int64_t q0 = __shfl_sync(gmask, qs, t, G);
-          int64_t q1 = __shfl_sync(gmask, qe, t, G);
-          accumulate_k<T, G>(a, q0, q1, bcol, bval, c0, acc, f, gl);
+      }
+      if (has) {  // group-uniform
+        if (MODE == MODE_UPDATE) {
+          for (int64_t p = a0 + gl; p < a1; p += G) {
+            int j = acol[p] - c0;
+            T xt = acc[j];
+            if (untouched<T, MARK>(xt)) xt = T(0);
+            acc[j] = ns_combine(aval[p], xt);
+            f[j] = 3;
+          }
           __syncwarp(gmask);
         }
-      }
-      if (MODE == MODE_UPDATE) {
-        for (int64_t p = a0 + gl; p < a1; p += G) {
-          int j = acol[p] - c0;
-          acc[j] = ns_combine(aval[p], acc[j]);
-          f[j] = 3;
+        int64_t out = cs[r];
+        SqAcc<T> racc;
+        double rdiag = 0.0;
+        bool diag = false;
+        for (int s0 = 0; s0 < L; s0 += G) {
+          int s = s0 + gl;
+          int fl = 0;
+          if (s < L) {
+            if (MARK) {  // touched: a product (acc is not -0) or, in an update, x_ij
+              fl = MODE == MODE_UPDATE ? f[s] : 0;
+              if (!fl && !untouched<T, MARK>(acc[s])) fl = 1;
+            } else {
+              fl = f[s];
+            }
+          }
+          unsigned m = (__ballot_sync(gmask, fl != 0) >> (g * G)) & gbits;
+          if (fl) {
+            int64_t pos = out + __popc(m & lt);
+            int32_t cj = c0 + s;
+            T v = acc[s];
+            if (MODE == MODE_UPDATE && !(fl & 2)) v = ns_combine(T(0), v);
+            ccol[pos] = cj;
+            cval[pos] = v;
+            if (MODE == MODE_SQUARE) {
+              if (cj == r) {  // (t_ii - 1)^2 in FP64, once per row
+                double d = double(v) - 1.0;
+                rdiag = d * d;
+                diag = true;
+              } else {
+                racc.add_sq(v);
+              }
+            }
+          }
+          out += __popc(m);
+        }
+        if (gl == 0) ce[r] = out;
+        if (MODE == MODE_SQUARE) {
+          SqAcc<T> xacc;
+          for (int64_t p = a0 + gl; p < a1; p += G) xacc.add_sq(aval[p]);
+          double rs = racc.value() + rdiag, xs = xacc.value();
+  #pragma unroll
+          for (int o = G / 2; o > 0; o >>= 1) {
+            rs += __shfl_xor_sync(gmask, rs, o, G);
+            xs += __shfl_xor_sync(gmask, xs, o, G);
+          }
+          bool any_diag = __any_sync(gmask, diag);
+          if (gl == 0) {
+            part[2 * int64_t(r)] = any_diag ? rs : rs + 1.0;
+            part[2 * int64_t(r) + 1] = xs;
+          }
         }
         __syncwarp(gmask);
       }
-      int64_t out = cs[r];
-      SqAcc<T> racc;
-      double rdiag = 0.0;
-      bool diag = false;
-      for (int s0 = 0; s0 < L; s0 += G) {
-        int s = s0 + gl;
-        int fl = s < L ? f[s] : 0;
-        unsigned m = (__ballot_sync(gmask, fl != 0) >> (g * G)) & gbits;
-        if (fl) {
-          int64_t pos = out + __popc(m & lt);
-          int32_t cj = c0 + s;
-          T v = acc[s];
-          if (MODE == MODE_UPDATE && !(fl & 2)) v = ns_combine(T(0), v);
-          ccol[pos] = cj;
-          cval[pos] = v;
-          if (MODE == MODE_SQUARE) {
-            if (cj == r) {  // (t_ii - 1)^2 in FP64, once per row
-              double d = double(v) - 1.0;
-              rdiag = d * d;
-              diag = true;
-            } else {
-              racc.add_sq(v);
-            }
-          }
-        }
-        out += __popc(m);
-      }
-      if (gl == 0) ce[r] = out;
-      if (MODE == MODE_SQUARE) {
-        SqAcc<T> xacc;
-        for (int64_t p = a0 + gl; p < a1; p += G) xacc.add_sq(aval[p]);
-        double rs = racc.value() + rdiag, xs = xacc.value();
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-          rs += __shfl_xor_sync(gmask, rs, o, G);
-          xs += __shfl_xor_sync(gmask, xs, o, G);
-        }
-        bool any_diag = __any_sync(gmask, diag);
-        if (gl == 0) {
-          part[2 * int64_t(r)] = any_diag ? rs : rs + 1.0;
-          part[2 * int64_t(r) + 1] = xs;
-        }
-      }
-      __syncwarp(gmask);
     }
     __syncwarp();
   }
@@ -585,13 +740,14 @@ void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, 
   SGN_LAUNCH_CHECK();
 }
 
-template <typename T, int MODE, int G>
+template <typename T, int MODE, int G, bool PAIR = false>
 static void group_launch(int64_t n, const Rows &A, const T *aval, const Rows &B, const T *bval,
                          const int32_t *lo, const int32_t *len, const int32_t *lists, int *ctr,
                          int cls, const int64_t *cs, int64_t *ce, int32_t *ccol, T *cval,
                          double *part, cudaStream_t s) {
-  k_num_group<T, MODE, G><<<grid_cap(n, WARPS_PER_CTA * (32 / G), WarpOcc<T>::value),
-                            WARPS_PER_CTA * 32, 0, s>>>(
+  k_num_group<T, MODE, G, PAIR><<<grid_cap(n, WARPS_PER_CTA * (32 / G),
+                                           PAIR ? PAIR_OCC : WarpOcc<T>::value),
+                                  WARPS_PER_CTA * 32, 0, s>>>(
       A.rs, A.re, A.col, aval, B.rs, B.re, B.col, bval, lo, len, lists + int64_t(cls) * n, ctr,
       cls, cs, ce, ccol, cval, part);
   SGN_LAUNCH_CHECK();
@@ -604,8 +760,9 @@ static void num_launch(int64_t n, const Rows &A, const T *aval, const Rows &B, c
                        cudaStream_t s) {
   group_launch<T, MODE, 32>(n, A, aval, B, bval, lo, len, lists, ctr, RC_G32, cs, ce, ccol, cval,
                             part, s);
-  group_launch<T, MODE, 16>(n, A, aval, B, bval, lo, len, lists, ctr, RC_G16, cs, ce, ccol, cval,
-                            part, s);
+  // FP32: the 16-lane class holds row pairs (GROUPS_PAIRS)
+  group_launch<T, MODE, 16, sizeof(T) == 4>(n, A, aval, B, bval, lo, len, lists, ctr, RC_G16, cs,
+                                            ce, ccol, cval, part, s);
   group_launch<T, MODE, 8>(n, A, aval, B, bval, lo, len, lists, ctr, RC_G8, cs, ce, ccol, cval,
                            part, s);
   constexpr size_t sm = num_cta_smem<T>();
