@@ -215,24 +215,32 @@ __global__ void __launch_bounds__(SEL_THREADS)
       int64_t p0 = e0 + lane * per, p1 = min(p0 + per, e1);
       int cur = -1;
       unsigned long long clo = 0, chi = 0, mymin = ~0ULL;
-      for (int64_t p = p0; p < p1; ++p) {
-        unsigned long long key = key_of(val, f32, p);
-        if (key > bkey) {
-          mymin = key < mymin ? key : mymin;
-          continue;
-        }
-        if (key < tiny) continue;
-        unsigned long long q = qval(key, qs);
-        if (!q) continue;
-        int bk = bucket0(key, bkey);
-        if (bk != cur) {
-          if (cur >= 0) add128(hist + 2 * cur, clo, chi);
-          cur = bk;
-          clo = q;
-          chi = 0;
-        } else {
-          clo += q;
-          if (clo < q) ++chi;
+      // four independent loads in flight, then the entries in order
+      for (int64_t pb = p0; pb < p1; pb += 4) {
+        unsigned long long keys[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) keys[u] = pb + u < p1 ? key_of(val, f32, pb + u) : 0ULL;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const unsigned long long key = keys[u];
+          if (pb + u >= p1) break;
+          if (key > bkey) {
+            mymin = key < mymin ? key : mymin;
+            continue;
+          }
+          if (key < tiny) continue;
+          unsigned long long q = qval(key, qs);
+          if (!q) continue;
+          int bk = bucket0(key, bkey);
+          if (bk != cur) {
+            if (cur >= 0) add128(hist + 2 * cur, clo, chi);
+            cur = bk;
+            clo = q;
+            chi = 0;
+          } else {
+            clo += q;
+            if (clo < q) ++chi;
+          }
         }
       }
       if (cur >= 0) add128(hist + 2 * cur, clo, chi);
@@ -416,7 +424,9 @@ __global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
       const float tf = __double2float_ru(tau);
       const float *v = static_cast<const float *>(val);
       float hi = 0.0f, lo = 0.0f;  // dropped squares, scaled by 2^96
-      for (int64_t p = rs[r] + lane; p < re[r]; p += 32) {
+      const int64_t pe = re[r];
+#pragma unroll 4
+      for (int64_t p = rs[r] + lane; p < pe; p += 32) {
         const float x = v[p];
         if (fabsf(x) >= tf && x != 0.0f)
           ++c;
@@ -435,7 +445,9 @@ __global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
       }
     } else if (active[m]) {
       const double *v = static_cast<const double *>(val);
-      for (int64_t p = rs[r] + lane; p < re[r]; p += 32) {
+      const int64_t pe = re[r];
+#pragma unroll 4
+      for (int64_t p = rs[r] + lane; p < pe; p += 32) {
         double x = v[p];
         if (fabs(x) >= tau && x != 0.0)
           ++c;

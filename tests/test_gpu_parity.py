@@ -104,6 +104,35 @@ def test_mixed_precision_matches_mixed_oracle(sg, orc):
     assert np.linalg.norm(d) / np.linalg.norm(ref64.to_dense(a.n)) < 1e-6
 
 
+def _with_explicit_zeros(a, b):
+    """a with every other entry of its outermost diagonals stored as +0 or -0."""
+    rows = np.repeat(np.arange(a.n), np.diff(a.rowptr))
+    val = a.val.copy()
+    edge = np.abs(a.col - rows) == b
+    key = np.minimum(rows, a.col)[edge]      # the same sign for (i, j) and (j, i)
+    val[np.flatnonzero(edge)[key % 2 == 0]] = np.where(key[key % 2 == 0] % 4 == 0, -0.0, 0.0)
+    return w.CSR(a.n, a.rowptr, a.col, val)
+
+
+@pytest.mark.parametrize("filt,max_iter", [("none", 1), ("none", 3), ("exact", 100)])
+def test_explicit_zeros_keep_pattern_and_signs(sg, orc, filt, max_iter):
+    """Products that are all +-0 still create their entry, with the value +0.
+
+    Explicit zeros on the outermost diagonals make some entries of X X and
+    X T reachable only through a zero factor; the FP32 accumulators mark
+    untouched slots with -0, so these entries test that marking. Signs of
+    zeros are compared bit for bit.
+    """
+    a = _with_explicit_zeros(w.banded(400, 5, w.BASE_SEED + 77), 5)
+    assert np.signbit(a.val[a.val == 0]).any() and (~np.signbit(a.val[a.val == 0])).any()
+    res = sg.solve(a, tol=1e-8, filter=filt, prec=1, max_iter=max_iter, dense_frac=2.0)
+    ref = orc.nsf(a, tol=1e-8, filter=filt, mixed=True, max_iter=max_iter)
+    assert_parity(res, ref)
+    assert np.array_equal(res.val.view(np.uint64), ref.val.view(np.uint64))
+    if filt == "none" and max_iter == 1:
+        assert (ref.val == 0).any()  # the case arises: entries whose products were all zero
+
+
 def res_dense(res, n):
     d = np.zeros((n, n))
     d[np.repeat(np.arange(n), np.diff(res.rowptr)), res.col] = res.val
