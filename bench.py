@@ -50,6 +50,13 @@ WORKLOAD = ("banded batch: 512 symmetric banded matrices, n log-uniform [200,800
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # FP32 peak: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic
+# byte of each product class, from one ncu capture of the first 128 matrices
+# of the batch (profiles/dram_traffic_products_banded128.md). A full-size
+# launch is taken to move DRAM bytes in the same proportion to its
+# algorithmic bytes. Valid for the product kernels as that capture built them.
+DRAM_PER_ALG_BYTE = {"numeric_square_f64": 0.896, "numeric_update_f64": 0.561,
+                     "numeric_square_f32": 0.845, "numeric_update_f32": 0.867}
 
 
 def rank_seed0(rank: int, count: int = BATCH) -> int:
@@ -460,8 +467,13 @@ def main():
         achieved = p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] else 0.0
         per_launch = p["bytes"] / max(p["launches"], 1)
     total_ms = sum(v["ms"] for v in prof.values())
+    alg_bytes = p["bytes"] / max(p["launches"], 1)
+    traffic = DRAM_PER_ALG_BYTE[name] * alg_bytes if name in DRAM_PER_ALG_BYTE else None
     roofline = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": ("ncu DRAM bytes per algorithmic byte on the first 128 matrices, "
+                                   "times this launch's algorithmic bytes" if traffic else None),
+                "algorithmic_bytes_per_launch": alg_bytes,
                 "peak_source": (f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if bound == "hbm"
                                 else "unit counts x 2.07 GHz (FP64: 2 FMA/clk/SM; FP32: 128)"),
                 "per_launch_work": per_launch, "avg_launch_ms": per_launch_ms,

@@ -275,9 +275,47 @@ __device__ __forceinline__ bool exceeds(unsigned long long lo, unsigned long lon
   return hi != 0ULL || lo > ONE62;
 }
 
+// The first of nbk buckets (128-bit sums h[2c], h[2c+1]) at which the running
+// sum, started at (lo, hi), exceeds 2^62, found by one warp: 32 buckets at a
+// time, lane c of a round holding bucket c and an inclusive prefix sum over
+// the round by shuffles. The sums are exact integers, so the crossing is the
+// one a serial walk finds. Returns the bucket (or -1, with (lo, hi) the total)
+// and leaves in (lo, hi) the sum of the buckets below it.
+__device__ __forceinline__ int warp_crossing(const unsigned long long *h, int nbk,
+                                             unsigned long long &lo, unsigned long long &hi) {
+  const int lane = threadIdx.x & 31;
+  for (int c0 = 0; c0 < nbk; c0 += 32) {
+    const int c = c0 + lane;
+    const unsigned long long blo = c < nbk ? h[2 * c] : 0ULL, bhi = c < nbk ? h[2 * c + 1] : 0ULL;
+    unsigned long long plo = blo, phi = bhi;  // inclusive prefix of the round
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long ulo = __shfl_up_sync(0xffffffffu, plo, o);
+      const unsigned long long uhi = __shfl_up_sync(0xffffffffu, phi, o);
+      if (lane >= o) u128_add(plo, phi, ulo, uhi);
+    }
+    unsigned long long rlo = lo, rhi = hi;
+    u128_add(rlo, rhi, plo, phi);
+    const unsigned over = __ballot_sync(0xffffffffu, c < nbk && exceeds(rlo, rhi));
+    if (over) {
+      const int f = __ffs(over) - 1;
+      // the sum below bucket f: start + inclusive prefix of f - h[f]
+      unsigned long long elo = rlo - blo, ehi = rhi - bhi - (rlo < blo ? 1ULL : 0ULL);
+      lo = __shfl_sync(0xffffffffu, elo, f);
+      hi = __shfl_sync(0xffffffffu, ehi, f);
+      return c0 + f;
+    }
+    lo = __shfl_sync(0xffffffffu, rlo, 31);
+    hi = __shfl_sync(0xffffffffu, rhi, 31);
+  }
+  return -1;
+}
+
+// One warp per matrix: the level-0 bucket where the exact sums cross 2^62.
 __global__ void k_sel_find0(int nb, const int *active, const MatScalars *ms, SelScratch sc) {
-  int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m == 0) *sc.ncand = 0ULL;
+  const int m = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (m == 0 && lane == 0) *sc.ncand = 0ULL;
   if (m >= nb) return;
   SelState st = {};
   if (active[m]) {
@@ -285,22 +323,15 @@ __global__ void k_sel_find0(int nb, const int *active, const MatScalars *ms, Sel
     long long base = (long long)(bkey >> 48) - (NB0 - 1);
     if (base < 0) base = 0;
     unsigned long long lo = 0, hi = 0;
-    const unsigned long long *h = sc.hist0 + size_t(m) * NB0 * 2;
-    for (int c = 0; c < NB0; ++c) {
-      unsigned long long nlo = lo, nhi = hi;
-      u128_add(nlo, nhi, h[2 * c], h[2 * c + 1]);
-      if (exceeds(nlo, nhi)) {
-        st.found = 1;
-        st.prefix = (unsigned long long)(base + c) << 48;
-        st.below_lo = lo;
-        st.below_hi = hi;
-        break;
-      }
-      lo = nlo;
-      hi = nhi;
+    const int c = warp_crossing(sc.hist0 + size_t(m) * NB0 * 2, NB0, lo, hi);
+    if (c >= 0) {
+      st.found = 1;
+      st.prefix = (unsigned long long)(base + c) << 48;
+      st.below_lo = lo;
+      st.below_hi = hi;
     }
   }
-  sc.st[m] = st;
+  if (lane == 0) sc.st[m] = st;
 }
 
 // Candidates: the entries of the crossing bucket (top 16 bits of the key equal
@@ -355,24 +386,19 @@ __global__ void k_sel_hist_digit(const MatScalars *ms, SelScratch sc, int shift)
   }
 }
 
+// One warp per matrix: the digit at `shift` where the sums cross 2^62.
 __global__ void k_sel_find_digit(int nb, SelScratch sc, int shift) {
-  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
   if (m >= nb) return;
   SelState &st = sc.st[m];
   if (!st.found) return;
-  const unsigned long long *h = sc.hdig + size_t(m) * NDIG * 2;
   unsigned long long lo = st.below_lo, hi = st.below_hi;
-  for (int d = 0; d < NDIG; ++d) {
-    unsigned long long nlo = lo, nhi = hi;
-    u128_add(nlo, nhi, h[2 * d], h[2 * d + 1]);
-    if (exceeds(nlo, nhi)) {
-      st.prefix |= (unsigned long long)d << shift;
-      st.below_lo = lo;
-      st.below_hi = hi;
-      return;
-    }
-    lo = nlo;
-    hi = nhi;
+  const int d = warp_crossing(sc.hdig + size_t(m) * NDIG * 2, NDIG, lo, hi);
+  __syncwarp();
+  if (d >= 0 && (threadIdx.x & 31) == 0) {
+    st.prefix |= (unsigned long long)d << shift;
+    st.below_lo = lo;
+    st.below_hi = hi;
   }
 }
 
@@ -556,7 +582,7 @@ void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *
           nb, R, active, val, val_f32, ms, sc);
       SGN_LAUNCH_CHECK();
     }
-    k_sel_find0<<<(nb + 127) / 128, 128, 0, s>>>(nb, active, ms, sc);
+    k_sel_find0<<<(nb + 3) / 4, 128, 0, s>>>(nb, active, ms, sc);
     SGN_LAUNCH_CHECK();
   }
   {
@@ -573,7 +599,7 @@ void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *
     SGN_CUDA(cudaMemsetAsync(sc.hdig, 0, size_t(nb) * NDIG * 2 * 8, s));
     k_sel_hist_digit<<<152 * 4, 256, 0, s>>>(ms, sc, shift);
     SGN_LAUNCH_CHECK();
-    k_sel_find_digit<<<(nb + 127) / 128, 128, 0, s>>>(nb, sc, shift);
+    k_sel_find_digit<<<(nb + 3) / 4, 128, 0, s>>>(nb, sc, shift);
     SGN_LAUNCH_CHECK();
   }
   k_sel_final<<<(nb + 127) / 128, 128, 0, s>>>(nb, active, sc, ms);
