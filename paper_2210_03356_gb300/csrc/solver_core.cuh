@@ -232,6 +232,40 @@ struct Stage {
   std::vector<std::unique_ptr<Parked>> incoming;  // matrices entering at the next round
 };
 
+// Pinned staging for the small host-to-device copies of the round loop.
+// cudaMemcpyAsync from pageable memory first waits for the stream, so every
+// such copy would stall the GPU; a copy from pinned memory is queued like a
+// kernel. The bytes are copied into the arena at once (the caller may reuse
+// its vector), and the arena is reused only after the stream has been
+// synchronized, when every copy from it has completed.
+struct Staging {
+  char *p = nullptr;
+  size_t cap = 0, used = 0;
+  Staging() = default;
+  Staging(const Staging &) = delete;
+  Staging &operator=(const Staging &) = delete;
+  ~Staging() {
+    if (p) cudaFreeHost(p);
+  }
+  bool fits(size_t bytes) const { return used + ((bytes + 63) & ~size_t(63)) <= cap; }
+  // the stream must be idle: nothing may still read the old arena
+  void reserve(size_t bytes) {
+    used = 0;
+    if (bytes <= cap) return;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    SGN_CUDA(cudaMallocHost(reinterpret_cast<void **>(&p), bytes));
+    cap = bytes;
+  }
+  void *put(const void *src, size_t bytes) {
+    char *d = p + used;
+    std::memcpy(d, src, bytes);
+    used += (bytes + 63) & ~size_t(63);
+    return d;
+  }
+};
+
 struct Solver {
   cudaStream_t s;
   sign_opts o;
@@ -242,6 +276,27 @@ struct Solver {
   HostMirror &hm = host_mirror();
   Stage<float> s32;          // FP32 stage of the mixed mode
   Stage<double> s64;
+  Staging stg;
+
+  ~Solver() {
+    if (stg.used) cudaStreamSynchronize(s);  // copies from the arena may be in flight
+  }
+  // Waits for the stream; the staging arena is free again afterwards.
+  void wait() {
+    sync(s);
+    stg.used = 0;
+  }
+  // h2d from host memory of any kind, through the pinned arena.
+  template <typename T>
+  void put(void *dst, const T *src, size_t count) {
+    const size_t bytes = sizeof(T) * count;
+    if (bytes == 0) return;
+    if (!stg.fits(bytes)) {
+      wait();
+      stg.reserve(std::max<size_t>(2 * stg.cap, std::max<size_t>(bytes + 64, size_t(1) << 18)));
+    }
+    SGN_CUDA(cudaMemcpyAsync(dst, stg.put(src, bytes), bytes, cudaMemcpyHostToDevice, s));
+  }
 
   // ---------------------------------------------------------------- helpers
   void set_layout(std::vector<int64_t> &moff, const std::vector<int> &mats, DevBuf &d_moff,
@@ -250,7 +305,7 @@ struct Solver {
     for (size_t i = 0; i < mats.size(); ++i) moff[i + 1] = moff[i] + m[mats[i]].h->n;
     int64_t N = moff.back();
     d_moff.ensure(sizeof(int64_t) * moff.size(), s);
-    h2d(d_moff.p, moff.data(), moff.size(), s);
+    put(d_moff.p, moff.data(), moff.size());
     d_seg.ensure(sizeof(int32_t) * size_t(N > 0 ? N : 1), s);
     launch_fill_seg(int(mats.size()), d_moff.as<int64_t>(), N, d_seg.as<int32_t>(), s);
   }
@@ -271,15 +326,13 @@ struct Solver {
     w.asm_off.ensure(sizeof(int64_t) * size_t(nb + 1), s);
     w.asm_lens.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
     w.scan_tmp.ensure(sizeof(int64_t) * size_t(scan_tmp_elems(N)), s);
-    h2d(w.asm_blocks.p, blocks.data(), blocks.size(), s);
-    h2d(w.asm_off.p, boff.data(), boff.size(), s);
+    put(w.asm_blocks.p, blocks.data(), blocks.size());
+    put(w.asm_off.p, boff.data(), boff.size());
     ProfScope ps(KC_ASSEMBLE, s, 0.0, double(nnz) * (8.0 + 4.0 + sizeof(TD)) + 16.0 * double(N));
     launch_assemble_rows(nb, w.asm_blocks.as<AsmBlock>(), w.asm_off.as<int64_t>(), N,
                          w.asm_lens.as<int64_t>(), dst.d_rp(), w.scan_tmp.as<int64_t>(), s);
     launch_assemble_vals(nb, w.asm_blocks.as<AsmBlock>(), w.asm_off.as<int64_t>(), N, dst.d_rp(),
                          dst.d_col(), dst.val.p, is_f32<TD>(), s);
-    // the block and offset arrays are pageable host copies: keep the stream in step
-    sync(s);
   }
 
   // ---------------------------------------------------------------- product
@@ -321,7 +374,7 @@ struct Solver {
     }
     d2h(hm.tot, C.rs.template as<int64_t>() + N, 1, s);
     d2h(hm.mults, w.mults.p, size_t(nb), s);
-    sync(s);
+    wait();
     int64_t slots = hm.tot[0];
     C.slots = slots;
     C.col.ensure(sizeof(int32_t) * size_t(slots > 0 ? slots : 1), s);
@@ -430,18 +483,17 @@ struct Solver {
       }
     }
     w.dslot.ensure(sizeof(int) * size_t(nb), s);
-    h2d(w.dslot.p, dp.slot.data(), size_t(nb), s);
+    put(w.dslot.p, dp.slot.data(), size_t(nb));
     if (f32) {
       w.dbufs.ensure(sizeof(DenseBuf) * size_t(dp.nd), s);
-      h2d(w.dbufs.p, dp.bufs.data(), size_t(dp.nd), s);
+      put(w.dbufs.p, dp.bufs.data(), size_t(dp.nd));
     } else {
       w.dbufs.ensure(sizeof(DenseBuf64) * size_t(dp.nd), s);
-      h2d(w.dbufs.p, dp.bufs64.data(), size_t(dp.nd), s);
+      put(w.dbufs.p, dp.bufs64.data(), size_t(dp.nd));
     }
     w.dcount.ensure(sizeof(unsigned long long) * size_t(dp.nd), s);
     w.derr.ensure(sizeof(int), s);
     SGN_CUDA(cudaMemsetAsync(w.derr.p, 0, sizeof(int), s));
-    sync(s);  // the host vectors above are pageable
     return dp;
   }
 
@@ -538,7 +590,7 @@ struct Solver {
     // a tensor-core wait that gave up leaves the products undefined
     int herr = 0;
     d2h(&herr, w.derr.p, 1, s);
-    sync(s);
+    wait();
     if (herr) throw Error(SIGN_ETIMEOUT, "a bounded wait of the dense tensor-core path gave up");
   }
 
@@ -554,7 +606,7 @@ struct Solver {
       launch_gather_offsets(nb, st.d_moff.template as<int64_t>(), st.X.d_rp(),
                             w.eoff.as<int64_t>(), s);
       d2h(eoff.data(), w.eoff.p, eoff.size(), s);
-      sync(s);
+      wait();
     }
     std::vector<int> mats;
     std::vector<AsmBlock> blocks;
@@ -596,7 +648,7 @@ struct Solver {
     hm.alloc(nb);
     int64_t N = st.moff.back();
     w.active.ensure(sizeof(int) * size_t(nb), s);
-    h2d(w.active.p, st.alive.data(), st.alive.size(), s);
+    put(w.active.p, st.alive.data(), st.alive.size());
     const int *d_act = w.active.as<int>();
     const std::vector<int64_t> ex = st.ex;  // entry offsets of the iterate per matrix
     // ---- check: T = X X, r, x, budget (steps a2, a4)
@@ -620,7 +672,7 @@ struct Solver {
     d2h(hm.nnz_t, w.nnzc.p, size_t(nb), s);
     std::vector<unsigned long long> dcount(dp.nd);
     if (dp.any()) d2h(dcount.data(), w.dcount.p, size_t(dp.nd), s);
-    sync(s);
+    wait();
     for (int d = 0; d < dp.nd; ++d) {  // the dense path's T: its nonzeros and multiply-adds
       int i = dp.mat[d];
       hm.nnz_t[i] += int64_t(dcount[d]);
@@ -715,10 +767,10 @@ struct Solver {
     live = 0;
     for (int a : st.alive) live += a;
     if (live == 0) {
-      sync(s);  // the extraction reads X and the pinned block list
+      wait();  // the extraction reads X and the pinned block list
       return;
     }
-    if (changed) h2d(w.active.p, st.alive.data(), st.alive.size(), s);
+    if (changed) put(w.active.p, st.alive.data(), st.alive.size());
     hdecide.stop();
     // ---- update: Xbar = 1.5 X - 0.5 X T (step a3)
     HostScope hupdate(KH_UPDATE);
@@ -785,7 +837,7 @@ struct Solver {
     d2h(hm.tot, st.Xh.d_rp() + N, 1, s);
     d2h(hm.ms, w.ms.p, size_t(nb), s);
     d2h(hm.dsum, w.sums.p, size_t(nb), s);
-    sync(s);
+    wait();
     int64_t nnz = hm.tot[0];
     st.Xh.n = N;
     st.Xh.nnz = nnz;
@@ -819,7 +871,7 @@ struct Solver {
     d2h(hm.ex, w.eoff.p, size_t(nbm + 1), s);
     d2h(hm.tot, st.Xh.d_rp() + N, 1, s);
     d2h(hm.ms, w.ms.p, size_t(nbm), s);
-    sync(s);
+    wait();
     for (int i = 0; i < nbm; ++i) hms[i].nnz_bar = hm.ms[i].nnz_bar;
     st.ex.assign(hm.ex, hm.ex + nbm + 1);
     int64_t nnz = hm.tot[0];
@@ -883,7 +935,7 @@ struct Solver {
                        w.norm.as<double>(), s);
       }
       d2h(nrm.data(), w.norm.p, size_t(count), s);
-      sync(s);
+      wait();
       for (int i = 0; i < count; ++i)
         if (!(nrm[i] > 0.0) || !std::isfinite(nrm[i])) {
           if (strict)
@@ -947,7 +999,7 @@ struct Solver {
       for (int i = 0; i < count; ++i) in.push_back(&infos[i]);
     std::vector<int> ids = admit(v, in, true);
     for (int guard = 0; guard < 4 * o.max_iter + 16 && busy(); ++guard) step();
-    sync(s);
+    wait();
     for (int i = 0; i < count; ++i) {
       MatState &ms = m[ids[i]];
       if (ms.status < 0) throw Error(SIGN_ESTATE, "solve loop ended with a running matrix");
