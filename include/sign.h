@@ -327,7 +327,10 @@ int64_t sign_kernel_launches(void);
  * flops counts two per multiply-add of a sparse product (the products the
  * method must do); bytes counts the algorithmic traffic of the class: each
  * operand's values, column indices and row pointers read once and each
- * output written once. */
+ * output written once. Classes named host_* are wall times of the solver's
+ * host phases, except host_sync_gap: the device time from the end of the
+ * work queued before each of the solver's host synchronizations to the start
+ * of the next timed launch, i.e. how long the GPU idles around the waits. */
 typedef struct {
   char name[32];
   int64_t launches; /* timed groups of launches                      */

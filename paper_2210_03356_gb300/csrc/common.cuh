@@ -51,7 +51,10 @@ enum KClass {
   KC_SCAN, KC_SEL_HIST, KC_SEL_EXTRACT, KC_SEL_DIGITS, KC_SELECT, KC_FILTER, KC_REDUCE,
   KC_ASSEMBLE, KC_NORM, KC_DENSE, KC_DENSE64,
   // host wall time of driver phases (synchronizations included)
-  KH_SETUP, KH_CHECK, KH_DECIDE, KH_UPDATE, KH_FILTER, KH_REBUILD, KC_COUNT
+  KH_SETUP, KH_CHECK, KH_DECIDE, KH_UPDATE, KH_FILTER, KH_REBUILD,
+  // device time from the end of the work before a host synchronization to the
+  // start of the next timed launch: the GPU's idle time around the wait
+  KH_SYNC_GAP, KC_COUNT
 };
 // Records CUDA events around the enclosed launches on stream s (no-op when
 // profiling is off); flops and bytes are the algorithmic work they do.
@@ -63,6 +66,10 @@ struct ProfScope {
   ProfScope(int c, cudaStream_t st, double f = 0.0, double b = 0.0);
   ~ProfScope();
 };
+
+// Marks a host synchronization of stream s (profiling only): the next
+// ProfScope on s closes a KH_SYNC_GAP interval that starts here.
+void prof_sync_point(cudaStream_t s);
 
 // The library's stream-ordered memory pool on the current device: it keeps
 // freed memory for reuse (release threshold = unlimited), so repeated solves
@@ -79,16 +86,33 @@ struct HostScope {
 };
 
 // Grow-only device buffer, allocated stream-ordered from lib_pool().
+// Device blocks of the library pool, cached per host thread. A freed block is
+// parked with the stream it was allocated on; a later request on the same
+// stream takes the smallest parked block that holds it (and is at most about
+// twice its size) before asking the pool. Reuse on the allocating stream is
+// ordered exactly like cudaFreeAsync followed by a new allocation there. The
+// round loop re-creates its buffers on every solve call, and a pool
+// allocation costs the host tens to hundreds of microseconds, during which
+// the GPU, just synchronized, waits.
+// block_alloc returns the owner token of the allocating thread; block_free
+// parks the block only on that thread (elsewhere it goes back to the pool).
+void *block_alloc(size_t bytes, cudaStream_t s, size_t &cap, const void *&owner);
+void block_free(void *p, size_t cap, cudaStream_t s, const void *owner);
+// Returns this thread's parked blocks to the pool (on their streams, which
+// must still exist); a thread that ends before the process calls it last.
+void block_cache_flush();
+
 struct DevBuf {
   void *p = nullptr;
   size_t cap = 0;
   cudaStream_t s = nullptr;
+  const void *owner = nullptr;
   DevBuf() = default;
   DevBuf(const DevBuf &) = delete;
   DevBuf &operator=(const DevBuf &) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFreeAsync(p, s);
+    if (p) block_free(p, cap, s, owner);
     p = nullptr;
     cap = 0;
   }
@@ -96,9 +120,7 @@ struct DevBuf {
     if (bytes <= cap && p) return p;
     release();
     s = st;
-    size_t want = bytes + bytes / 4 + 256;
-    SGN_CUDA(cudaMallocFromPoolAsync(&p, want, lib_pool(), st));
-    cap = want;
+    p = block_alloc(bytes + bytes / 4 + 256, st, cap, owner);
     return p;
   }
   template <typename T> T *as() const { return static_cast<T *>(p); }

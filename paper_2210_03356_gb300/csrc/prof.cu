@@ -3,6 +3,7 @@
 #include <chrono>
 #include <cstring>
 #include <mutex>
+#include <map>
 #include <vector>
 
 #include "../../include/sign.h"
@@ -37,7 +38,11 @@ const char *kNames[KC_COUNT] = {"numeric_square_f64", "numeric_update_f64", "num
                                 "dense_f64_slices",
                                 "host_setup",
                                 "host_check",         "host_decide",        "host_update",
-                                "host_filter",        "host_rebuild"};
+                                "host_filter",        "host_rebuild",       "host_sync_gap"};
+
+// the open sync-gap interval of this thread (its start event and stream)
+thread_local cudaEvent_t t_gap = nullptr;
+thread_local cudaStream_t t_gap_s = nullptr;
 
 long long now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -111,9 +116,87 @@ cudaMemPool_t lib_pool() {
   return pools[dev];
 }
 
+void prof_sync_point(cudaStream_t s) {
+  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (t_gap) g_pool.push_back(t_gap);  // an earlier mark that no scope closed
+  t_gap = get_event();
+  t_gap_s = s;
+  cudaEventRecord(t_gap, s);
+}
+
+namespace {
+// the parked blocks of this thread, by size
+struct BlockCache {
+  struct Block {
+    void *p;
+    cudaStream_t s;
+  };
+  std::multimap<size_t, Block> free;
+  size_t bytes = 0;
+  // No CUDA call here: at process exit the runtime may already be gone, and
+  // the process's memory goes with it. Threads that end before the process
+  // (server lanes) call block_cache_flush() first.
+  ~BlockCache() = default;
+  void flush() {
+    for (auto &kv : free) cudaFreeAsync(kv.second.p, kv.second.s);
+    free.clear();
+    bytes = 0;
+  }
+};
+thread_local BlockCache t_blocks;
+constexpr size_t kCacheMaxBytes = size_t(96) << 30;  // parked at most, per thread
+}  // namespace
+
+void *block_alloc(size_t bytes, cudaStream_t s, size_t &cap, const void *&owner) {
+  BlockCache &c = t_blocks;
+  owner = &c;
+  for (auto it = c.free.lower_bound(bytes); it != c.free.end() && it->first <= 2 * bytes + (1 << 20);
+       ++it) {
+    if (it->second.s != s) continue;
+    void *p = it->second.p;
+    cap = it->first;
+    c.bytes -= it->first;
+    c.free.erase(it);
+    return p;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, lib_pool(), s);
+  if (e == cudaErrorMemoryAllocation && !c.free.empty()) {
+    cudaGetLastError();
+    c.flush();  // parked blocks back to the pool, then once more
+    e = cudaMallocFromPoolAsync(&p, bytes, lib_pool(), s);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(e == cudaErrorMemoryAllocation ? 2 : 5,
+                std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e));
+  }
+  cap = bytes;
+  return p;
+}
+
+void block_cache_flush() { t_blocks.flush(); }
+
+void block_free(void *p, size_t cap, cudaStream_t s, const void *owner) {
+  BlockCache &c = t_blocks;
+  if (owner != &c || c.bytes + cap > kCacheMaxBytes) {
+    cudaFreeAsync(p, s);
+    return;
+  }
+  c.free.emplace(cap, BlockCache::Block{p, s});
+  c.bytes += cap;
+}
+
 ProfScope::ProfScope(int c, cudaStream_t st, double f, double b) : cls(c), s(st), flops(f), bytes(b) {
   if (!g_prof_on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lk(g_mu);
+  if (t_gap && t_gap_s == s) {
+    cudaEvent_t g = get_event();
+    cudaEventRecord(g, s);
+    g_recs.push_back(Rec{KH_SYNC_GAP, t_gap, g, 0.0, 0.0});
+    t_gap = nullptr;
+  }
   cudaEvent_t e = get_event();
   cudaEventRecord(e, s);
   ev0 = e;

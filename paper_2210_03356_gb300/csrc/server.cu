@@ -284,7 +284,11 @@ static sign_status server_create(const sign_server_opts *o, sign_server_t *out) 
     return set_last_error("stream creation failed"), SIGN_ECUDA;
   }
   try {
-    for (auto &L : S->lanes) L->worker = std::thread([p = S.get(), l = L.get()] { p->serve(*l); });
+    for (auto &L : S->lanes)
+      L->worker = std::thread([p = S.get(), l = L.get()] {
+        p->serve(*l);
+        sgn::block_cache_flush();  // the lane's parked blocks, while its stream exists
+      });
   } catch (const std::exception &e) {
     {
       std::lock_guard<std::mutex> lk(S->mu);

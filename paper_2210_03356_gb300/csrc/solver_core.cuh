@@ -283,6 +283,7 @@ struct Solver {
   }
   // Waits for the stream; the staging arena is free again afterwards.
   void wait() {
+    prof_sync_point(s);
     sync(s);
     stg.used = 0;
   }
