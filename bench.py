@@ -55,8 +55,8 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 # of the batch (profiles/dram_traffic_products_banded128.md). A full-size
 # launch is taken to move DRAM bytes in the same proportion to its
 # algorithmic bytes. Valid for the product kernels as that capture built them.
-DRAM_PER_ALG_BYTE = {"numeric_square_f64": 0.896, "numeric_update_f64": 0.561,
-                     "numeric_square_f32": 0.845, "numeric_update_f32": 0.867}
+DRAM_PER_ALG_BYTE = {"numeric_square_f64": 0.900, "numeric_update_f64": 0.563,
+                     "numeric_square_f32": 0.851, "numeric_update_f32": 0.871}
 
 
 def rank_seed0(rank: int, count: int = BATCH) -> int:
