@@ -324,7 +324,17 @@ __device__ __forceinline__ void accumulate_k2(T a, T b, int64_t q0, int64_t q1,
     mac<T, MARK>(accb, fb, c2 - cb, b, v2);
     mac<T, MARK>(accb, fb, c3 - cb, b, v3);
   }
-  for (; i < n; i += 32) {
+  // at most three entries per lane are left: two loaded together, then one
+  if (i + 32 < n) {
+    int32_t c0 = bc[i], c1 = bc[i + 32];
+    T v0 = bv[i], v1 = bv[i + 32];
+    mac<T, MARK>(acca, fa, c0 - ca, a, v0);
+    mac<T, MARK>(acca, fa, c1 - ca, a, v1);
+    mac<T, MARK>(accb, fb, c0 - cb, b, v0);
+    mac<T, MARK>(accb, fb, c1 - cb, b, v1);
+    i += 64;
+  }
+  if (i < n) {
     int32_t c = bc[i];
     T v = bv[i];
     mac<T, MARK>(acca, fa, c - ca, a, v);
