@@ -393,8 +393,11 @@ __global__ void k_sel_find_digit(int nb, SelScratch sc, int shift) {
   SelState &st = sc.st[m];
   if (!st.found) return;
   unsigned long long lo = st.below_lo, hi = st.below_hi;
-  const int d = warp_crossing(sc.hdig + size_t(m) * NDIG * 2, NDIG, lo, hi);
+  unsigned long long *h = sc.hdig + size_t(m) * NDIG * 2;
+  const int d = warp_crossing(h, NDIG, lo, hi);
   __syncwarp();
+  // the buckets are read: cleared here for the next digit, instead of a memset
+  for (int c = threadIdx.x & 31; c < 2 * NDIG; c += 32) h[c] = 0ULL;
   if (d >= 0 && (threadIdx.x & 31) == 0) {
     st.prefix |= (unsigned long long)d << shift;
     st.below_lo = lo;
@@ -594,9 +597,11 @@ void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *
     }
   }
   ProfScope ps(KC_SEL_DIGITS, s, 0.0, 0.0);
+  // zeroed once; after each level the matrices that fill buckets (those with
+  // a crossing) clear them again in k_sel_find_digit
+  SGN_CUDA(cudaMemsetAsync(sc.hdig, 0, size_t(nb) * NDIG * 2 * 8, s));
   for (int level = 0; level < 6; ++level) {
     int shift = 40 - 8 * level;
-    SGN_CUDA(cudaMemsetAsync(sc.hdig, 0, size_t(nb) * NDIG * 2 * 8, s));
     k_sel_hist_digit<<<152 * 4, 256, 0, s>>>(ms, sc, shift);
     SGN_LAUNCH_CHECK();
     k_sel_find_digit<<<(nb + 3) / 4, 128, 0, s>>>(nb, sc, shift);
