@@ -514,7 +514,6 @@ def main():
         def e2e_step():
             b2 = sg.Batch(pinned)
             b2.solve(opts)
-            nbytes = 0
             for i, hnd in enumerate(b2.handles):
                 nnz = hnd.result_nnz()
                 if i == len(outs) or outs[i][1].size < nnz:
@@ -526,8 +525,8 @@ def main():
                         outs.append(views)
                     else:
                         outs[i] = views
-                rp, col, val = hnd.result(out=outs[i])
-                nbytes += rp.nbytes + col.nbytes + val.nbytes
+            res = b2.results(outs)  # every copy queued, one wait
+            nbytes = sum(rp.nbytes + col.nbytes + val.nbytes for rp, col, val in res)
             b2.close()
             return nbytes
 

@@ -153,6 +153,15 @@ sign_status sign_solve_batch(sign_t *hs, int count, const sign_opts *o, sign_inf
 sign_status sign_get_csr(sign_t h, int64_t *nnz_out, int64_t *row_ptr, int32_t *col, double *val,
                          int on_device);
 
+/* sign_get_csr for `count` handles at once (arrays of its arguments): the
+ * copies are queued on each handle's stream, which is then waited for once
+ * (so a batch solved together costs one wait instead of count). Every handle
+ * must hold a result; row_ptr, col and val must all be given, each array with
+ * its handle's n+1 and nnz elements. On an error no copy is queued unless the
+ * status is SIGN_ECUDA; sign_last_error names the first bad handle. */
+sign_status sign_get_csr_batch(int count, const sign_t *hs, int64_t *const *row_ptr,
+                               int32_t *const *col, double *const *val, int on_device);
+
 /* Releases the handle and its device memory (NULL is ignored). */
 void sign_destroy(sign_t h);
 

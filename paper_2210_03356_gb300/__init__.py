@@ -20,12 +20,14 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import _native as N
-from ._native import (SIGN_EAGAIN, SIGN_EDIVERGED, SIGN_EINVAL, SIGN_ENOMEM, SIGN_ENOTCONV,
-                      SIGN_OK, SignError, default_opts, last_error, load, prof_read)
+from ._native import (SIGN_EAGAIN, SIGN_ECUDA, SIGN_EDIVERGED, SIGN_EINVAL, SIGN_ENOMEM,
+                      SIGN_ENOTCONV, SIGN_ESTATE, SIGN_ETIMEOUT, SIGN_OK, SignError, default_opts,
+                      last_error, load, prof_read)
 
-__all__ = ["solve", "solve_batch", "Handle", "Result", "Server", "default_opts", "load", "last_error",
-           "prof_read", "kernel_launches", "prof_enable", "prof_reset",
-           "SignError", "SIGN_OK", "SIGN_EINVAL", "SIGN_ENOTCONV", "SIGN_EDIVERGED"]
+__all__ = ["solve", "solve_batch", "Handle", "Batch", "Result", "Server", "default_opts", "load",
+           "last_error", "prof_read", "kernel_launches", "prof_enable", "prof_reset",
+           "SignError", "SIGN_OK", "SIGN_EINVAL", "SIGN_ENOMEM", "SIGN_ENOTCONV", "SIGN_EDIVERGED",
+           "SIGN_ECUDA", "SIGN_ETIMEOUT", "SIGN_ESTATE", "SIGN_EAGAIN"]
 
 _TRACE = [("nnz_x", np.int64), ("nnz_t", np.int64), ("resid_k", np.float64),
           ("xnorm_k", np.float64), ("beta_k", np.float64), ("tau_k", np.float64),
@@ -333,6 +335,34 @@ class Batch:
         if st != SIGN_OK:
             raise SignError(st, "sign_solve_batch")
         return [(s.status, s.iters, s.resid) for s in iarr]
+
+    def results(self, outs) -> list:
+        """sign_get_csr_batch: every result at once into caller-owned host arrays.
+
+        outs holds one (rowptr, col, val) per handle (numpy views, e.g. of
+        pinned memory, reused across solves), sized from result_nnz(); the
+        copies are queued together and waited for once. Returns views.
+        """
+        if len(outs) != len(self.handles):
+            raise ValueError("one (rowptr, col, val) per handle")
+        views = []
+        for h, (rp, col, val) in zip(self.handles, outs):
+            nnz = h.result_nnz()
+            if (rp.dtype != np.int64 or col.dtype != np.int32 or val.dtype != np.float64 or
+                    rp.size < h.n + 1 or col.size < nnz or val.size < nnz or
+                    not (rp.flags.c_contiguous and col.flags.c_contiguous and
+                         val.flags.c_contiguous)):
+                raise ValueError("out arrays: need contiguous int64[n+1], int32[nnz], "
+                                 "float64[nnz]")
+            views.append((rp[:h.n + 1], col[:nnz], val[:nnz]))
+        k = len(outs)
+        rps = (C.c_void_p * k)(*[_ptr(o[0]) for o in outs])
+        cols = (C.c_void_p * k)(*[_ptr(o[1]) for o in outs])
+        vals = (C.c_void_p * k)(*[_ptr(o[2]) for o in outs])
+        st = load().sign_get_csr_batch(k, self.arr, rps, cols, vals, 0)
+        if st != SIGN_OK:
+            raise SignError(st, "sign_get_csr_batch")
+        return views
 
     def traces(self) -> list:
         infos, iarr, _ = self.infos

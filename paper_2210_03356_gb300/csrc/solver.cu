@@ -217,6 +217,45 @@ sign_status sign_get_csr(sign_t h, int64_t *nnz_out, int64_t *row_ptr, int32_t *
   return SIGN_OK;
 }
 
+sign_status sign_get_csr_batch(int count, const sign_t *hs, int64_t *const *row_ptr,
+                               int32_t *const *col, double *const *val, int on_device) {
+  g_err.clear();
+  if (count < 1 || !hs || !row_ptr || !col || !val)
+    return fail(SIGN_EINVAL, "need count >= 1 and non-NULL arrays");
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return fail(SIGN_EINVAL, "handle " + std::to_string(i) + " is NULL");
+    if (!hs[i]->has_result)
+      return fail(SIGN_ESTATE, "handle " + std::to_string(i) + ": no result, call sign_solve first");
+    if (!row_ptr[i] || (hs[i]->result.nnz > 0 && (!col[i] || !val[i])))
+      return fail(SIGN_EINVAL, "handle " + std::to_string(i) + ": NULL output array");
+  }
+  try {
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    std::vector<cudaStream_t> streams;
+    for (int i = 0; i < count; ++i) {
+      sign_ctx *h = hs[i];
+      cudaStream_t s = h->stream;
+      SGN_CUDA(cudaMemcpyAsync(row_ptr[i], h->result.rp.p, sizeof(int64_t) * size_t(h->n + 1), kind,
+                               s));
+      if (h->result.nnz > 0) {
+        SGN_CUDA(cudaMemcpyAsync(col[i], h->result.col.p, sizeof(int32_t) * size_t(h->result.nnz),
+                                 kind, s));
+        SGN_CUDA(cudaMemcpyAsync(val[i], h->result.val.p, sizeof(double) * size_t(h->result.nnz),
+                                 kind, s));
+      }
+      if (std::find(streams.begin(), streams.end(), s) == streams.end()) streams.push_back(s);
+    }
+    for (cudaStream_t s : streams) SGN_CUDA(cudaStreamSynchronize(s));
+  } catch (const Error &e) {
+    return fail(e.status, e.what());
+  } catch (const std::bad_alloc &) {
+    return fail(SIGN_ENOMEM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(SIGN_ECUDA, e.what());
+  }
+  return SIGN_OK;
+}
+
 void sign_destroy(sign_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);

@@ -323,8 +323,24 @@ def test_create_batch_names_the_bad_matrix_and_reads_into_caller_buffers(sg):
             assert np.array_equal(val, val2)
             with pytest.raises(ValueError):
                 h.result(out=(pin[0], pin[1][:nnz - 1], pin[2]))
+            outs = [(np.empty(x.n + 1, np.int64), np.empty(x.result_nnz() + 3, np.int32),
+                     np.empty(x.result_nnz() + 3, np.float64)) for x in b.handles]
+            for x, (rp3, col3, val3) in zip(b.handles, b.results(outs)):
+                r1, c1, v1 = x.result()
+                assert np.array_equal(r1, rp3) and np.array_equal(c1, col3)
+                assert np.array_equal(v1, val3)
         finally:
             b.close()
+    # results before any solve: refused, naming the handle
+    b = Batch(good)
+    try:
+        outs = [(np.empty(x.n + 1, np.int64), np.empty(1, np.int32), np.empty(1, np.float64))
+                for x in b.handles]
+        with pytest.raises(SignError) as e:
+            b.results(outs)
+        assert e.value.status == sg.SIGN_ESTATE
+    finally:
+        b.close()
 
 
 # ---------------------------------------------------------------- threshold select (step a5)
