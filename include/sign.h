@@ -331,6 +331,13 @@ void sign_server_destroy(sign_server_t srv);
 /* Total CUDA kernel launches made by this library in this process. */
 int64_t sign_kernel_launches(void);
 
+/* Device memory. The library allocates from its own stream-ordered pool,
+ * which keeps freed memory for reuse, and each host thread that solves also
+ * keeps the blocks it freed for its next solve (server lanes do not). This
+ * returns the calling thread's kept blocks to the pool and the pool's unused
+ * memory to the device. It synchronizes the device. Errors: SIGN_ECUDA. */
+sign_status sign_trim_memory(void);
+
 /* Per-kernel-class timing. When enabled, every group of launches of one
  * class is bracketed by CUDA events recorded on the stream it runs on.
  * flops counts two per multiply-add of a sparse product (the products the

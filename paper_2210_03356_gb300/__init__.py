@@ -25,7 +25,7 @@ from ._native import (SIGN_EAGAIN, SIGN_ECUDA, SIGN_EDIVERGED, SIGN_EINVAL, SIGN
                       last_error, load, prof_read)
 
 __all__ = ["solve", "solve_batch", "Handle", "Batch", "Result", "Server", "default_opts", "load",
-           "last_error", "prof_read", "kernel_launches", "prof_enable", "prof_reset",
+           "last_error", "prof_read", "kernel_launches", "prof_enable", "prof_reset", "trim_memory",
            "SignError", "SIGN_OK", "SIGN_EINVAL", "SIGN_ENOMEM", "SIGN_ENOTCONV", "SIGN_EDIVERGED",
            "SIGN_ECUDA", "SIGN_ETIMEOUT", "SIGN_ESTATE", "SIGN_EAGAIN"]
 
@@ -228,6 +228,13 @@ def solve_batch(mats, opts=None, trace_cap: int = 256, device_out: bool = False,
     finally:
         for h in hs:
             h.close()
+
+
+def trim_memory() -> None:
+    """sign_trim_memory: kept device blocks and unused pool memory back to the device."""
+    st = load().sign_trim_memory()
+    if st != SIGN_OK:
+        raise SignError(st, "sign_trim_memory")
 
 
 def threshold_exact(values, b: float, stream=None) -> float:

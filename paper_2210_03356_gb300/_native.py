@@ -72,6 +72,7 @@ SIGNATURES = {
                                     C.POINTER(sign_t)]),
     "sign_get_csr_batch": (C.c_int, [C.c_int, C.POINTER(sign_t), C.POINTER(C.c_void_p),
                                      C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int]),
+    "sign_trim_memory": (C.c_int, []),
     "sign_solve": (C.c_int, [sign_t, C.POINTER(sign_opts), C.POINTER(sign_info)]),
     "sign_solve_batch": (C.c_int, [C.POINTER(sign_t), C.c_int, C.POINTER(sign_opts),
                                    C.POINTER(sign_info)]),

@@ -101,6 +101,11 @@ void block_free(void *p, size_t cap, cudaStream_t s, const void *owner);
 // Returns this thread's parked blocks to the pool (on their streams, which
 // must still exist); a thread that ends before the process calls it last.
 void block_cache_flush();
+// Turns parking off (flushing what is parked) or on for this thread. Server
+// lanes turn it off: they keep their buffers across rounds, and blocks parked
+// by one lane would be out of reach of the others under one memory budget.
+void block_cache_enable(bool on);
+void set_last_error(const std::string &msg);
 
 struct DevBuf {
   void *p = nullptr;

@@ -145,12 +145,18 @@ struct BlockCache {
   }
 };
 thread_local BlockCache t_blocks;
+thread_local bool t_cache_on = true;
 constexpr size_t kCacheMaxBytes = size_t(96) << 30;  // parked at most, per thread
 }  // namespace
 
+void block_cache_enable(bool on) {
+  if (!on) t_blocks.flush();
+  t_cache_on = on;
+}
+
 void *block_alloc(size_t bytes, cudaStream_t s, size_t &cap, const void *&owner) {
   BlockCache &c = t_blocks;
-  owner = &c;
+  owner = t_cache_on ? &c : nullptr;
   for (auto it = c.free.lower_bound(bytes); it != c.free.end() && it->first <= 2 * bytes + (1 << 20);
        ++it) {
     if (it->second.s != s) continue;
@@ -180,7 +186,7 @@ void block_cache_flush() { t_blocks.flush(); }
 
 void block_free(void *p, size_t cap, cudaStream_t s, const void *owner) {
   BlockCache &c = t_blocks;
-  if (owner != &c || c.bytes + cap > kCacheMaxBytes) {
+  if (!t_cache_on || owner != &c || c.bytes + cap > kCacheMaxBytes) {
     cudaFreeAsync(p, s);
     return;
   }
@@ -216,6 +222,20 @@ ProfScope::~ProfScope() {
 extern "C" {
 
 int64_t sign_kernel_launches(void) { return sgn::g_launches.load(); }
+
+sign_status sign_trim_memory(void) {
+  try {
+    sgn::block_cache_flush();
+    int dev = 0;
+    SGN_CUDA(cudaGetDevice(&dev));
+    SGN_CUDA(cudaDeviceSynchronize());  // frees queued on streams take effect first
+    SGN_CUDA(cudaMemPoolTrimTo(sgn::lib_pool(), 0));
+  } catch (const sgn::Error &e) {
+    sgn::set_last_error(e.what());
+    return sign_status(e.status);
+  }
+  return SIGN_OK;
+}
 
 int sign_prof_enable(int on) { return sgn::g_prof_on.exchange(on ? 1 : 0); }
 

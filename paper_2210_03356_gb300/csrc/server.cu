@@ -286,8 +286,9 @@ static sign_status server_create(const sign_server_opts *o, sign_server_t *out) 
   try {
     for (auto &L : S->lanes)
       L->worker = std::thread([p = S.get(), l = L.get()] {
+        sgn::block_cache_enable(false);  // lane memory goes back to the shared pool
         p->serve(*l);
-        sgn::block_cache_flush();  // the lane's parked blocks, while its stream exists
+        sgn::block_cache_flush();
       });
   } catch (const std::exception &e) {
     {

@@ -343,6 +343,16 @@ def test_create_batch_names_the_bad_matrix_and_reads_into_caller_buffers(sg):
         b.close()
 
 
+def test_trim_memory_between_solves(sg):
+    """Kept blocks and pool memory handed back; the next solve is unchanged."""
+    mats = [w.banded(n, b, s) for n, b, s in w.banded_batch_shapes(6, nmin=200, nmax=900)]
+    first = sg.solve_batch(mats, tol=1e-8, filter="exact", prec=1, dense_frac=2.0)
+    sg.trim_memory()
+    again = sg.solve_batch(mats, tol=1e-8, filter="exact", prec=1, dense_frac=2.0)
+    for r1, r2 in zip(first, again):
+        assert np.array_equal(r1.col, r2.col) and np.array_equal(r1.val, r2.val)
+
+
 # ---------------------------------------------------------------- threshold select (step a5)
 def _tau_ref(orc, vals, b):
     """tau of the oracle's EXACT filter for an array (laid out as one CSR row per value)."""
