@@ -3,7 +3,6 @@
 #include <chrono>
 #include <cstring>
 #include <mutex>
-#include <map>
 #include <vector>
 
 #include "../../include/sign.h"
@@ -95,26 +94,6 @@ void HostScope::stop() {
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-cudaMemPool_t lib_pool() {
-  static std::mutex mu;
-  static cudaMemPool_t pools[64] = {};
-  int dev = 0;
-  SGN_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) throw Error(5, "device index out of range");
-  std::lock_guard<std::mutex> lk(mu);
-  if (!pools[dev]) {
-    cudaMemPoolProps props = {};
-    props.allocType = cudaMemAllocationTypePinned;
-    props.location.type = cudaMemLocationTypeDevice;
-    props.location.id = dev;
-    cudaMemPool_t p = nullptr;
-    SGN_CUDA(cudaMemPoolCreate(&p, &props));
-    uint64_t keep = ~uint64_t(0);
-    SGN_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
-    pools[dev] = p;
-  }
-  return pools[dev];
-}
 
 void prof_sync_point(cudaStream_t s) {
   if (!g_prof_on.load(std::memory_order_relaxed)) return;
@@ -123,75 +102,6 @@ void prof_sync_point(cudaStream_t s) {
   t_gap = get_event();
   t_gap_s = s;
   cudaEventRecord(t_gap, s);
-}
-
-namespace {
-// the parked blocks of this thread, by size
-struct BlockCache {
-  struct Block {
-    void *p;
-    cudaStream_t s;
-  };
-  std::multimap<size_t, Block> free;
-  size_t bytes = 0;
-  // No CUDA call here: at process exit the runtime may already be gone, and
-  // the process's memory goes with it. Threads that end before the process
-  // (server lanes) call block_cache_flush() first.
-  ~BlockCache() = default;
-  void flush() {
-    for (auto &kv : free) cudaFreeAsync(kv.second.p, kv.second.s);
-    free.clear();
-    bytes = 0;
-  }
-};
-thread_local BlockCache t_blocks;
-thread_local bool t_cache_on = true;
-constexpr size_t kCacheMaxBytes = size_t(96) << 30;  // parked at most, per thread
-}  // namespace
-
-void block_cache_enable(bool on) {
-  if (!on) t_blocks.flush();
-  t_cache_on = on;
-}
-
-void *block_alloc(size_t bytes, cudaStream_t s, size_t &cap, const void *&owner) {
-  BlockCache &c = t_blocks;
-  owner = t_cache_on ? &c : nullptr;
-  for (auto it = c.free.lower_bound(bytes); it != c.free.end() && it->first <= 2 * bytes + (1 << 20);
-       ++it) {
-    if (it->second.s != s) continue;
-    void *p = it->second.p;
-    cap = it->first;
-    c.bytes -= it->first;
-    c.free.erase(it);
-    return p;
-  }
-  void *p = nullptr;
-  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, lib_pool(), s);
-  if (e == cudaErrorMemoryAllocation && !c.free.empty()) {
-    cudaGetLastError();
-    c.flush();  // parked blocks back to the pool, then once more
-    e = cudaMallocFromPoolAsync(&p, bytes, lib_pool(), s);
-  }
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    throw Error(e == cudaErrorMemoryAllocation ? 2 : 5,
-                std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e));
-  }
-  cap = bytes;
-  return p;
-}
-
-void block_cache_flush() { t_blocks.flush(); }
-
-void block_free(void *p, size_t cap, cudaStream_t s, const void *owner) {
-  BlockCache &c = t_blocks;
-  if (!t_cache_on || owner != &c || c.bytes + cap > kCacheMaxBytes) {
-    cudaFreeAsync(p, s);
-    return;
-  }
-  c.free.emplace(cap, BlockCache::Block{p, s});
-  c.bytes += cap;
 }
 
 ProfScope::ProfScope(int c, cudaStream_t st, double f, double b) : cls(c), s(st), flops(f), bytes(b) {
@@ -223,19 +133,6 @@ extern "C" {
 
 int64_t sign_kernel_launches(void) { return sgn::g_launches.load(); }
 
-sign_status sign_trim_memory(void) {
-  try {
-    sgn::block_cache_flush();
-    int dev = 0;
-    SGN_CUDA(cudaGetDevice(&dev));
-    SGN_CUDA(cudaDeviceSynchronize());  // frees queued on streams take effect first
-    SGN_CUDA(cudaMemPoolTrimTo(sgn::lib_pool(), 0));
-  } catch (const sgn::Error &e) {
-    sgn::set_last_error(e.what());
-    return sign_status(e.status);
-  }
-  return SIGN_OK;
-}
 
 int sign_prof_enable(int on) { return sgn::g_prof_on.exchange(on ? 1 : 0); }
 
