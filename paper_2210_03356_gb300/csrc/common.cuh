@@ -98,8 +98,9 @@ struct HostScope {
 // parks the block only on that thread (elsewhere it goes back to the pool).
 void *block_alloc(size_t bytes, cudaStream_t s, size_t &cap, const void *&owner);
 void block_free(void *p, size_t cap, cudaStream_t s, const void *owner);
-// Returns this thread's parked blocks to the pool (on their streams, which
-// must still exist); a thread that ends before the process calls it last.
+// Returns this thread's parked blocks to the pool: waits for the device to
+// be idle, then frees them (their streams may no longer exist). A thread that
+// ends before the process calls it last.
 void block_cache_flush();
 // Turns parking off (flushing what is parked) or on for this thread. Server
 // lanes turn it off: they keep their buffers across rounds, and blocks parked

@@ -40,10 +40,15 @@ struct BlockCache {
   size_t bytes = 0;
   // No CUDA call here: at process exit the runtime may already be gone, and
   // the process's memory goes with it. Threads that end before the process
-  // (server lanes) call block_cache_flush() first.
+  // call block_cache_flush() first.
   ~BlockCache() = default;
+  // The streams the blocks were parked with may have been destroyed since
+  // (a server's upload stream, a caller's stream), so none of them is used:
+  // once the device is idle, every parked block is unused and freed directly.
   void flush() {
-    for (auto &kv : free) cudaFreeAsync(kv.second.p, kv.second.s);
+    if (free.empty()) return;
+    cudaDeviceSynchronize();
+    for (auto &kv : free) cudaFree(kv.second.p);
     free.clear();
     bytes = 0;
   }

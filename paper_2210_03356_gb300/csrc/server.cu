@@ -288,7 +288,6 @@ static sign_status server_create(const sign_server_opts *o, sign_server_t *out) 
       L->worker = std::thread([p = S.get(), l = L.get()] {
         sgn::block_cache_enable(false);  // lane memory goes back to the shared pool
         p->serve(*l);
-        sgn::block_cache_flush();
       });
   } catch (const std::exception &e) {
     {
