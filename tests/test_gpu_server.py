@@ -133,3 +133,20 @@ def test_refusals_and_invalid_requests(sg):
         st = srv.stats()
     # the malformed matrix failed validation before admission: not counted
     assert st["submitted"] == 3 and st["refused"] == 1 and st["completed"] == 2
+
+
+def test_trim_after_a_destroyed_server(sg):
+    """Blocks freed on this thread for a server's upload stream outlive the
+    stream; trimming afterwards must not use it, and solving still works."""
+    mats = _mix(5, 4)
+    with sg.Server(tol=1e-8, filter="exact", prec="mixed") as srv:
+        tickets = [srv.submit(a) for a in mats]
+        for t in tickets:
+            while srv.poll(t, wait_ms=1000) is None:
+                pass
+        outs = [srv.take(t) for t in tickets]
+    del outs
+    sg.trim_memory()
+    lone = sg.solve(mats[0], tol=1e-8, filter="exact", prec=1)
+    assert lone.status == sg.SIGN_OK
+    sg.trim_memory()
