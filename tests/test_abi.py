@@ -65,3 +65,31 @@ def test_missing_library_fails_loudly(tmp_path):
             _native.load(str(tmp_path / "nope.so"))
     finally:
         _native._lib = saved
+
+
+def _prototypes():
+    """{name: (return type, parameter count)} of every function in include/sign.h."""
+    src = open(os.path.join(ROOT, "include", "sign.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    protos = {}
+    for ret, name, params in re.findall(r"([A-Za-z_][\w\s\*]*?)\s*\b(sign_[a-z0-9_]+)\s*\(([^)]*)\)\s*;",
+                                        src):
+        params = " ".join(params.split())
+        count = 0 if params in ("", "void") else params.count(",") + 1
+        protos[name] = (" ".join(ret.split()), count)
+    return protos
+
+
+def test_binding_arity_and_return_types_match_the_header():
+    """Each ctypes signature takes as many arguments as the C prototype and
+    returns the same kind of value (a wrong count would corrupt the call)."""
+    import ctypes as C
+    from paper_2210_03356_gb300 import _native
+    protos = _prototypes()
+    assert sorted(protos) == _declared()
+    kinds = {"void": None, "sign_status": C.c_int, "int": C.c_int, "int64_t": C.c_int64,
+             "double": C.c_double, "const char *": C.c_char_p}
+    for name, (ret, count) in protos.items():
+        restype, argtypes = _native.SIGNATURES[name]
+        assert len(argtypes) == count, (name, len(argtypes), count)
+        assert restype is kinds[ret], (name, ret, restype)
