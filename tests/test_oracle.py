@@ -166,6 +166,40 @@ def test_ns_update_obeys_lemma_2_1_1(oracle_lib, k):
     assert np.allclose(xbd, 0.5 * xd @ (3 * np.eye(n) - xd @ xd), rtol=0, atol=1e-14)
 
 
+def _csr_of(d):
+    n = d.shape[0]
+    rows, cols = np.nonzero(d)
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, rows + 1, 1)
+    return np.cumsum(rp), cols.astype(np.int32), d[rows, cols]
+
+
+def test_ns_step_keeps_the_anticommuting_part_of_an_error(oracle_lib):
+    """Near S = sign(A) one step X(3I - X^2)/2 maps S + E to S + (E - S E S)/2
+    + O(|E|^2): a perturbation commuting with S is removed, one anticommuting
+    with S passes unchanged. An FP64 finish therefore cannot remove the
+    anticommuting part of the FP32 stage's rounding error."""
+    n = 40
+    a = w.banded(n, 3, 5)
+    A = _dense(n, a.rowptr, a.col, a.val)
+    S = _sign_eig(A)
+    Pp, Pm = (np.eye(n) + S) / 2, (np.eye(n) - S) / 2
+    rng = np.random.default_rng(0)
+    B = rng.standard_normal((n, n)) * 1e-6
+    Ec = Pp @ B @ Pp + Pm @ B @ Pm      # commutes with S
+    Ea = Pp @ B @ Pm + Pm @ B @ Pp      # anticommutes with S
+    assert np.linalg.norm(S @ Ec - Ec @ S) < 1e-15 and np.linalg.norm(S @ Ea + Ea @ S) < 1e-15
+
+    def step(X):
+        Xc = _csr_of(X)
+        return _dense(n, *oracle_lib.ns_update(n, Xc, oracle_lib.spgemm(n, Xc, Xc)))
+
+    e2 = np.linalg.norm(B) ** 2
+    assert np.linalg.norm(step(S + Ec) - S) <= 10 * e2                 # removed
+    assert np.linalg.norm(step(S + Ea) - (S + Ea)) <= 10 * e2          # kept
+    assert np.linalg.norm(Ea) > 1e3 * 10 * e2                          # and the test can tell
+
+
 def test_diagonal_follows_scalar_map_exactly(oracle_lib):
     vals = np.array([0.3, -0.05, 2.0, -1.0, 0.9, -0.6])
     n = len(vals)
