@@ -99,8 +99,12 @@ void block_free(void *p, size_t cap, cudaStream_t s, const void *owner) {
     cudaFreeAsync(p, s);
     return;
   }
-  c.free.emplace(cap, BlockCache::Block{p, s});
-  c.bytes += cap;
+  try {  // runs in destructors: no exception may leave
+    c.free.emplace(cap, BlockCache::Block{p, s});
+    c.bytes += cap;
+  } catch (...) {
+    cudaFreeAsync(p, s);
+  }
 }
 
 }  // namespace sgn
