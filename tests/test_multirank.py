@@ -71,3 +71,26 @@ def test_single_process_reduction_is_the_identity():
     import bench
     assert bench.max_over_ranks(12.5) == 12.5
     assert bench.job_throughput(512, 1, 5, 1000.0) == 2560.0
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    """Rank 0 times the oracle on a bounded sample and prints one JSON line
+    with the keys the benchmark contract asks of the reference arm."""
+    import argparse
+    import json
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    args = argparse.Namespace(ref_sample=2, warmup=0, steps=1, gpus=1)
+    assert bench.run_reference(args) == 0
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"] == d["e2e"]["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"] == bench.WORKLOAD
