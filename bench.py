@@ -308,6 +308,65 @@ def laplacian3d_leg(sg, m: int, samples: int = 4000):
     return out
 
 
+# Table 4.2.1's NSF times (MATLAB on the paper's CPU), tol 1e-12, for context
+ODE_PAPER_NSF_SECONDS = {500: 0.0098, 1000: 0.011, 3000: 0.0268, 5000: 0.0481}
+
+
+def ode_closed_form(nb: int, lam: float = 1.0 / 16.0):
+    """sign([[0, B], [I, 0]]) = [[0, B^1/2], [B^-1/2, 0]] (Eq. 1.26) for
+    B = tridiag(lam, 7/8, lam) of order nb, from B's sine eigenbasis:
+    eigenvalues 7/8 + 2 lam cos(j pi/(nb+1)), eigenvectors
+    sqrt(2/(nb+1)) sin(i j pi/(nb+1))."""
+    j = np.arange(1, nb + 1)
+    h = np.pi / (nb + 1)
+    V = np.sqrt(2.0 / (nb + 1)) * np.sin(np.outer(j, j) * h)
+    mu = 7.0 / 8.0 + 2.0 * lam * np.cos(j * h)
+    S = np.zeros((2 * nb, 2 * nb))
+    S[:nb, nb:] = (V * np.sqrt(mu)) @ V.T
+    S[nb:, :nb] = (V / np.sqrt(mu)) @ V.T
+    return S
+
+
+def ode_leg(sg, sizes, reps: int = 3):
+    """Sec. 4.2's ODE block matrix A = [[0, B], [I, 0]], B = tridiag(1/16, 7/8,
+    1/16), solved as in Table 4.2.1: FP64 NSF (EXACT) to tol 1e-12 from X0 = A
+    (unscaled; A's eigenvalues are +-sqrt(eig B), within [0.87, 1] in modulus).
+    The table's n is read both ways: as the order of B and as the order of A.
+    Reports the device time per solve (one matrix per sign_solve_batch call,
+    after a warm-up) and the error against the closed form (Eq. 1.26)."""
+    import torch
+    out = []
+    o = sg.default_opts(tol=1e-12, filter="exact", prec="fp64", scale_1norm=0)
+    for n in sizes:
+        for reading, nb in (("n = order of B", n), ("n = order of A", n // 2)):
+            a = w.ode_block(nb)
+            b = sg.Batch([a])
+            try:
+                b.solve(o)  # warm-up
+                secs = []
+                for _ in range(reps):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    (st, iters, resid), = b.solve(o)
+                    torch.cuda.synchronize()
+                    secs.append(time.perf_counter() - t0)
+                rp, col, val = b.handles[0].result()
+            finally:
+                b.close()
+            D = np.zeros((a.n, a.n))
+            D[np.repeat(np.arange(a.n), np.diff(rp)), col] = val
+            S = ode_closed_form(nb)
+            out.append({"n": n, "reading": reading, "order_of_A": int(a.n), "status": int(st),
+                        "iters": int(iters), "resid": float(resid),
+                        "seconds_per_solve": statistics.median(secs),
+                        "max_abs_err": float(np.abs(D - S).max()),
+                        "rel_fro_err": float(np.linalg.norm(D - S) / np.linalg.norm(S)),
+                        "paper_nsf_seconds": ODE_PAPER_NSF_SECONDS.get(n)})
+            print(f"ode n={n} ({reading}): {out[-1]['seconds_per_solve'] * 1e3:.2f} ms, "
+                  f"max abs err {out[-1]['max_abs_err']:.2e}", file=sys.stderr, flush=True)
+    return out
+
+
 # ---------------------------------------------------------------------- clocks
 class Clocks:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -374,6 +433,8 @@ def main():
                     help="comma-separated m: also solve the m^3 3-D Laplacian against its closed form")
     ap.add_argument("--fill-iters", type=int, default=0,
                     help="also track fill on the n=65,536 2-D Laplacian for this many updates")
+    ap.add_argument("--ode", default="",
+                    help="comma-separated n: also solve Sec. 4.2's ODE block matrix as in Table 4.2.1")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -573,6 +634,8 @@ def main():
         line["laplacian2d_fill"] = fill_leg(sg, args.fill_iters)
     if args.laplacian3d and rank == 0:
         line["laplacian3d"] = [laplacian3d_leg(sg, int(m)) for m in args.laplacian3d.split(",")]
+    if args.ode and rank == 0:
+        line["ode_table_4_2_1"] = ode_leg(sg, [int(n) for n in args.ode.split(",")])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -1,0 +1,25 @@
+"""Host-side helpers of bench.py, checked without a GPU."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+@pytest.mark.parametrize("nb", [1, 7, 30])
+def test_ode_closed_form_is_the_sign_of_the_block_matrix(nb):
+    """Eq. (1.26) from B's sine eigenbasis agrees with scipy's signm of the
+    dense block matrix, and is an involution commuting with it."""
+    linalg = pytest.importorskip("scipy.linalg")
+    import bench
+    import workloads as w
+    a = w.ode_block(nb)
+    A = np.zeros((a.n, a.n))
+    A[np.repeat(np.arange(a.n), np.diff(a.rowptr)), a.col] = a.val
+    S = bench.ode_closed_form(nb)
+    assert np.allclose(S @ S, np.eye(a.n), atol=1e-13)
+    assert np.allclose(S @ A, A @ S, atol=1e-13)
+    assert np.allclose(S, np.real(linalg.signm(A)), atol=1e-10)
