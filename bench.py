@@ -367,6 +367,41 @@ def ode_leg(sg, sizes, reps: int = 3):
     return out
 
 
+def filter_error_leg(solve, sizes, seeds: int = 5, tol: float = 1e-12):
+    """Sec. 4.1's second test (Fig. 4.1.2): random sparse SPD matrices of
+    density 1% (the stand-in for sprandsym(n, 0.01, 1); workloads.spd_random),
+    NS and NSF (EXACT) in FP64 to tol 1e-12. For every iteration k, the
+    filtered and unfiltered iterates after k updates give
+    dX_k = Xhat_k - X_k and dR_k = Rhat_k - R_k (R = I - X^2), in RMS-Frobenius
+    norm; the paper shows both below tol. solve(a, filter, max_iter) returns
+    (status, iters, rowptr, col, val) of a run stopped after max_iter updates."""
+    out = []
+    for n in sizes:
+        for s in range(seeds):
+            a = w.spd_random(n, 0.01, seed=w.BASE_SEED + 7000 + 10 * n + s)
+            st, K, *_ = solve(a, "none", 100)
+            dX, dR, r = [], [], []
+            for k in range(1, K + 1):
+                mats = []
+                for filt in ("none", "exact"):
+                    _, _, rp, col, val = solve(a, filt, k)
+                    X = np.zeros((n, n))
+                    X[np.repeat(np.arange(n), np.diff(rp)), col] = val
+                    mats.append(X)
+                X, Xh = mats
+                R = np.eye(n) - X @ X
+                Rh = np.eye(n) - Xh @ Xh
+                rms = lambda M: float(np.linalg.norm(M) / np.sqrt(n))  # noqa: E731
+                dX.append(rms(Xh - X))
+                dR.append(rms(Rh - R))
+                r.append(rms(R))
+            out.append({"n": n, "seed": s, "ns_status": int(st), "iters": int(K), "dX": dX,
+                        "dR": dR, "resid": r, "max_dX": max(dX), "max_dR": max(dR)})
+            print(f"filter error n={n} seed {s}: {K} iterations, max dX {max(dX):.2e}, "
+                  f"max dR {max(dR):.2e}", file=sys.stderr, flush=True)
+    return out
+
+
 # ---------------------------------------------------------------------- clocks
 class Clocks:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -435,6 +470,8 @@ def main():
                     help="also track fill on the n=65,536 2-D Laplacian for this many updates")
     ap.add_argument("--ode", default="",
                     help="comma-separated n: also solve Sec. 4.2's ODE block matrix as in Table 4.2.1")
+    ap.add_argument("--filter-error", default="",
+                    help="comma-separated n: also run Sec. 4.1's NS vs NSF test (Fig. 4.1.2)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -636,6 +673,12 @@ def main():
         line["laplacian3d"] = [laplacian3d_leg(sg, int(m)) for m in args.laplacian3d.split(",")]
     if args.ode and rank == 0:
         line["ode_table_4_2_1"] = ode_leg(sg, [int(n) for n in args.ode.split(",")])
+    if args.filter_error and rank == 0:
+        def gpu_solve(a, filt, max_iter):
+            r = sg.solve(a, tol=1e-12, filter=filt, prec=0, max_iter=max_iter)
+            return r.status, r.iters, r.rowptr, r.col, r.val
+        line["filter_error_fig_4_1_2"] = filter_error_leg(
+            gpu_solve, [int(n) for n in args.filter_error.split(",")])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

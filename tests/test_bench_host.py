@@ -23,3 +23,20 @@ def test_ode_closed_form_is_the_sign_of_the_block_matrix(nb):
     assert np.allclose(S @ S, np.eye(a.n), atol=1e-13)
     assert np.allclose(S @ A, A @ S, atol=1e-13)
     assert np.allclose(S, np.real(linalg.signm(A)), atol=1e-10)
+
+
+def test_filter_error_leg_on_the_oracle(oracle_lib):
+    """bench.py's Fig. 4.1.2 leg driven by the oracle on a small SPD matrix:
+    the filtered and unfiltered iterates stay within tol = 1e-12 of each other
+    at every iteration, as Sec. 4.1 reports."""
+    import bench
+
+    def solve(a, filt, max_iter):
+        r = oracle_lib.nsf(a, tol=1e-12, filter=filt, max_iter=max_iter)
+        return r.status, r.iters, r.rowptr, r.col, r.val
+
+    (res,) = bench.filter_error_leg(solve, [150], seeds=1)
+    assert res["ns_status"] == 0 and res["iters"] >= 8
+    assert len(res["dX"]) == len(res["dR"]) == res["iters"]
+    assert res["max_dX"] < 1e-12 and res["max_dR"] < 1e-12
+    assert res["resid"][-1] <= 1e-12 < res["resid"][0]
