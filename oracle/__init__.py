@@ -80,6 +80,7 @@ def lib():
         L.oracle_nsf.argtypes = [C.c_int64, _P64, _P32, _PD, C.POINTER(_Opts), C.POINTER(_Trace),
                                  C.POINTER(C.c_int), _PD, C.POINTER(_P64), C.POINTER(_P32),
                                  C.POINTER(_PD)]
+        L.oracle_nmf.argtypes = L.oracle_nsf.argtypes
         L.oracle_nm_dense.argtypes = [C.c_int64, _PD, C.c_double, C.c_int, _PD,
                                       C.POINTER(C.c_int), _PD]
         _lib = L
@@ -214,6 +215,33 @@ def nsf(a, tol=1e-8, filter="exact", c4=1e-4, switch_resid=1e-6, max_iter=100, m
                           C.byref(vp))
     if rc in (EINVAL, ENOMEM):
         raise RuntimeError(f"oracle_nsf rc={rc}")
+    srp, scol, sval = _take(n, rp, cp, vp, np.float64)
+    trace = {k: v[:tr.count].copy() for k, v in arrs.items()}
+    return Result(rc, it.value, r.value, srp, scol, sval, trace)
+
+
+def nmf(a, tol=1e-12, filter="exact", c4=1e-4, switch_resid=1e-6, max_iter=100, div_limit=1e6,
+        trace_cap=256) -> Result:
+    """Runs the oracle's NMF (Alg. 3.1.1; filter='none' is Newton's method) on a
+    CSR input: X1 = A, dense inverse, filter budget c4*tol, then Eq. (1.13)."""
+    n = a.n
+    rowptr, col, val = _csr_args(a.rowptr, a.col, a.val)
+    o = _Opts(tol, _FILTERS[filter], c4, switch_resid, max_iter, 0, 0.0, 0, div_limit)
+    arrs = {k: np.zeros(trace_cap, dtype=t) for k, t in
+            [("nnz_x", np.int64), ("nnz_t", np.int64), ("resid", np.float64),
+             ("xnorm", np.float64), ("beta", np.float64), ("tau", np.float64),
+             ("fnorm", np.float64), ("nnz_bar", np.int64), ("prec", np.int32)]}
+    tr = _Trace(trace_cap, 0, _p(arrs["nnz_x"], _P64), _p(arrs["nnz_t"], _P64),
+                _p(arrs["resid"], _PD), _p(arrs["xnorm"], _PD), _p(arrs["beta"], _PD),
+                _p(arrs["tau"], _PD), _p(arrs["fnorm"], _PD), _p(arrs["nnz_bar"], _P64),
+                _p(arrs["prec"], C.POINTER(C.c_int)))
+    it, r = C.c_int(), C.c_double()
+    rp, cp, vp = _P64(), _P32(), _PD()
+    rc = lib().oracle_nmf(n, _p(rowptr, _P64), _p(col, _P32), _p(val, _PD), C.byref(o),
+                          C.byref(tr), C.byref(it), C.byref(r), C.byref(rp), C.byref(cp),
+                          C.byref(vp))
+    if rc in (EINVAL, ENOMEM):
+        raise RuntimeError(f"oracle_nmf rc={rc}")
     srp, scol, sval = _take(n, rp, cp, vp, np.float64)
     trace = {k: v[:tr.count].copy() for k, v in arrs.items()}
     return Result(rc, it.value, r.value, srp, scol, sval, trace)

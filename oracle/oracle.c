@@ -716,3 +716,115 @@ int oracle_nm_dense(int64_t n, const double *a, double tol, int max_iter, double
   if (resid) *resid = r;
   return status;
 }
+
+/* ---------------------------------------------------------------------- */
+/* Newton's method with filtering, Alg. 3.1.1                                */
+/* ---------------------------------------------------------------------- */
+/* X1 = A. While e_k = ||I - X_k^2|| > tol: Xbar_{k+1} = (X_k + X_k^-1)/2
+ * with a dense LU inverse, then the filter with an RMS budget of c4*tol in
+ * the fixed phase (e_k >= switch_resid) and, in the adaptive phase, the bound
+ * of Thm 3.1.2 (Eq. 1.13), ||F|| <= e_k^2 / (||X_k|| + ||X_k^-1||), all RMS
+ * norms and taken from the current filtered iterate (the readings used for
+ * Eq. 1.18). Xbar holds all n^2 entries of the dense sum; the EXACT and BOUND
+ * filters drop its zeros, NONE keeps them, which makes NONE plain Newton. */
+int oracle_nmf(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
+               const oracle_opts *o, oracle_trace *tr, int *iters, double *resid,
+               int64_t **srp, int32_t **scol, double **sval) {
+  if (!o || !valid_csr(n, rowptr, col, val)) return OR_EINVAL;
+  if (tr) tr->count = 0;
+  size_t nn = (size_t)(n * n);
+  int64_t nnz = rowptr[n];
+  double *dx = (double *)malloc(sizeof(double) * nn);
+  double *inv = (double *)malloc(sizeof(double) * nn);
+  double *lu = (double *)malloc(sizeof(double) * nn);
+  int64_t *piv = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t *brp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int32_t *bcol = (int32_t *)malloc(sizeof(int32_t) * nn);
+  double *bval = (double *)malloc(sizeof(double) * nn);
+  int64_t *xrp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int32_t *xcol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+  double *xval = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  if (!dx || !inv || !lu || !piv || !brp || !bcol || !bval || !xrp || !xcol || !xval) {
+    free(dx); free(inv); free(lu); free(piv); free(brp); free(bcol); free(bval);
+    free(xrp); free(xcol); free(xval);
+    return OR_ENOMEM;
+  }
+  memcpy(xrp, rowptr, sizeof(int64_t) * (size_t)(n + 1));
+  if (nnz > 0) {
+    memcpy(xcol, col, sizeof(int32_t) * (size_t)nnz);
+    memcpy(xval, val, sizeof(double) * (size_t)nnz);
+  }
+  int k = 0, status = OR_ENOTCONV;
+  double r = NAN;
+  for (;;) {
+    /* e_k = ||I - X_k^2|| (step 5, for k = 1 step 1) */
+    int64_t *trp = NULL;
+    int32_t *tcol = NULL;
+    double *tval = NULL;
+    if (oracle_spgemm(n, xrp, xcol, xval, xrp, xcol, xval, &trp, &tcol, &tval) != OR_OK) {
+      status = OR_ENOMEM;
+      break;
+    }
+    r = oracle_resid_rms(n, trp, tcol, tval);
+    int64_t nnz_t = trp[n];
+    free(trp); free(tcol); free(tval);
+    double x = oracle_fro_rms(n, xrp, xval);
+    trace_put(tr, xrp[n], nnz_t, r, x, 64);
+    if (r <= o->tol) {
+      status = OR_OK;
+      break;
+    }
+    if (!isfinite(r) || r > o->div_limit) {
+      status = OR_EDIVERGED;
+      break;
+    }
+    if (k >= o->max_iter) break;
+    /* X_k^-1, dense */
+    memset(dx, 0, sizeof(double) * nn);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = xrp[i]; p < xrp[i + 1]; ++p) dx[i * n + xcol[p]] = xval[p];
+    if (dense_inverse(n, dx, inv, lu, piv)) {
+      status = OR_EDIVERGED;  /* singular iterate */
+      break;
+    }
+    ksum isq = {0.0, 0.0};
+    for (size_t p = 0; p < nn; ++p) kadd(&isq, inv[p] * inv[p]);
+    double xinv = sqrt(kval(&isq)) / sqrt((double)n);
+    /* Xbar_{k+1} = (X_k + X_k^-1) / 2 (step 3), every entry kept */
+    for (int64_t i = 0; i <= n; ++i) brp[i] = i * n;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j) {
+        bcol[i * n + j] = (int32_t)j;
+        bval[i * n + j] = 0.5 * (dx[i * n + j] + inv[i * n + j]);
+      }
+    /* budget: fixed phase, else Eq. (1.13) */
+    double beta = r >= o->switch_resid ? o->c4 * o->tol : r * r / (x + xinv);
+    int64_t *frp = NULL;
+    int32_t *fcol = NULL;
+    double *fval = NULL;
+    double tau = 0.0, fnorm = 0.0;
+    int rc = oracle_filter(n, brp, bcol, bval, o->filter, sqrt((double)n) * beta, &frp, &fcol,
+                           &fval, &tau, &fnorm);
+    if (rc != OR_OK) {
+      status = rc;
+      break;
+    }
+    trace_filter(tr, beta, tau, fnorm, (int64_t)nn);
+    free(xrp); free(xcol); free(xval);
+    xrp = frp;
+    xcol = fcol;
+    xval = fval;
+    ++k;
+  }
+  free(dx); free(inv); free(lu); free(piv); free(brp); free(bcol); free(bval);
+  if (iters) *iters = k;
+  if (resid) *resid = r;
+  if (srp && scol && sval && (status == OR_OK || status == OR_ENOTCONV || status == OR_EDIVERGED)) {
+    *srp = xrp;
+    *scol = xcol;
+    *sval = xval;
+  } else {
+    free(xrp); free(xcol); free(xval);
+  }
+  return status;
+}

@@ -95,6 +95,13 @@ int oracle_nsf(int64_t n, const int64_t *rowptr, const int32_t *col, const doubl
                const oracle_opts *o, oracle_trace *tr, int *iters, double *resid,
                int64_t **srp, int32_t **scol, double **sval);
 
+/* Newton's method with filtering (Alg. 3.1.1) on CSR input, dense inverse;
+ * o->filter, tol, c4, switch_resid, max_iter and div_limit apply (no scaling,
+ * no mixed precision). Outputs as oracle_nsf. */
+int oracle_nmf(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
+               const oracle_opts *o, oracle_trace *tr, int *iters, double *resid,
+               int64_t **srp, int32_t **scol, double **sval);
+
 /* Newton's method X <- (X + X^-1)/2 on a dense row-major matrix, X0 = A. */
 int oracle_nm_dense(int64_t n, const double *a, double tol, int max_iter,
                     double *s, int *iters, double *resid);

@@ -327,6 +327,81 @@ def test_table_4_2_1_ae_not_worse_than_paper(oracle_lib):
 
 
 # --------------------------------------------------------------------------
+# Newton's method with filtering, Alg. 3.1.1
+# --------------------------------------------------------------------------
+def _dense_of(a):
+    d = np.zeros((a.n, a.n))
+    d[np.repeat(np.arange(a.n), np.diff(a.rowptr)), a.col] = a.val
+    return d
+
+
+@pytest.mark.parametrize("which", ["ode", "banded"])
+def test_nmf_without_filter_is_newton(oracle_lib, which):
+    """With no filter, NMF is Newton's method: bit for bit the dense NM."""
+    a = w.ode_block(60) if which == "ode" else w.banded(90, 3, 4)
+    r = oracle_lib.nmf(a, tol=1e-12, filter="none")
+    s, iters, resid, st = oracle_lib.nm_dense(_dense_of(a), tol=1e-12)
+    assert r.status == st == oracle_lib.OK and r.iters == iters
+    assert np.array_equal(r.to_dense(a.n), s)
+
+
+def test_nmf_table_4_2_1_ae_not_worse_than_paper(oracle_lib):
+    """AE = ||X_NM - X_NMF|| at or below the paper's NMF column, and the
+    filtered result at the closed form (Eq. 1.26)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table_4_2_1.txt"))
+            if l.strip() and not l.startswith("#")]
+    paper_ae = {int(r[0]): float(r[5]) for r in rows}
+    a = w.ode_block(250)  # n = 500 read as the order of the block matrix
+    r0 = oracle_lib.nmf(a, tol=1e-12, filter="none")
+    r1 = oracle_lib.nmf(a, tol=1e-12, filter="exact")
+    assert r0.status == r1.status == oracle_lib.OK
+    assert np.linalg.norm(r0.to_dense(a.n) - r1.to_dense(a.n)) <= paper_ae[500]
+    assert r1.nnz < r0.nnz // 10
+    lam = 1.0 / 16
+    nb = 250
+    j = np.arange(1, nb + 1)
+    h = np.pi / (nb + 1)
+    V = np.sqrt(2.0 / (nb + 1)) * np.sin(np.outer(j, j) * h)
+    mu = 7.0 / 8.0 + 2.0 * lam * np.cos(j * h)
+    S = np.zeros((2 * nb, 2 * nb))
+    S[:nb, nb:] = (V * np.sqrt(mu)) @ V.T
+    S[nb:, :nb] = (V / np.sqrt(mu)) @ V.T
+    assert np.abs(r1.to_dense(a.n) - S).max() <= 1e-13
+
+
+def test_nmf_matches_eig_on_symmetric(oracle_lib):
+    a = w.banded(200, 4, 9)
+    r = oracle_lib.nmf(a, tol=1e-12, filter="exact")
+    S = _sign_eig(_dense_of(a))
+    assert r.status == oracle_lib.OK
+    assert np.linalg.norm(r.to_dense(a.n) - S) / np.linalg.norm(S) <= 1e-12
+
+
+def test_nmf_theorem_3_1_2(oracle_lib):
+    """Once the budget of Eq. (1.13) is in force, ||dR_k|| <= 4 ||R_k|| with
+    dR_k = Rhat_k - R_k between NMF and Newton's method (Thm 3.1.2). The
+    adaptive phase starts early here (switch at 1e-2) to give it several steps."""
+    a = w.ode_block(60)
+    A = _dense_of(a)
+    full = oracle_lib.nmf(a, tol=1e-12, filter="exact", switch_resid=1e-2)
+    assert full.status == oracle_lib.OK
+    adaptive = [k for k in range(full.iters) if full.trace["resid"][k] < 1e-2]
+    assert len(adaptive) >= 2
+    checked = 0
+    for k in range(1, full.iters + 1):
+        if k - 1 not in adaptive:
+            continue  # X_k was not formed under Eq. (1.13)
+        # the same runs stopped after k updates (only the last k converges)
+        xh = oracle_lib.nmf(a, tol=1e-12, filter="exact", switch_resid=1e-2, max_iter=k)
+        xn, _, _, _ = oracle_lib.nm_dense(A, tol=1e-12, max_iter=k)
+        Rh = np.eye(a.n) - xh.to_dense(a.n) @ xh.to_dense(a.n)
+        R = np.eye(a.n) - xn @ xn
+        assert np.linalg.norm(Rh - R) <= 4 * np.linalg.norm(R) + 1e-15
+        checked += 1
+    assert checked >= 2
+
+
+# --------------------------------------------------------------------------
 # filters (steps a4-a6)
 # --------------------------------------------------------------------------
 def _brute_exact(vals, b):
