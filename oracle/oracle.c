@@ -25,6 +25,9 @@
  *     equal magnitudes dropped or kept together; BOUND mode drops
  *     |x| < b / sqrt(nnz), which can never exceed the bound.
  *   - Eq. (1.1): Newton's method X <- (X + X^-1)/2, dense, for comparison.
+ *   - Alg. 3.1.1 (NMF): Newton's method with the same filter, on CSR with a
+ *     dense inverse, budget c4*tol and then Thm 3.1.2's bound (Eq. 1.13),
+ *     r^2 / (x + x_inv).
  * Norms are Frobenius divided by sqrt(n) ("RMS"); the paper leaves the norm
  * unspecified.
  */
