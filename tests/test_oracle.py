@@ -377,6 +377,28 @@ def test_nmf_matches_eig_on_symmetric(oracle_lib):
     assert np.linalg.norm(r.to_dense(a.n) - S) / np.linalg.norm(S) <= 1e-12
 
 
+def test_newton_with_one_step_inverse_is_newton_schulz(oracle_lib):
+    """Newton's update (X + X^-1)/2 with X^-1 replaced by one Newton-Schulz
+    inverse step from Y0 = X, Y1 = X(2I - X X), is the NS update X(3I - X^2)/2:
+    the oracle's NS update reproduces it to rounding. (A GPU NMF built on an
+    iterative inverse is therefore the NS family again, one order per
+    extra inner step.)"""
+    a = w.banded(80, 3, 2)
+    x = oracle_lib.nsf(a, tol=0.0, filter="none", max_iter=3)  # r well below 1
+    n = a.n
+    X = _dense(n, x.rowptr, x.col, x.val)
+    Y1 = X @ (2 * np.eye(n) - X @ X)
+    newton_one_step = 0.5 * (X + Y1)
+    Xc = (x.rowptr, x.col, x.val)
+    ns = _dense(n, *oracle_lib.ns_update(n, Xc, oracle_lib.spgemm(n, Xc, Xc)))
+    assert np.abs(newton_one_step - ns).max() <= 1e-14
+    # and the exact inverse differs from it at second order in R = I - X^2
+    R = np.eye(n) - X @ X
+    exact = 0.5 * (X + np.linalg.inv(X))
+    assert np.linalg.norm(exact - ns) <= 2 * np.linalg.norm(R) ** 2 * np.linalg.norm(X)
+    assert np.linalg.norm(exact - ns) >= 1e-3 * np.linalg.norm(R) ** 2
+
+
 def test_nmf_theorem_3_1_2(oracle_lib):
     """Once the budget of Eq. (1.13) is in force, ||dR_k|| <= 4 ||R_k|| with
     dR_k = Rhat_k - R_k between NMF and Newton's method (Thm 3.1.2). The
