@@ -82,6 +82,17 @@ def job_throughput(per_rank: int, world: int, steps: int, ms_max: float) -> floa
     return per_rank * world * steps / (ms_max / 1000.0)
 
 
+def step_hbm(prof: dict, steps: int, ms_per_step: float, hbm_gbs: float) -> dict:
+    """The step's HBM roofline: the algorithmic bytes of the timed classes that
+    count them (sparse products, filter, assembly: operands read once, outputs
+    written once) per step, over the whole step's time."""
+    per_step = sum(v["bytes"] for v in prof.values()) / max(steps, 1)
+    gbs = per_step / (ms_per_step / 1e3) / 1e9 if ms_per_step > 0 else 0.0
+    return {"algorithmic_bytes_per_step": per_step, "achieved_gbs": gbs, "peak_gbs": hbm_gbs,
+            "frac": gbs / hbm_gbs if hbm_gbs else None,
+            "covers": sorted(k for k, v in prof.items() if v["bytes"] > 0)}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -592,6 +603,8 @@ def main():
                        "parallelism": f"{world} independent batches (one per GPU)",
                        "l2": "working set of every step (iterates, products) is several GB, > 129 MB L2"},
             "gpu_launches": int(launches), "clocks": ck, "roofline": roofline,
+            "hbm_roofline_step": step_hbm(prof, args.steps, ms_max / args.steps,
+                                          peaks["hbm_gbs"]),
             "kernels": by_kernel, "host_ms_per_step": host}
 
     if args.legs == "all":

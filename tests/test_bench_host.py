@@ -40,3 +40,16 @@ def test_filter_error_leg_on_the_oracle(oracle_lib):
     assert len(res["dX"]) == len(res["dR"]) == res["iters"]
     assert res["max_dX"] < 1e-12 and res["max_dR"] < 1e-12
     assert res["resid"][-1] <= 1e-12 < res["resid"][0]
+
+
+def test_step_hbm_roofline():
+    """The step-level HBM figure sums the classes' algorithmic bytes per step
+    and divides by the step time; classes without byte counts add nothing."""
+    import bench
+    prof = {"numeric_square_f64": {"launches": 25, "ms": 200.0, "flops": 1e12, "bytes": 30e9},
+            "filter": {"launches": 60, "ms": 50.0, "flops": 0.0, "bytes": 10e9},
+            "bounds": {"launches": 130, "ms": 49.0, "flops": 0.0, "bytes": 0.0}}
+    h = bench.step_hbm(prof, 5, 200.0, 8000.0)
+    assert h["algorithmic_bytes_per_step"] == 8e9
+    assert abs(h["achieved_gbs"] - 40.0) < 1e-9 and abs(h["frac"] - 0.005) < 1e-12
+    assert h["covers"] == ["filter", "numeric_square_f64"] and h["peak_gbs"] == 8000.0
