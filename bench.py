@@ -46,10 +46,10 @@ TOL = 1e-8
 WORKLOAD = ("banded batch: 512 symmetric banded matrices, n log-uniform [200,8000], "
             "half-bandwidth U{1..10}, diag +-(1+U[0,1)), off-diag U[-1,1] scaled to row sum <= 0.8; "
             "EXACT filter, FP32 until resid<1e-4 then FP64, tol 1e-8")
-# FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
-# FP32 peak: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
-FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+# Unit-count peaks, for reference beside the measured ones (fma_peak_leg):
+# FP64 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz; FP32 152 x 128 x 2 x 2.07 GHz
+FP64_UNIT_GFLOPS = 152 * 2 * 2 * 2.07
+FP32_UNIT_GFLOPS = 152 * 128 * 2 * 2.07
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic
 # byte of each product class, from one ncu capture of the first 128 matrices
 # of the batch (profiles/dram_traffic_products_banded128.md). A full-size
@@ -130,6 +130,55 @@ def oracle_sample(indices, rank=0, cores=None):
     wall = time.perf_counter() - t0
     cpu = sum(r[0] for r in res)
     return wall, cpu, cores, [r[1] for r in res]
+
+
+def cpu_baseline_leg(idx):
+    """The oracle timed on the host's cores on a sample of the batch (the
+    reported CPU baseline), and the same sample solved by the oracle in FP64
+    throughout: the references of the per-result error of the mixed GPU
+    results. Returns (cpu_baseline, {index: FP64 oracle result})."""
+    import oracle
+    wall, cpu_s, cores, st = oracle_sample(idx)
+    cpu = {"value": len(idx) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{len(idx)} of the 512 matrices (every {BATCH // len(idx)}th), "
+                     f"same solve settings; {cpu_s:.1f} s of CPU work in {wall:.1f} s wall"}
+    refs = oracle.nsf_many([_mat_by_index(0, i) for i in idx], tol=TOL, filter="exact",
+                           mixed=False)
+    return cpu, {i: (r.rowptr, r.col, r.val) for i, r in zip(idx, refs)}
+
+
+def result_errors(mats, results, ref64):
+    """Per-result error of the GPU results (host CSR triples, one per matrix):
+    ||S - S_ref64||_F / ||S_ref64||_F against the FP64 oracle on its sample, and
+    for every result the commutator ||S A - A S||_F / ||A||_F (sign(A) commutes
+    with A) and the involution residual ||S^2 - I||_F / sqrt(n)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+
+    def m(n, rp, col, val):
+        return sp.csr_matrix((val, col, rp), shape=(n, n))
+
+    rel = {}
+    for i, (rp, col, val) in (ref64 or {}).items():
+        n = mats[i].n
+        s_ref = m(n, rp, col, val)
+        rel[i] = float(spl.norm(m(n, *results[i]) - s_ref) / spl.norm(s_ref))
+    comm = []
+    for a, (rp, col, val) in zip(mats, results):
+        A, S = m(a.n, a.rowptr, a.col, a.val), m(a.n, rp, col, val)
+        comm.append(float(spl.norm(S @ A - A @ S) / spl.norm(A)))
+    out = {"commutator": {"definition": "||S A - A S||_F / ||A||_F, every result of the batch",
+                          "max": max(comm), "median": statistics.median(comm),
+                          "count": len(comm)}}
+    if rel:
+        v = list(rel.values())
+        out.update({"definition": "||S_gpu - S_ref64||_F / ||S_ref64||_F, S_ref64 the FP64 "
+                                  "oracle (FP64 throughout, EXACT, tol 1e-8)",
+                    "sample": sorted(rel), "max": max(v), "median": statistics.median(v),
+                    "per_result": [rel[i] for i in sorted(rel)],
+                    "note": "the mixed result converges to the sign of the switched FP32 "
+                            "iterate, not of A: its error is reported, not bounded by 1e-10"})
+    return out
 
 
 def sample_indices(k: int, offset: int = 0):
@@ -290,14 +339,13 @@ def laplacian3d_leg(sg, m: int, samples: int = 4000):
     workload): mixed and FP64 solves with their fill per iteration, and the
     error of each against the closed-form sign at seeded sampled entries."""
     import torch
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from test_gpu_laplacian import _closed_form_entries, _entries
+    from workloads import closed_form
     a = w.laplacian(m, 3)
     rng = np.random.default_rng(m)
     p = rng.integers(0, a.n, samples)
     pp = np.where(rng.random(samples) < 0.5, p + rng.integers(-3 * m * m, 3 * m * m, samples),
                   rng.integers(0, a.n, samples)) % a.n
-    ref = _closed_form_entries(m, 3, p, pp)
+    ref = closed_form.laplacian_sign_entries(m, 3, p, pp)
     out = {"workload": f"laplacian3d m={m} (n={a.n}), sigma = 6, EXACT, tol 1e-8",
            "samples": samples}
     # FP64 throughout only up to n = 16384: before the iterate reaches the dense
@@ -308,7 +356,7 @@ def laplacian3d_leg(sg, m: int, samples: int = 4000):
         t0 = time.perf_counter()
         r = sg.solve(a, tol=TOL, filter="exact", prec=prec, max_iter=200)
         torch.cuda.synchronize()
-        got = _entries(r, a.n, p, pp)
+        got = closed_form.csr_entries(r.rowptr, r.col, r.val, p, pp)
         tr = r.trace
         out[name] = {"status": int(r.status), "updates": int(r.iters), "resid": float(r.resid),
                      "seconds": time.perf_counter() - t0,
@@ -323,21 +371,6 @@ def laplacian3d_leg(sg, m: int, samples: int = 4000):
 ODE_PAPER_NSF_SECONDS = {500: 0.0098, 1000: 0.011, 3000: 0.0268, 5000: 0.0481}
 
 
-def ode_closed_form(nb: int, lam: float = 1.0 / 16.0):
-    """sign([[0, B], [I, 0]]) = [[0, B^1/2], [B^-1/2, 0]] (Eq. 1.26) for
-    B = tridiag(lam, 7/8, lam) of order nb, from B's sine eigenbasis:
-    eigenvalues 7/8 + 2 lam cos(j pi/(nb+1)), eigenvectors
-    sqrt(2/(nb+1)) sin(i j pi/(nb+1))."""
-    j = np.arange(1, nb + 1)
-    h = np.pi / (nb + 1)
-    V = np.sqrt(2.0 / (nb + 1)) * np.sin(np.outer(j, j) * h)
-    mu = 7.0 / 8.0 + 2.0 * lam * np.cos(j * h)
-    S = np.zeros((2 * nb, 2 * nb))
-    S[:nb, nb:] = (V * np.sqrt(mu)) @ V.T
-    S[nb:, :nb] = (V / np.sqrt(mu)) @ V.T
-    return S
-
-
 def ode_leg(sg, sizes, reps: int = 3):
     """Sec. 4.2's ODE block matrix A = [[0, B], [I, 0]], B = tridiag(1/16, 7/8,
     1/16), solved as in Table 4.2.1: FP64 NSF (EXACT) to tol 1e-12 from X0 = A
@@ -346,6 +379,7 @@ def ode_leg(sg, sizes, reps: int = 3):
     Reports the device time per solve (one matrix per sign_solve_batch call,
     after a warm-up) and the error against the closed form (Eq. 1.26)."""
     import torch
+    from workloads import closed_form
     out = []
     o = sg.default_opts(tol=1e-12, filter="exact", prec="fp64", scale_1norm=0)
     for n in sizes:
@@ -366,7 +400,7 @@ def ode_leg(sg, sizes, reps: int = 3):
                 b.close()
             D = np.zeros((a.n, a.n))
             D[np.repeat(np.arange(a.n), np.diff(rp)), col] = val
-            S = ode_closed_form(nb)
+            S = closed_form.ode_block_sign(nb)
             out.append({"n": n, "reading": reading, "order_of_A": int(a.n), "status": int(st),
                         "iters": int(iters), "resid": float(resid),
                         "seconds_per_solve": statistics.median(secs),
@@ -410,6 +444,51 @@ def filter_error_leg(solve, sizes, seeds: int = 5, tol: float = 1e-12):
                         "dR": dR, "resid": r, "max_dX": max(dX), "max_dR": max(dR)})
             print(f"filter error n={n} seed {s}: {K} iterations, max dX {max(dX):.2e}, "
                   f"max dR {max(dR):.2e}", file=sys.stderr, flush=True)
+    return out
+
+
+# ---------------------------------------------------------------------- FMA peaks
+def fma_peak_leg(sg, gpu_index: int, seconds: float = 1.0):
+    """Measured FP64 and FP32 fused multiply-add peaks of this GPU: the
+    library's probe (register-resident FMA chains on every SM) timed with CUDA
+    events, the median of the launches, with the SM clock sampled while it
+    runs. The sparse products' rooflines divide by these."""
+    import ctypes
+    import torch
+    L = sg.load()
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    sms = torch.cuda.get_device_properties(gpu_index).multi_processor_count
+    out = {}
+    for name, fp64, iters in (("fp64", 1, 4096), ("fp32", 0, 65536)):
+        fl = ctypes.c_double()
+
+        def launch():
+            st = L.sign_fma_probe(fp64, sms * 8, 256, iters, sp, ctypes.byref(fl))
+            if st != sg.SIGN_OK:
+                raise sg.SignError(st, "sign_fma_probe")
+
+        for _ in range(3):
+            launch()
+        torch.cuda.synchronize()
+        ck = Clocks(gpu_index)
+        ck.start()
+        times = []
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end or len(times) < 5:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launch()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        clk = ck.stop()
+        ms = statistics.median(times)
+        out[name] = {"gflops": fl.value / (ms / 1e3) / 1e9, "ms_per_launch": ms,
+                     "launches": len(times), "clocks": clk,
+                     "unit_count_gflops": FP64_UNIT_GFLOPS if fp64 else FP32_UNIT_GFLOPS}
+    out["how"] = (f"sign_fma_probe: {sms * 8} CTAs x 256 threads, 8 independent FMA chains per "
+                  "thread; median of the launches over ~1 s each, CUDA events")
     return out
 
 
@@ -492,13 +571,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     # CPU baseline first: the spawn pool runs before this process touches CUDA
-    cpu = None
+    cpu = ref64 = None
     if args.legs == "all" and rank == 0 and world == 1:
         idx = sample_indices(args.cpu_sample)
-        wall, cpu_s, cores, st = oracle_sample(idx)
-        cpu = {"value": len(idx) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{len(idx)} of the 512 matrices (every {BATCH // len(idx)}th), "
-                         f"same solve settings; {cpu_s:.1f} s of CPU work in {wall:.1f} s wall"}
+        cpu, ref64 = cpu_baseline_leg(idx)
 
     import torch
     torch.cuda.set_device(local)
@@ -553,8 +629,10 @@ def main():
     ms_max = max_over_ranks(ms, dist, "cuda")
     value = job_throughput(len(mats), world, args.steps, ms_max)
 
-    # roofline of the dominant kernel class
+    # roofline of the dominant kernel class; the FMA peaks are measured here
     peaks, peak_kind = measured_peaks()
+    fma = fma_peak_leg(sg, local)
+    FP64_PEAK_GFLOPS, FP32_PEAK_GFLOPS = fma["fp64"]["gflops"], fma["fp32"]["gflops"]
     top = max(prof.items(), key=lambda kv: kv[1]["ms"])
     name, p = top
     per_launch_ms = p["ms"] / max(p["launches"], 1)
@@ -584,7 +662,10 @@ def main():
                                    "times this launch's algorithmic bytes" if traffic else None),
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "peak_source": (f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if bound == "hbm"
-                                else "unit counts x 2.07 GHz (FP64: 2 FMA/clk/SM; FP32: 128)"),
+                                else "measured in this run: FMA probe (fma_peaks), "
+                                     f"{'FP64' if name.endswith('f64') else 'FP32'}"),
+                "unit_count_peak": (None if bound == "hbm" else
+                                    FP64_UNIT_GFLOPS if name.endswith("f64") else FP32_UNIT_GFLOPS),
                 "per_launch_work": per_launch, "avg_launch_ms": per_launch_ms,
                 "share_of_kernel_time": p["ms"] / total_ms if total_ms else None}
     by_kernel = {k: {"share": v["ms"] / total_ms if total_ms else 0.0, "launches": v["launches"],
@@ -592,6 +673,10 @@ def main():
                      "gflops": v["flops"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else 0.0,
                      "gbs": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else 0.0}
                  for k, v in prof.items() if v["launches"]}
+    for k, v in by_kernel.items():  # the sparse products against their FMA pipe
+        if k.startswith("numeric_"):
+            v["frac_of_fma_peak"] = v["gflops"] / (FP64_PEAK_GFLOPS if k.endswith("f64")
+                                                   else FP32_PEAK_GFLOPS)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -605,7 +690,7 @@ def main():
             "gpu_launches": int(launches), "clocks": ck, "roofline": roofline,
             "hbm_roofline_step": step_hbm(prof, args.steps, ms_max / args.steps,
                                           peaks["hbm_gbs"]),
-            "kernels": by_kernel, "host_ms_per_step": host}
+            "kernels": by_kernel, "host_ms_per_step": host, "fma_peaks": fma}
 
     if args.legs == "all":
         # end to end through the public API: pinned host inputs -> device -> host result
@@ -621,6 +706,8 @@ def main():
         # result buffers in pinned memory, sized by an untimed first pass and
         # reused by every step (a caller sizes them from result_nnz())
         outs = []
+
+        last = []
 
         def e2e_step():
             b2 = sg.Batch(pinned)
@@ -639,6 +726,7 @@ def main():
             res = b2.results(outs)  # every copy queued, one wait
             nbytes = sum(rp.nbytes + col.nbytes + val.nbytes for rp, col, val in res)
             b2.close()
+            last[:] = res
             return nbytes
 
         e2e_step()
@@ -650,6 +738,10 @@ def main():
         e2e_s = time.perf_counter() - t0
         line["e2e"] = {"value": len(mats) * world * args.steps / e2e_s, "unit": UNIT,
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        # the results of the last end-to-end step: identical to the timed steps'
+        # (every solve is deterministic); their errors, outside any timed region
+        if rank == 0:
+            line["err_vs_fp64_oracle"] = result_errors(mats, last, ref64)
 
         # unfiltered FP64 Newton-Schulz on the same GPU, on a sample of the batch
         idx = sample_indices(args.unfiltered_sample)

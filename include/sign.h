@@ -355,6 +355,16 @@ typedef struct {
   double bytes;     /* algorithmic DRAM bytes                           */
 } sign_prof_entry;
 
+/* Peak probe of the FMA pipes (FP64 if fp64, else FP32), for the rooflines
+ * of the sparse products: queues one launch of `blocks` x `threads` threads
+ * (threads a multiple of 32, at most 1024), each running 8 independent
+ * register-resident fused multiply-add chains for `iters` steps, on
+ * cuda_stream, and returns at once; the caller times it (CUDA events on that
+ * stream). *flops_out receives the launch's flops, 2 per multiply-add.
+ * SIGN_EINVAL for bad sizes, SIGN_ECUDA if the launch failed. */
+sign_status sign_fma_probe(int fp64, int blocks, int threads, int iters, void *cuda_stream,
+                           double *flops_out);
+
 /* Turns timing on (1) or off (0); returns the previous setting. */
 int sign_prof_enable(int on);
 /* Waits for the recorded events, writes up to cap entries (one per kernel

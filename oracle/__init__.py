@@ -220,6 +220,23 @@ def nsf(a, tol=1e-8, filter="exact", c4=1e-4, switch_resid=1e-6, max_iter=100, m
     return Result(rc, it.value, r.value, srp, scol, sval, trace)
 
 
+def _nsf_worker(job):
+    a, kw = job
+    return nsf(a, **kw)
+
+
+def nsf_many(mats, processes=None, **kw) -> list:
+    """nsf(a, **kw) for every matrix, spread over a pool of spawned processes
+    (spawn, so that callers that already use CUDA stay safe); results in order."""
+    import multiprocessing as mp
+    build()
+    procs = max(1, min(len(mats), processes or (os.cpu_count() or 1)))
+    if procs == 1:
+        return [nsf(a, **kw) for a in mats]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_nsf_worker, [(a, kw) for a in mats], chunksize=1)
+
+
 def nmf(a, tol=1e-12, filter="exact", c4=1e-4, switch_resid=1e-6, max_iter=100, div_limit=1e6,
         trace_cap=256) -> Result:
     """Runs the oracle's NMF (Alg. 3.1.1; filter='none' is Newton's method) on a

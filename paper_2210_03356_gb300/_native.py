@@ -103,6 +103,8 @@ SIGNATURES = {
     "sign_prof_enable": (C.c_int, [C.c_int]),
     "sign_prof_read": (C.c_int, [C.c_void_p, C.c_int]),
     "sign_prof_reset": (None, []),
+    "sign_fma_probe": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                 C.POINTER(C.c_double)]),
 }
 
 _lib = None

@@ -127,9 +127,53 @@ ProfScope::~ProfScope() {
   if (g_recs.size() > 4096) drain();
 }
 
+// Peak probe of the FMA pipes: every thread runs CHAINS independent
+// register-resident chains x <- fma(x, a, b) for `iters` steps, so the pipe,
+// not memory or latency, bounds the kernel. 2 * CHAINS * iters flops per
+// thread. The result is stored only if it equals a value it cannot reach
+// (|a| < 1 keeps every chain bounded), which keeps the arithmetic alive.
+constexpr int PROBE_CHAINS = 8;
+__device__ double g_probe_sink;
+
+template <typename T>
+__global__ void k_fma_probe(int iters) {
+  const T a = T(0.5) + T(threadIdx.x & 31) * T(1.0 / 128.0);
+  const T b = T(blockIdx.x & 7) * T(1.0 / 64.0);
+  T x[PROBE_CHAINS];
+#pragma unroll
+  for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = T(c) * T(0.125);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = fma(x[c], a, b);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < PROBE_CHAINS; ++c) s += x[c];
+  if (s == T(-12345.0)) g_probe_sink = double(s);
+}
+
 }  // namespace sgn
 
 extern "C" {
+
+sign_status sign_fma_probe(int fp64, int blocks, int threads, int iters, void *cuda_stream,
+                           double *flops_out) {
+  if (blocks < 1 || threads < 32 || threads > 1024 || threads % 32 || iters < 1 || !flops_out)
+    return SIGN_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (fp64)
+    sgn::k_fma_probe<double><<<blocks, threads, 0, s>>>(iters);
+  else
+    sgn::k_fma_probe<float><<<blocks, threads, 0, s>>>(iters);
+  sgn::count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    sgn::set_last_error(std::string("sign_fma_probe: ") + cudaGetErrorString(e));
+    return SIGN_ECUDA;
+  }
+  *flops_out = 2.0 * sgn::PROBE_CHAINS * double(iters) * double(blocks) * double(threads);
+  return SIGN_OK;
+}
 
 int64_t sign_kernel_launches(void) { return sgn::g_launches.load(); }
 

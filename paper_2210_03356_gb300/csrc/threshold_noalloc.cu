@@ -68,6 +68,16 @@ void *scratch_address(std::string &why) {
   return g_addr[dev];
 }
 
+// Drops the current device's cached address, so that the next call looks it
+// up again (a failed call may follow a reset of the device's context, after
+// which the module and its array can sit elsewhere).
+void forget_address() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_addr[dev] = nullptr;
+}
+
 }  // namespace
 
 extern "C" sign_status sign_threshold_exact_noalloc(const double *val, int64_t nnz, double b,
@@ -101,6 +111,7 @@ extern "C" sign_status sign_threshold_exact_noalloc(const double *val, int64_t n
     SGN_CUDA(cudaStreamSynchronize(s));
     *tau_out = h.ms.tau;
   } catch (const Error &e) {
+    forget_address();  // after a CUDA error the next call looks the array up again
     set_last_error(e.what());
     return sign_status(e.status);
   } catch (const std::bad_alloc &) {

@@ -14,12 +14,12 @@ def test_ode_closed_form_is_the_sign_of_the_block_matrix(nb):
     """Eq. (1.26) from B's sine eigenbasis agrees with scipy's signm of the
     dense block matrix, and is an involution commuting with it."""
     linalg = pytest.importorskip("scipy.linalg")
-    import bench
     import workloads as w
+    from workloads import closed_form
     a = w.ode_block(nb)
     A = np.zeros((a.n, a.n))
     A[np.repeat(np.arange(a.n), np.diff(a.rowptr)), a.col] = a.val
-    S = bench.ode_closed_form(nb)
+    S = closed_form.ode_block_sign(nb)
     assert np.allclose(S @ S, np.eye(a.n), atol=1e-13)
     assert np.allclose(S @ A, A @ S, atol=1e-13)
     assert np.allclose(S, np.real(linalg.signm(A)), atol=1e-10)
@@ -53,3 +53,21 @@ def test_step_hbm_roofline():
     assert h["algorithmic_bytes_per_step"] == 8e9
     assert abs(h["achieved_gbs"] - 40.0) < 1e-9 and abs(h["frac"] - 0.005) < 1e-12
     assert h["covers"] == ["filter", "numeric_square_f64"] and h["peak_gbs"] == 8000.0
+
+
+@pytest.mark.parametrize("dim,m", [(2, 6), (3, 4)])
+def test_laplacian_closed_form_entries_match_eigh(dim, m):
+    """The closed-form entries of sign(L - sigma I) agree with the sign from a
+    dense eigendecomposition of the shifted Laplacian."""
+    import workloads as w
+    from workloads import closed_form
+    a = w.laplacian(m, dim)
+    d = a.to_dense()
+    ev, v = np.linalg.eigh(d)
+    S = (v * np.sign(ev)) @ v.T
+    rng = np.random.default_rng(3)
+    p, pp = rng.integers(0, a.n, 200), rng.integers(0, a.n, 200)
+    assert np.allclose(closed_form.laplacian_sign_entries(m, dim, p, pp), S[p, pp], atol=1e-12)
+    rp = np.arange(a.n + 1) * a.n
+    col = np.tile(np.arange(a.n, dtype=np.int32), a.n)
+    assert np.array_equal(closed_form.csr_entries(rp, col, S.ravel(), p, pp), S[p, pp])

@@ -3,12 +3,11 @@ dense path serves (n = 4096), against the closed-form sign from the sine
 eigenbasis: S = V sign(Lambda - sigma) V^T with V = kron of the 1-D bases,
 evaluated at 10^4 seeded entries (an O(m^dim) sum each), and the trace
 n_plus - n_minus counted from the closed-form spectrum."""
-import math
-
 import numpy as np
 import pytest
 
 import workloads as w
+from workloads import closed_form
 
 pytestmark = pytest.mark.gpu
 
@@ -25,34 +24,8 @@ def sg():
     return sg
 
 
-def _closed_form_entries(m, dim, p, pp):
-    """S[p, pp] of sign(L - sigma I) for grid indices p, pp (x + m y + m^2 z)."""
-    sigma = w.laplacian_shift(m, dim)
-    h = math.pi / (m + 1)
-    k = np.arange(1, m + 1)
-    lam1 = 2 - 2 * np.cos(k * h)
-    q = np.sqrt(2.0 / (m + 1)) * np.sin(np.outer(np.arange(1, m + 1), k) * h)  # q[x, i]
-
-    def coord(idx, a):
-        return (idx // m ** a) % m
-
-    f = [q[coord(p, a)] * q[coord(pp, a)] for a in range(dim)]  # (samples, m) each
-    if dim == 2:
-        sgn = np.sign(lam1[:, None] + lam1[None, :] - sigma)
-        return np.einsum("si,ij,sj->s", f[0], sgn, f[1])
-    sgn = np.sign(lam1[:, None, None] + lam1[None, :, None] + lam1[None, None, :] - sigma)
-    return np.einsum("si,sj,sk,ijk->s", f[0], f[1], f[2], sgn)
-
-
 def _entries(res, n, p, pp):
-    """Entries (p, pp) of a CSR result (0 where absent)."""
-    out = np.zeros(len(p))
-    for t, (i, j) in enumerate(zip(p, pp)):
-        lo, hi = res.rowptr[i], res.rowptr[i + 1]
-        k = np.searchsorted(res.col[lo:hi], j)
-        if k < hi - lo and res.col[lo + k] == j:
-            out[t] = res.val[lo + k]
-    return out
+    return closed_form.csr_entries(res.rowptr, res.col, res.val, p, pp)
 
 
 @pytest.mark.parametrize("dim,m,prec,bound", [(2, 64, "fp64", 1e-7), (2, 64, "mixed", 1e-5),
@@ -74,7 +47,7 @@ def test_laplacian_sign_against_closed_form(sg, dim, m, prec, bound):
     p = rng.integers(0, n, 10000)
     pp = np.where(rng.random(10000) < 0.5, p + rng.integers(-3 * m, 3 * m, 10000),
                   rng.integers(0, n, 10000)) % n  # near and far entries
-    ref = _closed_form_entries(m, dim, p, pp)
+    ref = closed_form.laplacian_sign_entries(m, dim, p, pp)
     got = _entries(res, n, p, pp)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= bound
     # trace = n_plus - n_minus of the closed-form spectrum

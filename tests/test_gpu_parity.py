@@ -231,6 +231,48 @@ def test_batch_full_512_sampled(sg, orc):
     assert max(r.resid for r in out) <= 1e-8
 
 
+def _dense_records(res, n, o):
+    """Records of a result whose round ran the dense tensor-core path, by the
+    solver's rule: a filter on, n <= 32768 and nnz(X_k) >= dense_frac n^2, and
+    in the FP64 stage also n >= dense64_min_n."""
+    t = res.trace
+    dense = (t["nnz_x"] >= o.dense_frac * n * n) & (n <= 32768) & (o.filter != 0)
+    return dense & ((t["prec_k"] == 32) | (n >= o.dense64_min_n))
+
+
+def test_batch_full_512_bench_options(sg, orc):
+    """The benchmark's own configuration, all options at their defaults
+    (dense_frac 0.25, dense64_min_n 1024; mixed, EXACT, tol 1e-8): the full
+    batch of 512 in one call. Every member that took the dense tensor-core
+    path is compared with the oracle's mixed run within the dense path's
+    1e-5 (relative Frobenius; its products round differently), and a spread
+    of the others, which stay on the sparse path, bit for bit."""
+    shapes = w.banded_batch_shapes()
+    mats = [w.banded(n, b, s) for n, b, s in shapes]
+    o = sg.default_opts(tol=1e-8, filter="exact", prec="mixed")
+    assert o.dense_frac == 0.25 and o.dense64_min_n == 1024
+    sg.prof_reset()
+    sg.prof_enable(True)
+    out = sg.solve_batch(mats, opts=o)
+    sg.prof_enable(False)
+    prof = sg.prof_read()
+    assert all(r.status == sg.SIGN_OK for r in out)
+    assert max(r.resid for r in out) <= 1e-8
+    assert prof.get("dense_tf32x3", {}).get("launches", 0) > 0  # the dense path ran
+    dense = [i for i, (a, r) in enumerate(zip(mats, out)) if _dense_records(r, a.n, o).any()]
+    assert dense, "no member met the dense path's rule"
+    order = [i for i in np.argsort([n * (b + 1) for n, b, _ in shapes]) if i not in dense]
+    sparse = [int(order[j]) for j in np.linspace(0, len(order) - 1, 12).astype(int)]
+    refs = orc.nsf_many([mats[i] for i in dense + sparse], tol=1e-8, filter="exact", mixed=True)
+    for i, ref in zip(dense, refs[:len(dense)]):
+        n = mats[i].n
+        err = _rel(res_dense(out[i], n), ref.to_dense(n))
+        assert err <= 1e-5, (i, n, err)
+    for i, ref in zip(sparse, refs[len(dense):]):
+        assert not _dense_records(out[i], mats[i].n, o).any()
+        assert_parity(out[i], ref)
+
+
 # ---------------------------------------------------------------- device pointers
 def test_device_pointers_in_and_out(sg, orc):
     import torch

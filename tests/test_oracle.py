@@ -238,6 +238,21 @@ def test_tridiagonal_500_matches_eigendecomposition(oracle_lib, mode):
     assert np.linalg.norm(S @ S - np.eye(a.n)) / math.sqrt(a.n) < 1e-11
 
 
+def test_tridiagonal_2000_matches_eigendecomposition(oracle_lib):
+    """The tridiagonal workload at its full size (n = 2000, tol 1e-8, EXACT)
+    against the dense eigendecomposition; the filtered iterate stays a small
+    fraction of n^2 (the unfiltered one fills to about a quarter)."""
+    a = w.tridiagonal()
+    d = a.to_dense()
+    ref = _sign_eig(d)
+    r = oracle_lib.nsf(a, tol=1e-8, filter="exact")
+    assert r.status == oracle_lib.OK and r.resid <= 1e-8
+    S = _dense(a.n, r.rowptr, r.col, r.val)
+    assert np.linalg.norm(S - ref) / np.linalg.norm(ref) < 1e-9
+    assert np.linalg.norm(S @ d - d @ S) / np.linalg.norm(d) < 1e-9
+    assert r.trace["nnz_x"].max() < 0.02 * a.n * a.n
+
+
 def test_spd_gives_identity(oracle_lib):
     a = w.spd_random(300, 0.01)
     r = oracle_lib.nsf(a, tol=1e-12, filter="exact")
