@@ -89,6 +89,10 @@ typedef struct {
   double div_limit;    /* residual above this = diverged; 1e6                */
   int dense64_min_n;   /* the FP64 stage's dense path (36 exact digit-pair
                           products per tile) only for n >= this; 1024      */
+  int fp32_band;       /* 1: FP32 products of groups of 16 narrow-band rows
+                          run as band tiles (dense register-blocked FMAs in
+                          ascending k; the same values bit for bit); 0: the
+                          row-wise kernels only; 1                        */
 } sign_opts;
 
 /* Per-iteration record, filled by sign_solve when non-NULL. The arrays are

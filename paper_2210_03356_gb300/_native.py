@@ -23,7 +23,7 @@ class sign_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("filter", C.c_int), ("c4", C.c_double),
                 ("switch_resid", C.c_double), ("max_iter", C.c_int), ("prec", C.c_int),
                 ("fp32_until", C.c_double), ("dense_frac", C.c_double), ("scale_1norm", C.c_int),
-                ("div_limit", C.c_double), ("dense64_min_n", C.c_int)]
+                ("div_limit", C.c_double), ("dense64_min_n", C.c_int), ("fp32_band", C.c_int)]
 
 
 class sign_info(C.Structure):

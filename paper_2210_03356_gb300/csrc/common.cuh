@@ -49,7 +49,7 @@ constexpr int K_BATCH = 256;  // k entries whose B-row ranges are located at onc
 enum KClass {
   KC_NUM_SQUARE_F64, KC_NUM_UPDATE_F64, KC_NUM_SQUARE_F32, KC_NUM_UPDATE_F32, KC_BOUNDS,
   KC_SCAN, KC_SEL_HIST, KC_SEL_EXTRACT, KC_SEL_DIGITS, KC_SELECT, KC_FILTER, KC_REDUCE,
-  KC_ASSEMBLE, KC_NORM, KC_DENSE, KC_DENSE64,
+  KC_ASSEMBLE, KC_NORM, KC_DENSE, KC_DENSE64, KC_BAND_LAYOUT, KC_BAND_SQUARE, KC_BAND_UPDATE,
   // host wall time of driver phases (synchronizations included)
   KH_SETUP, KH_CHECK, KH_DECIDE, KH_UPDATE, KH_FILTER, KH_REBUILD,
   // device time from the end of the work before a host synchronization to the

@@ -109,25 +109,63 @@ struct Rows {
   const int32_t *col;
 };
 
+// Row classes of the numeric kernels: groups of 32, 16 or 8 lanes per row,
+// one CTA per row, or band tiles of 16 rows (FP32 only; the list holds each
+// tile's first row).
+enum RowClass { RC_G32 = 0, RC_CTA = 1, RC_G16 = 2, RC_G8 = 3, RC_BAND = 4, RC_NONE = 5, RC_N = 5 };
+constexpr int RC_QUEUE = RC_N;        // counters[RC_QUEUE + c]: work-queue head of class c
+constexpr int RC_COUNTERS = 2 * RC_N;  // ints in the counters array
+
 // Per row i of C = A B (rows of inactive matrices are empty): the column
 // range [lo, lo+len) of the row (including A's own row in MODE_UPDATE), the
 // slot size ub[i] = min(len, work + (UPDATE ? nnz(A_i) : 0)) >= nnz(C_i), and
 // work[i] = sum_{k in A_i} nnz(B_k), the multiply-adds of the row. Non-empty
 // rows are listed, in row order within tiles, by the numeric kernel that takes
-// them: lists holds 4 lists of n entries (32-, 16- or 8-lane groups, or one
-// CTA per row); counters[0..3] are their lengths and counters[4..7] the
-// work-queue heads of the numeric kernels (all zeroed by the caller).
-// groups: 0 keeps every warp-sized row on 32 lanes; 1 (FP64 products, bound
-// by the FP64 pipe) picks 32, 16 or 8 lanes by lane utilisation; 2 (FP32
-// products) lists every row of extent <= 512 in the 16-lane class, whose FP32
-// kernel runs the rows two per warp with shared passes over B.
+// them: lists holds RC_N lists of n entries (32-, 16- or 8-lane groups, one
+// CTA per row, band tiles); counters[c] is the length of list c and
+// counters[RC_QUEUE + c] the work-queue head of its kernel (all zeroed by the
+// caller). groups: 0 keeps every warp-sized row on 32 lanes; 1 (FP64
+// products, bound by the FP64 pipe) picks 32, 16 or 8 lanes by lane
+// utilisation; 2 (FP32 products) lists every row of extent <= 512 in the
+// 16-lane class, whose FP32 kernel runs the rows two per warp with shared
+// passes over B. band (FP32 products only): aligned groups of 16 rows of one
+// matrix whose band tile costs fewer instructions than the row-wise product
+// (by the work estimate in k_bounds) go to the band list instead, and their
+// multiply-adds are added to *band_work (nullable; zeroed by the caller).
 // dslot (nullable, per matrix): matrices with dslot[m] >= 0 take the dense
 // path; their rows get no sparse work, and in MODE_UPDATE a whole row of
 // slots (moff gives the matrix sizes).
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
-                   int mode, int groups, const int *dslot, const int64_t *moff, int32_t *lo,
-                   int32_t *len, int64_t *ub, int32_t *lists, int *counters, double *work,
-                   cudaStream_t s);
+                   int mode, int groups, int band, const int *dslot, const int64_t *moff,
+                   int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists, int *counters,
+                   double *work, double *band_work, cudaStream_t s);
+
+// Band layout of the rows of an FP32 operand: row k's values dense over the
+// columns [fc[k], fc[k] + nf[k]) (fc and nf multiples of 4, holes +0) at
+// val[pos[k]], pos[k] a multiple of 4 (16-byte aligned rows); its pattern as
+// bit words of absolute column blocks, word w (columns 32w .. 32w + 31) at
+// mask[pos[k] / 2 + w - (fc[k] >> 5)] (nf/2 words per row always suffice).
+struct Band {
+  const int64_t *pos;
+  const int32_t *fc, *nf;
+  const float *val;
+  const unsigned *mask;
+};
+constexpr int BAND_JW = 64;   // widest output hull of a band tile, in 32-column words
+constexpr int BAND_KT = 320;  // widest k hull (A rows' columns) of a band tile
+// fc, nf and span[k] = nf[k] of each row (span is scanned into pos).
+void launch_band_spans(int64_t n, const Rows &R, int32_t *fc, int32_t *nf, int64_t *span,
+                       cudaStream_t s);
+// Scatters the rows into the band (val and mask zeroed by the caller).
+void launch_band_fill(int64_t n, const Rows &R, const float *val, const int64_t *pos,
+                      const int32_t *fc, float *bval, unsigned *bmask, cudaStream_t s);
+// The band tiles of an FP32 product (the RC_BAND list of k_bounds): C = A A
+// (SQUARE, with the partial sums of launch_numeric) or 1.5 A - 0.5 A B
+// (UPDATE), A's rows as CSR (its stored k) and both operands as bands.
+void launch_band_product(int64_t n, int mode, const Rows &A, const float *aval, const Band &bandA,
+                         const Band &bandB, const int32_t *lo, const int32_t *len,
+                         const int32_t *lists, int *counters, const int64_t *cs, int64_t *ce,
+                         int32_t *ccol, float *cval, double *part, cudaStream_t s);
 // Numeric product. Row i is written at cs[i] (exclusive scan of ub) and its
 // end stored in ce[i]. MODE_SQUARE: C = A A, and part[2i] = sum_j (C_ij -
 // delta_ij)^2, part[2i+1] = sum_k a_ik^2. MODE_UPDATE: C = 1.5 A - 0.5 A B.

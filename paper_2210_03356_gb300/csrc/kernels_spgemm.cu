@@ -88,11 +88,12 @@ __device__ __forceinline__ int64_t lower_bound(const int32_t *a, int64_t lo, int
   return lo;
 }
 
-// Row classes of the numeric kernels: groups of 32, 16 or 8 lanes per row
-// (rows whose column range fits the group's share of a warp's accumulator),
-// or one CTA per row.
-enum RowClass { RC_G32 = 0, RC_CTA = 1, RC_G16 = 2, RC_G8 = 3, RC_NONE = 4, RC_N = 4 };
 constexpr int BOUNDS_TILE = 256;  // rows per CTA of k_bounds; lists keep this order
+static_assert(BOUNDS_TILE % 16 == 0, "band tiles are aligned groups of 16 rows");
+// A 16-row group goes to a band tile when its multiply-adds are at least this
+// fraction of the tile's estimated FMA slots: the band kernel spends about 2.5
+// instructions per slot, the row-wise product tens per multiply-add.
+constexpr float BAND_MIN_EFF = 0.08f;
 
 // Row grouping of k_bounds: GROUPS_NONE keeps every row on 32 lanes.
 // GROUPS_THROUGHPUT (FP64 products, bound by the FP64 pipe) picks the group
@@ -108,16 +109,21 @@ __device__ __forceinline__ float lane_use(float avg, int g) {
   return avg / (rounds * float(g));
 }
 
-// counters: [RC_*] list lengths, [4 + RC_*] work-queue heads of the numeric kernels.
+// counters: [RC_*] list lengths, [RC_QUEUE + RC_*] work-queue heads of the numeric kernels.
 __global__ void __launch_bounds__(BOUNDS_TILE)
     k_bounds(int64_t n, const int64_t *ars, const int64_t *are, const int32_t *acol,
              const int64_t *brs, const int64_t *bre, const int32_t *bcol, const int32_t *seg,
-             const int *active, int mode, int groups, const int *dslot, const int64_t *moff,
-             int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists, int *counters,
-             double *work) {
+             const int *active, int mode, int groups, int band, const int *dslot,
+             const int64_t *moff, int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists,
+             int *counters, double *work, double *band_work) {
   __shared__ unsigned char s_cls[BOUNDS_TILE];
   __shared__ int s_cnt[BOUNDS_TILE / 32][RC_N];
   __shared__ int s_base[RC_N];
+  // per-row statistics of the band decision (rows of sparse work only)
+  __shared__ int s_seg[BOUNDS_TILE], s_lo[BOUNDS_TILE], s_L[BOUNDS_TILE];
+  __shared__ int s_kf[BOUNDS_TILE], s_kl[BOUNDS_TILE], s_na[BOUNDS_TILE];
+  __shared__ float s_wk[BOUNDS_TILE];
+  __shared__ unsigned char s_band[BOUNDS_TILE / 16];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = BOUNDS_TILE / 32;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t ntiles = (n + BOUNDS_TILE - 1) / BOUNDS_TILE;
@@ -126,6 +132,7 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
     for (int i = warp; i < BOUNDS_TILE; i += nw) {
       int64_t r = t0 + i;
       int cls = RC_NONE;
+      if (lane == 0) s_seg[i] = -1;  // not eligible for a band tile
       if (r < n) {
         const int m = seg[r];
         if (!active[m] || (dslot && dslot[m] >= 0)) {
@@ -139,11 +146,13 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
             work[r] = 0.0;
           }
         } else {
-          int32_t mn = INT_MAX, mx = -1;
+          int32_t mn = INT_MAX, mx = -1, kf = INT_MAX, kl = -1;
           int64_t wk = 0;
           int64_t a0 = ars[r], a1 = are[r];
           for (int64_t p = a0 + lane; p < a1; p += 32) {
             int32_t k = acol[p];
+            kf = min(kf, k);
+            kl = max(kl, k);
             int64_t b0 = brs[k], b1 = bre[k];
             wk += b1 - b0;
             if (b1 > b0) {
@@ -160,6 +169,10 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
             mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
             mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             wk += __shfl_xor_sync(0xffffffffu, wk, o);
+            if (band) {
+              kf = min(kf, __shfl_xor_sync(0xffffffffu, kf, o));
+              kl = max(kl, __shfl_xor_sync(0xffffffffu, kl, o));
+            }
           }
           if (mx < 0) {
             if (lane == 0) {
@@ -191,13 +204,56 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
               work[r] = double(wk);
             }
           }
+          if (band && lane == 0) {
+            s_seg[i] = m;
+            s_lo[i] = mx < 0 ? 0 : mn;
+            s_L[i] = mx < 0 ? 0 : mx - mn + 1;
+            s_kf[i] = kf;
+            s_kl[i] = kl;
+            s_na[i] = int(a1 - a0);
+            s_wk[i] = float(wk);
+          }
         }
       }
       if (lane == 0) s_cls[i] = (unsigned char)cls;
     }
     __syncthreads();
+    // band tiles: aligned groups of 16 rows of one matrix, all with sparse
+    // work, whose estimated FMA slots the multiply-adds fill well enough
+    if (band && threadIdx.x < BOUNDS_TILE / 16) {
+      const int b0 = threadIdx.x * 16;
+      bool ok = s_seg[b0] >= 0;
+      int jlo = INT_MAX, jhi = -1, klo = INT_MAX, khi = -1;
+      float wsum = 0.0f, nsum = 0.0f;
+      double wexact = 0.0;
+      for (int i = b0; i < b0 + 16 && ok; ++i) {
+        ok = s_seg[i] == s_seg[b0];
+        if (s_L[i] > 0) {
+          jlo = min(jlo, s_lo[i]);
+          jhi = max(jhi, s_lo[i] + s_L[i] - 1);
+        }
+        klo = min(klo, s_kf[i]);
+        khi = max(khi, s_kl[i]);
+        wsum += s_wk[i];
+        wexact += double(s_wk[i]);
+        nsum += float(s_na[i]);
+      }
+      if (ok && jhi >= 0 && khi >= 0) {
+        const int nwords = (jhi >> 5) - (jlo >> 5) + 1;
+        const float bavg = wsum / fmaxf(nsum, 1.0f);  // mean entries of a B row
+        const float kc = fminf(float(khi - klo + 1), bavg + 35.0f);
+        const float slots = 16.0f * 32.0f * float(nwords) * kc;
+        ok = nwords <= BAND_JW && khi - klo < BAND_KT - 3 && wsum >= BAND_MIN_EFF * slots;
+      } else {
+        ok = false;
+      }
+      s_band[threadIdx.x] = ok ? 1 : 0;
+      if (ok && band_work) atomicAdd(band_work, wexact);  // multiply-adds of the band tiles
+    }
+    __syncthreads();
     // ordered compaction of the tile's rows into one list per class
     int my = s_cls[threadIdx.x];
+    if (band && s_band[threadIdx.x >> 4]) my = (threadIdx.x & 15) == 0 ? RC_BAND : RC_NONE;
     unsigned bal[RC_N];
 #pragma unroll
     for (int c = 0; c < RC_N; ++c) {
@@ -468,7 +524,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, PAIR ? PAIR_OCC : WarpOcc<
   const int total = counters[cls];
   for (;;) {
     int base = 0;
-    if (lane == 0) base = atomicAdd(&counters[4 + cls], NG);
+    if (lane == 0) base = atomicAdd(&counters[RC_QUEUE + cls], NG);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= total) break;
     const int idx = base + g;
@@ -594,7 +650,7 @@ __global__ void __launch_bounds__(CTA_THREADS)
               const int32_t *lo, const int32_t *len, const int32_t *clist, int *counters,
               const int64_t *cs, int64_t *ce, int32_t *ccol, T *cval, double *part) {
   constexpr int CW = CtaW<T>::value;
-  // the CTA class uses counters[RC_CTA] (length) and counters[4 + RC_CTA] (queue head)
+  // the CTA class uses counters[RC_CTA] (length) and counters[RC_QUEUE + RC_CTA] (queue head)
   constexpr int NW = CTA_THREADS / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int64_t *ks = reinterpret_cast<int64_t *>(smem_raw);
@@ -607,7 +663,7 @@ __global__ void __launch_bounds__(CTA_THREADS)
   int lane = lane_id(), w = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   for (;;) {
-    if (threadIdx.x == 0) s_idx = atomicAdd(&counters[4 + RC_CTA], 1);
+    if (threadIdx.x == 0) s_idx = atomicAdd(&counters[RC_QUEUE + RC_CTA], 1);
     __syncthreads();
     int idx = s_idx;
     __syncthreads();
@@ -775,14 +831,15 @@ int grid_cap(int64_t items, int per_block, int per_sm) {
 }  // namespace
 
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
-                   int mode, int groups, const int *dslot, const int64_t *moff, int32_t *lo,
-                   int32_t *len, int64_t *ub, int32_t *lists, int *counters, double *work,
-                   cudaStream_t s) {
+                   int mode, int groups, int band, const int *dslot, const int64_t *moff,
+                   int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists, int *counters,
+                   double *work, double *band_work, cudaStream_t s) {
   if (n == 0) return;
   int tiles = int((n + BOUNDS_TILE - 1) / BOUNDS_TILE);
   int g = tiles < sm_count() * 8 ? tiles : sm_count() * 8;
   k_bounds<<<g, BOUNDS_TILE, 0, s>>>(n, A.rs, A.re, A.col, B.rs, B.re, B.col, seg, active, mode,
-                                     groups, dslot, moff, lo, len, ub, lists, counters, work);
+                                     groups, band, dslot, moff, lo, len, ub, lists, counters,
+                                     work, band_work);
   SGN_LAUNCH_CHECK();
 }
 

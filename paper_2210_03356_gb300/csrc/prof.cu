@@ -34,7 +34,8 @@ const char *kNames[KC_COUNT] = {"numeric_square_f64", "numeric_update_f64", "num
                                 "select_hist",        "select_extract",     "select_digits",
                                 "select_bound",       "filter",             "reduce",
                                 "assemble",           "onenorm",            "dense_tf32x3",
-                                "dense_f64_slices",
+                                "dense_f64_slices", "band_layout",
+                                "band_square_f32",    "band_update_f32",
                                 "host_setup",
                                 "host_check",         "host_decide",        "host_update",
                                 "host_filter",        "host_rebuild",       "host_sync_gap"};

@@ -28,6 +28,7 @@ bool valid_opts(const sign_opts *o, std::string &why) {
     return why = "c4, switch_resid must be >= 0 and fp32_until > 0", false;
   if (!(o->div_limit > 0.0)) return why = "div_limit must be > 0", false;
   if (o->dense64_min_n < 0) return why = "dense64_min_n < 0", false;
+  if (o->fp32_band < 0 || o->fp32_band > 1) return why = "fp32_band must be 0 or 1", false;
   return true;
 }
 
@@ -52,6 +53,7 @@ void sign_default_opts(sign_opts *o) {
   o->scale_1norm = 1;
   o->div_limit = 1e6;
   o->dense64_min_n = 1024;
+  o->fp32_band = 1;
 }
 
 const char *sign_last_error(void) { return g_err.c_str(); }

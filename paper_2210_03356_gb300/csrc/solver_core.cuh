@@ -157,11 +157,23 @@ Rows compact_rows(const Csr<T> &c) {
   return Rows{c.d_rp(), c.d_rp() + 1, c.d_col()};
 }
 
+// Band layout of one FP32 operand (see Band in kernels.h).
+struct BandBuf {
+  DevBuf fc, nf, span, pos, val, mask;
+  int64_t total = 0;   // floats of the band (pos[n])
+  bool filled = false;  // val and mask written for the current operand
+  Band view() const {
+    return Band{pos.as<int64_t>(), fc.as<int32_t>(), nf.as<int32_t>(), val.as<float>(),
+                mask.as<unsigned>()};
+  }
+};
+
 // Shared scratch of one solve call.
 struct Work {
   DevBuf lo, len, ub, wlist, clist, counters, part, scan_tmp, eoff, sums, ms, active, sel,
       asm_blocks, asm_off, asm_lens, dropped, norm_work, norm, work, mults, cnt, nnzc, xblocks,
       dslot, dmem, dbufs, djobs, dscratch, dcount, derr;
+  BandBuf bx, bt;  // bands of the iterate X and of T = X X (FP32 stage)
 };
 
 // The matrices of one round on the dense path (FP32 stage): their slots,
@@ -185,9 +197,11 @@ struct HostMirror {
   int64_t *ex = nullptr, *nnz_t = nullptr, *nnz_bar = nullptr, *tot = nullptr;
   double *mults = nullptr, *dsum = nullptr;
   ExtractBlock *xb = nullptr;
+  int *ctr = nullptr;  // the product's class counters
   void alloc(int nb) {
     size_t bytes = sizeof(MatScalars) * nb + sizeof(int64_t) * (4 * size_t(nb) + 8) +
-                   sizeof(double) * 2 * size_t(nb) + sizeof(ExtractBlock) * nb + 1024;
+                   sizeof(double) * 2 * size_t(nb) + sizeof(ExtractBlock) * nb +
+                   sizeof(int) * RC_COUNTERS + 1024;
     if (bytes > cap) {
       if (p) cudaFreeHost(p);
       p = nullptr;
@@ -208,6 +222,7 @@ struct HostMirror {
     mults = reinterpret_cast<double *>(take(sizeof(double) * nb));
     dsum = reinterpret_cast<double *>(take(sizeof(double) * nb));
     xb = reinterpret_cast<ExtractBlock *>(take(sizeof(ExtractBlock) * nb));
+    ctr = reinterpret_cast<int *>(take(sizeof(int) * RC_COUNTERS));
   }
   ~HostMirror() {
     if (p) cudaFreeHost(p);
@@ -336,6 +351,11 @@ struct Solver {
                          dst.d_col(), dst.val.p, is_f32<TD>(), s);
   }
 
+  // the band tiles' multiply-adds, a double after the class counters
+  double *band_work_dev() {
+    return reinterpret_cast<double *>(w.counters.as<char>() + sizeof(int) * RC_COUNTERS);
+  }
+
   // ---------------------------------------------------------------- product
   // C = A B for a stage. Enqueues everything; on return C is allocated and the
   // product queued, hm.mults holds the per-matrix multiply-adds (synced) and
@@ -349,22 +369,38 @@ struct Solver {
     w.lo.ensure(sizeof(int32_t) * size_t(N), s);
     w.len.ensure(sizeof(int32_t) * size_t(N), s);
     w.ub.ensure(sizeof(int64_t) * size_t(N), s);
-    w.wlist.ensure(sizeof(int32_t) * size_t(4 * N), s);
+    w.wlist.ensure(sizeof(int32_t) * size_t(RC_N) * size_t(N), s);
     w.work.ensure(sizeof(double) * size_t(N), s);
     w.mults.ensure(sizeof(double) * size_t(nb), s);
     w.nnzc.ensure(sizeof(int64_t) * size_t(nb), s);
-    w.counters.ensure(sizeof(int) * 8, s);
+    w.counters.ensure(sizeof(int) * RC_COUNTERS + sizeof(double), s);  // + band multiply-adds
     w.scan_tmp.ensure(sizeof(int64_t) * size_t(scan_tmp_elems(N)), s);
-    SGN_CUDA(cudaMemsetAsync(w.counters.p, 0, sizeof(int) * 8, s));
+    SGN_CUDA(cudaMemsetAsync(w.counters.p, 0, sizeof(int) * RC_COUNTERS + sizeof(double), s));
+    // band tiles (FP32): the band of B (X in SQUARE, T in UPDATE) is laid out
+    // here, its size read with the slot total below
+    const bool band = sizeof(T) == 4 && o.fp32_band;
+    BandBuf &bb = mode == MODE_SQUARE ? w.bx : w.bt;
     {
       ProfScope ps(KC_BOUNDS, s);
       launch_bounds(N, A, B, st.d_seg.template as<int32_t>(), active, mode, sizeof(T) == 8 ? 1 : 2,
-                    dp && dp->any() ? w.dslot.as<int>() : nullptr,
+                    band ? 1 : 0, dp && dp->any() ? w.dslot.as<int>() : nullptr,
                     st.d_moff.template as<int64_t>(), w.lo.as<int32_t>(),
                     w.len.as<int32_t>(), w.ub.as<int64_t>(), w.wlist.as<int32_t>(),
-                    w.counters.as<int>(), w.work.as<double>(), s);
+                    w.counters.as<int>(), w.work.as<double>(), band_work_dev(), s);
       launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.work.as<double>(), 1,
                         w.mults.as<double>(), s);
+      if (band) {
+        bb.filled = false;
+        bb.fc.ensure(sizeof(int32_t) * size_t(N), s);
+        bb.nf.ensure(sizeof(int32_t) * size_t(N), s);
+        bb.span.ensure(sizeof(int64_t) * size_t(N), s);
+        bb.pos.ensure(sizeof(int64_t) * size_t(N + 1), s);
+        launch_band_spans(N, B, bb.fc.as<int32_t>(), bb.nf.as<int32_t>(), bb.span.as<int64_t>(), s);
+        launch_scan(N, bb.span.as<int64_t>(), bb.pos.as<int64_t>(), w.scan_tmp.as<int64_t>(), s);
+        d2h(hm.tot + 1, bb.pos.as<int64_t>() + N, 1, s);
+        d2h(hm.ctr, w.counters.p, RC_COUNTERS, s);
+        d2h(hm.dsum, band_work_dev(), 1, s);
+      }
     }
     C.n = N;
     C.rs.ensure(sizeof(int64_t) * size_t(N + 1), s);
@@ -377,12 +413,35 @@ struct Solver {
     d2h(hm.mults, w.mults.p, size_t(nb), s);
     wait();
     int64_t slots = hm.tot[0];
+    const bool band_tiles = band && hm.ctr[RC_BAND] > 0;
+    if (band) bb.total = hm.tot[1];
+    if (band_tiles) {
+      // the bands of B and (UPDATE) of A = X, from the scan above and SQUARE's
+      auto fill = [&](BandBuf &b, const Rows &R, const T *v) {
+        if (b.filled) return;
+        b.val.ensure(sizeof(float) * size_t(b.total + 4), s);
+        b.mask.ensure(sizeof(unsigned) * size_t(b.total / 2 + 4), s);
+        SGN_CUDA(cudaMemsetAsync(b.val.p, 0, sizeof(float) * size_t(b.total + 4), s));
+        SGN_CUDA(cudaMemsetAsync(b.mask.p, 0, sizeof(unsigned) * size_t(b.total / 2 + 4), s));
+        launch_band_fill(N, R, reinterpret_cast<const float *>(v), b.pos.as<int64_t>(),
+                         b.fc.as<int32_t>(), b.val.as<float>(), b.mask.as<unsigned>(), s);
+        b.filled = true;
+      };
+      ProfScope ps(KC_BAND_LAYOUT, s, 0.0,
+                   double(nnzB) * 8.0 + double(bb.total) * 6.0 +
+                       (mode == MODE_UPDATE && !w.bx.filled ? double(nnzA) * 8.0 +
+                                                                  double(w.bx.total) * 6.0
+                                                            : 0.0));
+      fill(bb, B, bval);
+      if (mode == MODE_UPDATE) fill(w.bx, A, aval);
+    }
     C.slots = slots;
     C.col.ensure(sizeof(int32_t) * size_t(slots > 0 ? slots : 1), s);
     C.val.ensure(sizeof(T) * size_t(slots > 0 ? slots : 1), s);
     if (mode == MODE_SQUARE) w.part.ensure(sizeof(double) * size_t(2 * N), s);
     double fl = 0.0;
     for (int i = 0; i < nb; ++i) fl += 2.0 * hm.mults[i];
+    const double fl_band = band_tiles ? 2.0 * hm.dsum[0] : 0.0;  // the band tiles' share
     double per = 4.0 + sizeof(T);
     // algorithmic bytes: A and B read once, C written once (its size is known
     // after the launch; the slot total bounds it and is used here)
@@ -392,11 +451,21 @@ struct Solver {
     int cls = mode == MODE_SQUARE ? (sizeof(T) == 8 ? KC_NUM_SQUARE_F64 : KC_NUM_SQUARE_F32)
                                   : (sizeof(T) == 8 ? KC_NUM_UPDATE_F64 : KC_NUM_UPDATE_F32);
     {
-      ProfScope ps(cls, s, fl, by);
+      // bytes: the row-wise class keeps the whole product's algorithmic bytes
+      ProfScope ps(cls, s, fl - fl_band, by);
       launch_numeric<T>(N, A, aval, B, bval, mode, w.lo.as<int32_t>(), w.len.as<int32_t>(),
                         w.wlist.as<int32_t>(), w.counters.as<int>(), C.rs.template as<int64_t>(),
                         C.re.template as<int64_t>(), C.col.template as<int32_t>(), C.d_val(),
                         mode == MODE_SQUARE ? w.part.as<double>() : nullptr, s);
+    }
+    if (band_tiles) {
+      ProfScope ps(mode == MODE_SQUARE ? KC_BAND_SQUARE : KC_BAND_UPDATE, s, fl_band, 0.0);
+      launch_band_product(N, mode, A, reinterpret_cast<const float *>(aval), w.bx.view(), bb.view(),
+                          w.lo.as<int32_t>(), w.len.as<int32_t>(), w.wlist.as<int32_t>(),
+                          w.counters.as<int>(), C.rs.template as<int64_t>(),
+                          C.re.template as<int64_t>(), C.col.template as<int32_t>(),
+                          reinterpret_cast<float *>(C.val.p),
+                          mode == MODE_SQUARE ? w.part.as<double>() : nullptr, s);
     }
     if (dp && dp->any()) dense_step(st, mode, C, active, *dp);
     launch_seg_count(nb, st.d_moff.template as<int64_t>(), C.rs.template as<int64_t>(),
