@@ -131,14 +131,15 @@ constexpr int RC_COUNTERS = 2 * RC_N;  // ints in the counters array
 // passes over B. band (FP32 products only): aligned groups of 16 rows of one
 // matrix whose band tile costs fewer instructions than the row-wise product
 // (by the work estimate in k_bounds) go to the band list instead, and their
-// multiply-adds are added to *band_work (nullable; zeroed by the caller).
+// multiply-adds are added to *band_work (nullable; zeroed by the caller);
+// bandrow (nullable) gets 1 for the rows of band tiles, 0 for the others.
 // dslot (nullable, per matrix): matrices with dslot[m] >= 0 take the dense
 // path; their rows get no sparse work, and in MODE_UPDATE a whole row of
 // slots (moff gives the matrix sizes).
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
                    int mode, int groups, int band, const int *dslot, const int64_t *moff,
                    int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists, int *counters,
-                   double *work, double *band_work, cudaStream_t s);
+                   double *work, double *band_work, unsigned char *bandrow, cudaStream_t s);
 
 // Band layout of the rows of an FP32 operand: row k's values dense over the
 // columns [fc[k], fc[k] + nf[k]) (fc and nf multiples of 4, holes +0) at
@@ -151,21 +152,37 @@ struct Band {
   const float *val;
   const unsigned *mask;
 };
+// A band being written (the square T = X X of the band tiles, for the update).
+struct BandOut {
+  const int64_t *pos = nullptr;
+  const int32_t *fc = nullptr, *nf = nullptr;
+  float *val = nullptr;
+  unsigned *mask = nullptr;
+};
 constexpr int BAND_JW = 64;   // widest output hull of a band tile, in 32-column words
-constexpr int BAND_KT = 320;  // widest k hull (A rows' columns) of a band tile
+constexpr int BAND_KT = 312;  // widest k hull (A rows' columns) of a band tile
 // fc, nf and span[k] = nf[k] of each row (span is scanned into pos).
 void launch_band_spans(int64_t n, const Rows &R, int32_t *fc, int32_t *nf, int64_t *span,
                        cudaStream_t s);
-// Scatters the rows into the band (val and mask zeroed by the caller).
+// The same layout from a product's row column ranges [lo, lo + len) (the
+// first and last column of a product row are stored entries).
+void launch_band_spans_range(int64_t n, const int32_t *lo, const int32_t *len, int32_t *fc,
+                             int32_t *nf, int64_t *span, cudaStream_t s);
+// Writes the rows' bands (cleared first) from their CSR; rows with skip[r]
+// set (skip nullable) are left as they are.
 void launch_band_fill(int64_t n, const Rows &R, const float *val, const int64_t *pos,
-                      const int32_t *fc, float *bval, unsigned *bmask, cudaStream_t s);
+                      const int32_t *fc, const int32_t *nf, const unsigned char *skip, float *bval,
+                      unsigned *bmask, cudaStream_t s);
 // The band tiles of an FP32 product (the RC_BAND list of k_bounds): C = A A
 // (SQUARE, with the partial sums of launch_numeric) or 1.5 A - 0.5 A B
-// (UPDATE), A's rows as CSR (its stored k) and both operands as bands.
+// (UPDATE), A's rows as CSR (its stored k) and both operands as bands. In
+// SQUARE, bandC (val nullable) receives the band of the tiles' rows of C, laid
+// out by launch_band_spans_range.
 void launch_band_product(int64_t n, int mode, const Rows &A, const float *aval, const Band &bandA,
-                         const Band &bandB, const int32_t *lo, const int32_t *len,
-                         const int32_t *lists, int *counters, const int64_t *cs, int64_t *ce,
-                         int32_t *ccol, float *cval, double *part, cudaStream_t s);
+                         const Band &bandB, const BandOut &bandC, const int32_t *lo,
+                         const int32_t *len, const int32_t *lists, int *counters,
+                         const int64_t *cs, int64_t *ce, int32_t *ccol, float *cval, double *part,
+                         cudaStream_t s);
 // Numeric product. Row i is written at cs[i] (exclusive scan of ub) and its
 // end stored in ce[i]. MODE_SQUARE: C = A A, and part[2i] = sum_j (C_ij -
 // delta_ij)^2, part[2i+1] = sum_k a_ik^2. MODE_UPDATE: C = 1.5 A - 0.5 A B.

@@ -91,35 +91,62 @@ __global__ void k_band_spans(int64_t n, const int64_t *rs, const int64_t *re, co
   }
 }
 
-// One warp per row: values scattered into the zeroed band, pattern bits
-// OR-ed into the zeroed mask words (one atomic per run of a word's columns).
+// The band layout of the rows of a product from their column ranges
+// [lo, lo + len): the first and last column of a product row are stored
+// entries (each is the first or last column of some B_k), so this is the
+// layout k_band_spans gives for the finished rows.
+__global__ void k_band_spans_range(int64_t n, const int32_t *lo, const int32_t *len, int32_t *fc,
+                                   int32_t *nf, int64_t *span) {
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t L = len[r];
+    int32_t f = 0, w = 0;
+    if (L > 0) {
+      f = lo[r] & ~3;
+      w = ((lo[r] + L - 1 + 4) & ~3) - f;
+    }
+    fc[r] = f;
+    nf[r] = w;
+    span[r] = w;
+  }
+}
+
+// One warp per row (rows with skip[r] set are left alone): the row's band
+// and pattern words are cleared, then its values scattered and its pattern
+// bits OR-ed in (one atomic per run of a word's columns).
 __global__ void k_band_fill(int64_t n, const int64_t *rs, const int64_t *re, const int32_t *col,
-                            const float *val, const int64_t *pos, const int32_t *fc, float *bval,
+                            const float *val, const int64_t *pos, const int32_t *fc,
+                            const int32_t *nf, const unsigned char *skip, float *bval,
                             unsigned *bmask) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < n; r += nwarps) {
+    const int32_t w = nf[r];
+    if (w == 0 || (skip && skip[r])) continue;
     const int64_t a = rs[r], b = re[r];
-    if (b <= a) continue;
     const int64_t p0 = pos[r];
     const int32_t f = fc[r];
-    float *dv = bval + p0 - f;
+    float4 *z = reinterpret_cast<float4 *>(bval + p0);
+    for (int t = lane; t < w / 4; t += 32) z[t] = make_float4(0.f, 0.f, 0.f, 0.f);
     unsigned *dm = bmask + p0 / 2 - (f >> 5);
+    for (int x = (f >> 5) + lane; x <= (f + w - 1) >> 5; x += 32) dm[x] = 0u;
+    __syncwarp();
+    float *dv = bval + p0 - f;
     for (int64_t p = a; p < b; p += 32) {
       const bool ok = p + lane < b;
       int32_t c = ok ? col[p + lane] : INT_MAX;
       if (ok) dv[c] = val[p + lane];
-      int w = ok ? (c >> 5) : INT_MAX;
+      int wd = ok ? (c >> 5) : INT_MAX;
       unsigned bits = ok ? (1u << (c & 31)) : 0u;
       // suffix OR over the lanes holding the same word (columns ascend)
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
         unsigned ob = __shfl_down_sync(0xffffffffu, bits, d);
-        int ow = __shfl_down_sync(0xffffffffu, w, d);
-        if (lane + d < 32 && ow == w) bits |= ob;
+        int ow = __shfl_down_sync(0xffffffffu, wd, d);
+        if (lane + d < 32 && ow == wd) bits |= ob;
       }
-      int pw = __shfl_up_sync(0xffffffffu, w, 1);
-      if (ok && (lane == 0 || pw != w)) atomicOr(dm + w, bits);
+      int pw = __shfl_up_sync(0xffffffffu, wd, 1);
+      if (ok && (lane == 0 || pw != wd)) atomicOr(dm + wd, bits);
     }
   }
 }
@@ -148,6 +175,8 @@ struct BandSmem {
   int32_t kfc[BAND_KT + 4], kend[BAND_KT + 4];  // ... over columns [kfc[t], kend[t])
   int64_t aoff[16];                // band of A row r0 + i at A.val + aoff[i]
   int32_t afc[16], aend[16];
+  int64_t coff[16];                // (SQUARE) band of C row r0 + i being written
+  int32_t cfc[16], cend[16];
 };
 static_assert(sizeof(BandSmem) % 16 == 0, "per-warp areas stay 16-byte aligned");
 static_assert(BT_CTAS * (BT_WARPS * sizeof(BandSmem) + 1024) <= 228 * 1024, "CTAs per SM fit");
@@ -163,9 +192,9 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem, int src_
 template <int MODE>
 __global__ void __launch_bounds__(BT_WARPS * 32, BT_CTAS)
     k_band(const int64_t *ars, const int64_t *are, const int32_t *acol, const float *aval,
-           Band A, Band B, const int32_t *lo, const int32_t *len, const int32_t *list,
-           int *counters, int cls, const int64_t *cs, int64_t *ce, int32_t *ccol, float *cval,
-           double *part) {
+           Band A, Band B, BandOut Cb, const int32_t *lo, const int32_t *len,
+           const int32_t *list, int *counters, int cls, const int64_t *cs, int64_t *ce,
+           int32_t *ccol, float *cval, double *part) {
   extern __shared__ __align__(16) unsigned char band_smem[];
   BandSmem &sm = reinterpret_cast<BandSmem *>(band_smem)[threadIdx.x >> 5];
   constexpr unsigned FULL = 0xffffffffu;
@@ -211,6 +240,11 @@ __global__ void __launch_bounds__(BT_WARPS * 32, BT_CTAS)
       sm.afc[lane] = f;
       sm.aend[lane] = f + A.nf[r0 + lane];
       sm.aoff[lane] = A.pos[r0 + lane] - f;
+    } else if (MODE == MODE_SQUARE && Cb.val) {
+      const int32_t i = lane - 16, f = Cb.fc[r0 + i];
+      sm.cfc[i] = f;
+      sm.cend[i] = f + Cb.nf[r0 + i];
+      sm.coff[i] = Cb.pos[r0 + i] - f;
     }
     __syncwarp();
 
@@ -368,6 +402,23 @@ __global__ void __launch_bounds__(BT_WARPS * 32, BT_CTAS)
         if (e > f && wj >= (f >> 5) && wj <= (e - 1) >> 5)
           patw |= A.mask[(sm.aoff[hi] + f) / 2 + (wj - (f >> 5))];
       }
+      if (MODE == MODE_SQUARE && Cb.val) {
+        // the rows' band (values at every position of the band, +0 outside
+        // the pattern, where every product was zero) and pattern words
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int ri = rg * 4 + r;
+          const int j = j0 + cg * 4;
+          if (j >= sm.cfc[ri] && j < sm.cend[ri])
+            *reinterpret_cast<float4 *>(Cb.val + sm.coff[ri] + j) =
+                make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+        }
+        if (lane < 16) {
+          const int32_t f = sm.cfc[lane], e = sm.cend[lane], wj = j0 >> 5;
+          if (e > f && wj >= (f >> 5) && wj <= (e - 1) >> 5)
+            Cb.mask[(sm.coff[lane] + f) / 2 + (wj - (f >> 5))] = patw;
+        }
+      }
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int ri = rg * 4 + r;
@@ -452,19 +503,31 @@ void launch_band_spans(int64_t n, const Rows &R, int32_t *fc, int32_t *nf, int64
   SGN_LAUNCH_CHECK();
 }
 
+void launch_band_spans_range(int64_t n, const int32_t *lo, const int32_t *len, int32_t *fc,
+                             int32_t *nf, int64_t *span, cudaStream_t s) {
+  if (n == 0) return;
+  int64_t g = (n + 255) / 256;
+  if (g > int64_t(sm_count_band()) * 8) g = int64_t(sm_count_band()) * 8;
+  k_band_spans_range<<<unsigned(g), 256, 0, s>>>(n, lo, len, fc, nf, span);
+  SGN_LAUNCH_CHECK();
+}
+
 void launch_band_fill(int64_t n, const Rows &R, const float *val, const int64_t *pos,
-                      const int32_t *fc, float *bval, unsigned *bmask, cudaStream_t s) {
+                      const int32_t *fc, const int32_t *nf, const unsigned char *skip, float *bval,
+                      unsigned *bmask, cudaStream_t s) {
   if (n == 0) return;
   int64_t g = (n + 7) / 8;
   if (g > int64_t(sm_count_band()) * 16) g = int64_t(sm_count_band()) * 16;
-  k_band_fill<<<unsigned(g), 256, 0, s>>>(n, R.rs, R.re, R.col, val, pos, fc, bval, bmask);
+  k_band_fill<<<unsigned(g), 256, 0, s>>>(n, R.rs, R.re, R.col, val, pos, fc, nf, skip, bval,
+                                          bmask);
   SGN_LAUNCH_CHECK();
 }
 
 void launch_band_product(int64_t n, int mode, const Rows &A, const float *aval, const Band &bandA,
-                         const Band &bandB, const int32_t *lo, const int32_t *len,
-                         const int32_t *lists, int *counters, const int64_t *cs, int64_t *ce,
-                         int32_t *ccol, float *cval, double *part, cudaStream_t s) {
+                         const Band &bandB, const BandOut &bandC, const int32_t *lo,
+                         const int32_t *len, const int32_t *lists, int *counters,
+                         const int64_t *cs, int64_t *ce, int32_t *ccol, float *cval, double *part,
+                         cudaStream_t s) {
   if (n == 0) return;
   const int32_t *list = lists + int64_t(RC_BAND) * n;
   constexpr size_t smem = sizeof(BandSmem) * BT_WARPS;
@@ -478,13 +541,13 @@ void launch_band_product(int64_t n, int mode, const Rows &A, const float *aval, 
   (void)attr;
   const int g = sm_count_band() * BT_CTAS;
   if (mode == MODE_SQUARE)
-    k_band<MODE_SQUARE><<<g, BT_WARPS * 32, smem, s>>>(A.rs, A.re, A.col, aval, bandA, bandB, lo,
-                                                       len, list, counters, RC_BAND, cs, ce, ccol,
-                                                       cval, part);
+    k_band<MODE_SQUARE><<<g, BT_WARPS * 32, smem, s>>>(A.rs, A.re, A.col, aval, bandA, bandB,
+                                                       bandC, lo, len, list, counters, RC_BAND, cs,
+                                                       ce, ccol, cval, part);
   else
-    k_band<MODE_UPDATE><<<g, BT_WARPS * 32, smem, s>>>(A.rs, A.re, A.col, aval, bandA, bandB, lo,
-                                                       len, list, counters, RC_BAND, cs, ce, ccol,
-                                                       cval, part);
+    k_band<MODE_UPDATE><<<g, BT_WARPS * 32, smem, s>>>(A.rs, A.re, A.col, aval, bandA, bandB,
+                                                       BandOut{}, lo, len, list, counters, RC_BAND,
+                                                       cs, ce, ccol, cval, part);
   SGN_LAUNCH_CHECK();
 }
 

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
              const int64_t *brs, const int64_t *bre, const int32_t *bcol, const int32_t *seg,
              const int *active, int mode, int groups, int band, const int *dslot,
              const int64_t *moff, int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists,
-             int *counters, double *work, double *band_work) {
+             int *counters, double *work, double *band_work, unsigned char *bandrow) {
   __shared__ unsigned char s_cls[BOUNDS_TILE];
   __shared__ int s_cnt[BOUNDS_TILE / 32][RC_N];
   __shared__ int s_base[RC_N];
@@ -253,7 +253,9 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
     __syncthreads();
     // ordered compaction of the tile's rows into one list per class
     int my = s_cls[threadIdx.x];
-    if (band && s_band[threadIdx.x >> 4]) my = (threadIdx.x & 15) == 0 ? RC_BAND : RC_NONE;
+    const bool inband = band && s_band[threadIdx.x >> 4];
+    if (inband) my = (threadIdx.x & 15) == 0 ? RC_BAND : RC_NONE;
+    if (bandrow && t0 + threadIdx.x < n) bandrow[t0 + threadIdx.x] = inband ? 1 : 0;
     unsigned bal[RC_N];
 #pragma unroll
     for (int c = 0; c < RC_N; ++c) {
@@ -833,13 +835,13 @@ int grid_cap(int64_t items, int per_block, int per_sm) {
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
                    int mode, int groups, int band, const int *dslot, const int64_t *moff,
                    int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists, int *counters,
-                   double *work, double *band_work, cudaStream_t s) {
+                   double *work, double *band_work, unsigned char *bandrow, cudaStream_t s) {
   if (n == 0) return;
   int tiles = int((n + BOUNDS_TILE - 1) / BOUNDS_TILE);
   int g = tiles < sm_count() * 8 ? tiles : sm_count() * 8;
   k_bounds<<<g, BOUNDS_TILE, 0, s>>>(n, A.rs, A.re, A.col, B.rs, B.re, B.col, seg, active, mode,
                                      groups, band, dslot, moff, lo, len, ub, lists, counters,
-                                     work, band_work);
+                                     work, band_work, bandrow);
   SGN_LAUNCH_CHECK();
 }
 

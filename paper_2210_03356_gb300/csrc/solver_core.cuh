@@ -174,6 +174,8 @@ struct Work {
       asm_blocks, asm_off, asm_lens, dropped, norm_work, norm, work, mults, cnt, nnzc, xblocks,
       dslot, dmem, dbufs, djobs, dscratch, dcount, derr;
   BandBuf bx, bt;  // bands of the iterate X and of T = X X (FP32 stage)
+  DevBuf bandrow;  // rows of T written by the square's band tiles (1) or not (0)
+  bool bt_rows_done = false;  // the square's band tiles wrote their rows of T's band
 };
 
 // The matrices of one round on the dense path (FP32 stage): their slots,
@@ -376,28 +378,44 @@ struct Solver {
     w.counters.ensure(sizeof(int) * RC_COUNTERS + sizeof(double), s);  // + band multiply-adds
     w.scan_tmp.ensure(sizeof(int64_t) * size_t(scan_tmp_elems(N)), s);
     SGN_CUDA(cudaMemsetAsync(w.counters.p, 0, sizeof(int) * RC_COUNTERS + sizeof(double), s));
-    // band tiles (FP32): the band of B (X in SQUARE, T in UPDATE) is laid out
-    // here, its size read with the slot total below
+    // band tiles (FP32): in SQUARE the bands of X (both operands) and of T
+    // (the output, for the update) are laid out here, their sizes read with
+    // the slot total below; the band tiles write the rows of T's band they
+    // compute, and the update fills in the other rows of T it needs
     const bool band = sizeof(T) == 4 && o.fp32_band;
-    BandBuf &bb = mode == MODE_SQUARE ? w.bx : w.bt;
     {
       ProfScope ps(KC_BOUNDS, s);
+      if (band && mode == MODE_SQUARE) w.bandrow.ensure(size_t(N > 0 ? N : 1), s);
       launch_bounds(N, A, B, st.d_seg.template as<int32_t>(), active, mode, sizeof(T) == 8 ? 1 : 2,
                     band ? 1 : 0, dp && dp->any() ? w.dslot.as<int>() : nullptr,
                     st.d_moff.template as<int64_t>(), w.lo.as<int32_t>(),
                     w.len.as<int32_t>(), w.ub.as<int64_t>(), w.wlist.as<int32_t>(),
-                    w.counters.as<int>(), w.work.as<double>(), band_work_dev(), s);
+                    w.counters.as<int>(), w.work.as<double>(), band_work_dev(),
+                    band && mode == MODE_SQUARE ? w.bandrow.as<unsigned char>() : nullptr, s);
       launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.work.as<double>(), 1,
                         w.mults.as<double>(), s);
       if (band) {
-        bb.filled = false;
-        bb.fc.ensure(sizeof(int32_t) * size_t(N), s);
-        bb.nf.ensure(sizeof(int32_t) * size_t(N), s);
-        bb.span.ensure(sizeof(int64_t) * size_t(N), s);
-        bb.pos.ensure(sizeof(int64_t) * size_t(N + 1), s);
-        launch_band_spans(N, B, bb.fc.as<int32_t>(), bb.nf.as<int32_t>(), bb.span.as<int64_t>(), s);
-        launch_scan(N, bb.span.as<int64_t>(), bb.pos.as<int64_t>(), w.scan_tmp.as<int64_t>(), s);
-        d2h(hm.tot + 1, bb.pos.as<int64_t>() + N, 1, s);
+        if (mode == MODE_SQUARE) {
+          for (BandBuf *b : {&w.bx, &w.bt}) {
+            b->filled = false;
+            b->fc.ensure(sizeof(int32_t) * size_t(N), s);
+            b->nf.ensure(sizeof(int32_t) * size_t(N), s);
+            b->span.ensure(sizeof(int64_t) * size_t(N), s);
+            b->pos.ensure(sizeof(int64_t) * size_t(N + 1), s);
+          }
+          w.bt_rows_done = false;
+          launch_band_spans(N, B, w.bx.fc.as<int32_t>(), w.bx.nf.as<int32_t>(),
+                            w.bx.span.as<int64_t>(), s);
+          launch_scan(N, w.bx.span.as<int64_t>(), w.bx.pos.as<int64_t>(),
+                      w.scan_tmp.as<int64_t>(), s);
+          launch_band_spans_range(N, w.lo.as<int32_t>(), w.len.as<int32_t>(),
+                                  w.bt.fc.as<int32_t>(), w.bt.nf.as<int32_t>(),
+                                  w.bt.span.as<int64_t>(), s);
+          launch_scan(N, w.bt.span.as<int64_t>(), w.bt.pos.as<int64_t>(),
+                      w.scan_tmp.as<int64_t>(), s);
+          d2h(hm.tot + 1, w.bx.pos.as<int64_t>() + N, 1, s);
+          d2h(hm.tot + 2, w.bt.pos.as<int64_t>() + N, 1, s);
+        }
         d2h(hm.ctr, w.counters.p, RC_COUNTERS, s);
         d2h(hm.dsum, band_work_dev(), 1, s);
       }
@@ -414,26 +432,36 @@ struct Solver {
     wait();
     int64_t slots = hm.tot[0];
     const bool band_tiles = band && hm.ctr[RC_BAND] > 0;
-    if (band) bb.total = hm.tot[1];
+    if (band && mode == MODE_SQUARE) {
+      w.bx.total = hm.tot[1];
+      w.bt.total = hm.tot[2];
+    }
     if (band_tiles) {
-      // the bands of B and (UPDATE) of A = X, from the scan above and SQUARE's
-      auto fill = [&](BandBuf &b, const Rows &R, const T *v) {
-        if (b.filled) return;
+      auto alloc = [&](BandBuf &b) {
         b.val.ensure(sizeof(float) * size_t(b.total + 4), s);
         b.mask.ensure(sizeof(unsigned) * size_t(b.total / 2 + 4), s);
-        SGN_CUDA(cudaMemsetAsync(b.val.p, 0, sizeof(float) * size_t(b.total + 4), s));
-        SGN_CUDA(cudaMemsetAsync(b.mask.p, 0, sizeof(unsigned) * size_t(b.total / 2 + 4), s));
+      };
+      // fills a band from its CSR rows (skipping the rows the band tiles wrote)
+      auto fill = [&](BandBuf &b, const Rows &R, const T *v, const unsigned char *skip) {
+        if (b.filled) return;
+        alloc(b);
         launch_band_fill(N, R, reinterpret_cast<const float *>(v), b.pos.as<int64_t>(),
-                         b.fc.as<int32_t>(), b.val.as<float>(), b.mask.as<unsigned>(), s);
+                         b.fc.as<int32_t>(), b.nf.as<int32_t>(), skip, b.val.as<float>(),
+                         b.mask.as<unsigned>(), s);
         b.filled = true;
       };
       ProfScope ps(KC_BAND_LAYOUT, s, 0.0,
-                   double(nnzB) * 8.0 + double(bb.total) * 6.0 +
-                       (mode == MODE_UPDATE && !w.bx.filled ? double(nnzA) * 8.0 +
-                                                                  double(w.bx.total) * 6.0
-                                                            : 0.0));
-      fill(bb, B, bval);
-      if (mode == MODE_UPDATE) fill(w.bx, A, aval);
+                   mode == MODE_SQUARE || !w.bt.filled
+                       ? double(nnzB) * 8.0 + double(mode == MODE_SQUARE ? w.bx.total
+                                                                         : w.bt.total) * 6.0
+                       : 0.0);
+      if (mode == MODE_SQUARE) {
+        fill(w.bx, B, bval, nullptr);  // B = A = X
+        alloc(w.bt);                    // written by the band tiles below
+      } else {
+        fill(w.bx, A, aval, nullptr);
+        fill(w.bt, B, bval, w.bt_rows_done ? w.bandrow.as<unsigned char>() : nullptr);
+      }
     }
     C.slots = slots;
     C.col.ensure(sizeof(int32_t) * size_t(slots > 0 ? slots : 1), s);
@@ -460,7 +488,14 @@ struct Solver {
     }
     if (band_tiles) {
       ProfScope ps(mode == MODE_SQUARE ? KC_BAND_SQUARE : KC_BAND_UPDATE, s, fl_band, 0.0);
-      launch_band_product(N, mode, A, reinterpret_cast<const float *>(aval), w.bx.view(), bb.view(),
+      BandOut tout;
+      if (mode == MODE_SQUARE) {
+        tout = BandOut{w.bt.pos.as<int64_t>(), w.bt.fc.as<int32_t>(), w.bt.nf.as<int32_t>(),
+                       w.bt.val.as<float>(), w.bt.mask.as<unsigned>()};
+        w.bt_rows_done = true;  // the rows of bandrow; the update fills the rest
+      }
+      launch_band_product(N, mode, A, reinterpret_cast<const float *>(aval), w.bx.view(),
+                          mode == MODE_SQUARE ? w.bx.view() : w.bt.view(), tout,
                           w.lo.as<int32_t>(), w.len.as<int32_t>(), w.wlist.as<int32_t>(),
                           w.counters.as<int>(), C.rs.template as<int64_t>(),
                           C.re.template as<int64_t>(), C.col.template as<int32_t>(),
