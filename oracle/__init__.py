@@ -37,7 +37,8 @@ def build(force: bool = False) -> str:
 class _Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("filter", C.c_int), ("c4", C.c_double),
                 ("switch_resid", C.c_double), ("max_iter", C.c_int), ("mixed", C.c_int),
-                ("fp32_until", C.c_double), ("scale_1norm", C.c_int), ("div_limit", C.c_double)]
+                ("fp32_until", C.c_double), ("scale_1norm", C.c_int), ("div_limit", C.c_double),
+                ("filter_t", C.c_int), ("budget_norm", C.c_int)]
 
 
 class _Trace(C.Structure):
@@ -46,7 +47,7 @@ class _Trace(C.Structure):
                 ("resid", C.POINTER(C.c_double)), ("xnorm", C.POINTER(C.c_double)),
                 ("beta", C.POINTER(C.c_double)), ("tau", C.POINTER(C.c_double)),
                 ("fnorm", C.POINTER(C.c_double)), ("nnz_bar", C.POINTER(C.c_int64)),
-                ("prec", C.POINTER(C.c_int))]
+                ("prec", C.POINTER(C.c_int)), ("nnz_that", C.POINTER(C.c_int64))]
 
 
 _lib = None
@@ -83,6 +84,8 @@ def lib():
         L.oracle_nmf.argtypes = L.oracle_nsf.argtypes
         L.oracle_nm_dense.argtypes = [C.c_int64, _PD, C.c_double, C.c_int, _PD,
                                       C.POINTER(C.c_int), _PD]
+        L.oracle_norm2_est.restype = C.c_double
+        L.oracle_norm2_est.argtypes = [C.c_int64, _P64, _P32, _PD, C.c_int]
         _lib = L
     return _lib
 
@@ -193,21 +196,36 @@ class Result:
         return d
 
 
-def nsf(a, tol=1e-8, filter="exact", c4=1e-4, switch_resid=1e-6, max_iter=100, mixed=False,
-        fp32_until=1e-4, scale_1norm=True, div_limit=1e6, trace_cap=256) -> Result:
-    """Runs the oracle's NSF (filter='none' is plain Newton-Schulz) on a CSR input."""
-    n = a.n
-    rowptr, col, val = _csr_args(a.rowptr, a.col, a.val)
-    o = _Opts(tol, _FILTERS[filter], c4, switch_resid, max_iter, int(mixed), fp32_until,
-              int(scale_1norm), div_limit)
+def _trace(trace_cap):
     arrs = {k: np.zeros(trace_cap, dtype=t) for k, t in
             [("nnz_x", np.int64), ("nnz_t", np.int64), ("resid", np.float64),
              ("xnorm", np.float64), ("beta", np.float64), ("tau", np.float64),
-             ("fnorm", np.float64), ("nnz_bar", np.int64), ("prec", np.int32)]}
+             ("fnorm", np.float64), ("nnz_bar", np.int64), ("prec", np.int32),
+             ("nnz_that", np.int64)]}
     tr = _Trace(trace_cap, 0, _p(arrs["nnz_x"], _P64), _p(arrs["nnz_t"], _P64),
                 _p(arrs["resid"], _PD), _p(arrs["xnorm"], _PD), _p(arrs["beta"], _PD),
                 _p(arrs["tau"], _PD), _p(arrs["fnorm"], _PD), _p(arrs["nnz_bar"], _P64),
-                _p(arrs["prec"], C.POINTER(C.c_int)))
+                _p(arrs["prec"], C.POINTER(C.c_int)), _p(arrs["nnz_that"], _P64))
+    return arrs, tr
+
+
+def norm2_est(n, rowptr, col, val, steps=8) -> float:
+    """The oracle's power-iteration estimate of ||X||_2 (budget_norm variant)."""
+    rowptr, col, val = _csr_args(rowptr, col, val)
+    return lib().oracle_norm2_est(n, _p(rowptr, _P64), _p(col, _P32), _p(val, _PD), steps)
+
+
+def nsf(a, tol=1e-8, filter="exact", c4=1e-4, switch_resid=1e-6, max_iter=100, mixed=False,
+        fp32_until=1e-4, scale_1norm=True, div_limit=1e6, trace_cap=256, filter_t=False,
+        budget_norm="rms") -> Result:
+    """Runs the oracle's NSF (filter='none' is plain Newton-Schulz) on a CSR input.
+    Variants: filter_t=True filters T = X^2 with the same budget before the
+    update; budget_norm='2' takes ||X||_2 (power iteration) in Eq. (1.18)."""
+    n = a.n
+    rowptr, col, val = _csr_args(a.rowptr, a.col, a.val)
+    o = _Opts(tol, _FILTERS[filter], c4, switch_resid, max_iter, int(mixed), fp32_until,
+              int(scale_1norm), div_limit, int(bool(filter_t)), int(budget_norm == "2"))
+    arrs, tr = _trace(trace_cap)
     it, r = C.c_int(), C.c_double()
     rp, cp, vp = _P64(), _P32(), _PD()
     rc = lib().oracle_nsf(n, _p(rowptr, _P64), _p(col, _P32), _p(val, _PD), C.byref(o),
@@ -243,15 +261,8 @@ def nmf(a, tol=1e-12, filter="exact", c4=1e-4, switch_resid=1e-6, max_iter=100, 
     CSR input: X1 = A, dense inverse, filter budget c4*tol, then Eq. (1.13)."""
     n = a.n
     rowptr, col, val = _csr_args(a.rowptr, a.col, a.val)
-    o = _Opts(tol, _FILTERS[filter], c4, switch_resid, max_iter, 0, 0.0, 0, div_limit)
-    arrs = {k: np.zeros(trace_cap, dtype=t) for k, t in
-            [("nnz_x", np.int64), ("nnz_t", np.int64), ("resid", np.float64),
-             ("xnorm", np.float64), ("beta", np.float64), ("tau", np.float64),
-             ("fnorm", np.float64), ("nnz_bar", np.int64), ("prec", np.int32)]}
-    tr = _Trace(trace_cap, 0, _p(arrs["nnz_x"], _P64), _p(arrs["nnz_t"], _P64),
-                _p(arrs["resid"], _PD), _p(arrs["xnorm"], _PD), _p(arrs["beta"], _PD),
-                _p(arrs["tau"], _PD), _p(arrs["fnorm"], _PD), _p(arrs["nnz_bar"], _P64),
-                _p(arrs["prec"], C.POINTER(C.c_int)))
+    o = _Opts(tol, _FILTERS[filter], c4, switch_resid, max_iter, 0, 0.0, 0, div_limit, 0, 0)
+    arrs, tr = _trace(trace_cap)
     it, r = C.c_int(), C.c_double()
     rp, cp, vp = _P64(), _P32(), _PD()
     rc = lib().oracle_nmf(n, _p(rowptr, _P64), _p(col, _P32), _p(val, _PD), C.byref(o),

@@ -425,6 +425,50 @@ static int filter_f32(int64_t n, const int64_t *rp, const int32_t *col, const fl
 }
 
 /* ---------------------------------------------------------------------- */
+/* 2-norm estimate (the budget_norm variant of the reading of ||.||)        */
+/* ---------------------------------------------------------------------- */
+double oracle_norm2_est(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                        int steps) {
+  double *v = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *y = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  long double *z = (long double *)malloc(sizeof(long double) * (size_t)(n > 0 ? n : 1));
+  double out = NAN;
+  if (!v || !y || !z || n <= 0) goto done;
+  for (int64_t i = 0; i < n; ++i) v[i] = 1.0 / sqrt((double)n);
+  for (int s = 0; s <= steps; ++s) {
+    for (int64_t i = 0; i < n; ++i) { /* y = X v */
+      long double a = 0.0L;
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) a += (long double)val[p] * v[col[p]];
+      y[i] = (double)a;
+    }
+    if (s == steps) { /* ||X v|| of the last v */
+      long double a = 0.0L;
+      for (int64_t i = 0; i < n; ++i) a += (long double)y[i] * y[i];
+      out = sqrt((double)a);
+      break;
+    }
+    for (int64_t j = 0; j < n; ++j) z[j] = 0.0L; /* z = X^T y */
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) z[col[p]] += (long double)val[p] * y[i];
+    long double a = 0.0L;
+    for (int64_t j = 0; j < n; ++j) a += z[j] * z[j];
+    double nz = sqrt((double)a);
+    if (!(nz > 0.0)) { /* X v = 0 or X^T y = 0: the estimate so far is the norm */
+      long double b = 0.0L;
+      for (int64_t i = 0; i < n; ++i) b += (long double)y[i] * y[i];
+      out = sqrt((double)b);
+      break;
+    }
+    for (int64_t j = 0; j < n; ++j) v[j] = (double)(z[j] / nz);
+  }
+done:
+  free(v);
+  free(y);
+  free(z);
+  return out;
+}
+
+/* ---------------------------------------------------------------------- */
 /* budget, Eq. (1.18) and the fixed phase of Sec. 3.2 / Sec. 4              */
 /* ---------------------------------------------------------------------- */
 /* r = ||R_k|| of the iterate being updated, x = ||X_k||; both RMS. The
@@ -442,6 +486,7 @@ static void trace_put(oracle_trace *tr, int64_t nnz_x, int64_t nnz_t, double r, 
   int k = tr->count++;
   tr->nnz_x[k] = nnz_x;
   tr->nnz_t[k] = nnz_t;
+  if (tr->nnz_that) tr->nnz_that[k] = nnz_t;
   tr->resid[k] = r;
   tr->xnorm[k] = x;
   tr->beta[k] = 0.0;
@@ -449,6 +494,11 @@ static void trace_put(oracle_trace *tr, int64_t nnz_x, int64_t nnz_t, double r, 
   tr->fnorm[k] = 0.0;
   tr->nnz_bar[k] = 0;
   tr->prec[k] = prec;
+}
+
+static void trace_that(oracle_trace *tr, int64_t nnz_that) {
+  if (!tr || tr->count == 0 || tr->count > tr->cap || !tr->nnz_that) return;
+  tr->nnz_that[tr->count - 1] = nnz_that;
 }
 
 static void trace_filter(oracle_trace *tr, double beta, double tau, double fnorm, int64_t nnz_bar) {
@@ -526,7 +576,33 @@ int oracle_nsf(int64_t n, const int64_t *rowptr, const int32_t *col, const doubl
         status = OR_ENOTCONV;
         break;
       }
-      double beta = oracle_budget(r, x, o->c4, o->fp32_until, o->switch_resid);
+      double xb = x;
+      if (o->budget_norm && r < o->switch_resid) { /* the 2-norm of the widened iterate */
+        double *xw = (double *)malloc(sizeof(double) * (size_t)(xrp[n] > 0 ? xrp[n] : 1));
+        if (!xw) {
+          free(trp); free(tcol); free(tval);
+          goto nomem;
+        }
+        for (int64_t p = 0; p < xrp[n]; ++p) xw[p] = (double)xf[p];
+        xb = oracle_norm2_est(n, xrp, xcol, xw, ORACLE_POW_STEPS);
+        free(xw);
+      }
+      double beta = oracle_budget(r, xb, o->c4, o->fp32_until, o->switch_resid);
+      if (o->filter_t && o->filter != OR_FILTER_NONE) {
+        /* variant: T filtered with the same budget before the update */
+        int64_t *frp;
+        int32_t *fcol;
+        float *fval;
+        double ttau = 0.0, tfn = 0.0;
+        int rt = filter_f32(n, trp, tcol, tval, o->filter, sqrt((double)n) * beta, &frp, &fcol,
+                            &fval, &ttau, &tfn);
+        free(trp); free(tcol); free(tval);
+        if (rt) goto nomem;
+        trp = frp;
+        tcol = fcol;
+        tval = fval;
+        trace_that(tr, trp[n]);
+      }
       int64_t *brp;
       int32_t *bcol;
       float *bval;
@@ -571,7 +647,25 @@ int oracle_nsf(int64_t n, const int64_t *rowptr, const int32_t *col, const doubl
         status = OR_ENOTCONV;
         break;
       }
-      double beta = oracle_budget(r, x, o->c4, o->tol, o->switch_resid);
+      double xb = x;
+      if (o->budget_norm && r < o->switch_resid)
+        xb = oracle_norm2_est(n, xrp, xcol, xval, ORACLE_POW_STEPS);
+      double beta = oracle_budget(r, xb, o->c4, o->tol, o->switch_resid);
+      if (o->filter_t && o->filter != OR_FILTER_NONE) {
+        /* variant: T filtered with the same budget before the update */
+        int64_t *frp;
+        int32_t *fcol;
+        double *fval;
+        double ttau = 0.0, tfn = 0.0;
+        int rt = oracle_filter(n, trp, tcol, tval, o->filter, sqrt((double)n) * beta, &frp, &fcol,
+                               &fval, &ttau, &tfn);
+        free(trp); free(tcol); free(tval);
+        if (rt) goto nomem;
+        trp = frp;
+        tcol = fcol;
+        tval = fval;
+        trace_that(tr, trp[n]);
+      }
       int64_t *brp;
       int32_t *bcol;
       double *bval;

@@ -31,7 +31,15 @@ typedef struct {
   double fp32_until;   /* 1e-4                                               */
   int scale_1norm;     /* 1: X0 = A / ||A||_1, 0: X0 = A                     */
   double div_limit;    /* residual above this (or non-finite) = diverged     */
+  int filter_t;        /* variant: 1 = T = X^2 filtered too, with the same
+                          budget, before the update uses it                  */
+  int budget_norm;     /* variant: 1 = x in Eq. (1.18) is the 2-norm of X,
+                          estimated by ORACLE_POW_STEPS power steps on X^T X;
+                          0 = RMS Frobenius (the default reading)            */
 } oracle_opts;
+
+/* Power steps of the 2-norm estimate (budget_norm = 1). */
+#define ORACLE_POW_STEPS 8
 
 /* Per-iteration record. Arrays are caller-owned with `cap` slots; entry k
  * describes the check of iterate X_k (k = 0 is X0) and, when an update
@@ -47,6 +55,7 @@ typedef struct {
   double *fnorm;    /* ||F_{k+1}||_F, the dropped part            */
   int64_t *nnz_bar; /* nnz of Xbar_{k+1} before filtering         */
   int *prec;        /* 32 or 64: precision of iterate k           */
+  int64_t *nnz_that; /* nnz of T after its filter (filter_t; else nnz_t); nullable */
 } oracle_trace;
 
 typedef struct {
@@ -85,6 +94,12 @@ int oracle_ns_update(int64_t n, const int64_t *xrp, const int32_t *xcol, const d
 int oracle_filter(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
                   int mode, double b, int64_t **orp, int32_t **ocol, double **oval,
                   double *tau, double *fnorm);
+
+/* 2-norm estimate of X: v_0 = (1, ..., 1)/sqrt(n), then `steps` times
+ * v <- X^T X v / ||X^T X v||, and ||X v|| of the last v (long double sums).
+ * A lower bound of ||X||_2 that converges to it as steps grow. */
+double oracle_norm2_est(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                        int steps);
 
 /* Budget (RMS) for the next filter: c4*tol_stage in the fixed phase, else
  * Eq. (1.18) as 3/4 r^2 / (3x + x^3). */

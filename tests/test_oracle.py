@@ -575,3 +575,79 @@ def test_edge_cases(oracle_lib):
     sing = w.csr_from_dense(np.diag([1.0, 0.0, -2.0]))
     r = oracle_lib.nsf(sing, tol=1e-12, max_iter=30)
     assert r.status == oracle_lib.ENOTCONV and r.iters == 30
+
+
+# --------------------------------------------------------------------------
+# variants of the readings (NEXT: filtered T, 2-norm budget)
+# --------------------------------------------------------------------------
+def test_norm2_estimate_converges_to_the_spectral_norm(oracle_lib):
+    """The power iteration on X^T X from (1,...,1)/sqrt(n): exact on a diagonal
+    matrix, a lower bound that converges to sigma_max on a random matrix with
+    a gap, and non-decreasing in the number of steps."""
+    d = np.diag([3.0, -1.0, 0.5, 0.2] + [0.1] * 20)
+    a = w.csr_from_dense(d)
+    assert abs(oracle_lib.norm2_est(a.n, a.rowptr, a.col, a.val, 8) - 3.0) < 1e-12
+    rng = np.random.default_rng(1)
+    U, _ = np.linalg.qr(rng.standard_normal((30, 30)))
+    V, _ = np.linalg.qr(rng.standard_normal((30, 30)))
+    s = np.r_[10.0, np.linspace(6.0, 0.1, 29)]
+    M = (U * s) @ V.T
+    b = w.csr_from_dense(M)
+    est = [oracle_lib.norm2_est(b.n, b.rowptr, b.col, b.val, k) for k in (1, 2, 4, 8, 16)]
+    assert all(e <= 10.0 * (1 + 1e-14) for e in est)
+    assert all(e2 >= e1 - 1e-12 for e1, e2 in zip(est, est[1:]))
+    assert abs(est[-1] - 10.0) < 1e-6
+
+
+def test_filtered_t_variant_steps_and_theorem_3_2_1(oracle_lib):
+    """filter_t: each update multiplies by T filtered with the iterate's own
+    budget (checked step by step against the oracle's primitives), and the
+    run still satisfies Thm 3.2.1 and stays within 10 tol of plain NS."""
+    a = w.banded(300, 4, w.BASE_SEED + 61)
+    n = a.n
+    tol = 1e-12
+    run = oracle_lib.nsf(a, tol=tol, filter="exact", filter_t=True)
+    assert run.status == oracle_lib.OK
+    tr = run.trace
+    assert np.any(tr["nnz_that"][:run.iters] < tr["nnz_t"][:run.iters])  # T really was filtered
+    for k in (1, 3):
+        xk = oracle_lib.nsf(a, tol=tol, filter="exact", filter_t=True, max_iter=k)
+        x1 = oracle_lib.nsf(a, tol=tol, filter="exact", filter_t=True, max_iter=k + 1)
+        X = (xk.rowptr, xk.col, xk.val)
+        T = oracle_lib.spgemm(n, X, X)
+        b = math.sqrt(n) * tr["beta"][k]
+        Th, _, _ = oracle_lib.filter_csr(n, T, "exact", b)
+        assert Th[0][-1] == tr["nnz_that"][k]
+        Xb = oracle_lib.ns_update(n, X, Th)
+        Xn, _, _ = oracle_lib.filter_csr(n, Xb, "exact", b)
+        assert np.array_equal(Xn[1], x1.col) and np.array_equal(Xn[2], x1.val)
+    for k in range(run.iters + 1):
+        r1 = oracle_lib.nsf(a, tol=tol, filter="exact", filter_t=True, max_iter=k)
+        r0 = oracle_lib.nsf(a, tol=0.0, filter="none", max_iter=r1.iters)
+        X0, X1 = r0.to_dense(n), r1.to_dense(n)
+        R0, R1 = np.eye(n) - X0 @ X0, np.eye(n) - X1 @ X1
+        assert np.linalg.norm(R1 - R0) <= 3 * np.linalg.norm(R0) + 1e-13
+        assert np.linalg.norm(X1 - X0) / math.sqrt(n) <= 10 * tol
+    S = run.to_dense(n)
+    assert np.linalg.norm(S - _sign_eig(a.to_dense())) / np.linalg.norm(S) < 1e-10
+
+
+def test_budget_norm_variant_uses_the_spectral_estimate(oracle_lib):
+    """budget_norm='2': in the adaptive phase beta = 3/4 r^2 / (3 x + x^3) with
+    x the power-iteration estimate of ||X_k||_2 (within 1e-6 of numpy's 2-norm
+    here); the converged sign matches the eigendecomposition."""
+    a = w.tridiagonal(500)
+    n = a.n
+    run = oracle_lib.nsf(a, tol=1e-13, filter="exact", budget_norm="2")
+    assert run.status == oracle_lib.OK
+    tr = run.trace
+    adaptive = [k for k in range(run.iters) if tr["resid"][k] < 1e-6]
+    assert adaptive
+    for k in adaptive:
+        xk = oracle_lib.nsf(a, tol=1e-13, filter="exact", budget_norm="2", max_iter=k)
+        x2 = oracle_lib.norm2_est(n, xk.rowptr, xk.col, xk.val, 8)
+        assert abs(x2 - np.linalg.norm(xk.to_dense(n), 2)) < 1e-6
+        r = tr["resid"][k]
+        assert tr["beta"][k] == 0.75 * r * r / (3.0 * x2 + x2 * x2 * x2)
+    S = run.to_dense(n)
+    assert np.linalg.norm(S - _sign_eig(a.to_dense())) / np.linalg.norm(S) < 1e-10
