@@ -492,6 +492,62 @@ def fma_peak_leg(sg, gpu_index: int, seconds: float = 1.0):
     return out
 
 
+# ---------------------------------------------------------------------- variants
+VARIANTS = (("default", {}), ("filter_t", {"filter_t": 1}), ("budget_norm_2", {"budget_norm": 1}),
+            ("both", {"filter_t": 1, "budget_norm": 1}))
+
+
+def variants_leg(sg, mats, reps: int = 2):
+    """The two variants of the readings against the default, on the banded
+    batch: T filtered with the same budget (filter_t) and the 2-norm in Eq.
+    (1.18) (budget_norm). Two workloads: the whole batch as benchmarked (mixed,
+    tol 1e-8) and every 8th matrix in FP64 to tol 1e-12, where the adaptive
+    budget of Eq. (1.18) is reached. Per variant: solves/s (CUDA events, after
+    a warm-up), iterations, and the entries per iteration summed over the
+    matrices (X, T and the T the update multiplies by)."""
+    import torch
+    out = []
+    for label, sub, base in (("banded batch, mixed, EXACT, tol 1e-8", mats,
+                              dict(tol=TOL, filter="exact", prec="mixed")),
+                             ("every 8th matrix, FP64, EXACT, tol 1e-12", mats[::8],
+                              dict(tol=1e-12, filter="exact", prec="fp64"))):
+        b = sg.Batch(sub)
+        try:
+            rows = {}
+            for name, kw in VARIANTS:
+                o = sg.default_opts(**base, **kw)
+                b.solve(o)
+                ms = []
+                for _ in range(reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    b.solve(o)
+                    e1.record()
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                res = b.solve(o, trace_cap=64)
+                tr = b.traces()
+                depth = max(len(t["nnz_x"]) for t in tr)
+
+                def per_iter(key):
+                    return [int(sum(int(t[key][k]) for t in tr if k < len(t[key])))
+                            for k in range(depth)]
+
+                rows[name] = {"solves_per_s": len(sub) / (statistics.median(ms) / 1e3),
+                              "ms_per_batch": statistics.median(ms),
+                              "all_converged": all(s == sg.SIGN_OK for s, _, _ in res),
+                              "mean_updates": float(np.mean([it for _, it, _ in res])),
+                              "max_resid": float(max(r for _, _, r in res)),
+                              "nnz_x_per_iter": per_iter("nnz_x"),
+                              "nnz_t_per_iter": per_iter("nnz_t"),
+                              "nnz_t_used_per_iter": per_iter("nnz_that")}
+            out.append({"workload": label, "matrices": len(sub), "variants": rows})
+        finally:
+            b.close()
+    return out
+
+
 # ---------------------------------------------------------------------- clocks
 class Clocks:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -769,6 +825,8 @@ def main():
         if cpu:
             line["cpu_baseline"] = cpu
     batch.close()
+    if args.legs == "all" and rank == 0:
+        line["variants"] = variants_leg(sg, mats)
     if args.legs == "all" and args.serve_seconds > 0 and rank == 0:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
         line["serving"] = serve_leg(sg, rates, args.serve_seconds)

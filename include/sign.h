@@ -93,6 +93,12 @@ typedef struct {
                           run as band tiles (dense register-blocked FMAs in
                           ascending k; the same values bit for bit); 0: the
                           row-wise kernels only; 1                        */
+  int filter_t;        /* variant: 1 = T = X^2 is filtered too, with the same
+                          budget and filter, before the update uses it (the
+                          dense path is then off); 0                       */
+  int budget_norm;     /* variant: 1 = x in Eq. (1.18) is ||X||_2, estimated
+                          by 8 power steps on X^T X from (1,...,1)/sqrt(n);
+                          0 = RMS Frobenius ||X||_F/sqrt(n); 0             */
 } sign_opts;
 
 /* Per-iteration record, filled by sign_solve when non-NULL. The arrays are
@@ -118,6 +124,8 @@ typedef struct {
   int *prec_k;        /* 32 or 64                                            */
   double *mults_t;    /* multiply-adds of T = X_k X_k                        */
   double *mults_bar;  /* multiply-adds of X_k T of the next update           */
+  int64_t *nnz_that;  /* nnz of the T the next update multiplies by (after
+                         its filter with filter_t, else nnz_t)              */
 } sign_info;
 
 /* Fills *o with the defaults listed in sign_opts. */

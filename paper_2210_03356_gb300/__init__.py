@@ -32,7 +32,7 @@ __all__ = ["solve", "solve_batch", "Handle", "Batch", "Result", "Server", "defau
 _TRACE = [("nnz_x", np.int64), ("nnz_t", np.int64), ("resid_k", np.float64),
           ("xnorm_k", np.float64), ("beta_k", np.float64), ("tau_k", np.float64),
           ("fnorm_k", np.float64), ("nnz_bar", np.int64), ("prec_k", np.int32),
-          ("mults_t", np.float64), ("mults_bar", np.float64)]
+          ("mults_t", np.float64), ("mults_bar", np.float64), ("nnz_that", np.int64)]
 
 
 def _is_torch_cuda(x) -> bool:
@@ -342,6 +342,13 @@ class Batch:
         if st != SIGN_OK:
             raise SignError(st, "sign_solve_batch")
         return [(s.status, s.iters, s.resid) for s in iarr]
+
+    def traces(self) -> list:
+        """The per-iteration records of the last solve(trace_cap > 0), one dict per matrix."""
+        if self.infos is None:
+            return []
+        infos, iarr, _ = self.infos
+        return [i.trace(s) for i, s in zip(infos, iarr)]
 
     def results(self, outs) -> list:
         """sign_get_csr_batch: every result at once into caller-owned host arrays.

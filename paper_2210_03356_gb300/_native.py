@@ -23,7 +23,8 @@ class sign_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("filter", C.c_int), ("c4", C.c_double),
                 ("switch_resid", C.c_double), ("max_iter", C.c_int), ("prec", C.c_int),
                 ("fp32_until", C.c_double), ("dense_frac", C.c_double), ("scale_1norm", C.c_int),
-                ("div_limit", C.c_double), ("dense64_min_n", C.c_int), ("fp32_band", C.c_int)]
+                ("div_limit", C.c_double), ("dense64_min_n", C.c_int), ("fp32_band", C.c_int),
+                ("filter_t", C.c_int), ("budget_norm", C.c_int)]
 
 
 class sign_info(C.Structure):
@@ -34,7 +35,7 @@ class sign_info(C.Structure):
                 ("beta_k", C.POINTER(C.c_double)), ("tau_k", C.POINTER(C.c_double)),
                 ("fnorm_k", C.POINTER(C.c_double)), ("nnz_bar", C.POINTER(C.c_int64)),
                 ("prec_k", C.POINTER(C.c_int)), ("mults_t", C.POINTER(C.c_double)),
-                ("mults_bar", C.POINTER(C.c_double))]
+                ("mults_bar", C.POINTER(C.c_double)), ("nnz_that", C.POINTER(C.c_int64))]
 
 
 class sign_server_opts(C.Structure):

@@ -208,6 +208,26 @@ struct MatScalars {
 // From sums[2m] = sum (T-I)^2, sums[2m+1] = sum X^2: r, x, beta, b.
 void launch_matrix_scalars(int nb, const int64_t *moff, const double *sums, double c4,
                            double tol_stage, double switch_resid, MatScalars *ms, cudaStream_t s);
+// ---------------------------------------------------------------- 2-norm
+// ||X||_2 estimates for the budget_norm variant (see kernels_norm2.cu):
+// v_0 = (1,...,1)/sqrt(n), NORM2_STEPS steps v <- X^T X v / ||X^T X v||, then
+// x2[m] = ||X v||. Work arrays: v, y, z, part of n doubles, zacc of 2n
+// uint64, xmax, ymax of nb uint64, nrm of nb doubles.
+constexpr int NORM2_STEPS = 8;
+struct Norm2Work {
+  double *v, *y, *z, *part, *nrm;
+  unsigned long long *zacc, *xmax, *ymax;
+};
+// Only the matrices with ms[m].r < switch_resid (the adaptive phase) are
+// estimated; x2 of the others is left undefined.
+void launch_norm2_est(int nb, const int64_t *moff, const int32_t *seg, int64_t n, const Rows &X,
+                      const void *val, int val_f32, const MatScalars *ms, double switch_resid,
+                      const Norm2Work &wk, double *x2, cudaStream_t s);
+
+// budget_norm: beta and b of Eq. (1.18) recomputed with x = x2[m] for the
+// matrices in the adaptive phase (r < switch_resid).
+void launch_budget_x2(int nb, const int64_t *moff, const double *x2, double switch_resid,
+                      MatScalars *ms, cudaStream_t s);
 
 // The values a threshold is selected over: row r holds entries [rs[r], re[r])
 // of matrix seg[r]; rs == nullptr means one flat array of flat_nnz values of

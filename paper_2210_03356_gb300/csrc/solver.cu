@@ -29,6 +29,8 @@ bool valid_opts(const sign_opts *o, std::string &why) {
   if (!(o->div_limit > 0.0)) return why = "div_limit must be > 0", false;
   if (o->dense64_min_n < 0) return why = "dense64_min_n < 0", false;
   if (o->fp32_band < 0 || o->fp32_band > 1) return why = "fp32_band must be 0 or 1", false;
+  if (o->filter_t < 0 || o->filter_t > 1) return why = "filter_t must be 0 or 1", false;
+  if (o->budget_norm < 0 || o->budget_norm > 1) return why = "budget_norm must be 0 or 1", false;
   return true;
 }
 
@@ -54,6 +56,8 @@ void sign_default_opts(sign_opts *o) {
   o->div_limit = 1e6;
   o->dense64_min_n = 1024;
   o->fp32_band = 1;
+  o->filter_t = 0;
+  o->budget_norm = 0;
 }
 
 const char *sign_last_error(void) { return g_err.c_str(); }

@@ -115,6 +115,14 @@ void trace_put(MatState &ms, int64_t nnz_x, int64_t nnz_t, double r, double x, i
   if (in->prec_k) in->prec_k[k] = prec;
   if (in->mults_t) in->mults_t[k] = mults_t;
   if (in->mults_bar) in->mults_bar[k] = 0.0;
+  if (in->nnz_that) in->nnz_that[k] = nnz_t;
+}
+
+// nnz of the filtered T the next update multiplies by (filter_t)
+void trace_that(MatState &ms, int64_t nnz_that) {
+  sign_info *in = ms.info;
+  if (!in || !in->nnz_that || ms.trace_count == 0 || ms.trace_count > in->cap) return;
+  in->nnz_that[ms.trace_count - 1] = nnz_that;
 }
 
 void trace_filter(MatState &ms, double beta, double tau, double fnorm, int64_t nnz_bar,
@@ -175,6 +183,7 @@ struct Work {
       dslot, dmem, dbufs, djobs, dscratch, dcount, derr;
   BandBuf bx, bt;  // bands of the iterate X and of T = X X (FP32 stage)
   DevBuf bandrow;  // rows of T written by the square's band tiles (1) or not (0)
+  DevBuf n2v, n2y, n2z, n2part, n2zacc, n2xmax, n2ymax, n2nrm, x2;  // budget_norm
   bool bt_rows_done = false;  // the square's band tiles wrote their rows of T's band
 };
 
@@ -246,6 +255,7 @@ struct Stage {
   DevBuf d_moff, d_seg;
   Csr<T> X, Xh;                   // compact iterate and filtered update
   Slotted<T> Tm, Xb;              // X X and 1.5 X - 0.5 X T
+  Csr<T> Th;                      // T after its filter (the filter_t variant)
   std::vector<std::unique_ptr<Parked>> incoming;  // matrices entering at the next round
 };
 
@@ -365,7 +375,7 @@ struct Solver {
   template <typename T>
   void product(Stage<T> &st, const Rows &A, const T *aval, int64_t nnzA, const Rows &B,
                const T *bval, int64_t nnzB, int mode, Slotted<T> &C, const int *active,
-               const DensePlan *dp = nullptr) {
+               const DensePlan *dp = nullptr, bool b_is_square_t = true) {
     int64_t N = int64_t(st.moff.back());
     int nb = int(st.mats.size());
     w.lo.ensure(sizeof(int32_t) * size_t(N), s);
@@ -415,6 +425,18 @@ struct Solver {
                       w.scan_tmp.as<int64_t>(), s);
           d2h(hm.tot + 1, w.bx.pos.as<int64_t>() + N, 1, s);
           d2h(hm.tot + 2, w.bt.pos.as<int64_t>() + N, 1, s);
+        } else if (!b_is_square_t) {  // B is not the square's T: its own layout
+          w.bt.filled = false;
+          w.bt_rows_done = false;
+          w.bt.fc.ensure(sizeof(int32_t) * size_t(N), s);
+          w.bt.nf.ensure(sizeof(int32_t) * size_t(N), s);
+          w.bt.span.ensure(sizeof(int64_t) * size_t(N), s);
+          w.bt.pos.ensure(sizeof(int64_t) * size_t(N + 1), s);
+          launch_band_spans(N, B, w.bt.fc.as<int32_t>(), w.bt.nf.as<int32_t>(),
+                            w.bt.span.as<int64_t>(), s);
+          launch_scan(N, w.bt.span.as<int64_t>(), w.bt.pos.as<int64_t>(),
+                      w.scan_tmp.as<int64_t>(), s);
+          d2h(hm.tot + 2, w.bt.pos.as<int64_t>() + N, 1, s);
         }
         d2h(hm.ctr, w.counters.p, RC_COUNTERS, s);
         d2h(hm.dsum, band_work_dev(), 1, s);
@@ -434,6 +456,8 @@ struct Solver {
     const bool band_tiles = band && hm.ctr[RC_BAND] > 0;
     if (band && mode == MODE_SQUARE) {
       w.bx.total = hm.tot[1];
+      w.bt.total = hm.tot[2];
+    } else if (band && !b_is_square_t) {
       w.bt.total = hm.tot[2];
     }
     if (band_tiles) {
@@ -515,7 +539,7 @@ struct Solver {
     DensePlan dp;
     int nb = int(st.mats.size());
     dp.slot.assign(nb, -1);
-    if (!(o.dense_frac <= 1.0) || o.filter == SIGN_FILTER_NONE) return dp;
+    if (!(o.dense_frac <= 1.0) || o.filter == SIGN_FILTER_NONE || o.filter_t) return dp;
     constexpr bool f32 = sizeof(T) == 4;
     size_t total = 0;  // bytes
     auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
@@ -773,6 +797,26 @@ struct Solver {
       launch_matrix_scalars(nb, st.d_moff.template as<int64_t>(), w.sums.as<double>(), o.c4,
                             tol_stage, o.switch_resid, w.ms.as<MatScalars>(), s);
     }
+    if (o.budget_norm) {  // variant: x = ||X||_2 in Eq. (1.18)
+      ProfScope ps(KC_REDUCE, s);
+      Norm2Work nw{w.n2v.ensure(sizeof(double) * size_t(N), s) ? w.n2v.as<double>() : nullptr,
+                   w.n2y.ensure(sizeof(double) * size_t(N), s) ? w.n2y.as<double>() : nullptr,
+                   w.n2z.ensure(sizeof(double) * size_t(N), s) ? w.n2z.as<double>() : nullptr,
+                   w.n2part.ensure(sizeof(double) * size_t(N), s) ? w.n2part.as<double>() : nullptr,
+                   w.n2nrm.ensure(sizeof(double) * size_t(nb), s) ? w.n2nrm.as<double>() : nullptr,
+                   w.n2zacc.ensure(sizeof(unsigned long long) * 2 * size_t(N), s)
+                       ? w.n2zacc.as<unsigned long long>() : nullptr,
+                   w.n2xmax.ensure(sizeof(unsigned long long) * size_t(nb), s)
+                       ? w.n2xmax.as<unsigned long long>() : nullptr,
+                   w.n2ymax.ensure(sizeof(unsigned long long) * size_t(nb), s)
+                       ? w.n2ymax.as<unsigned long long>() : nullptr};
+      w.x2.ensure(sizeof(double) * size_t(nb), s);
+      launch_norm2_est(nb, st.d_moff.template as<int64_t>(), st.d_seg.template as<int32_t>(), N,
+                       xr, st.X.val.p, is_f32<T>(), w.ms.as<MatScalars>(), o.switch_resid, nw,
+                       w.x2.as<double>(), s);
+      launch_budget_x2(nb, st.d_moff.template as<int64_t>(), w.x2.as<double>(), o.switch_resid,
+                       w.ms.as<MatScalars>(), s);
+    }
     d2h(hm.ms, w.ms.p, size_t(nb), s);
     d2h(hm.nnz_t, w.nnzc.p, size_t(nb), s);
     std::vector<unsigned long long> dcount(dp.nd);
@@ -881,8 +925,19 @@ struct Solver {
     HostScope hupdate(KH_UPDATE);
     int64_t nnz_t_all = 0;
     for (int i = 0; i < nb; ++i) nnz_t_all += hm.nnz_t[i];
-    product(st, xr, st.X.d_val(), st.X.nnz, st.Tm.rows(), st.Tm.d_val(), nnz_t_all, MODE_UPDATE,
-            st.Xb, d_act, &dp);
+    if (o.filter_t && o.filter != SIGN_FILTER_NONE) {
+      // variant: T filtered with the same budget and filter before the update
+      select_threshold(st, st.Tm, d_act);
+      std::vector<int64_t> tex;
+      filter_rows(st, st.Tm, st.Th, d_act, tex, nullptr);
+      for (int i = 0; i < nb; ++i)
+        if (st.alive[i]) trace_that(m[st.mats[i]], tex[i + 1] - tex[i]);
+      product(st, xr, st.X.d_val(), st.X.nnz, compact_rows(st.Th), st.Th.d_val(), st.Th.nnz,
+              MODE_UPDATE, st.Xb, d_act, &dp, false);
+    } else {
+      product(st, xr, st.X.d_val(), st.X.nnz, st.Tm.rows(), st.Tm.d_val(), nnz_t_all,
+              MODE_UPDATE, st.Xb, d_act, &dp);
+    }
     std::vector<double> mb(hm.mults, hm.mults + nb);
     for (int d = 0; d < dp.nd; ++d) {
       double n = double(st.moff[dp.mat[d] + 1] - st.moff[dp.mat[d]]);
@@ -896,19 +951,8 @@ struct Solver {
       // keep every entry: compact the slotted rows as they are
       hms_none(st, hms);
     } else {
-      {
-        // ---- threshold (step a5)
-        if (o.filter == SIGN_FILTER_EXACT) {
-          w.sel.ensure(select_scratch_bytes(nb, st.Xb.slots), s);
-          SelRows R{N, st.d_seg.template as<int32_t>(), st.Xb.rs.template as<int64_t>(),
-                    st.Xb.re.template as<int64_t>(), 0};
-          launch_select_exact(nb, R, st.Xb.slots, d_act, st.Xb.val.p, is_f32<T>(),
-                              w.ms.as<MatScalars>(), w.sel.p, s);
-        } else {
-          ProfScope psel(KC_SELECT, s);
-          launch_select_bound(nb, d_act, w.ms.as<MatScalars>(), s);
-        }
-      }
+      // ---- threshold (step a5); nnz(Xbar) is in the scalars for BOUND
+      select_threshold(st, st.Xb, d_act);
       filter(st, d_act, hms);
     }
     for (int i = 0; i < nb; ++i) {
@@ -921,43 +965,76 @@ struct Solver {
     st.X.swap(st.Xh);
   }
 
-  // Filter + compaction (step a6): Xh = entries of Xb with |x| >= tau, x != 0.
+  // Threshold (step a5) of each active matrix over the values of `in`, into
+  // the device scalars: EXACT by the radix select, BOUND by b/sqrt(nnz) with
+  // nnz the last product's per-matrix count (launch_seg_count).
   template <typename T>
-  void filter(Stage<T> &st, const int *d_act, std::vector<MatScalars> &hms) {
+  void select_threshold(Stage<T> &st, Slotted<T> &in, const int *d_act) {
+    int64_t N = st.moff.back();
+    int nb = int(st.mats.size());
+    if (o.filter == SIGN_FILTER_EXACT) {
+      w.sel.ensure(select_scratch_bytes(nb, in.slots), s);
+      SelRows R{N, st.d_seg.template as<int32_t>(), in.rs.template as<int64_t>(),
+                in.re.template as<int64_t>(), 0};
+      launch_select_exact(nb, R, in.slots, d_act, in.val.p, is_f32<T>(), w.ms.as<MatScalars>(),
+                          w.sel.p, s);
+    } else {
+      ProfScope psel(KC_SELECT, s);
+      launch_store_nnz_bar(nb, w.nnzc.as<int64_t>(), w.ms.as<MatScalars>(), s);
+      launch_select_bound(nb, d_act, w.ms.as<MatScalars>(), s);
+    }
+  }
+
+  // Filter + compaction (step a6) of the slotted rows `in` into the compact
+  // `out`: the entries with |x| >= tau and x != 0. ex receives the entry
+  // offsets of the matrices; dsum (nullable) the dropped sums of squares.
+  template <typename T>
+  void filter_rows(Stage<T> &st, Slotted<T> &in, Csr<T> &out, const int *d_act,
+                   std::vector<int64_t> &ex, std::vector<double> *dsum) {
     int64_t N = st.moff.back();
     int nb = int(st.mats.size());
     w.dropped.ensure(sizeof(double) * size_t(N > 0 ? N : 1), s);
     w.cnt.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
-    ProfScope pf(KC_FILTER, s, 0.0, double(st.Xb.slots) * (2.0 * sizeof(T) + 4.0) + 24.0 * double(N));
-    launch_filter_count(N, st.d_seg.template as<int32_t>(), d_act, st.Xb.rs.template as<int64_t>(),
-                        st.Xb.re.template as<int64_t>(), st.Xb.val.p, is_f32<T>(),
+    ProfScope pf(KC_FILTER, s, 0.0, double(in.slots) * (2.0 * sizeof(T) + 4.0) + 24.0 * double(N));
+    launch_filter_count(N, st.d_seg.template as<int32_t>(), d_act, in.rs.template as<int64_t>(),
+                        in.re.template as<int64_t>(), in.val.p, is_f32<T>(),
                         w.ms.as<MatScalars>(), w.cnt.as<int64_t>(), w.dropped.as<double>(), s);
-    st.Xh.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
-    launch_scan(N, w.cnt.as<int64_t>(), st.Xh.d_rp(), w.scan_tmp.as<int64_t>(), s);
+    out.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
+    launch_scan(N, w.cnt.as<int64_t>(), out.d_rp(), w.scan_tmp.as<int64_t>(), s);
     launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.dropped.as<double>(), 1,
                       w.sums.as<double>(), s);
     w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
-    launch_gather_offsets(nb, st.d_moff.template as<int64_t>(), st.Xh.d_rp(), w.eoff.as<int64_t>(), s);
+    launch_gather_offsets(nb, st.d_moff.template as<int64_t>(), out.d_rp(), w.eoff.as<int64_t>(), s);
     d2h(hm.ex, w.eoff.p, size_t(nb + 1), s);
-    d2h(hm.tot, st.Xh.d_rp() + N, 1, s);
+    d2h(hm.tot, out.d_rp() + N, 1, s);
     d2h(hm.ms, w.ms.p, size_t(nb), s);
     d2h(hm.dsum, w.sums.p, size_t(nb), s);
     wait();
     int64_t nnz = hm.tot[0];
-    st.Xh.n = N;
-    st.Xh.nnz = nnz;
-    st.Xh.col.ensure(sizeof(int32_t) * size_t(nnz > 0 ? nnz : 1), s);
-    st.Xh.val.ensure(sizeof(T) * size_t(nnz > 0 ? nnz : 1), s);
-    launch_filter_write(N, st.d_seg.template as<int32_t>(), d_act, st.Xb.rs.template as<int64_t>(),
-                        st.Xb.re.template as<int64_t>(), st.Xb.col.template as<int32_t>(),
-                        st.Xb.val.p, is_f32<T>(), w.ms.as<MatScalars>(), st.Xh.d_rp(),
-                        st.Xh.d_col(), st.Xh.val.p, s);
+    out.n = N;
+    out.nnz = nnz;
+    out.col.ensure(sizeof(int32_t) * size_t(nnz > 0 ? nnz : 1), s);
+    out.val.ensure(sizeof(T) * size_t(nnz > 0 ? nnz : 1), s);
+    launch_filter_write(N, st.d_seg.template as<int32_t>(), d_act, in.rs.template as<int64_t>(),
+                        in.re.template as<int64_t>(), in.col.template as<int32_t>(), in.val.p,
+                        is_f32<T>(), w.ms.as<MatScalars>(), out.d_rp(), out.d_col(), out.val.p, s);
+    ex.assign(hm.ex, hm.ex + nb + 1);
+    if (dsum) dsum->assign(hm.dsum, hm.dsum + nb);
+  }
+
+  // Filter + compaction (step a6): Xh = entries of Xb with |x| >= tau, x != 0.
+  template <typename T>
+  void filter(Stage<T> &st, const int *d_act, std::vector<MatScalars> &hms) {
+    int nb = int(st.mats.size());
+    std::vector<int64_t> ex;
+    std::vector<double> dsum;
+    filter_rows(st, st.Xb, st.Xh, d_act, ex, &dsum);
     for (int i = 0; i < nb; ++i) {
       hms[i].tau = hm.ms[i].tau;
       hms[i].nnz_bar = hm.ms[i].nnz_bar;
-      hms[i].fnorm = std::sqrt(hm.dsum[i]);
+      hms[i].fnorm = std::sqrt(dsum[i]);
     }
-    st.ex.assign(hm.ex, hm.ex + nb + 1);
+    st.ex = ex;
   }
 
   // No filter: the update is compacted with every entry kept (exact zeros too).
