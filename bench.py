@@ -333,6 +333,74 @@ def fill_leg(sg, iters: int):
     return out
 
 
+# ---------------------------------------------------------------------- 2-D Laplacian, solved
+def laplacian2d_leg(sg, m: int = 256, rows: int = 100, per_row: int = 100):
+    """The 2-D shifted Laplacian on m x m points (m = 256: n = 65,536) solved
+    to ||X^2 - I||_F/sqrt(n) <= 1e-8, filtered (EXACT), mixed FP32 -> FP64;
+    once its iterate holds a quarter of n^2 it runs on the dense tensor-core
+    path. Reports the fill and residual per iteration, the time, the time of
+    the dense products, and the error against the closed-form sign at
+    rows x per_row seeded entries (half near the diagonal, half anywhere)."""
+    import torch
+    from workloads import closed_form
+    a = w.laplacian(m, 2)
+    n = a.n
+    sg.trim_memory()
+    sg.prof_reset()
+    sg.prof_enable(True)
+    import ctypes
+    from paper_2210_03356_gb300 import _Info
+    o = sg.default_opts(tol=TOL, filter="exact", prec="mixed", max_iter=200)
+    info = _Info(256)
+    with sg.Handle(a) as h:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = sg.load().sign_solve(h.h, ctypes.byref(o), ctypes.byref(info.s))
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        sg.prof_enable(False)
+        if st not in (sg.SIGN_OK, sg.SIGN_ENOTCONV, sg.SIGN_EDIVERGED):
+            raise sg.SignError(st, "sign_solve")
+        sg.trim_memory()  # the solve's cached memory back to the device before the copy
+        rpd, cold, vald = h.result(device=True)
+    prof = sg.prof_read()
+    tr = info.trace()
+    status, iters, resid = info.s.status, info.s.iters, info.s.resid
+    rng = np.random.default_rng(m)
+    p = np.sort(rng.choice(n, rows, replace=False))
+    rp = rpd.cpu().numpy()
+    got, pi, ppi = [], [], []
+    for i in p:
+        lo, hi = int(rp[i]), int(rp[i + 1])
+        col = cold[lo:hi].cpu().numpy()
+        val = vald[lo:hi].cpu().numpy()
+        near = (i + rng.integers(-3 * m, 3 * m, per_row // 2)) % n
+        far = rng.integers(0, n, per_row - per_row // 2)
+        for j in np.r_[near, far]:
+            k = np.searchsorted(col, j)
+            got.append(val[k] if k < col.size and col[k] == j else 0.0)
+            pi.append(i)
+            ppi.append(j)
+    got = np.array(got)
+    ref = closed_form.laplacian_sign_entries(m, 2, np.array(pi), np.array(ppi))
+    dense = {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in prof.items()
+             if k.startswith("dense") and v["launches"]}
+    out = {"workload": f"laplacian2d m={m} (n={n}), sigma mid-gap, EXACT, mixed FP32->FP64, "
+                       "tol 1e-8", "status": int(status), "updates": int(iters),
+           "resid": float(resid), "seconds": secs, "nnz_final": int(rp[-1]),
+           "density_final": float(rp[-1]) / n / n,
+           "err_vs_closed_form": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+           "max_abs_err": float(np.abs(got - ref).max()), "samples": int(got.size),
+           "nnz_x": [int(x) for x in tr["nnz_x"]], "nnz_t": [int(x) for x in tr["nnz_t"]],
+           "resid_k": [float(x) for x in tr["resid_k"]], "prec_k": [int(x) for x in tr["prec_k"]],
+           "dense_classes": dense}
+    del rpd, cold, vald
+    torch.cuda.empty_cache()
+    print(f"laplacian2d m={m}: {secs:.1f} s, {out['updates']} updates, error "
+          f"{out['err_vs_closed_form']:.3g}", file=sys.stderr, flush=True)
+    return out
+
+
 # ---------------------------------------------------------------------- 3-D Laplacian (scaled)
 def laplacian3d_leg(sg, m: int, samples: int = 4000):
     """The 3-D shifted Laplacian on m^3 points (scaled variants of the 64^3
@@ -614,6 +682,8 @@ def main():
                     help="comma-separated m: also solve the m^3 3-D Laplacian against its closed form")
     ap.add_argument("--fill-iters", type=int, default=0,
                     help="also track fill on the n=65,536 2-D Laplacian for this many updates")
+    ap.add_argument("--laplacian2d", type=int, default=0,
+                    help="m: also solve the m x m 2-D Laplacian (m = 256: n = 65,536) to tol")
     ap.add_argument("--ode", default="",
                     help="comma-separated n: also solve Sec. 4.2's ODE block matrix as in Table 4.2.1")
     ap.add_argument("--filter-error", default="",
@@ -832,6 +902,8 @@ def main():
         line["serving"] = serve_leg(sg, rates, args.serve_seconds)
     if args.fill_iters > 0 and rank == 0:
         line["laplacian2d_fill"] = fill_leg(sg, args.fill_iters)
+    if args.laplacian2d and rank == 0:
+        line["laplacian2d_solve"] = laplacian2d_leg(sg, args.laplacian2d)
     if args.laplacian3d and rank == 0:
         line["laplacian3d"] = [laplacian3d_leg(sg, int(m)) for m in args.laplacian3d.split(",")]
     if args.ode and rank == 0:

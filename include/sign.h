@@ -82,7 +82,8 @@ typedef struct {
   int prec;            /* sign_prec; SIGN_PREC_FP64                          */
   double fp32_until;   /* FP32 stage ends below this residual; 1e-4          */
   double dense_frac;   /* a matrix whose iterate holds at least
-                          dense_frac n^2 entries (n <= 32768, a filter on)
+                          dense_frac n^2 entries (n <= 65536, a filter on,
+                          its dense blocks fitting in the free memory)
                           runs its products on the dense tensor-core path
                           in that round; > 1 turns the path off; 0.25      */
   int scale_1norm;     /* 1: X_1 = A/||A||_1 (default); 0: X_1 = A (paper)   */

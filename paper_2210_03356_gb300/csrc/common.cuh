@@ -122,11 +122,14 @@ struct DevBuf {
     p = nullptr;
     cap = 0;
   }
+  // Grows by a quarter more than asked (a sixteenth above 4 GB), so that a
+  // buffer that grows round by round is seldom reallocated.
   void *ensure(size_t bytes, cudaStream_t st) {
     if (bytes <= cap && p) return p;
     release();
     s = st;
-    p = block_alloc(bytes + bytes / 4 + 256, st, cap, owner);
+    const size_t slack = bytes > (size_t(4) << 30) ? bytes / 16 : bytes / 4;
+    p = block_alloc(bytes + slack + 256, st, cap, owner);
     return p;
   }
   template <typename T> T *as() const { return static_cast<T *>(p); }

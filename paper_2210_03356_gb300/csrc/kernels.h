@@ -253,10 +253,14 @@ constexpr size_t select_scratch_bytes(int nb, int64_t cap) {
          sel_align(size_t(nb) * 8) + sel_align(size_t(nb) * kSelStateBytes) + sel_align(8) +
          sel_align(size_t(cap > 0 ? cap : 1) * 8) + sel_align(size_t(cap > 0 ? cap : 1) * 4);
 }
-// cand_cap (the scratch's candidate room) must be at least the number of values.
+// cand_cap is the scratch's candidate room. Candidates past it are counted
+// but not kept, and the thresholds are then not valid: the caller compares
+// the count (*select_cand_count) with cand_cap and selects again with room
+// for every value when it is exceeded.
 void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *active,
                          const void *val, int val_f32, MatScalars *ms, void *scratch,
                          cudaStream_t s);
+const unsigned long long *select_cand_count(void *scratch, int nb);
 // ms[m].nnz_bar = nnz[m].
 void launch_store_nnz_bar(int nb, const int64_t *nnz, MatScalars *ms, cudaStream_t s);
 // BOUND: tau = b / sqrt(nnz_bar) per matrix.
@@ -318,6 +322,7 @@ struct SliceJob {
   const int *ea, *eb;
   double *C;
   int ldc;
+  int accum;  // 1: C += A Bt^T (a later K block); 0: C = A Bt^T
 };
 size_t f64x_digits_bytes(int rows, int ld);
 size_t slice_jobs_scratch_bytes(int njobs);
@@ -331,16 +336,22 @@ void launch_slice_jobs(int njobs, const SliceJob *jobs_host, SliceJob *jobs_dev,
 int f64x_pairs();  // digit pairs one product multiplies
 
 // The dense blocks of one matrix on the dense path of the FP64 stage, n x n
-// with leading dimension ld (a multiple of 8): X, X^T, T^T = (X X)^T and
-// P = X T in FP64, and the digit planes and scale exponents of X, X^T, T^T.
+// with leading dimension ld (a multiple of 8): X, T^T = (X X)^T and P = X T
+// in FP64, and the digit planes (rows of kd BF16 digits) and row exponents of
+// the two operands of one K block of F64X_MAX_K columns at a time: the
+// products run block by block, each block's digits cut from X, X^T (read
+// transposed from X) or T^T just before its product, so that no whole-matrix
+// digit planes are held.
 struct DenseBuf64 {
-  double *X, *XT, *TT, *P;
-  uint16_t *dX, *dXT, *dTT;
-  int *eX, *eXT, *eTT;
-  int n, ld;
+  double *X, *TT, *P;
+  uint16_t *dA, *dB;
+  int *eA, *eB;
+  int n, ld, kd;
 };
+// K-block digit row length of a dense FP64 block of leading dimension ld.
+constexpr int f64x_kd(int ld) { return ((ld < F64X_MAX_K ? ld : F64X_MAX_K) + 31) / 32 * 32; }
 // The FP64 stage's CSR rows of the dense-path matrices into their zeroed X
-// and X^T blocks.
+// blocks.
 void launch_densify64(int64_t n, const int32_t *seg, const int *dslot, const int64_t *moff,
                       const int64_t *rp, const int32_t *col, const double *val,
                       const DenseBuf64 *bufs, cudaStream_t s);

@@ -252,10 +252,11 @@ __global__ void __launch_bounds__(XTHREADS, 1)
           const int gc = n0 + col;
           if (gr >= J.M) continue;
           double *crow = J.C + int64_t(gr) * J.ldc + gc;
+          const bool add = u != 0 || J.accum;  // C holds earlier terms
           if (gc + 32 <= J.N) {
             // all sixteen loads of the row's chunk in flight before any store
             double2 c2[16];
-            if (u != 0) {
+            if (add) {
 #pragma unroll
               for (int i = 0; i < 16; ++i) c2[i] = reinterpret_cast<const double2 *>(crow)[i];
             }
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
               const int2 eb = reinterpret_cast<const int2 *>(J.eb + gc)[i];
               double2 t2 = make_double2(exact_scaled(__uint_as_float(v[2 * i]), er + eb.x),
                                         exact_scaled(__uint_as_float(v[2 * i + 1]), er + eb.y));
-              if (u != 0) {
+              if (add) {
                 t2.x = c2[i].x + t2.x;
                 t2.y = c2[i].y + t2.y;
               }
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
               double2 t2 = make_double2(exact_scaled(__uint_as_float(v[k]), er + eb.x),
                                         exact_scaled(__uint_as_float(v[k + 1]), er + eb.y));
               double2 *cp = reinterpret_cast<double2 *>(crow + k);
-              if (u != 0) {
+              if (add) {
                 const double2 c2 = *cp;
                 t2.x = c2.x + t2.x;
                 t2.y = c2.y + t2.y;
@@ -365,11 +366,7 @@ __global__ void k_densify64(int64_t n, const int32_t *seg, const int *dslot, con
     if (d < 0) return;
     const DenseBuf64 B = bufs[d];
     const int64_t r0 = moff[m], i = r - r0;
-    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) {
-      const int64_t j = col[p] - r0;
-      B.X[i * B.ld + j] = val[p];
-      B.XT[j * B.ld + i] = val[p];
-    }
+    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) B.X[i * B.ld + (col[p] - r0)] = val[p];
   });
 }
 

@@ -73,6 +73,7 @@ struct SelScratch {
   unsigned long long *ncand;    // 1
   unsigned long long *cand;     // cap
   int *cand_m;                  // cap
+  unsigned long long cap;       // candidate room; *ncand may count past it (overflow)
 };
 
 static_assert(sizeof(SelState) <= kSelStateBytes, "select state outgrew its scratch slot");
@@ -96,6 +97,7 @@ SelScratch carve(void *base, int nb, int64_t cap) {
   s.cand = reinterpret_cast<unsigned long long *>(p);
   p += align_up(size_t(cap > 0 ? cap : 1) * 8);
   s.cand_m = reinterpret_cast<int *>(p);
+  s.cap = (unsigned long long)(cap > 0 ? cap : 1);
   return s;
 }
 
@@ -366,8 +368,10 @@ __global__ void __launch_bounds__(SEL_THREADS)
       base = __shfl_sync(0xffffffffu, base, 0);
       if (take) {
         unsigned long long i = base + __popc(mask & lt);
-        sc.cand[i] = key;
-        sc.cand_m[i] = m;
+        if (i < sc.cap) {  // past the room: counted only (the caller retries with more)
+          sc.cand[i] = key;
+          sc.cand_m[i] = m;
+        }
       }
     }
   }
@@ -375,6 +379,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
 
 __global__ void k_sel_hist_digit(const MatScalars *ms, SelScratch sc, int shift) {
   unsigned long long total = *sc.ncand;
+  if (total > sc.cap) total = sc.cap;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     int m = sc.cand_m[i];
@@ -567,6 +572,10 @@ void launch_store_nnz_bar(int nb, const int64_t *nnz, MatScalars *ms, cudaStream
 void launch_select_bound(int nb, const int *active, MatScalars *ms, cudaStream_t s) {
   k_select_bound<<<(nb + 127) / 128, 128, 0, s>>>(nb, active, ms);
   SGN_LAUNCH_CHECK();
+}
+
+const unsigned long long *select_cand_count(void *scratch, int nb) {
+  return carve(scratch, nb, 1).ncand;
 }
 
 void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *active,

@@ -32,6 +32,12 @@ using namespace sgn;
 
 namespace {
 
+// Largest matrix order of the dense tensor-core path.
+constexpr int64_t DENSE_MAX_N = 65536;
+// Buffers above this size are handed back as soon as they are not needed
+// (between the update and the filter; when a stage empties).
+constexpr size_t BIG_BUFFER = size_t(4) << 30;
+
 // ------------------------------------------------------------------ CSR
 template <typename T>
 struct Csr {
@@ -184,6 +190,7 @@ struct Work {
   BandBuf bx, bt;  // bands of the iterate X and of T = X X (FP32 stage)
   DevBuf bandrow;  // rows of T written by the square's band tiles (1) or not (0)
   DevBuf n2v, n2y, n2z, n2part, n2zacc, n2xmax, n2ymax, n2nrm, x2;  // budget_norm
+  int64_t sel_cap = 0;  // candidate room of the last threshold select
   bool bt_rows_done = false;  // the square's band tiles wrote their rows of T's band
 };
 
@@ -532,8 +539,11 @@ struct Solver {
   }
 
   // ---------------------------------------------------------------- dense path (a9)
-  // Chooses the FP32-stage matrices whose iterate has filled in (density >=
-  // dense_frac, n <= 4096) and lays out their dense blocks.
+  // Chooses the matrices of a stage whose iterate has filled in (density >=
+  // dense_frac, n <= DENSE_MAX_N; in the FP64 stage also n >= dense64_min_n)
+  // and lays out their dense blocks. A matrix whose blocks would not fit in
+  // the device memory left (beside what the blocks of the last plan hold)
+  // stays on the sparse path.
   template <typename T>
   DensePlan plan_dense(Stage<T> &st) {
     DensePlan dp;
@@ -543,22 +553,43 @@ struct Solver {
     constexpr bool f32 = sizeof(T) == 4;
     size_t total = 0;  // bytes
     auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
-    // FP32: X, X^T, T^T split hi/lo and P; FP64: X, X^T, T^T, P, the digit
-    // planes of X, X^T, T^T and their row exponents
+    // FP32: X, X^T, T^T split hi/lo and P; FP64: X, T^T, P and one K block's
+    // digit planes and row exponents of the two operands
     auto bytes_of = [&](size_t ld) {
       return f32 ? 7 * 4 * ld * ld
-                 : 4 * r256(8 * ld * ld) + 3 * r256(f64x_digits_bytes(int(ld), int(ld))) +
-                       3 * r256(4 * ld);
+                 : 3 * r256(8 * ld * ld) + 2 * r256(f64x_digits_bytes(int(ld), f64x_kd(int(ld)))) +
+                       2 * r256(4 * ld);
     };
+    size_t room = 0;
+    bool room_known = false;
     for (int i = 0; i < nb; ++i) {
       if (!st.alive[i]) continue;
       int64_t n = st.moff[i + 1] - st.moff[i];
       int64_t nnz = st.ex[i + 1] - st.ex[i];
-      // up to n = 32768: seven FP32 blocks (30 GB) in the FP32 stage; four
-      // FP64 blocks and 24 BF16 digit planes (86 GB) in the FP64 stage
-      if (n > 32768 || double(nnz) < o.dense_frac * double(n) * double(n)) continue;
+      // up to n = 65536: seven FP32 blocks (120 GB) in the FP32 stage; three
+      // FP64 blocks and one K block's digit planes (112 GB) in the FP64 stage
+      if (n > DENSE_MAX_N || double(nnz) < o.dense_frac * double(n) * double(n)) continue;
       if (!f32 && n < o.dense64_min_n) continue;  // too small to repay 36 passes per tile
       int ld = f32 ? int((n + 3) / 4 * 4) : int((n + 7) / 8 * 8);
+      auto measure = [&] {  // free memory and the last plan's blocks, less headroom
+        size_t fr = 0, tot = 0;
+        SGN_CUDA(cudaMemGetInfo(&fr, &tot));
+        const size_t have = fr + w.dmem.cap, keep = size_t(8) << 30;
+        room = have > keep ? have - keep : 0;
+      };
+      if (!room_known) {
+        measure();
+        room_known = true;
+      }
+      if (total + bytes_of(size_t(ld)) > room && bytes_of(size_t(ld)) > BIG_BUFFER) {
+        // memory kept for reuse (this thread's parked blocks, the pool's
+        // free memory) goes back to the device before the path is refused
+        block_cache_flush();
+        SGN_CUDA(cudaDeviceSynchronize());
+        SGN_CUDA(cudaMemPoolTrimTo(lib_pool(), 0));
+        measure();
+      }
+      if (total + bytes_of(size_t(ld)) > room) continue;
       dp.slot[i] = dp.nd++;
       dp.mat.push_back(i);
       if (f32) {
@@ -594,20 +625,18 @@ struct Solver {
     } else {
       for (DenseBuf64 &b : dp.bufs64) {
         const size_t ld = size_t(b.ld), fb = r256(8 * ld * ld);
-        const size_t db = r256(f64x_digits_bytes(b.ld, b.ld)), eb = r256(4 * ld);
+        b.kd = f64x_kd(b.ld);
+        const size_t db = r256(f64x_digits_bytes(b.ld, b.kd)), eb = r256(4 * ld);
         unsigned char *p = mem + off;
-        b.X = reinterpret_cast<double *>(p);  // X and X^T adjacent: zeroed together
-        b.XT = reinterpret_cast<double *>(p + fb);
-        b.TT = reinterpret_cast<double *>(p + 2 * fb);
-        b.P = reinterpret_cast<double *>(p + 3 * fb);
-        p += 4 * fb;
-        b.dX = reinterpret_cast<uint16_t *>(p);
-        b.dXT = reinterpret_cast<uint16_t *>(p + db);
-        b.dTT = reinterpret_cast<uint16_t *>(p + 2 * db);
-        p += 3 * db;
-        b.eX = reinterpret_cast<int *>(p);
-        b.eXT = reinterpret_cast<int *>(p + eb);
-        b.eTT = reinterpret_cast<int *>(p + 2 * eb);
+        b.X = reinterpret_cast<double *>(p);
+        b.TT = reinterpret_cast<double *>(p + fb);
+        b.P = reinterpret_cast<double *>(p + 2 * fb);
+        p += 3 * fb;
+        b.dA = reinterpret_cast<uint16_t *>(p);
+        b.dB = reinterpret_cast<uint16_t *>(p + db);
+        p += 2 * db;
+        b.eA = reinterpret_cast<int *>(p);
+        b.eB = reinterpret_cast<int *>(p + eb);
         off += bytes_of(ld);
       }
     }
@@ -672,34 +701,41 @@ struct Solver {
       }
     } else {
       int64_t N = st.moff.back();
-      std::vector<SliceJob> jobs;
-      double fl = 0.0;
       const DenseBuf64 *bufs = w.dbufs.as<DenseBuf64>();
       if (mode == MODE_SQUARE) {
-        // X and X^T are adjacent in each matrix's block
         for (const DenseBuf64 &b : dp.bufs64)
-          SGN_CUDA(cudaMemsetAsync(b.X, 0, sizeof(double) * (size_t(b.XT - b.X) +
-                                                             size_t(b.ld) * size_t(b.ld)), s));
+          SGN_CUDA(cudaMemsetAsync(b.X, 0, sizeof(double) * size_t(b.ld) * size_t(b.ld), s));
         launch_densify64(N, st.d_seg.template as<int32_t>(), w.dslot.as<int>(),
                          st.d_moff.template as<int64_t>(), st.X.d_rp(), st.X.d_col(),
                          reinterpret_cast<const double *>(st.X.val.p), bufs, s);
       }
-      for (const DenseBuf64 &b : dp.bufs64) {
-        if (mode == MODE_SQUARE) {  // T^T = X^T X^T: C = A Bt^T with A = X^T, Bt = X
-          launch_slices(b.ld, b.ld, b.X, b.ld, 0, b.dX, b.ld, b.eX, s);
-          launch_slices(b.ld, b.ld, b.XT, b.ld, 0, b.dXT, b.ld, b.eXT, s);
-          jobs.push_back(SliceJob{b.ld, b.ld, b.ld, b.dXT, b.ld, b.dX, b.ld, b.eXT, b.eX, b.TT,
-                                  b.ld});
-        } else {  // P = X T as C = A Bt^T with A = X, Bt = T^T
-          launch_slices(b.ld, b.ld, b.TT, b.ld, 0, b.dTT, b.ld, b.eTT, s);
-          jobs.push_back(SliceJob{b.ld, b.ld, b.ld, b.dX, b.ld, b.dTT, b.ld, b.eX, b.eTT, b.P,
-                                  b.ld});
+      // K blocks of F64X_MAX_K: every block's digits are cut just before its
+      // product, which adds into C (SQUARE: C = T^T = X^T X^T as A Bt^T with
+      // A = X^T, read transposed from X, and Bt = X; UPDATE: C = P = X T with
+      // A = X and Bt = T^T)
+      w.djobs.ensure(sizeof(SliceJob) * size_t(dp.nd), s);
+      w.dscratch.ensure(slice_jobs_scratch_bytes(dp.nd), s);
+      std::vector<SliceJob> jobs;
+      for (int64_t k0 = 0; k0 < dp.max_ld; k0 += F64X_MAX_K) {
+        jobs.clear();
+        double fl = 0.0;
+        for (const DenseBuf64 &b : dp.bufs64) {
+          if (k0 >= b.ld) continue;
+          const int K = int(std::min<int64_t>(F64X_MAX_K, b.ld - k0));
+          const size_t ld = size_t(b.ld);
+          if (mode == MODE_SQUARE) {
+            launch_slices(b.ld, K, b.X + size_t(k0) * ld, b.ld, 1, b.dA, b.kd, b.eA, s);
+            launch_slices(b.ld, K, b.X + size_t(k0), b.ld, 0, b.dB, b.kd, b.eB, s);
+            jobs.push_back(SliceJob{b.ld, b.ld, K, b.dA, b.kd, b.dB, b.kd, b.eA, b.eB, b.TT, b.ld,
+                                    k0 > 0 ? 1 : 0});
+          } else {
+            launch_slices(b.ld, K, b.X + size_t(k0), b.ld, 0, b.dA, b.kd, b.eA, s);
+            launch_slices(b.ld, K, b.TT + size_t(k0), b.ld, 0, b.dB, b.kd, b.eB, s);
+            jobs.push_back(SliceJob{b.ld, b.ld, K, b.dA, b.kd, b.dB, b.kd, b.eA, b.eB, b.P, b.ld,
+                                    k0 > 0 ? 1 : 0});
+          }
+          fl += 2.0 * f64x_pairs() * double(b.ld) * double(b.ld) * double(K);
         }
-        fl += 2.0 * f64x_pairs() * double(b.ld) * double(b.ld) * double(b.ld);
-      }
-      w.djobs.ensure(sizeof(SliceJob) * jobs.size(), s);
-      w.dscratch.ensure(slice_jobs_scratch_bytes(int(jobs.size())), s);
-      {
         ProfScope ps(KC_DENSE64, s, fl, 0.0);
         launch_slice_jobs(int(jobs.size()), jobs.data(), w.djobs.as<SliceJob>(), w.dscratch.p,
                           w.derr.as<int>(), s);
@@ -945,6 +981,12 @@ struct Solver {
     }
     // per-matrix nnz(Xbar) straight into the device scalars (BOUND needs it)
     launch_store_nnz_bar(nb, w.nnzc.as<int64_t>(), w.ms.as<MatScalars>(), s);
+    // the iterate is not read again this round: a large one's memory can take
+    // the filtered update (reuse is ordered after the update on this stream)
+    if (st.X.col.cap + st.X.val.cap > BIG_BUFFER) {
+      st.X.col.release();
+      st.X.val.release();
+    }
     hupdate.stop();
     HostScope hfilter(KH_FILTER);
     if (o.filter == SIGN_FILTER_NONE) {
@@ -954,6 +996,10 @@ struct Solver {
       // ---- threshold (step a5); nnz(Xbar) is in the scalars for BOUND
       select_threshold(st, st.Xb, d_act);
       filter(st, d_act, hms);
+    }
+    if (st.Xb.col.cap + st.Xb.val.cap > BIG_BUFFER) {  // large update slots: memory for others
+      st.Xb.col.release();
+      st.Xb.val.release();
     }
     for (int i = 0; i < nb; ++i) {
       if (!st.alive[i]) continue;
@@ -968,15 +1014,20 @@ struct Solver {
   // Threshold (step a5) of each active matrix over the values of `in`, into
   // the device scalars: EXACT by the radix select, BOUND by b/sqrt(nnz) with
   // nnz the last product's per-matrix count (launch_seg_count).
+  // Above 2^28 values the candidate room is a sixteenth of them (at least
+  // 2^28); filter_rows selects again with full room if the crossing bucket
+  // held more.
   template <typename T>
-  void select_threshold(Stage<T> &st, Slotted<T> &in, const int *d_act) {
+  void select_threshold(Stage<T> &st, Slotted<T> &in, const int *d_act, bool full_room = false) {
     int64_t N = st.moff.back();
     int nb = int(st.mats.size());
     if (o.filter == SIGN_FILTER_EXACT) {
-      w.sel.ensure(select_scratch_bytes(nb, in.slots), s);
+      const int64_t big = int64_t(1) << 28;
+      w.sel_cap = full_room || in.slots <= big ? in.slots : std::max(big, in.slots / 16);
+      w.sel.ensure(select_scratch_bytes(nb, w.sel_cap), s);
       SelRows R{N, st.d_seg.template as<int32_t>(), in.rs.template as<int64_t>(),
                 in.re.template as<int64_t>(), 0};
-      launch_select_exact(nb, R, in.slots, d_act, in.val.p, is_f32<T>(), w.ms.as<MatScalars>(),
+      launch_select_exact(nb, R, w.sel_cap, d_act, in.val.p, is_f32<T>(), w.ms.as<MatScalars>(),
                           w.sel.p, s);
     } else {
       ProfScope psel(KC_SELECT, s);
@@ -995,29 +1046,45 @@ struct Solver {
     int nb = int(st.mats.size());
     w.dropped.ensure(sizeof(double) * size_t(N > 0 ? N : 1), s);
     w.cnt.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
-    ProfScope pf(KC_FILTER, s, 0.0, double(in.slots) * (2.0 * sizeof(T) + 4.0) + 24.0 * double(N));
-    launch_filter_count(N, st.d_seg.template as<int32_t>(), d_act, in.rs.template as<int64_t>(),
-                        in.re.template as<int64_t>(), in.val.p, is_f32<T>(),
-                        w.ms.as<MatScalars>(), w.cnt.as<int64_t>(), w.dropped.as<double>(), s);
     out.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
-    launch_scan(N, w.cnt.as<int64_t>(), out.d_rp(), w.scan_tmp.as<int64_t>(), s);
-    launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.dropped.as<double>(), 1,
-                      w.sums.as<double>(), s);
     w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
-    launch_gather_offsets(nb, st.d_moff.template as<int64_t>(), out.d_rp(), w.eoff.as<int64_t>(), s);
-    d2h(hm.ex, w.eoff.p, size_t(nb + 1), s);
-    d2h(hm.tot, out.d_rp() + N, 1, s);
-    d2h(hm.ms, w.ms.p, size_t(nb), s);
-    d2h(hm.dsum, w.sums.p, size_t(nb), s);
-    wait();
+    for (;;) {
+      {
+        ProfScope pf(KC_FILTER, s, 0.0, double(in.slots) * sizeof(T) + 24.0 * double(N));
+        launch_filter_count(N, st.d_seg.template as<int32_t>(), d_act,
+                            in.rs.template as<int64_t>(), in.re.template as<int64_t>(), in.val.p,
+                            is_f32<T>(), w.ms.as<MatScalars>(), w.cnt.as<int64_t>(),
+                            w.dropped.as<double>(), s);
+        launch_scan(N, w.cnt.as<int64_t>(), out.d_rp(), w.scan_tmp.as<int64_t>(), s);
+        launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.dropped.as<double>(), 1,
+                          w.sums.as<double>(), s);
+        launch_gather_offsets(nb, st.d_moff.template as<int64_t>(), out.d_rp(),
+                              w.eoff.as<int64_t>(), s);
+      }
+      d2h(hm.ex, w.eoff.p, size_t(nb + 1), s);
+      d2h(hm.tot, out.d_rp() + N, 1, s);
+      d2h(hm.ms, w.ms.p, size_t(nb), s);
+      d2h(hm.dsum, w.sums.p, size_t(nb), s);
+      const bool capped = o.filter == SIGN_FILTER_EXACT && w.sel_cap < in.slots;
+      if (capped) d2h(reinterpret_cast<unsigned long long *>(hm.tot + 3),
+                      select_cand_count(w.sel.p, nb), 1, s);
+      wait();
+      if (!capped || uint64_t(hm.tot[3]) <= uint64_t(w.sel_cap)) break;
+      select_threshold(st, in, d_act, true);  // the crossing bucket outgrew the room
+    }
     int64_t nnz = hm.tot[0];
     out.n = N;
     out.nnz = nnz;
     out.col.ensure(sizeof(int32_t) * size_t(nnz > 0 ? nnz : 1), s);
     out.val.ensure(sizeof(T) * size_t(nnz > 0 ? nnz : 1), s);
-    launch_filter_write(N, st.d_seg.template as<int32_t>(), d_act, in.rs.template as<int64_t>(),
-                        in.re.template as<int64_t>(), in.col.template as<int32_t>(), in.val.p,
-                        is_f32<T>(), w.ms.as<MatScalars>(), out.d_rp(), out.d_col(), out.val.p, s);
+    {
+      ProfScope pw(KC_FILTER, s, 0.0,
+                   double(in.slots + nnz) * (sizeof(T) + 4.0) + 24.0 * double(N));
+      launch_filter_write(N, st.d_seg.template as<int32_t>(), d_act, in.rs.template as<int64_t>(),
+                          in.re.template as<int64_t>(), in.col.template as<int32_t>(), in.val.p,
+                          is_f32<T>(), w.ms.as<MatScalars>(), out.d_rp(), out.d_col(), out.val.p,
+                          s);
+    }
     ex.assign(hm.ex, hm.ex + nb + 1);
     if (dsum) dsum->assign(hm.dsum, hm.dsum + nb);
   }
@@ -1149,9 +1216,52 @@ struct Solver {
   }
 
   // One round of each stage; the FP32 stage's movers enter FP64 in the same step.
+  // A stage left without matrices hands large buffers back (to this thread's
+  // block cache and the pool), so that the other stage can use the memory;
+  // small ones are kept for the next solve.
   void step() {
     round<float, double>(s32, &s64);
+    if (s32.incoming.empty() && !has_live(s32) && stage_bytes(s32) > BIG_BUFFER) release_stage(s32);
     round<double, double>(s64, nullptr);
+    if (s64.incoming.empty() && !has_live(s64) && stage_bytes(s64) > BIG_BUFFER) release_stage(s64);
+  }
+
+  template <typename T>
+  static size_t stage_bytes(const Stage<T> &st) {
+    size_t b = 0;
+    for (const Csr<T> *c : {&st.X, &st.Xh, &st.Th}) b += c->rp.cap + c->col.cap + c->val.cap;
+    for (const Slotted<T> *c : {&st.Tm, &st.Xb}) b += c->rs.cap + c->re.cap + c->col.cap + c->val.cap;
+    return b;
+  }
+
+  template <typename T>
+  static bool has_live(const Stage<T> &st) {
+    for (int a : st.alive)
+      if (a) return true;
+    return false;
+  }
+
+  // The stage then holds no matrix at all (a later admission rebuilds it from
+  // its incoming matrices alone, reading none of the released buffers).
+  template <typename T>
+  void release_stage(Stage<T> &st) {
+    st.mats.clear();
+    st.alive.clear();
+    st.moff.assign(1, 0);
+    st.ex.assign(1, 0);
+    for (Csr<T> *c : {&st.X, &st.Xh, &st.Th}) {
+      c->rp.release();
+      c->col.release();
+      c->val.release();
+      c->n = c->nnz = 0;
+    }
+    for (Slotted<T> *c : {&st.Tm, &st.Xb}) {
+      c->rs.release();
+      c->re.release();
+      c->col.release();
+      c->val.release();
+      c->n = c->slots = 0;
+    }
   }
 
   bool busy() const {
