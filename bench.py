@@ -480,18 +480,20 @@ def ode_leg(sg, sizes, reps: int = 3):
     return out
 
 
-def filter_error_leg(solve, sizes, seeds: int = 5, tol: float = 1e-12):
+def filter_error_leg(solve, sizes, seeds: int = 5, tol: float = 1e-12, make=None):
     """Sec. 4.1's second test (Fig. 4.1.2): random sparse SPD matrices of
     density 1% (the stand-in for sprandsym(n, 0.01, 1); workloads.spd_random),
-    NS and NSF (EXACT) in FP64 to tol 1e-12. For every iteration k, the
+    NS and NSF (EXACT) in FP64 to tol 1e-12 (make: another matrix family, as
+    Sec. 4.1's first test with Newton's method). For every iteration k, the
     filtered and unfiltered iterates after k updates give
     dX_k = Xhat_k - X_k and dR_k = Rhat_k - R_k (R = I - X^2), in RMS-Frobenius
     norm; the paper shows both below tol. solve(a, filter, max_iter) returns
     (status, iters, rowptr, col, val) of a run stopped after max_iter updates."""
     out = []
+    make = make or (lambda n, s: w.spd_random(n, 0.01, seed=w.BASE_SEED + 7000 + 10 * n + s))
     for n in sizes:
         for s in range(seeds):
-            a = w.spd_random(n, 0.01, seed=w.BASE_SEED + 7000 + 10 * n + s)
+            a = make(n, s)
             st, K, *_ = solve(a, "none", 100)
             dX, dR, r = [], [], []
             for k in range(1, K + 1):
@@ -688,6 +690,8 @@ def main():
                     help="comma-separated n: also solve Sec. 4.2's ODE block matrix as in Table 4.2.1")
     ap.add_argument("--filter-error", default="",
                     help="comma-separated n: also run Sec. 4.1's NS vs NSF test (Fig. 4.1.2)")
+    ap.add_argument("--filter-error-nm", default="",
+                    help="comma-separated n: also run Sec. 4.1's NM vs NMF test (Fig. 4.1.1)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -914,6 +918,13 @@ def main():
             return r.status, r.iters, r.rowptr, r.col, r.val
         line["filter_error_fig_4_1_2"] = filter_error_leg(
             gpu_solve, [int(n) for n in args.filter_error.split(",")])
+    if args.filter_error_nm and rank == 0:
+        def gpu_nmf(a, filt, max_iter):
+            r = sg.solve(a, tol=1e-12, filter=filt, method="nmf", max_iter=max_iter)
+            return r.status, r.iters, r.rowptr, r.col, r.val
+        line["filter_error_fig_4_1_1"] = filter_error_leg(
+            gpu_nmf, [int(n) for n in args.filter_error_nm.split(",")],
+            make=lambda n, s: w.sprand_like(n, 0.01, seed=w.BASE_SEED + 8000 + 10 * n + s))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

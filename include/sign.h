@@ -67,6 +67,15 @@ typedef enum {
 } sign_filter;
 
 typedef enum {
+  SIGN_METHOD_NSF = 0, /* filtered Newton-Schulz, Alg. 3.2.1                  */
+  SIGN_METHOD_NMF = 1  /* Newton's method with filtering, Alg. 3.1.1: X_{k+1} =
+                          (Xhat_k + Xhat_k^-1)/2 with a dense inverse (LU with
+                          partial pivoting), budget c4*tol, then Eq. (1.13)
+                          r^2/(x + ||X^-1||); X_1 = A (no scaling), FP64 only,
+                          n <= 32768; filter NONE is Newton's method, Eq. (1.1) */
+} sign_method;
+
+typedef enum {
   SIGN_PREC_FP64 = 0,  /* FP64 values and fused multiply-adds throughout     */
   SIGN_PREC_MIXED = 1  /* FP32 values and accumulation until the residual is
                           below fp32_until, then FP64; norms, budgets and
@@ -100,6 +109,7 @@ typedef struct {
   int budget_norm;     /* variant: 1 = x in Eq. (1.18) is ||X||_2, estimated
                           by 8 power steps on X^T X from (1,...,1)/sqrt(n);
                           0 = RMS Frobenius ||X||_F/sqrt(n); 0             */
+  int method;          /* sign_method; SIGN_METHOD_NSF                       */
 } sign_opts;
 
 /* Per-iteration record, filled by sign_solve when non-NULL. The arrays are

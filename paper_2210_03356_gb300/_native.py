@@ -24,7 +24,7 @@ class sign_opts(C.Structure):
                 ("switch_resid", C.c_double), ("max_iter", C.c_int), ("prec", C.c_int),
                 ("fp32_until", C.c_double), ("dense_frac", C.c_double), ("scale_1norm", C.c_int),
                 ("div_limit", C.c_double), ("dense64_min_n", C.c_int), ("fp32_band", C.c_int),
-                ("filter_t", C.c_int), ("budget_norm", C.c_int)]
+                ("filter_t", C.c_int), ("budget_norm", C.c_int), ("method", C.c_int)]
 
 
 class sign_info(C.Structure):
@@ -146,6 +146,8 @@ def default_opts(**kw) -> sign_opts:
             v = {"none": 0, "exact": 1, "bound": 2}[v]
         if k == "prec" and isinstance(v, str):
             v = {"fp64": 0, "mixed": 1}[v]
+        if k == "method" and isinstance(v, str):
+            v = {"nsf": 0, "nmf": 1}[v]
         setattr(o, k, v)
     return o
 

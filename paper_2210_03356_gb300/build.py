@@ -11,7 +11,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsign_gb300.so")
 SOURCES = ["kernels_csr.cu", "kernels_spgemm.cu", "kernels_select.cu", "solver.cu", "prof.cu",
            "memory.cu", "threshold.cu", "threshold_noalloc.cu", "kernels_dense.cu", "server.cu",
-           "kernels_f64x.cu", "kernels_band.cu", "kernels_norm2.cu"]
+           "kernels_f64x.cu", "kernels_band.cu", "kernels_norm2.cu",
+           "kernels_nmf.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("common.cuh", "kernels.h", "solver_core.cuh", "tc.cuh")] + [
     os.path.join(ROOT, "include", "sign.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -276,6 +276,30 @@ void launch_filter_write(int64_t n, const int32_t *seg, const int *active, const
                          const MatScalars *ms, const int64_t *orp, int32_t *ocol, void *oval,
                          cudaStream_t s);
 
+// ---------------------------------------------------------------- NMF (Alg. 3.1.1)
+// The inverse of the n x n FP64 matrix in lu (leading dimension ld; factored
+// in place) by LU with partial pivoting and one forward and back substitution
+// per column of the identity, into inv (same ld). perm: n ints; pivot: one
+// int; *singular = 1 (and inv undefined) if a pivot column is zero.
+void launch_dense_inverse(int n, int ld, double *lu, int *perm, int *pivot, int *singular,
+                          double *inv, cudaStream_t s);
+// *out = ||inv||_F / sqrt(n) (part: n doubles of scratch).
+void launch_inv_norm(int n, int ld, const double *inv, double *part, double *out,
+                     cudaStream_t s);
+// The n rows of a matrix (rows row0 .. of a compact CSR, columns from row0)
+// into the zeroed dense block dx.
+void launch_nmf_densify(int n, int ld, const int64_t *rp, const int32_t *col, const double *val,
+                        int64_t row0, double *dx, cudaStream_t s);
+// Xbar = (X + X^-1) / 2 into n full rows of slots from slot0: rows row0 ..
+// of (rs, re, col, val), global columns from row0.
+void launch_nmf_combine(int n, int ld, const double *dx, const double *inv, int64_t row0,
+                        int64_t slot0, int64_t *rs, int64_t *re, int32_t *col, double *val,
+                        cudaStream_t s);
+// ms[m].beta and .b by Eq. (1.13): c4 tol while r >= switch_resid, else
+// r^2 / (x + ||X^-1||) with *xinv = ||X^-1||_F / sqrt(n).
+void launch_nmf_budget(int m, int64_t n, const double *xinv, double c4, double tol,
+                       double switch_resid, MatScalars *ms, cudaStream_t s);
+
 // ---------------------------------------------------------------- dense (a9)
 // C = A Bt^T on the tensor cores (split TF32: three kind::tf32 MMAs per K step,
 // FP32 accumulation in tensor memory). A (M x K) and Bt (N x K) are row-major

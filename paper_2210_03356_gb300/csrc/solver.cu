@@ -31,6 +31,9 @@ bool valid_opts(const sign_opts *o, std::string &why) {
   if (o->fp32_band < 0 || o->fp32_band > 1) return why = "fp32_band must be 0 or 1", false;
   if (o->filter_t < 0 || o->filter_t > 1) return why = "filter_t must be 0 or 1", false;
   if (o->budget_norm < 0 || o->budget_norm > 1) return why = "budget_norm must be 0 or 1", false;
+  if (o->method < 0 || o->method > 1) return why = "unknown method", false;
+  if (o->method == SIGN_METHOD_NMF && o->prec != SIGN_PREC_FP64)
+    return why = "NMF runs in FP64 (prec = SIGN_PREC_FP64)", false;
   return true;
 }
 
@@ -58,6 +61,7 @@ void sign_default_opts(sign_opts *o) {
   o->fp32_band = 1;
   o->filter_t = 0;
   o->budget_norm = 0;
+  o->method = SIGN_METHOD_NSF;
 }
 
 const char *sign_last_error(void) { return g_err.c_str(); }

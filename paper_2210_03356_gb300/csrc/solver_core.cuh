@@ -34,6 +34,8 @@ namespace {
 
 // Largest matrix order of the dense tensor-core path.
 constexpr int64_t DENSE_MAX_N = 65536;
+// Largest matrix order of NMF (its inverse is dense: three n x n FP64 blocks).
+constexpr int64_t NMF_MAX_N = 32768;
 // Buffers above this size are handed back as soon as they are not needed
 // (between the update and the filter; when a stage empties).
 constexpr size_t BIG_BUFFER = size_t(4) << 30;
@@ -191,6 +193,7 @@ struct Work {
   DevBuf bandrow;  // rows of T written by the square's band tiles (1) or not (0)
   DevBuf n2v, n2y, n2z, n2part, n2zacc, n2xmax, n2ymax, n2nrm, x2;  // budget_norm
   int64_t sel_cap = 0;  // candidate room of the last threshold select
+  DevBuf nmf_int, nmf_dbl;  // NMF: permutation, pivot, singular flags; ||X^-1||
   bool bt_rows_done = false;  // the square's band tiles wrote their rows of T's band
 };
 
@@ -549,7 +552,9 @@ struct Solver {
     DensePlan dp;
     int nb = int(st.mats.size());
     dp.slot.assign(nb, -1);
-    if (!(o.dense_frac <= 1.0) || o.filter == SIGN_FILTER_NONE || o.filter_t) return dp;
+    if (!(o.dense_frac <= 1.0) || o.filter == SIGN_FILTER_NONE || o.filter_t ||
+        o.method == SIGN_METHOD_NMF)
+      return dp;
     constexpr bool f32 = sizeof(T) == 4;
     size_t total = 0;  // bytes
     auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
@@ -957,11 +962,18 @@ struct Solver {
     }
     if (changed) put(w.active.p, st.alive.data(), st.alive.size());
     hdecide.stop();
-    // ---- update: Xbar = 1.5 X - 0.5 X T (step a3)
+    // ---- update: Xbar = 1.5 X - 0.5 X T (step a3), or NMF's (X + X^-1) / 2
     HostScope hupdate(KH_UPDATE);
     int64_t nnz_t_all = 0;
     for (int i = 0; i < nb; ++i) nnz_t_all += hm.nnz_t[i];
-    if (o.filter_t && o.filter != SIGN_FILTER_NONE) {
+    std::vector<double> mb(nb, 0.0);
+    bool nmf = false;
+    if constexpr (sizeof(T) == 8) nmf = o.method == SIGN_METHOD_NMF;
+    if (nmf) {
+      if constexpr (sizeof(T) == 8) {
+        if (!nmf_update(st, d_act)) return;  // every updating iterate was singular
+      }
+    } else if (o.filter_t && o.filter != SIGN_FILTER_NONE) {
       // variant: T filtered with the same budget and filter before the update
       select_threshold(st, st.Tm, d_act);
       std::vector<int64_t> tex;
@@ -974,10 +986,12 @@ struct Solver {
       product(st, xr, st.X.d_val(), st.X.nnz, st.Tm.rows(), st.Tm.d_val(), nnz_t_all,
               MODE_UPDATE, st.Xb, d_act, &dp);
     }
-    std::vector<double> mb(hm.mults, hm.mults + nb);
-    for (int d = 0; d < dp.nd; ++d) {
-      double n = double(st.moff[dp.mat[d] + 1] - st.moff[dp.mat[d]]);
-      mb[dp.mat[d]] = n * n * n;
+    if (!nmf) {
+      mb.assign(hm.mults, hm.mults + nb);
+      for (int d = 0; d < dp.nd; ++d) {
+        double n = double(st.moff[dp.mat[d] + 1] - st.moff[dp.mat[d]]);
+        mb[dp.mat[d]] = n * n * n;
+      }
     }
     // per-matrix nnz(Xbar) straight into the device scalars (BOUND needs it)
     launch_store_nnz_bar(nb, w.nnzc.as<int64_t>(), w.ms.as<MatScalars>(), s);
@@ -1014,6 +1028,91 @@ struct Solver {
   // Threshold (step a5) of each active matrix over the values of `in`, into
   // the device scalars: EXACT by the radix select, BOUND by b/sqrt(nnz) with
   // nnz the last product's per-matrix count (launch_seg_count).
+  // NMF (Alg. 3.1.1) in place of the Newton-Schulz update, FP64 stage: for
+  // every updating matrix the dense inverse of its iterate, Xbar = (X +
+  // X^-1) / 2 into full rows of slots of st.Xb and the budget of Eq. (1.13).
+  // A matrix whose iterate is singular stops with SIGN_EDIVERGED, its
+  // iterate as the result. Returns false if no matrix is left to filter.
+  bool nmf_update(Stage<double> &st, const int *d_act) {
+    const int nb = int(st.mats.size());
+    const int64_t N = st.moff.back();
+    int64_t slots = 0, nmax = 0;
+    for (int i = 0; i < nb; ++i)
+      if (st.alive[i]) {
+        const int64_t n = st.moff[i + 1] - st.moff[i];
+        slots += n * n;
+        nmax = std::max(nmax, n);
+      }
+    Slotted<double> &C = st.Xb;
+    C.n = N;
+    C.slots = slots;
+    C.rs.ensure(sizeof(int64_t) * size_t(N + 1), s);
+    C.re.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
+    C.col.ensure(sizeof(int32_t) * size_t(slots > 0 ? slots : 1), s);
+    C.val.ensure(sizeof(double) * size_t(slots > 0 ? slots : 1), s);
+    SGN_CUDA(cudaMemsetAsync(C.rs.p, 0, sizeof(int64_t) * size_t(N + 1), s));
+    SGN_CUDA(cudaMemsetAsync(C.re.p, 0, sizeof(int64_t) * size_t(N > 0 ? N : 1), s));
+    const size_t blk = size_t(nmax) * size_t(nmax);
+    double *dx = static_cast<double *>(w.dmem.ensure(sizeof(double) * (3 * blk + size_t(nmax)), s));
+    double *lu = dx + blk, *inv = lu + blk, *part = inv + blk;
+    w.nmf_int.ensure(sizeof(int) * size_t(nmax + 2 + nb), s);
+    w.nmf_dbl.ensure(sizeof(double) * size_t(nb), s);
+    int *perm = w.nmf_int.as<int>(), *pivot = perm + nmax, *sing = pivot + 2;
+    double *xinv = w.nmf_dbl.as<double>();
+    SGN_CUDA(cudaMemsetAsync(sing, 0, sizeof(int) * size_t(nb), s));
+    int64_t slot0 = 0;
+    for (int i = 0; i < nb; ++i) {
+      if (!st.alive[i]) continue;
+      const int64_t row0 = st.moff[i], n = st.moff[i + 1] - row0;
+      const int ni = int(n);
+      ProfScope ps(KC_DENSE64, s, 2.0 * double(n) * double(n) * double(n), 0.0);
+      SGN_CUDA(cudaMemsetAsync(dx, 0, sizeof(double) * size_t(n) * size_t(n), s));
+      launch_nmf_densify(ni, ni, st.X.d_rp(), st.X.d_col(), st.X.d_val(), row0, dx, s);
+      SGN_CUDA(cudaMemcpyAsync(lu, dx, sizeof(double) * size_t(n) * size_t(n),
+                               cudaMemcpyDeviceToDevice, s));
+      launch_dense_inverse(ni, ni, lu, perm, pivot, sing + i, inv, s);
+      launch_inv_norm(ni, ni, inv, part, xinv + i, s);
+      launch_nmf_combine(ni, ni, dx, inv, row0, slot0, C.rs.as<int64_t>(), C.re.as<int64_t>(),
+                         C.col.as<int32_t>(), C.val.as<double>(), s);
+      launch_nmf_budget(i, n, xinv + i, o.c4, o.tol, o.switch_resid, w.ms.as<MatScalars>(), s);
+      slot0 += n * n;
+    }
+    std::vector<int> hsing(nb, 0);
+    d2h(hsing.data(), sing, size_t(nb), s);
+    wait();
+    // singular iterates stop here, their iterate as the result
+    int nx = 0;
+    int64_t xmax = 0;
+    for (int i = 0; i < nb; ++i) {
+      if (!st.alive[i] || !hsing[i]) continue;
+      MatState &ms = m[st.mats[i]];
+      ms.status = SIGN_EDIVERGED;
+      st.alive[i] = 0;
+      const int64_t n_i = st.moff[i + 1] - st.moff[i], nnz_i = st.ex[i + 1] - st.ex[i];
+      Csr<double> *dst = &ms.h->result;
+      ms.h->has_result = true;
+      retired.push_back(st.mats[i]);
+      dst->ensure(n_i, nnz_i, s);
+      xmax = std::max(xmax, std::max(nnz_i, n_i + 1));
+      hm.xb[nx++] = ExtractBlock{st.X.d_rp(), st.X.d_col(), st.X.val.p, 0, st.moff[i], n_i,
+                                 -st.moff[i], dst->d_rp(), dst->d_col(), dst->d_val()};
+    }
+    if (nx > 0) {
+      w.xblocks.ensure(sizeof(ExtractBlock) * size_t(nx), s);
+      h2d(w.xblocks.p, hm.xb, size_t(nx), s);
+      launch_extract(nx, w.xblocks.as<ExtractBlock>(), xmax, s);
+      put(w.active.p, st.alive.data(), st.alive.size());
+    }
+    launch_seg_count(nb, st.d_moff.template as<int64_t>(), C.rs.as<int64_t>(), C.re.as<int64_t>(),
+                     w.nnzc.as<int64_t>(), s);
+    launch_store_nnz_bar(nb, w.nnzc.as<int64_t>(), w.ms.as<MatScalars>(), s);
+    int live = 0;
+    for (int a : st.alive) live += a;
+    if (live == 0) wait();  // the extraction reads X and the pinned block list
+    (void)d_act;
+    return live > 0;
+  }
+
   // Above 2^28 values the candidate room is a sixteenth of them (at least
   // 2^28); filter_rows selects again with full room if the crossing bucket
   // held more.
@@ -1099,6 +1198,7 @@ struct Solver {
     for (int i = 0; i < nb; ++i) {
       hms[i].tau = hm.ms[i].tau;
       hms[i].nnz_bar = hm.ms[i].nnz_bar;
+      hms[i].beta = hm.ms[i].beta;  // NMF sets its own budget after the check
       hms[i].fnorm = std::sqrt(dsum[i]);
     }
     st.ex = ex;
@@ -1121,7 +1221,10 @@ struct Solver {
     d2h(hm.tot, st.Xh.d_rp() + N, 1, s);
     d2h(hm.ms, w.ms.p, size_t(nbm), s);
     wait();
-    for (int i = 0; i < nbm; ++i) hms[i].nnz_bar = hm.ms[i].nnz_bar;
+    for (int i = 0; i < nbm; ++i) {
+      hms[i].nnz_bar = hm.ms[i].nnz_bar;
+      hms[i].beta = hm.ms[i].beta;  // NMF sets its own budget after the check
+    }
     st.ex.assign(hm.ex, hm.ex + nbm + 1);
     int64_t nnz = hm.tot[0];
     st.Xh.n = N;
@@ -1158,6 +1261,11 @@ struct Solver {
       hs[i]->has_result = false;
       ids[i] = id;
     }
+    if (o.method == SIGN_METHOD_NMF)
+      for (int i = 0; i < count; ++i)
+        if (hs[i]->n > NMF_MAX_N)
+          throw Error(SIGN_EINVAL, "NMF: matrix " + std::to_string(i) + " is larger than " +
+                                       std::to_string(NMF_MAX_N) + " (dense inverse)");
     HostScope hsetup(KH_SETUP);
     std::vector<AsmBlock> blocks;
     std::vector<int64_t> bnnz, moff;
@@ -1173,7 +1281,7 @@ struct Solver {
     set_layout(moff, ids, d_moff, d_seg);
     const int64_t N = off;
     std::vector<char> ok(count, 1);
-    if (o.scale_1norm) {
+    if (o.scale_1norm && o.method != SIGN_METHOD_NMF) {  // NMF starts from X_1 = A
       w.norm_work.ensure(sizeof(unsigned long long) * size_t(2 * N + 4 * count), s);
       w.norm.ensure(sizeof(double) * size_t(count), s);
       std::vector<double> nrm(count);

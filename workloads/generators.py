@@ -304,6 +304,33 @@ def spd_random(n: int, density: float = 0.01, seed: int = BASE_SEED + 7000) -> C
     return csr_from_coo(n, rows, cols, vals, f"spd n={n} density={density}")
 
 
+def sprand_like(n: int, density: float = 0.01, seed: int = BASE_SEED + 8000) -> CSR:
+    """Random sparse nonsymmetric matrix, the stand-in for sprand(n, n, density)
+    of the paper's first filter-error test (Sec. 4.1, Fig. 4.1.1).
+
+    About density * n^2 off-diagonal entries at uniformly drawn positions,
+    values U[0, 1) (as sprand draws them), plus a diagonal s_i (1 + u_i) with
+    random signs s_i = +-1. The diagonal keeps the matrix nonsingular and its
+    eigenvalues off the imaginary axis (the off-diagonal part alone would
+    leave empty rows at this density), so Newton's method converges.
+    """
+    m = int(round(density * n * n))
+    z = splitmix64(seed, 3 * m + 2 * n)
+    i = (z[:m] % np.uint64(n)).astype(np.int64)
+    j = (z[m:2 * m] % np.uint64(n)).astype(np.int64)
+    u = (z[2 * m:3 * m] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    keep = i != j
+    i, j, u = i[keep], j[keep], u[keep]
+    _, first = np.unique(i * n + j, return_index=True)
+    i, j, u = i[first], j[first], u[first]
+    ud = (z[3 * m:3 * m + n] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    sd = np.where((z[3 * m + n:] >> np.uint64(63)) == np.uint64(1), -1.0, 1.0)
+    rows = np.concatenate([np.arange(n), i])
+    cols = np.concatenate([np.arange(n), j])
+    vals = np.concatenate([sd * (1.0 + ud), u])
+    return csr_from_coo(n, rows, cols, vals, f"sprand-like n={n} density={density}")
+
+
 def block_diagonal(mats: list[CSR]) -> CSR:
     """Concatenates matrices into one block-diagonal CSR (column indices shifted)."""
     offs = np.cumsum([0] + [a.n for a in mats])
