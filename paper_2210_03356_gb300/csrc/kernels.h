@@ -133,13 +133,16 @@ constexpr int RC_COUNTERS = 2 * RC_N;  // ints in the counters array
 // (by the work estimate in k_bounds) go to the band list instead, and their
 // multiply-adds are added to *band_work (nullable; zeroed by the caller);
 // bandrow (nullable) gets 1 for the rows of band tiles, 0 for the others.
+// binfo: scratch of n records (B's rows' first/last column and length; B has
+// n rows, as every operand of a stage).
 // dslot (nullable, per matrix): matrices with dslot[m] >= 0 take the dense
 // path; their rows get no sparse work, and in MODE_UPDATE a whole row of
 // slots (moff gives the matrix sizes).
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
                    int mode, int groups, int band, const int *dslot, const int64_t *moff,
                    int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists, int *counters,
-                   double *work, double *band_work, unsigned char *bandrow, cudaStream_t s);
+                   double *work, double *band_work, unsigned char *bandrow, int4 *binfo,
+                   cudaStream_t s);
 
 // Band layout of the rows of an FP32 operand: row k's values dense over the
 // columns [fc[k], fc[k] + nf[k]) (fc and nf multiples of 4, holes +0) at

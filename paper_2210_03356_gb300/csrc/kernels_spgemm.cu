@@ -109,10 +109,21 @@ __device__ __forceinline__ float lane_use(float avg, int g) {
   return avg / (rounds * float(g));
 }
 
+// Per row k of B: (first column, last column, entries, 0), so that k_bounds
+// reads one 16-byte record per k instead of a chain of dependent loads.
+__global__ void k_row_info(int64_t n, const int64_t *rs, const int64_t *re, const int32_t *col,
+                           int4 *info) {
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t a = rs[r], b = re[r];
+    info[r] = b > a ? make_int4(col[a], col[b - 1], int(b - a), 0) : make_int4(0, -1, 0, 0);
+  }
+}
+
 // counters: [RC_*] list lengths, [RC_QUEUE + RC_*] work-queue heads of the numeric kernels.
 __global__ void __launch_bounds__(BOUNDS_TILE)
     k_bounds(int64_t n, const int64_t *ars, const int64_t *are, const int32_t *acol,
-             const int64_t *brs, const int64_t *bre, const int32_t *bcol, const int32_t *seg,
+             const int4 *binfo, const int32_t *seg,
              const int *active, int mode, int groups, int band, const int *dslot,
              const int64_t *moff, int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists,
              int *counters, double *work, double *band_work, unsigned char *bandrow) {
@@ -153,11 +164,11 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
             int32_t k = acol[p];
             kf = min(kf, k);
             kl = max(kl, k);
-            int64_t b0 = brs[k], b1 = bre[k];
-            wk += b1 - b0;
-            if (b1 > b0) {
-              mn = min(mn, bcol[b0]);
-              mx = max(mx, bcol[b1 - 1]);
+            const int4 bi = binfo[k];  // B_k: first column, last column, length
+            wk += bi.z;
+            if (bi.z > 0) {
+              mn = min(mn, bi.x);
+              mx = max(mx, bi.y);
             }
             if (mode == MODE_UPDATE) {
               mn = min(mn, k);
@@ -835,13 +846,16 @@ int grid_cap(int64_t items, int per_block, int per_sm) {
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
                    int mode, int groups, int band, const int *dslot, const int64_t *moff,
                    int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists, int *counters,
-                   double *work, double *band_work, unsigned char *bandrow, cudaStream_t s) {
+                   double *work, double *band_work, unsigned char *bandrow, int4 *binfo,
+                   cudaStream_t s) {
   if (n == 0) return;
+  k_row_info<<<grid_cap(n, 256, 8), 256, 0, s>>>(n, B.rs, B.re, B.col, binfo);
+  SGN_LAUNCH_CHECK();
   int tiles = int((n + BOUNDS_TILE - 1) / BOUNDS_TILE);
   int g = tiles < sm_count() * 8 ? tiles : sm_count() * 8;
-  k_bounds<<<g, BOUNDS_TILE, 0, s>>>(n, A.rs, A.re, A.col, B.rs, B.re, B.col, seg, active, mode,
-                                     groups, band, dslot, moff, lo, len, ub, lists, counters,
-                                     work, band_work, bandrow);
+  k_bounds<<<g, BOUNDS_TILE, 0, s>>>(n, A.rs, A.re, A.col, binfo, seg, active, mode, groups,
+                                     band, dslot, moff, lo, len, ub, lists, counters, work,
+                                     band_work, bandrow);
   SGN_LAUNCH_CHECK();
 }
 

@@ -193,6 +193,7 @@ struct Work {
   DevBuf bandrow;  // rows of T written by the square's band tiles (1) or not (0)
   DevBuf n2v, n2y, n2z, n2part, n2zacc, n2xmax, n2ymax, n2nrm, x2;  // budget_norm
   int64_t sel_cap = 0;  // candidate room of the last threshold select
+  DevBuf binfo;         // per row of a product's B: first/last column, length
   DevBuf nmf_int, nmf_dbl;  // NMF: permutation, pivot, singular flags; ||X^-1||
   bool bt_rows_done = false;  // the square's band tiles wrote their rows of T's band
 };
@@ -411,7 +412,9 @@ struct Solver {
                     st.d_moff.template as<int64_t>(), w.lo.as<int32_t>(),
                     w.len.as<int32_t>(), w.ub.as<int64_t>(), w.wlist.as<int32_t>(),
                     w.counters.as<int>(), w.work.as<double>(), band_work_dev(),
-                    band && mode == MODE_SQUARE ? w.bandrow.as<unsigned char>() : nullptr, s);
+                    band && mode == MODE_SQUARE ? w.bandrow.as<unsigned char>() : nullptr,
+                    static_cast<int4 *>(w.binfo.ensure(sizeof(int4) * size_t(N > 0 ? N : 1), s)),
+                    s);
       launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.work.as<double>(), 1,
                         w.mults.as<double>(), s);
       if (band) {
