@@ -205,8 +205,11 @@ struct MatScalars {
   double tau;    // element threshold of the filter
   double fnorm;  // ||F||_F dropped
   int64_t nnz_x, nnz_t, nnz_bar, nnz_hat;
-  double qs;                // threshold select: 2^31 / b (0 if b == 0 or too small)
-  unsigned long long tiny;  // keys below this (|x| < b 2^-33) have q == 0
+  // threshold select: squares on the grid 2^(2e - 62) with 2^e <= b < 2^(e+1)
+  unsigned long long sel_q;  // q(b) = floor(b^2 / 2^(2e - 62))
+  unsigned long long tiny;   // keys below this have q == 0 (all ones: no key is summed)
+  int sel_e;                 // e + 1023, the biased exponent of b (1 for a subnormal b)
+  int sel_pad;
 };
 // From sums[2m] = sum (T-I)^2, sums[2m+1] = sum X^2: r, x, beta, b.
 void launch_matrix_scalars(int nb, const int64_t *moff, const double *sums, double c4,
@@ -248,7 +251,7 @@ struct SelRows {
 // The scratch holds, 256-byte aligned each: the level-0 histograms (1024
 // 128-bit sums per matrix), the digit histograms (256 per matrix), one
 // minimum per matrix, one select state of at most kSelStateBytes per matrix,
-// the candidate count, and room for cap candidates (8-byte key + matrix id).
+// the candidate count, and room for cap candidates (8-byte key + row).
 constexpr size_t kSelStateBytes = 64;
 constexpr size_t sel_align(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t select_scratch_bytes(int nb, int64_t cap) {
@@ -257,12 +260,21 @@ constexpr size_t select_scratch_bytes(int nb, int64_t cap) {
          sel_align(size_t(cap > 0 ? cap : 1) * 8) + sel_align(size_t(cap > 0 ? cap : 1) * 4);
 }
 // cand_cap is the scratch's candidate room. Candidates past it are counted
-// but not kept, and the thresholds are then not valid: the caller compares
-// the count (*select_cand_count) with cand_cap and selects again with room
-// for every value when it is exceeded.
+// but not kept, and the thresholds (and counts) are then not valid: the
+// caller compares the count (*select_cand_count) with cand_cap and selects
+// again with room for every value when it is exceeded.
+// cnt, dropped (nullable, R.nrows each; R must have rows rs/re): the
+// filter's per-row kept counts and dropped sums of squares under the
+// selected tau, as launch_filter_count gives them, except that the squares of
+// the dropped entries of the crossing bucket are left out: add them per
+// matrix with launch_select_drop_fix once dropped is summed per matrix.
 void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *active,
                          const void *val, int val_f32, MatScalars *ms, void *scratch,
-                         cudaStream_t s);
+                         int64_t *cnt, double *dropped, cudaStream_t s);
+// sums[m] += the squares of matrix m's dropped entries of its crossing bucket
+// (after launch_select_exact with counts, on the same scratch).
+void launch_select_drop_fix(int nb, const int *active, void *scratch, const MatScalars *ms,
+                            double *sums, cudaStream_t s);
 const unsigned long long *select_cand_count(void *scratch, int nb);
 // ms[m].nnz_bar = nnz[m].
 void launch_store_nnz_bar(int nb, const int64_t *nnz, MatScalars *ms, cudaStream_t s);

@@ -13,8 +13,10 @@
 // pattern of |x| (positive doubles order like unsigned integers): a
 // histogram of the top 16 bits over a 1024-bucket window below b, then six
 // 8-bit digits over the candidates of the crossing bucket. The squares are
-// summed as exact 128-bit integers q = round((x/b)^2 * 2^62), b^2 = 2^62, so
-// the decision does not depend on the order of the additions.
+// summed as exact 128-bit integers on a fixed grid of the matrix, q(x) =
+// floor(x^2 / 2^(2e - 62)) with 2^e <= b < 2^(e+1), against Q = q(b): the
+// decision does not depend on the order of the additions, and it is the exact
+// one up to the flooring, less than one grid step (2^-62 b^2) per entry.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -24,7 +26,6 @@ namespace {
 
 constexpr int NB0 = 1024;        // level-0 buckets
 constexpr int NDIG = 256;        // digit buckets
-constexpr unsigned long long ONE62 = 1ULL << 62;
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
@@ -58,13 +59,14 @@ __global__ void k_select_bound(int nb, const int *active, MatScalars *ms) {
 struct SelState {
   unsigned long long prefix;              // key bits known so far
   unsigned long long below_lo, below_hi;  // 128-bit sum of q strictly below the prefix range
+  unsigned long long below0_lo, below0_hi;  // the same below the crossing level-0 bucket
   int found;                              // 1: a crossing exists; 0: everything <= b fits
   int pad;
 };
 
 // Scratch: 128-bit sums (lo, hi) per bucket for the level-0 and digit
 // histograms, the smallest key above b per matrix, the select states, the
-// candidate count and the candidates (key, matrix).
+// candidate count and the candidates (key, row of the values).
 struct SelScratch {
   unsigned long long *hist0;    // nb * NB0 * 2
   unsigned long long *hdig;     // nb * NDIG * 2
@@ -72,7 +74,7 @@ struct SelScratch {
   SelState *st;                 // nb
   unsigned long long *ncand;    // 1
   unsigned long long *cand;     // cap
-  int *cand_m;                  // cap
+  int *cand_r;                  // cap
   unsigned long long cap;       // candidate room; *ncand may count past it (overflow)
 };
 
@@ -96,7 +98,7 @@ SelScratch carve(void *base, int nb, int64_t cap) {
   p += align_up(8);
   s.cand = reinterpret_cast<unsigned long long *>(p);
   p += align_up(size_t(cap > 0 ? cap : 1) * 8);
-  s.cand_m = reinterpret_cast<int *>(p);
+  s.cand_r = reinterpret_cast<int *>(p);
   s.cap = (unsigned long long)(cap > 0 ? cap : 1);
   return s;
 }
@@ -105,10 +107,20 @@ SelScratch carve(void *base, int nb, int64_t cap) {
 // belongs to matrix seg[r]; with rs == nullptr the values are one flat array
 // of flat_nnz entries cut into rows of FLAT_ROW, all of matrix 0.
 constexpr int64_t FLAT_ROW = kFlatRow;
-constexpr int64_t ROWS_PER_CHUNK = 64;
 constexpr int SEL_THREADS = 256;
 
 __device__ __forceinline__ int row_mat(const SelRows &R, int64_t r) { return R.seg ? R.seg[r] : 0; }
+
+constexpr unsigned long long INF_KEY = 0x7FF0000000000000ULL;
+
+// The filter's rule on keys: x is kept when x != 0 and |x| >= tau, tau given
+// by its bit pattern. For every |x| that is not NaN this is the comparison of
+// the two doubles (non-negative doubles order like their bit patterns); NaN
+// entries are dropped, as by the floating-point comparison. The count and
+// the write of a filter both decide with this one function.
+__device__ __forceinline__ bool keep_key(unsigned long long key, unsigned long long tkey) {
+  return key != 0ULL && key <= INF_KEY && key >= tkey;
+}
 
 __device__ __forceinline__ void row_range(const SelRows &R, int64_t r, int64_t &b, int64_t &e) {
   if (R.rs) {
@@ -124,39 +136,91 @@ __device__ __forceinline__ void row_range(const SelRows &R, int64_t r, int64_t &
 // it is built with integer operations (exponent rebiased by 1023 - 127 = 896,
 // mantissa widened by 29 bits): the same bits as the exact conversion, with
 // no work for the FP64 pipe, which this GPU runs at 1/64 of its FP32 rate.
+__device__ __forceinline__ unsigned long long key_f32(float x) {
+  const uint32_t b = __float_as_uint(x) & 0x7FFFFFFFu, e = b >> 23;
+  if (e != 0u && e != 0xFFu)
+    return ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29);
+  if (b == 0u) return 0ULL;
+  return (unsigned long long)__double_as_longlong(fabs(double(x)));  // subnormal, inf, NaN
+}
+
+__device__ __forceinline__ unsigned long long key_f64(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
+}
+
+template <typename T>
+__device__ __forceinline__ unsigned long long key_t(T x);
+template <>
+__device__ __forceinline__ unsigned long long key_t<float>(float x) { return key_f32(x); }
+template <>
+__device__ __forceinline__ unsigned long long key_t<double>(double x) { return key_f64(x); }
+
 __device__ __forceinline__ unsigned long long key_of(const void *val, int f32, int64_t p) {
-  if (f32) {
-    const float x = static_cast<const float *>(val)[p];
-    const uint32_t b = __float_as_uint(x) & 0x7FFFFFFFu, e = b >> 23;
-    if (e != 0u && e != 0xFFu)
-      return ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29);
-    if (b == 0u) return 0ULL;
-    return (unsigned long long)__double_as_longlong(fabs(double(x)));  // subnormal, inf, NaN
+  return f32 ? key_f32(static_cast<const float *>(val)[p])
+             : key_f64(static_cast<const double *>(val)[p]);
+}
+
+// (hi, lo) += x^2 for FP32 x, exactly: the square's rounding error comes from
+// an FMA and the sum's from TwoSum; all in FP32, which this GPU runs at 64x
+// its FP64 rate. Inputs are scaled by 2^48 (exact), so that squares of
+// entries from 2^-111 to 2^16 stay normal FP32 numbers.
+__device__ __forceinline__ void ff_add_sq48(float x, float &hi, float &lo) {
+  const float y = __fmul_rn(x, 281474976710656.0f);  // 2^48
+  const float p = __fmul_rn(y, y), e = __fmaf_rn(y, y, -p);
+  const float s = __fadd_rn(hi, p), bb = __fsub_rn(s, hi);
+  lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb)), e));
+  hi = s;
+}
+
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float h2, float l2) {
+  const float s = __fadd_rn(hi, h2), bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+  lo = __fadd_rn(__fadd_rn(lo, l2), err);
+  hi = s;
+}
+
+// q = floor(x^2 / 2^(2e - 62)) for 0 < |x| <= b, with |x| given by its FP64
+// bit pattern (significand M, biased exponent E; a subnormal counts as E = 1)
+// and e the biased exponent of b (likewise): x^2 / 2^(2e - 62) = M^2 2^-s with
+// s = 42 + 2 (e - E) >= 42, so q is M^2 shifted right by s, exactly, in
+// integers (q < 2^64 since |x| <= b). q >= 1 exactly when E >= e - 31.
+// FP32 values have M = m 2^29 with m < 2^24, and q = m^2 2^(58 - s) needs one
+// 32 x 32-bit product.
+template <typename T>
+__device__ __forceinline__ unsigned long long qval(unsigned long long key, int eb) {
+  const int ex = int(key >> 52);
+  const int s = 42 + 2 * (eb - (ex ? ex : 1));
+  if (s >= 106) return 0ULL;
+  const unsigned long long M = (key & 0xFFFFFFFFFFFFFULL) | (ex ? (1ULL << 52) : 0ULL);
+  if constexpr (sizeof(T) == 4) {
+    const unsigned m = unsigned(M >> 29);
+    const unsigned long long m2 = (unsigned long long)m * m;  // < 2^48
+    return s <= 58 ? m2 << (58 - s) : m2 >> (s - 58);
+  } else {
+    const unsigned long long lo = M * M, hi = __umul64hi(M, M);
+    if (s >= 64) return hi >> (s - 64);
+    return (lo >> s) | (hi << (64 - s));
   }
-  return (unsigned long long)__double_as_longlong(static_cast<const double *>(val)[p]) &
-         0x7FFFFFFFFFFFFFFFULL;
 }
 
-// q = round((x * s)^2) with s = 2^31 / b, i.e. (x/b)^2 in units of 2^-62 of
-// b^2: two FP64 multiplies per entry (the division is done once per matrix).
-// Entries with q == 0 add nothing to any sum and are always dropped, so the
-// histograms skip them; keys below ms.tiny (|x| < b 2^-33) are known to have
-// q == 0 without any floating-point work.
-__device__ __forceinline__ unsigned long long qval(unsigned long long key, double qs) {
-  double t = __dmul_rn(__longlong_as_double((long long)key), qs);
-  return __double2ull_rn(__dmul_rn(t, t));
-}
-
-// Per matrix: qs = 2^31 / b and the key of b 2^-33 (b = 0, or b so small that
-// 2^31 / b overflows, gives qs = 0: every q is 0).
+// Per matrix: e (the biased exponent of b, 1 for a subnormal b), Q = q(b) and
+// the smallest key with q >= 1 (the key of 2^(e - 31 - 1023)). b = 0, +inf or
+// NaN: no key is summed (tiny = all ones), every q counts as 0.
 __global__ void k_sel_prepare(int nb, MatScalars *ms) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= nb) return;
-  double b = ms[m].b;
-  double qs = b > 0.0 ? __ddiv_rn(2147483648.0, b) : 0.0;
-  if (!isfinite(qs)) qs = 0.0;
-  ms[m].qs = qs;
-  ms[m].tiny = (unsigned long long)__double_as_longlong(__dmul_rn(b, 0x1p-33));
+  const unsigned long long bkey = (unsigned long long)__double_as_longlong(ms[m].b);
+  const int e = int(bkey >> 52);
+  if (bkey == 0ULL || e >= 0x7FF) {  // b <= 0 (sign bit) is caught here as well
+    ms[m].sel_e = 0;
+    ms[m].sel_q = 0ULL;
+    ms[m].tiny = ~0ULL;
+    return;
+  }
+  const int eb = e ? e : 1;
+  ms[m].sel_e = eb;
+  ms[m].sel_q = qval<double>(bkey, eb);
+  ms[m].tiny = eb > 32 ? (unsigned long long)(eb - 31) << 52 : 0ULL;
 }
 
 // (lo, hi) += (alo, ahi) atomically in memory; exact, order-independent.
@@ -183,36 +247,72 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
   return v;
 }
 
+// A chunk of consecutive rows, their extents and matrices staged in shared
+// memory by one thread per row, so that a warp's loop over the chunk's rows
+// waits on the values only, not on the chain row -> matrix -> scalars.
+// Rows of inactive matrices are staged empty.
+constexpr int RPC = 64;  // rows per chunk (row lists); flat values: 8 rows of kFlatRow
+__device__ __forceinline__ int64_t chunk_rows(const SelRows &R) { return R.rs ? RPC : 8; }
+
+struct ChunkRows {
+  int64_t b[RPC], e[RPC];
+  int m[RPC];
+};
+
+// Stages rows [r0, r1) (r1 - r0 <= RPC) and returns the thread's row
+// slot (-1 if none) with its matrix in m; the caller adds its own per-row
+// scalars, then synchronises.
+__device__ __forceinline__ int stage_rows(const SelRows &R, const int *active, int64_t r0,
+                                          int64_t r1, ChunkRows &cr, int &m) {
+  const int t = threadIdx.x;
+  if (t >= r1 - r0) return -1;
+  const int64_t r = r0 + t;
+  m = row_mat(R, r);
+  int64_t b, e;
+  row_range(R, r, b, e);
+  cr.b[t] = b;
+  cr.e[t] = active[m] ? e : b;
+  cr.m[t] = m;
+  return t;
+}
+
 // Level-0 histogram. A CTA takes a chunk of consecutive rows, a warp one row
 // at a time, each lane a contiguous run of the row's entries. Neighbouring
 // entries of a row have similar magnitudes, so a lane sums its run per bucket
 // in registers and adds the run's total once when the bucket changes: into a
 // shared histogram for the chunk's first matrix (almost every row: matrices
 // span many chunks), else into the global one.
+template <typename T>
 __global__ void __launch_bounds__(SEL_THREADS)
-    k_sel_hist0(int nb, SelRows R, const int *active, const void *val, int f32,
-                const MatScalars *ms, SelScratch sc) {
+    k_sel_hist0(SelRows R, const int *active, const T *val, const MatScalars *ms, SelScratch sc) {
   __shared__ unsigned long long s_h[NB0 * 2];
   __shared__ unsigned long long s_min;
-  (void)nb;
+  __shared__ ChunkRows cr;
+  __shared__ unsigned long long s_bkey[RPC], s_tiny[RPC];
+  __shared__ int s_eb[RPC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = SEL_THREADS / 32;
-  const int64_t rpc = R.rs ? ROWS_PER_CHUNK : 1;
+  const int64_t rpc = chunk_rows(R);
   const int64_t nchunks = (R.nrows + rpc - 1) / rpc;
   for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-    int64_t r0 = c * rpc, r1 = min(r0 + rpc, R.nrows);
-    int m0 = row_mat(R, r0);
+    const int64_t r0 = c * rpc, r1 = min(r0 + rpc, R.nrows);
     for (int t = threadIdx.x; t < 2 * NB0; t += SEL_THREADS) s_h[t] = 0ULL;
     if (threadIdx.x == 0) s_min = ~0ULL;
+    int mt = 0;
+    const int t = stage_rows(R, active, r0, r1, cr, mt);
+    if (t >= 0) {
+      s_bkey[t] = (unsigned long long)__double_as_longlong(ms[mt].b);
+      s_eb[t] = ms[mt].sel_e;
+      s_tiny[t] = ms[mt].tiny;
+    }
     __syncthreads();
-    for (int64_t r = r0 + warp; r < r1; r += nw) {
-      int m = row_mat(R, r);
-      if (!active[m]) continue;
-      unsigned long long bkey = (unsigned long long)__double_as_longlong(ms[m].b);
-      double qs = ms[m].qs;
-      unsigned long long tiny = ms[m].tiny;
+    const int m0 = cr.m[0];
+    for (int i = warp; i < r1 - r0; i += nw) {
+      const int64_t e0 = cr.b[i], e1 = cr.e[i];
+      if (e0 >= e1) continue;
+      const int m = cr.m[i];
+      const unsigned long long bkey = s_bkey[i], tiny = s_tiny[i];
+      const int eb = s_eb[i];
       unsigned long long *hist = m == m0 ? s_h : sc.hist0 + size_t(m) * NB0 * 2;
-      int64_t e0, e1;
-      row_range(R, r, e0, e1);
       int64_t per = (e1 - e0 + 31) / 32;
       int64_t p0 = e0 + lane * per, p1 = min(p0 + per, e1);
       int cur = -1;
@@ -221,7 +321,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
       for (int64_t pb = p0; pb < p1; pb += 4) {
         unsigned long long keys[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) keys[u] = pb + u < p1 ? key_of(val, f32, pb + u) : 0ULL;
+        for (int u = 0; u < 4; ++u) keys[u] = pb + u < p1 ? key_t<T>(val[pb + u]) : 0ULL;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const unsigned long long key = keys[u];
@@ -231,7 +331,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
             continue;
           }
           if (key < tiny) continue;
-          unsigned long long q = qval(key, qs);
+          unsigned long long q = qval<T>(key, eb);
           if (!q) continue;
           int bk = bucket0(key, bkey);
           if (bk != cur) {
@@ -257,8 +357,8 @@ __global__ void __launch_bounds__(SEL_THREADS)
     __syncthreads();
     if (active[m0]) {
       unsigned long long *g = sc.hist0 + size_t(m0) * NB0 * 2;
-      for (int t = threadIdx.x; t < NB0; t += SEL_THREADS)
-        if (s_h[2 * t] | s_h[2 * t + 1]) add128(g + 2 * t, s_h[2 * t], s_h[2 * t + 1]);
+      for (int t2 = threadIdx.x; t2 < NB0; t2 += SEL_THREADS)
+        if (s_h[2 * t2] | s_h[2 * t2 + 1]) add128(g + 2 * t2, s_h[2 * t2], s_h[2 * t2 + 1]);
       if (threadIdx.x == 0 && s_min != ~0ULL) atomicMin(&sc.minabove[m0], s_min);
     }
     __syncthreads();
@@ -272,19 +372,21 @@ __device__ __forceinline__ void u128_add(unsigned long long &lo, unsigned long l
   hi += ahi + (lo < o ? 1ULL : 0ULL);
 }
 
-// (hi, lo) > 2^62 ?
-__device__ __forceinline__ bool exceeds(unsigned long long lo, unsigned long long hi) {
-  return hi != 0ULL || lo > ONE62;
+// (hi, lo) > Q ?
+__device__ __forceinline__ bool exceeds(unsigned long long lo, unsigned long long hi,
+                                        unsigned long long Q) {
+  return hi != 0ULL || lo > Q;
 }
 
 // The first of nbk buckets (128-bit sums h[2c], h[2c+1]) at which the running
-// sum, started at (lo, hi), exceeds 2^62, found by one warp: 32 buckets at a
+// sum, started at (lo, hi), exceeds Q = q(b), found by one warp: 32 buckets at a
 // time, lane c of a round holding bucket c and an inclusive prefix sum over
 // the round by shuffles. The sums are exact integers, so the crossing is the
 // one a serial walk finds. Returns the bucket (or -1, with (lo, hi) the total)
 // and leaves in (lo, hi) the sum of the buckets below it.
 __device__ __forceinline__ int warp_crossing(const unsigned long long *h, int nbk,
-                                             unsigned long long &lo, unsigned long long &hi) {
+                                             unsigned long long Q, unsigned long long &lo,
+                                             unsigned long long &hi) {
   const int lane = threadIdx.x & 31;
   for (int c0 = 0; c0 < nbk; c0 += 32) {
     const int c = c0 + lane;
@@ -298,7 +400,7 @@ __device__ __forceinline__ int warp_crossing(const unsigned long long *h, int nb
     }
     unsigned long long rlo = lo, rhi = hi;
     u128_add(rlo, rhi, plo, phi);
-    const unsigned over = __ballot_sync(0xffffffffu, c < nbk && exceeds(rlo, rhi));
+    const unsigned over = __ballot_sync(0xffffffffu, c < nbk && exceeds(rlo, rhi, Q));
     if (over) {
       const int f = __ffs(over) - 1;
       // the sum below bucket f: start + inclusive prefix of f - h[f]
@@ -313,7 +415,7 @@ __device__ __forceinline__ int warp_crossing(const unsigned long long *h, int nb
   return -1;
 }
 
-// One warp per matrix: the level-0 bucket where the exact sums cross 2^62.
+// One warp per matrix: the level-0 bucket where the exact sums cross Q.
 __global__ void k_sel_find0(int nb, const int *active, const MatScalars *ms, SelScratch sc) {
   const int m = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
@@ -325,81 +427,198 @@ __global__ void k_sel_find0(int nb, const int *active, const MatScalars *ms, Sel
     long long base = (long long)(bkey >> 48) - (NB0 - 1);
     if (base < 0) base = 0;
     unsigned long long lo = 0, hi = 0;
-    const int c = warp_crossing(sc.hist0 + size_t(m) * NB0 * 2, NB0, lo, hi);
+    const int c = warp_crossing(sc.hist0 + size_t(m) * NB0 * 2, NB0, ms[m].sel_q, lo, hi);
     if (c >= 0) {
       st.found = 1;
       st.prefix = (unsigned long long)(base + c) << 48;
-      st.below_lo = lo;
-      st.below_hi = hi;
+      st.below_lo = st.below0_lo = lo;
+      st.below_hi = st.below0_hi = hi;
     }
   }
   if (lane == 0) sc.st[m] = st;
 }
 
-// Candidates: the entries of the crossing bucket (top 16 bits of the key equal
-// to the prefix, key <= b), appended with one atomic per warp.
-__global__ void __launch_bounds__(SEL_THREADS)
-    k_sel_extract(int nb, SelRows R, const int *active, const void *val, int f32,
-                  const MatScalars *ms, SelScratch sc) {
-  (void)nb;
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t r = warp; r < R.nrows; r += nwarps) {
-    int m = row_mat(R, r);
-    if (!active[m] || !sc.st[m].found) continue;
-    unsigned long long bkey = (unsigned long long)__double_as_longlong(ms[m].b);
-    unsigned long long top = sc.st[m].prefix >> 48;
-    int64_t e0, e1;
-    row_range(R, r, e0, e1);
-    for (int64_t p0 = e0; p0 < e1; p0 += 32) {
-      int64_t p = p0 + lane;
-      bool take = false;
-      unsigned long long key = 0;
-      if (p < e1) {
-        key = key_of(val, f32, p);
-        take = key <= bkey && (key >> 48) == top;
+// Per-lane square sums of dropped entries: FP32 values exactly in FP32 pairs
+// (scaled by 2^96), FP64 values by FMA.
+struct DropSum {
+  float hi = 0.0f, lo = 0.0f;
+  double d = 0.0;
+  __device__ __forceinline__ void add(float x) { ff_add_sq48(x, hi, lo); }
+  __device__ __forceinline__ void add(double x) { d = __fma_rn(x, x, d); }
+  // the warp's total, valid in every lane
+  template <typename T>
+  __device__ __forceinline__ double warp_total() {
+    if constexpr (sizeof(T) == 4) {
+      if (!__any_sync(0xffffffffu, hi != 0.0f)) return 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        ff_add(hi, lo, h2, l2);
       }
-      unsigned mask = __ballot_sync(0xffffffffu, take);
-      if (!mask) continue;
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(sc.ncand, (unsigned long long)__popc(mask));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (take) {
-        unsigned long long i = base + __popc(mask & lt);
-        if (i < sc.cap) {  // past the room: counted only (the caller retries with more)
-          sc.cand[i] = key;
-          sc.cand_m[i] = m;
+      return ldexp(double(hi) + double(lo), -96);
+    } else {
+      if (!__any_sync(0xffffffffu, d != 0.0)) return 0.0;  // FP64 adds only for rows that drop
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      return d;
+    }
+  }
+};
+
+constexpr int EX_U = 4;  // 32-entry chunks of a row loaded at once
+
+// Candidates: the entries of the crossing bucket (top 16 bits of the key equal
+// to the prefix, 0 < key <= b), appended with one atomic per warp.
+// With cnt (the filter of a solve) the same pass also counts, per row, what
+// does not depend on where tau falls inside the crossing bucket: entries
+// above the bucket or above b are kept (cnt[r]); entries below it are
+// dropped, their squares summed into dropped[r] as in k_filter_count. A
+// matrix without a crossing already has its tau (the smallest key above b),
+// so every entry is decided here. k_sel_cand_keep adds the kept candidates
+// once tau is final; the dropped candidates' squares come from the select's
+// exact sums (k_sel_drop_fix). Rows of inactive matrices get 0 and 0.
+template <typename T>
+__global__ void __launch_bounds__(SEL_THREADS)
+    k_sel_extract(SelRows R, const int *active, const T *val, const MatScalars *ms,
+                  SelScratch sc, int64_t *cnt, double *dropped) {
+  __shared__ ChunkRows cr;
+  __shared__ unsigned long long s_bkey[RPC], s_top[RPC], s_tkey[RPC];
+  __shared__ int s_found[RPC];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = SEL_THREADS / 32;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t rpc = chunk_rows(R);
+  const int64_t nchunks = (R.nrows + rpc - 1) / rpc;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int64_t r0 = ch * rpc, r1 = min(r0 + rpc, R.nrows);
+    __syncthreads();  // the previous chunk's rows are read
+    int mt = 0;
+    const int t = stage_rows(R, active, r0, r1, cr, mt);
+    if (t >= 0) {
+      const bool found = active[mt] && sc.st[mt].found != 0;
+      const unsigned long long above = sc.minabove[mt];
+      s_found[t] = found;
+      s_bkey[t] = (unsigned long long)__double_as_longlong(ms[mt].b);
+      s_top[t] = found ? sc.st[mt].prefix >> 48 : 0ULL;
+      s_tkey[t] = above == ~0ULL ? INF_KEY : above;  // tau without a crossing
+    }
+    __syncthreads();
+    for (int i = warp; i < r1 - r0; i += nw) {
+      const int64_t r = r0 + i;
+      const bool found = s_found[i] != 0;
+      if (!cnt && !found) continue;
+      const int64_t e0 = cr.b[i], e1 = cr.e[i];  // empty for inactive matrices: 0 and 0
+      const unsigned long long bkey = s_bkey[i], top = s_top[i], tkey = s_tkey[i];
+      int c = 0;
+      DropSum ds;
+      for (int64_t p0 = e0; p0 < e1; p0 += 32 * EX_U) {
+        T x[EX_U];
+#pragma unroll
+        for (int u = 0; u < EX_U; ++u) {
+          const int64_t p = p0 + 32 * u + lane;
+          x[u] = p < e1 ? val[p] : T(0);  // a zero is neither counted nor dropped
         }
+        bool take[EX_U];
+#pragma unroll
+        for (int u = 0; u < EX_U; ++u) {
+          const unsigned long long key = key_t<T>(x[u]);
+          take[u] = false;
+          if (key == 0ULL) continue;
+          bool drop;
+          if (found) {
+            const unsigned long long t16 = key >> 48;
+            take[u] = key <= bkey && t16 == top;
+            if (take[u] || !cnt) continue;
+            drop = !(key <= INF_KEY && (t16 > top || key > bkey));
+          } else {
+            drop = !keep_key(key, tkey);
+          }
+          if (drop)
+            ds.add(x[u]);
+          else
+            ++c;
+        }
+        if (!found) continue;
+#pragma unroll
+        for (int u = 0; u < EX_U; ++u) {
+          const unsigned mask = __ballot_sync(0xffffffffu, take[u]);
+          if (!mask) continue;
+          unsigned long long base = 0;
+          if (lane == 0) base = atomicAdd(sc.ncand, (unsigned long long)__popc(mask));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (take[u]) {
+            const unsigned long long slot = base + __popc(mask & lt);
+            if (slot < sc.cap) {  // past the room: counted only (the caller retries with more)
+              sc.cand[slot] = key_t<T>(x[u]);
+              sc.cand_r[slot] = int(r);
+            }
+          }
+        }
+      }
+      if (!cnt) continue;
+      c = __reduce_add_sync(0xffffffffu, c);
+      const double d = ds.warp_total<T>();
+      if (lane == 0) {
+        cnt[r] = c;
+        dropped[r] = d;
       }
     }
   }
 }
 
-__global__ void k_sel_hist_digit(const MatScalars *ms, SelScratch sc, int shift) {
+// The kept candidates (key >= tau, tau final) into their rows' counts.
+__global__ void k_sel_cand_keep(SelRows R, const MatScalars *ms, SelScratch sc, int64_t *cnt) {
   unsigned long long total = *sc.ncand;
   if (total > sc.cap) total = sc.cap;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (unsigned long long)gridDim.x * blockDim.x) {
-    int m = sc.cand_m[i];
+    const int64_t r = sc.cand_r[i];
+    const unsigned long long tkey =
+        (unsigned long long)__double_as_longlong(ms[row_mat(R, r)].tau);
+    if (keep_key(sc.cand[i], tkey))
+      atomicAdd(reinterpret_cast<unsigned long long *>(cnt + r), 1ULL);
+  }
+}
+
+// sums[m] += the squares of the dropped candidates: the exact sum of their q
+// (the select's sum below tau minus its sum below the crossing bucket) in
+// grid steps 2^(2e - 62). A candidate's magnitude is at least b / sqrt(1.1
+// nnz) (a bucket spans a factor 2^(1/16)), so its q is above 2^62 / (1.1 nnz)
+// and its flooring to an integer is far below the FP64 rounding of the sum.
+__global__ void k_sel_drop_fix(int nb, const int *active, SelScratch sc, const MatScalars *ms,
+                               double *sums) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nb || !active[m] || !sc.st[m].found) return;
+  const SelState st = sc.st[m];
+  const unsigned long long lo = st.below_lo - st.below0_lo;
+  const unsigned long long hi = st.below_hi - st.below0_hi - (st.below_lo < st.below0_lo ? 1ULL : 0ULL);
+  const double q = __fma_rn(double(hi), 18446744073709551616.0, double(lo));
+  sums[m] = __dadd_rn(sums[m], ldexp(q, 2 * (ms[m].sel_e - 1023) - 62));
+}
+
+__global__ void k_sel_hist_digit(SelRows R, const MatScalars *ms, SelScratch sc, int shift) {
+  unsigned long long total = *sc.ncand;
+  if (total > sc.cap) total = sc.cap;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    int m = row_mat(R, sc.cand_r[i]);
     unsigned long long key = sc.cand[i];
     if ((key >> (shift + 8)) != (sc.st[m].prefix >> (shift + 8))) continue;
     int d = int((key >> shift) & 255ULL);
-    unsigned long long q = qval(key, ms[m].qs);
+    unsigned long long q = qval<double>(key, ms[m].sel_e);
     if (q) add128(sc.hdig + (size_t(m) * NDIG + d) * 2, q, 0ULL);
   }
 }
 
-// One warp per matrix: the digit at `shift` where the sums cross 2^62.
-__global__ void k_sel_find_digit(int nb, SelScratch sc, int shift) {
+// One warp per matrix: the digit at `shift` where the sums cross Q.
+__global__ void k_sel_find_digit(int nb, const MatScalars *ms, SelScratch sc, int shift) {
   const int m = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
   if (m >= nb) return;
   SelState &st = sc.st[m];
   if (!st.found) return;
   unsigned long long lo = st.below_lo, hi = st.below_hi;
   unsigned long long *h = sc.hdig + size_t(m) * NDIG * 2;
-  const int d = warp_crossing(h, NDIG, lo, hi);
+  const int d = warp_crossing(h, NDIG, ms[m].sel_q, lo, hi);
   __syncwarp();
   // the buckets are read: cleared here for the next digit, instead of a memset
   for (int c = threadIdx.x & 31; c < 2 * NDIG; c += 32) h[c] = 0ULL;
@@ -423,25 +642,6 @@ __global__ void k_sel_final(int nb, const int *active, SelScratch sc, MatScalars
 }
 
 // ------------------------------------------------------------ filter
-// (hi, lo) += x^2 for FP32 x, exactly: the square's rounding error comes from
-// an FMA and the sum's from TwoSum; all in FP32, which this GPU runs at 64x
-// its FP64 rate. Inputs are scaled by 2^48 (exact), so that squares of
-// entries from 2^-111 to 2^16 stay normal FP32 numbers.
-__device__ __forceinline__ void ff_add_sq48(float x, float &hi, float &lo) {
-  const float y = __fmul_rn(x, 281474976710656.0f);  // 2^48
-  const float p = __fmul_rn(y, y), e = __fmaf_rn(y, y, -p);
-  const float s = __fadd_rn(hi, p), bb = __fsub_rn(s, hi);
-  lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb)), e));
-  hi = s;
-}
-
-__device__ __forceinline__ void ff_add(float &hi, float &lo, float h2, float l2) {
-  const float s = __fadd_rn(hi, h2), bb = __fsub_rn(s, hi);
-  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
-  lo = __fadd_rn(__fadd_rn(lo, l2), err);
-  hi = s;
-}
-
 __global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
                                const int64_t *rs, const int64_t *re, const void *val, int f32,
                                const MatScalars *ms, int64_t *cnt, double *dropped) {
@@ -450,21 +650,20 @@ __global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
   int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t r = warp; r < n; r += nwarps) {
     int m = seg[r];
-    double tau = ms[m].tau;
+    const unsigned long long tkey = (unsigned long long)__double_as_longlong(ms[m].tau);
     int c = 0;
     double d2 = 0.0;
     if (active[m] && f32) {
-      // the smallest float >= tau: for a float x, |x| >= tf exactly when |x| >= tau
-      const float tf = __double2float_ru(tau);
       const float *v = static_cast<const float *>(val);
       float hi = 0.0f, lo = 0.0f;  // dropped squares, scaled by 2^96
       const int64_t pe = re[r];
 #pragma unroll 4
       for (int64_t p = rs[r] + lane; p < pe; p += 32) {
         const float x = v[p];
-        if (fabsf(x) >= tf && x != 0.0f)
+        const unsigned long long key = key_f32(x);
+        if (keep_key(key, tkey))
           ++c;
-        else if (x != 0.0f)
+        else if (key != 0ULL)
           ff_add_sq48(x, hi, lo);
       }
       c = __reduce_add_sync(0xffffffffu, c);
@@ -483,7 +682,7 @@ __global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
 #pragma unroll 4
       for (int64_t p = rs[r] + lane; p < pe; p += 32) {
         double x = v[p];
-        if (fabs(x) >= tau && x != 0.0)
+        if (keep_key(key_f64(x), tkey))
           ++c;
         else
           d2 = __fma_rn(x, x, d2);
@@ -501,44 +700,56 @@ __global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
   }
 }
 
-__global__ void k_filter_write(int64_t n, const int32_t *seg, const int *active,
-                               const int64_t *rs, const int64_t *re, const int32_t *col,
-                               const void *val, int f32,
-                               const MatScalars *ms, const int64_t *orp, int32_t *ocol,
-                               void *oval) {
-  int lane = lane_id();
+template <typename T>
+__global__ void __launch_bounds__(SEL_THREADS)
+    k_filter_write(int64_t n, const int32_t *seg, const int *active, const int64_t *rs,
+                   const int64_t *re, const int32_t *col, const T *val, const MatScalars *ms,
+                   const int64_t *orp, int32_t *ocol, T *oval) {
+  __shared__ ChunkRows cr;
+  __shared__ int64_t s_out[RPC], s_oend[RPC];
+  __shared__ unsigned long long s_tkey[RPC];
+  const int lane = lane_id(), warp = threadIdx.x >> 5, nw = SEL_THREADS / 32;
   const unsigned lt = (1u << lane) - 1u;
-  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t r = warp; r < n; r += nwarps) {
-    int m = seg[r];
-    if (!active[m]) continue;
-    double tau = ms[m].tau;
-    float tf = __double2float_ru(tau);  // |x| >= tf  <=>  |x| >= tau for a float x
-    int64_t out = orp[r];
-    int64_t b = rs[r], e = re[r];
-    for (int64_t p0 = b; p0 < e; p0 += 32) {
-      int64_t p = p0 + lane;
-      bool keep = false;
-      if (p < e) {
-        if (f32) {
-          float x = static_cast<const float *>(val)[p];
-          keep = fabsf(x) >= tf && x != 0.0f;
-        } else {
-          double x = static_cast<const double *>(val)[p];
-          keep = fabs(x) >= tau && x != 0.0;
+  const SelRows R{n, seg, rs, re, 0};
+  const int64_t nchunks = (n + RPC - 1) / RPC;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int64_t r0 = ch * RPC, r1 = min(r0 + RPC, n);
+    __syncthreads();  // the previous chunk's rows are read
+    int mt = 0;
+    const int t = stage_rows(R, active, r0, r1, cr, mt);
+    if (t >= 0) {
+      s_out[t] = orp[r0 + t];
+      s_oend[t] = orp[r0 + t + 1];
+      s_tkey[t] = (unsigned long long)__double_as_longlong(ms[mt].tau);
+    }
+    __syncthreads();
+    for (int i = warp; i < r1 - r0; i += nw) {
+      // the row's room from the counts; the same rule decides both, and the
+      // bound keeps a write inside the row whatever the values are
+      const unsigned long long tkey = s_tkey[i];
+      int64_t out = s_out[i];
+      const int64_t oend = s_oend[i], b = cr.b[i], e = cr.e[i];
+      for (int64_t p0 = b; p0 < e; p0 += 32 * EX_U) {
+        T x[EX_U];
+        int32_t c[EX_U];
+#pragma unroll
+        for (int u = 0; u < EX_U; ++u) {
+          const int64_t p = p0 + 32 * u + lane;
+          x[u] = p < e ? val[p] : T(0);  // a zero is never kept
+          c[u] = p < e ? col[p] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < EX_U; ++u) {
+          const bool keep = keep_key(key_t<T>(x[u]), tkey);
+          const unsigned m32 = __ballot_sync(0xffffffffu, keep);
+          const int64_t pos = out + __popc(m32 & lt);
+          if (keep && pos < oend) {
+            ocol[pos] = c[u];
+            oval[pos] = x[u];
+          }
+          out += __popc(m32);
         }
       }
-      unsigned m32 = __ballot_sync(0xffffffffu, keep);
-      if (keep) {
-        int64_t pos = out + __popc(m32 & lt);
-        ocol[pos] = col[p];
-        if (f32)
-          static_cast<float *>(oval)[pos] = static_cast<const float *>(val)[p];
-        else
-          static_cast<double *>(oval)[pos] = static_cast<const double *>(val)[p];
-      }
-      out += __popc(m32);
     }
   }
 }
@@ -580,18 +791,23 @@ const unsigned long long *select_cand_count(void *scratch, int nb) {
 
 void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *active,
                          const void *val, int val_f32, MatScalars *ms, void *scratch,
-                         cudaStream_t s) {
+                         int64_t *cnt, double *dropped, cudaStream_t s) {
   SelScratch sc = carve(scratch, nb, cand_cap);
   SGN_CUDA(cudaMemsetAsync(sc.hist0, 0, size_t(nb) * NB0 * 2 * 8, s));
   SGN_CUDA(cudaMemsetAsync(sc.minabove, 0xff, size_t(nb) * 8, s));
   k_sel_prepare<<<(nb + 127) / 128, 128, 0, s>>>(nb, ms);
   SGN_LAUNCH_CHECK();
-  int64_t rpc = R.rs ? ROWS_PER_CHUNK : 1;
+  const int64_t rpc = R.rs ? RPC : 8;
   {
     ProfScope ps(KC_SEL_HIST, s, 0.0, 0.0);
     if (R.nrows > 0) {
-      k_sel_hist0<<<grid_for((R.nrows + rpc - 1) / rpc, 1, 152 * 8), SEL_THREADS, 0, s>>>(
-          nb, R, active, val, val_f32, ms, sc);
+      const int g = grid_for((R.nrows + rpc - 1) / rpc, 1, 152 * 8);
+      if (val_f32)
+        k_sel_hist0<float><<<g, SEL_THREADS, 0, s>>>(R, active, static_cast<const float *>(val),
+                                                     ms, sc);
+      else
+        k_sel_hist0<double><<<g, SEL_THREADS, 0, s>>>(R, active,
+                                                      static_cast<const double *>(val), ms, sc);
       SGN_LAUNCH_CHECK();
     }
     k_sel_find0<<<(nb + 3) / 4, 128, 0, s>>>(nb, active, ms, sc);
@@ -600,8 +816,13 @@ void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *
   {
     ProfScope ps(KC_SEL_EXTRACT, s, 0.0, 0.0);
     if (R.nrows > 0) {
-      k_sel_extract<<<grid_for(R.nrows, 8, 152 * 8), SEL_THREADS, 0, s>>>(nb, R, active, val,
-                                                                          val_f32, ms, sc);
+      const int g = grid_for((R.nrows + rpc - 1) / rpc, 1, 152 * 8);
+      if (val_f32)
+        k_sel_extract<float><<<g, SEL_THREADS, 0, s>>>(R, active, static_cast<const float *>(val),
+                                                       ms, sc, cnt, dropped);
+      else
+        k_sel_extract<double><<<g, SEL_THREADS, 0, s>>>(
+            R, active, static_cast<const double *>(val), ms, sc, cnt, dropped);
       SGN_LAUNCH_CHECK();
     }
   }
@@ -611,12 +832,22 @@ void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *
   SGN_CUDA(cudaMemsetAsync(sc.hdig, 0, size_t(nb) * NDIG * 2 * 8, s));
   for (int level = 0; level < 6; ++level) {
     int shift = 40 - 8 * level;
-    k_sel_hist_digit<<<152 * 4, 256, 0, s>>>(ms, sc, shift);
+    k_sel_hist_digit<<<152 * 4, 256, 0, s>>>(R, ms, sc, shift);
     SGN_LAUNCH_CHECK();
-    k_sel_find_digit<<<(nb + 3) / 4, 128, 0, s>>>(nb, sc, shift);
+    k_sel_find_digit<<<(nb + 3) / 4, 128, 0, s>>>(nb, ms, sc, shift);
     SGN_LAUNCH_CHECK();
   }
   k_sel_final<<<(nb + 127) / 128, 128, 0, s>>>(nb, active, sc, ms);
+  SGN_LAUNCH_CHECK();
+  if (cnt) {
+    k_sel_cand_keep<<<152 * 2, 256, 0, s>>>(R, ms, sc, cnt);
+    SGN_LAUNCH_CHECK();
+  }
+}
+
+void launch_select_drop_fix(int nb, const int *active, void *scratch, const MatScalars *ms,
+                            double *sums, cudaStream_t s) {
+  k_sel_drop_fix<<<(nb + 127) / 128, 128, 0, s>>>(nb, active, carve(scratch, nb, 1), ms, sums);
   SGN_LAUNCH_CHECK();
 }
 
@@ -634,8 +865,14 @@ void launch_filter_write(int64_t n, const int32_t *seg, const int *active, const
                          const MatScalars *ms, const int64_t *orp, int32_t *ocol, void *oval,
                          cudaStream_t s) {
   if (n == 0) return;
-  k_filter_write<<<grid_for(n, 8), 256, 0, s>>>(n, seg, active, rs, re, col, val, val_f32, ms,
-                                                 orp, ocol, oval);
+  if (val_f32)
+    k_filter_write<float><<<grid_for(n, RPC, 152 * 8), SEL_THREADS, 0, s>>>(
+        n, seg, active, rs, re, col, static_cast<const float *>(val), ms, orp, ocol,
+        static_cast<float *>(oval));
+  else
+    k_filter_write<double><<<grid_for(n, RPC, 152 * 8), SEL_THREADS, 0, s>>>(
+        n, seg, active, rs, re, col, static_cast<const double *>(val), ms, orp, ocol,
+        static_cast<double *>(oval));
   SGN_LAUNCH_CHECK();
 }
 

@@ -1030,7 +1030,9 @@ struct Solver {
 
   // Threshold (step a5) of each active matrix over the values of `in`, into
   // the device scalars: EXACT by the radix select, BOUND by b/sqrt(nnz) with
-  // nnz the last product's per-matrix count (launch_seg_count).
+  // nnz the last product's per-matrix count (launch_seg_count). EXACT also
+  // leaves the filter's per-row counts and dropped squares in w.cnt and
+  // w.dropped (filter_rows reads them instead of counting again).
   // NMF (Alg. 3.1.1) in place of the Newton-Schulz update, FP64 stage: for
   // every updating matrix the dense inverse of its iterate, Xbar = (X +
   // X^-1) / 2 into full rows of slots of st.Xb and the budget of Eq. (1.13).
@@ -1127,10 +1129,12 @@ struct Solver {
       const int64_t big = int64_t(1) << 28;
       w.sel_cap = full_room || in.slots <= big ? in.slots : std::max(big, in.slots / 16);
       w.sel.ensure(select_scratch_bytes(nb, w.sel_cap), s);
+      w.dropped.ensure(sizeof(double) * size_t(N > 0 ? N : 1), s);
+      w.cnt.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
       SelRows R{N, st.d_seg.template as<int32_t>(), in.rs.template as<int64_t>(),
                 in.re.template as<int64_t>(), 0};
       launch_select_exact(nb, R, w.sel_cap, d_act, in.val.p, is_f32<T>(), w.ms.as<MatScalars>(),
-                          w.sel.p, s);
+                          w.sel.p, w.cnt.as<int64_t>(), w.dropped.as<double>(), s);
     } else {
       ProfScope psel(KC_SELECT, s);
       launch_store_nnz_bar(nb, w.nnzc.as<int64_t>(), w.ms.as<MatScalars>(), s);
@@ -1150,16 +1154,23 @@ struct Solver {
     w.cnt.ensure(sizeof(int64_t) * size_t(N > 0 ? N : 1), s);
     out.rp.ensure(sizeof(int64_t) * size_t(N + 1), s);
     w.eoff.ensure(sizeof(int64_t) * size_t(nb + 1), s);
+    const bool exact = o.filter == SIGN_FILTER_EXACT;
     for (;;) {
       {
-        ProfScope pf(KC_FILTER, s, 0.0, double(in.slots) * sizeof(T) + 24.0 * double(N));
-        launch_filter_count(N, st.d_seg.template as<int32_t>(), d_act,
-                            in.rs.template as<int64_t>(), in.re.template as<int64_t>(), in.val.p,
-                            is_f32<T>(), w.ms.as<MatScalars>(), w.cnt.as<int64_t>(),
-                            w.dropped.as<double>(), s);
+        // EXACT: the select counted already (all but the crossing buckets' squares)
+        ProfScope pf(KC_FILTER, s, 0.0,
+                     (exact ? 0.0 : double(in.slots) * sizeof(T)) + 24.0 * double(N));
+        if (!exact)
+          launch_filter_count(N, st.d_seg.template as<int32_t>(), d_act,
+                              in.rs.template as<int64_t>(), in.re.template as<int64_t>(),
+                              in.val.p, is_f32<T>(), w.ms.as<MatScalars>(), w.cnt.as<int64_t>(),
+                              w.dropped.as<double>(), s);
         launch_scan(N, w.cnt.as<int64_t>(), out.d_rp(), w.scan_tmp.as<int64_t>(), s);
         launch_seg_reduce(nb, st.d_moff.template as<int64_t>(), w.dropped.as<double>(), 1,
                           w.sums.as<double>(), s);
+        if (exact)
+          launch_select_drop_fix(nb, d_act, w.sel.p, w.ms.as<MatScalars>(), w.sums.as<double>(),
+                                 s);
         launch_gather_offsets(nb, st.d_moff.template as<int64_t>(), out.d_rp(),
                               w.eoff.as<int64_t>(), s);
       }
@@ -1167,7 +1178,7 @@ struct Solver {
       d2h(hm.tot, out.d_rp() + N, 1, s);
       d2h(hm.ms, w.ms.p, size_t(nb), s);
       d2h(hm.dsum, w.sums.p, size_t(nb), s);
-      const bool capped = o.filter == SIGN_FILTER_EXACT && w.sel_cap < in.slots;
+      const bool capped = exact && w.sel_cap < in.slots;
       if (capped) d2h(reinterpret_cast<unsigned long long *>(hm.tot + 3),
                       select_cand_count(w.sel.p, nb), 1, s);
       wait();

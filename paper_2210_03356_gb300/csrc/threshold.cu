@@ -45,7 +45,7 @@ extern "C" sign_status sign_threshold_exact(const double *val, int64_t nnz, doub
     Small *d = small.as<Small>();
     scratch.ensure(select_scratch_bytes(1, nnz), s);
     SelRows R{(nnz + kFlatRow - 1) / kFlatRow, nullptr, nullptr, nullptr, nnz};
-    launch_select_exact(1, R, nnz, d->active, dval, 0, &d->ms, scratch.p, s);
+    launch_select_exact(1, R, nnz, d->active, dval, 0, &d->ms, scratch.p, nullptr, nullptr, s);
     SGN_CUDA(cudaMemcpyAsync(&hs, small.p, sizeof(Small), cudaMemcpyDeviceToHost, s));
     SGN_CUDA(cudaStreamSynchronize(s));
     *tau_out = hs.ms.tau;

@@ -106,7 +106,7 @@ extern "C" sign_status sign_threshold_exact_noalloc(const double *val, int64_t n
     SGN_CUDA(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     // the select kernels clear their histograms and state themselves
     SelRows R{(nnz + kFlatRow - 1) / kFlatRow, nullptr, nullptr, nullptr, nnz};
-    launch_select_exact(1, R, nnz, d->active, val, 0, &d->ms, base + kHeadBytes, s);
+    launch_select_exact(1, R, nnz, d->active, val, 0, &d->ms, base + kHeadBytes, nullptr, nullptr, s);
     SGN_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
     SGN_CUDA(cudaStreamSynchronize(s));
     *tau_out = h.ms.tau;

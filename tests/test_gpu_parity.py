@@ -427,3 +427,22 @@ def test_threshold_exact_edge_cases(sg, orc):
         assert sg.threshold_exact(v, b) == _tau_ref(orc, v, b)
     with pytest.raises(Exception):
         sg.threshold_exact(v, -1.0)
+
+
+def test_threshold_exact_boundary(sg, orc):
+    """Squares that add up to exactly b^2 fit the budget (Alg. 3.2.1 step 4:
+    dropped while the sum stays within it); one more tips it over. Every
+    square here is exact in FP64, so the oracle's sums are exact too."""
+    cases = [
+        ([0.5] * 4 + [2.0], 1.0),          # 4 x 0.25 = 1 = b^2: all fit
+        ([0.5] * 5 + [2.0], 1.0),          # 1.25 > 1: the 0.5 group is kept
+        ([0.375] * 4 + [1.0], 0.75),       # 4 x 0.140625 = 0.5625 = b^2
+        ([0.375] * 4 + [2.0 ** -20, 1.0], 0.75),  # the same plus a small square
+        ([0.25] * 16 + [0.25 + 2.0 ** -54], 1.0),  # 16 x 1/16 = 1, then just above
+        ([3.0 * 2.0 ** -1060] * 3, 2.0 ** -1055),  # subnormal values and budget
+        ([1e-300] * 7 + [1e300], 3e-300),
+    ]
+    for v, b in cases:
+        v = np.array(v, dtype=np.float64)
+        for w in (v, -v[::-1]):
+            assert sg.threshold_exact(w, b) == _tau_ref(orc, w, b), (v, b)
