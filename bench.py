@@ -618,6 +618,54 @@ def variants_leg(sg, mats, reps: int = 2):
     return out
 
 
+def tune_leg(sg, mats, reps: int = 3):
+    """sign_tune_batch on two workloads: the banded batch as benchmarked and a
+    Laplacian-heavy batch (shifted 2-D Laplacians, m = 24..46, and 3-D ones,
+    m = 8..13). Per workload: the schedule the tuner chose, its own best times
+    of a batch solve (base schedule and chosen one, host wall time), then the
+    solves/s of the default and of the chosen schedule (CUDA events, median of
+    reps after a warm-up). Every schedule gives the same results bit for bit."""
+    import torch
+    lap = [w.laplacian(m, 2) for m in range(24, 48, 2)] + [w.laplacian(m, 3) for m in range(8, 14)]
+    out = []
+    for label, sub in (("banded batch, mixed, EXACT, tol 1e-8", mats),
+                       ("Laplacian-heavy batch: 12 shifted 2-D (m 24..46) + 6 shifted 3-D "
+                        "(m 8..13) Laplacians, mixed, EXACT, tol 1e-8", lap)):
+        b = sg.Batch(sub)
+        try:
+            base = sg.default_opts(tol=TOL, filter="exact", prec="mixed")
+            best, rep = b.tune(base, reps=2, force=True)
+
+            def median_ms(o):
+                b.solve(o)
+                ms = []
+                for _ in range(reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    b.solve(o)
+                    e1.record()
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                return statistics.median(ms)
+
+            m0, m1 = median_ms(base), median_ms(best)
+            out.append({"workload": label, "matrices": len(sub),
+                        "chosen": {"band_min_eff": best.band_min_eff,
+                                   "group_margin": best.group_margin,
+                                   "pair_rows": best.pair_rows},
+                        "default": {"band_min_eff": base.band_min_eff,
+                                    "group_margin": base.group_margin,
+                                    "pair_rows": base.pair_rows},
+                        "tuner_solves_timed": rep["timed"],
+                        "tuner_ms_base": rep["ms_base"], "tuner_ms_best": rep["ms_best"],
+                        "solves_per_s_default": len(sub) / (m0 / 1e3),
+                        "solves_per_s_tuned": len(sub) / (m1 / 1e3), "gain": m0 / m1})
+        finally:
+            b.close()
+    return out
+
+
 # ---------------------------------------------------------------------- clocks
 class Clocks:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -873,34 +921,51 @@ def main():
         if rank == 0:
             line["err_vs_fp64_oracle"] = result_errors(mats, last, ref64)
 
-        # unfiltered FP64 Newton-Schulz on the same GPU, on a sample of the batch
-        idx = sample_indices(args.unfiltered_sample)
-        sub = sg.Batch([mats[i] for i in idx])
+        # unfiltered FP64 Newton-Schulz on the same GPU: two disjoint samples of
+        # the batch (every 64th matrix from 0 and from 32), each batch call
+        # timed three times, filtered (the benchmarked options) and unfiltered
         o_f = sg.default_opts(tol=TOL, filter="exact", prec="mixed")
         o_u = sg.default_opts(tol=TOL, filter="none", prec="fp64")
-        sub.solve(o_f)
-        barrier()
-        t0 = time.perf_counter()
-        sub.solve(o_f)
-        barrier()
-        tf = time.perf_counter() - t0
-        sub.solve(o_u)  # warm-up of the unfiltered run
-        barrier()
-        t0 = time.perf_counter()
-        ru = sub.solve(o_u)
-        barrier()
-        tu = time.perf_counter() - t0
-        assert all(s == sg.SIGN_OK for s, _, _ in ru)
-        sub.close()
+        samples = []
+        for off in (0, BATCH // (2 * args.unfiltered_sample)):
+            idx = sample_indices(args.unfiltered_sample, off)
+            sub = sg.Batch([mats[i] for i in idx])
+            times = {}
+            for name, o in (("filtered", o_f), ("unfiltered", o_u)):
+                sub.solve(o)  # warm-up
+                ts = []
+                for _ in range(3):
+                    barrier()
+                    t0 = time.perf_counter()
+                    r = sub.solve(o)
+                    barrier()
+                    ts.append(time.perf_counter() - t0)
+                    assert all(st == sg.SIGN_OK for st, _, _ in r)
+                times[name] = ts
+            sub.close()
+            tf, tu = statistics.median(times["filtered"]), statistics.median(times["unfiltered"])
+            samples.append({"indices": idx, "filtered_mixed_solves_per_s": len(idx) / tf,
+                            "unfiltered_fp64_solves_per_s": len(idx) / tu,
+                            "speedup_median": tu / tf,
+                            "speedup_range": [min(times["unfiltered"]) / max(times["filtered"]),
+                                              max(times["unfiltered"]) / min(times["filtered"])]})
+        tf_all = sum(len(x["indices"]) / x["filtered_mixed_solves_per_s"] for x in samples)
+        tu_all = sum(len(x["indices"]) / x["unfiltered_fp64_solves_per_s"] for x in samples)
+        n_all = sum(len(x["indices"]) for x in samples)
         line["vs_unfiltered_fp64"] = {
-            "sample": f"{len(idx)} of the 512 matrices (every {BATCH // len(idx)}th), one batch call each",
-            "filtered_mixed_solves_per_s": len(idx) / tf,
-            "unfiltered_fp64_solves_per_s": len(idx) / tu, "speedup": tu / tf}
+            "sample": f"2 x {args.unfiltered_sample} of the 512 matrices (every "
+                      f"{BATCH // args.unfiltered_sample}th from 0 and from "
+                      f"{BATCH // (2 * args.unfiltered_sample)}), one batch call per sample, "
+                      "median of 3 timed calls after a warm-up",
+            "filtered_mixed_solves_per_s": n_all / tf_all,
+            "unfiltered_fp64_solves_per_s": n_all / tu_all, "speedup": tu_all / tf_all,
+            "samples": samples}
         if cpu:
             line["cpu_baseline"] = cpu
     batch.close()
     if args.legs == "all" and rank == 0:
         line["variants"] = variants_leg(sg, mats)
+        line["tuning"] = tune_leg(sg, mats)
     if args.legs == "all" and args.serve_seconds > 0 and rank == 0:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
         line["serving"] = serve_leg(sg, rates, args.serve_seconds)

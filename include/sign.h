@@ -110,6 +110,21 @@ typedef struct {
                           by 8 power steps on X^T X from (1,...,1)/sqrt(n);
                           0 = RMS Frobenius ||X||_F/sqrt(n); 0             */
   int method;          /* sign_method; SIGN_METHOD_NSF                       */
+  /* Schedule: which kernel runs which rows. It changes the speed; every
+   * schedule gives the same products bit for bit (each still adds its terms
+   * in ascending k), and so the same iterates and results, except where a
+   * residual within a rounding of a threshold (tol, fp32_until,
+   * switch_resid) is summed in another order. sign_tune_batch picks one by
+   * timing. */
+  double band_min_eff; /* an FP32 group of 16 rows runs as a band tile when its
+                          multiply-adds fill at least this fraction of the
+                          tile's FMA slots (>= 0); 0.08                     */
+  double group_margin; /* an FP64 row moves to 16 or 8 lanes when that raises
+                          the lanes' use in a k-step by more than this; < 0
+                          keeps every row on 32 lanes; 0.05                */
+  int pair_rows;       /* 1: FP32 rows that fit half a warp's accumulator run
+                          two per warp, sharing their passes over B; 0: one
+                          row per warp; 1                                  */
 } sign_opts;
 
 /* Per-iteration record, filled by sign_solve when non-NULL. The arrays are
@@ -169,6 +184,29 @@ sign_status sign_solve(sign_t h, const sign_opts *o, sign_info *info);
  * array of `count`. Returns SIGN_OK if the batch ran (per-matrix outcomes are
  * in infos[i].status) or an error that applies to the whole call. */
 sign_status sign_solve_batch(sign_t *hs, int count, const sign_opts *o, sign_info *infos);
+
+/* Schedule tuning for a batch. */
+typedef struct {
+  int timed;          /* out: batch solves timed (0 when the choice was cached) */
+  int cached;         /* out: 1 if the schedule came from the cache             */
+  double ms_base;     /* out: best time of a batch solve with base's schedule
+                         (0 when cached)                                       */
+  double ms_best;     /* out: best time with the chosen schedule (0 when cached) */
+} sign_tune_report;
+
+/* Times schedules on this batch and writes the fastest into *best (a copy of
+ * *base with band_min_eff, group_margin and pair_rows chosen). The sweep goes
+ * one field at a time from base's values: band_min_eff over {0.02, 0.04,
+ * 0.08, 0.16, 0.32}, group_margin over {-1, 0, 0.05, 0.15}, pair_rows over
+ * {0, 1}; each candidate is timed as `reps` (>= 1) full sign_solve_batch
+ * calls, keeping the best time. The choice is cached per workload key (the
+ * precision mode, filter, method, count rounded to a power of two, and the
+ * powers of two of the mean n and of the mean nnz per row), and a later call
+ * with an equal key returns it without timing unless force = 1. The handles
+ * are left with the result of the last solve (the same for every schedule).
+ * rep may be NULL. Errors of a solve are returned as they are. */
+sign_status sign_tune_batch(sign_t *hs, int count, const sign_opts *base, int reps, int force,
+                            sign_opts *best, sign_tune_report *rep);
 
 /* Copies the result out. Call first with row_ptr = col = val = NULL to get
  * *nnz_out; then with buffers of n+1, nnz and nnz elements (device pointers if

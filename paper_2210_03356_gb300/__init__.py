@@ -343,6 +343,19 @@ class Batch:
             raise SignError(st, "sign_solve_batch")
         return [(s.status, s.iters, s.resid) for s in iarr]
 
+    def tune(self, opts, reps: int = 1, force: bool = False):
+        """sign_tune_batch: the fastest schedule for this batch (timed, or from
+        the cache). Returns (opts with the chosen schedule, report dict)."""
+        best = N.sign_opts()
+        rep = N.sign_tune_report()
+        st = load().sign_tune_batch(self.arr, len(self.handles), C.byref(opts), int(reps),
+                                    int(force), C.byref(best), C.byref(rep))
+        if st != SIGN_OK:
+            raise SignError(st, "sign_tune_batch")
+        return best, {"timed": rep.timed, "cached": bool(rep.cached), "ms_base": rep.ms_base,
+                      "ms_best": rep.ms_best, "band_min_eff": best.band_min_eff,
+                      "group_margin": best.group_margin, "pair_rows": best.pair_rows}
+
     def traces(self) -> list:
         """The per-iteration records of the last solve(trace_cap > 0), one dict per matrix."""
         if self.infos is None:

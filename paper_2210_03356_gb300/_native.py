@@ -24,7 +24,14 @@ class sign_opts(C.Structure):
                 ("switch_resid", C.c_double), ("max_iter", C.c_int), ("prec", C.c_int),
                 ("fp32_until", C.c_double), ("dense_frac", C.c_double), ("scale_1norm", C.c_int),
                 ("div_limit", C.c_double), ("dense64_min_n", C.c_int), ("fp32_band", C.c_int),
-                ("filter_t", C.c_int), ("budget_norm", C.c_int), ("method", C.c_int)]
+                ("filter_t", C.c_int), ("budget_norm", C.c_int), ("method", C.c_int),
+                ("band_min_eff", C.c_double), ("group_margin", C.c_double),
+                ("pair_rows", C.c_int)]
+
+
+class sign_tune_report(C.Structure):
+    _fields_ = [("timed", C.c_int), ("cached", C.c_int), ("ms_base", C.c_double),
+                ("ms_best", C.c_double)]
 
 
 class sign_info(C.Structure):
@@ -77,6 +84,8 @@ SIGNATURES = {
     "sign_solve": (C.c_int, [sign_t, C.POINTER(sign_opts), C.POINTER(sign_info)]),
     "sign_solve_batch": (C.c_int, [C.POINTER(sign_t), C.c_int, C.POINTER(sign_opts),
                                    C.POINTER(sign_info)]),
+    "sign_tune_batch": (C.c_int, [C.POINTER(sign_t), C.c_int, C.POINTER(sign_opts), C.c_int,
+                                  C.c_int, C.POINTER(sign_opts), C.POINTER(sign_tune_report)]),
     "sign_get_csr": (C.c_int, [sign_t, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_int]),
     "sign_destroy": (None, [sign_t]),

@@ -126,11 +126,14 @@ constexpr int RC_COUNTERS = 2 * RC_N;  // ints in the counters array
 // counters[RC_QUEUE + c] the work-queue head of its kernel (all zeroed by the
 // caller). groups: 0 keeps every warp-sized row on 32 lanes; 1 (FP64
 // products, bound by the FP64 pipe) picks 32, 16 or 8 lanes by lane
-// utilisation; 2 (FP32 products) lists every row of extent <= 512 in the
+// utilisation, a narrower group only when it raises the use by more than
+// group_margin; 2 (FP32 products) lists every row of extent <= 512 in the
 // 16-lane class, whose FP32 kernel runs the rows two per warp with shared
 // passes over B. band (FP32 products only): aligned groups of 16 rows of one
-// matrix whose band tile costs fewer instructions than the row-wise product
-// (by the work estimate in k_bounds) go to the band list instead, and their
+// matrix whose multiply-adds fill at least band_min_eff of the band tile's
+// FMA slots (by the work estimate in k_bounds; at the default 0.08 the tile
+// costs fewer instructions than the row-wise product) go to the band list
+// instead, and their
 // multiply-adds are added to *band_work (nullable; zeroed by the caller);
 // bandrow (nullable) gets 1 for the rows of band tiles, 0 for the others.
 // binfo: scratch of n records (B's rows' first/last column and length; B has
@@ -139,10 +142,10 @@ constexpr int RC_COUNTERS = 2 * RC_N;  // ints in the counters array
 // path; their rows get no sparse work, and in MODE_UPDATE a whole row of
 // slots (moff gives the matrix sizes).
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
-                   int mode, int groups, int band, const int *dslot, const int64_t *moff,
-                   int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists, int *counters,
-                   double *work, double *band_work, unsigned char *bandrow, int4 *binfo,
-                   cudaStream_t s);
+                   int mode, int groups, float group_margin, int band, float band_min_eff,
+                   const int *dslot, const int64_t *moff, int32_t *lo, int32_t *len,
+                   int64_t *ub, int32_t *lists, int *counters, double *work,
+                   double *band_work, unsigned char *bandrow, int4 *binfo, cudaStream_t s);
 
 // Band layout of the rows of an FP32 operand: row k's values dense over the
 // columns [fc[k], fc[k] + nf[k]) (fc and nf multiples of 4, holes +0) at

@@ -90,10 +90,10 @@ __device__ __forceinline__ int64_t lower_bound(const int32_t *a, int64_t lo, int
 
 constexpr int BOUNDS_TILE = 256;  // rows per CTA of k_bounds; lists keep this order
 static_assert(BOUNDS_TILE % 16 == 0, "band tiles are aligned groups of 16 rows");
-// A 16-row group goes to a band tile when its multiply-adds are at least this
-// fraction of the tile's estimated FMA slots: the band kernel spends about 2.5
-// instructions per slot, the row-wise product tens per multiply-add.
-constexpr float BAND_MIN_EFF = 0.08f;
+// A 16-row group goes to a band tile when its multiply-adds are at least a
+// fraction band_min_eff (a schedule option, 0.08 by default) of the tile's
+// estimated FMA slots: the band kernel spends about 2.5 instructions per slot,
+// the row-wise product tens per multiply-add.
 
 // Row grouping of k_bounds: GROUPS_NONE keeps every row on 32 lanes.
 // GROUPS_THROUGHPUT (FP64 products, bound by the FP64 pipe) picks the group
@@ -124,7 +124,8 @@ __global__ void k_row_info(int64_t n, const int64_t *rs, const int64_t *re, cons
 __global__ void __launch_bounds__(BOUNDS_TILE)
     k_bounds(int64_t n, const int64_t *ars, const int64_t *are, const int32_t *acol,
              const int4 *binfo, const int32_t *seg,
-             const int *active, int mode, int groups, int band, const int *dslot,
+             const int *active, int mode, int groups, float group_margin, int band,
+             float band_min_eff, const int *dslot,
              const int64_t *moff, int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists,
              int *counters, double *work, double *band_work, unsigned char *bandrow) {
   __shared__ unsigned char s_cls[BOUNDS_TILE];
@@ -205,8 +206,8 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
               float avg = float(wk) / float(a1 > a0 ? a1 - a0 : 1);
               float u32 = lane_use(avg, 32), u16 = lane_use(avg, 16), u8 = lane_use(avg, 8);
               cls = RC_G32;
-              if (L <= WARP_W / 2 && u16 > u32 + 0.05f) cls = RC_G16;
-              if (L <= WARP_W / 4 && u8 > (cls == RC_G16 ? u16 : u32) + 0.05f) cls = RC_G8;
+              if (L <= WARP_W / 2 && u16 > u32 + group_margin) cls = RC_G16;
+              if (L <= WARP_W / 4 && u8 > (cls == RC_G16 ? u16 : u32) + group_margin) cls = RC_G8;
             }
             if (lane == 0) {
               lo[r] = mn;
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
         const float bavg = wsum / fmaxf(nsum, 1.0f);  // mean entries of a B row
         const float kc = fminf(float(khi - klo + 1), bavg + 35.0f);
         const float slots = 16.0f * 32.0f * float(nwords) * kc;
-        ok = nwords <= BAND_JW && khi - klo < BAND_KT - 3 && wsum >= BAND_MIN_EFF * slots;
+        ok = nwords <= BAND_JW && khi - klo < BAND_KT - 3 && wsum >= band_min_eff * slots;
       } else {
         ok = false;
       }
@@ -844,18 +845,18 @@ int grid_cap(int64_t items, int per_block, int per_sm) {
 }  // namespace
 
 void launch_bounds(int64_t n, const Rows &A, const Rows &B, const int32_t *seg, const int *active,
-                   int mode, int groups, int band, const int *dslot, const int64_t *moff,
-                   int32_t *lo, int32_t *len, int64_t *ub, int32_t *lists, int *counters,
-                   double *work, double *band_work, unsigned char *bandrow, int4 *binfo,
-                   cudaStream_t s) {
+                   int mode, int groups, float group_margin, int band, float band_min_eff,
+                   const int *dslot, const int64_t *moff, int32_t *lo, int32_t *len,
+                   int64_t *ub, int32_t *lists, int *counters, double *work,
+                   double *band_work, unsigned char *bandrow, int4 *binfo, cudaStream_t s) {
   if (n == 0) return;
   k_row_info<<<grid_cap(n, 256, 8), 256, 0, s>>>(n, B.rs, B.re, B.col, binfo);
   SGN_LAUNCH_CHECK();
   int tiles = int((n + BOUNDS_TILE - 1) / BOUNDS_TILE);
   int g = tiles < sm_count() * 8 ? tiles : sm_count() * 8;
   k_bounds<<<g, BOUNDS_TILE, 0, s>>>(n, A.rs, A.re, A.col, binfo, seg, active, mode, groups,
-                                     band, dslot, moff, lo, len, ub, lists, counters, work,
-                                     band_work, bandrow);
+                                     group_margin, band, band_min_eff, dslot, moff, lo, len, ub,
+                                     lists, counters, work, band_work, bandrow);
   SGN_LAUNCH_CHECK();
 }
 

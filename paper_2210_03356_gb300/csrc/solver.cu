@@ -1,5 +1,11 @@
 // C ABI of the filtered Newton-Schulz sign solver: handles, batch solves,
 // results. The round loop itself is in solver_core.cuh.
+#include <chrono>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "solver_core.cuh"
 
 namespace {
@@ -34,8 +40,33 @@ bool valid_opts(const sign_opts *o, std::string &why) {
   if (o->method < 0 || o->method > 1) return why = "unknown method", false;
   if (o->method == SIGN_METHOD_NMF && o->prec != SIGN_PREC_FP64)
     return why = "NMF runs in FP64 (prec = SIGN_PREC_FP64)", false;
+  if (!(o->band_min_eff >= 0.0)) return why = "band_min_eff must be >= 0", false;
+  if (!(o->group_margin == o->group_margin)) return why = "group_margin is NaN", false;
+  if (o->pair_rows < 0 || o->pair_rows > 1) return why = "pair_rows must be 0 or 1", false;
   return true;
 }
+
+// Schedules chosen by sign_tune_batch, per workload key.
+struct TuneKey {
+  int prec, filter, method, count_log2, n_log2, deg_log2;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(prec, filter, method, count_log2, n_log2, deg_log2) <
+           std::tie(o.prec, o.filter, o.method, o.count_log2, o.n_log2, o.deg_log2);
+  }
+};
+struct TunedSchedule {
+  double band_min_eff, group_margin;
+  int pair_rows;
+  void apply(sign_opts &o) const {
+    o.band_min_eff = band_min_eff;
+    o.group_margin = group_margin;
+    o.pair_rows = pair_rows;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TunedSchedule> g_tune;
+
+int log2_bin(double v) { return v > 0.0 ? int(std::floor(std::log2(v))) : -1; }
 
 }  // namespace
 
@@ -62,6 +93,9 @@ void sign_default_opts(sign_opts *o) {
   o->filter_t = 0;
   o->budget_norm = 0;
   o->method = SIGN_METHOD_NSF;
+  o->band_min_eff = 0.08;
+  o->group_margin = 0.05;
+  o->pair_rows = 1;
 }
 
 const char *sign_last_error(void) { return g_err.c_str(); }
@@ -263,6 +297,86 @@ sign_status sign_get_csr_batch(int count, const sign_t *hs, int64_t *const *row_
   } catch (const std::exception &e) {
     return fail(SIGN_ECUDA, e.what());
   }
+  return SIGN_OK;
+}
+
+sign_status sign_tune_batch(sign_t *hs, int count, const sign_opts *base, int reps, int force,
+                            sign_opts *best, sign_tune_report *rep) {
+  g_err.clear();
+  if (!hs || count < 1 || !best) return fail(SIGN_EINVAL, "need handles and best");
+  for (int i = 0; i < count; ++i)
+    if (!hs[i]) return fail(SIGN_EINVAL, "NULL handle");
+  if (reps < 1) return fail(SIGN_EINVAL, "reps must be >= 1");
+  std::string why;
+  if (!valid_opts(base, why)) return fail(SIGN_EINVAL, why);
+  sign_tune_report local;
+  if (!rep) rep = &local;
+  std::memset(rep, 0, sizeof(*rep));
+  double nsum = 0.0, nnzsum = 0.0;
+  for (int i = 0; i < count; ++i) {
+    nsum += double(hs[i]->n);
+    nnzsum += double(hs[i]->nnz);
+  }
+  const TuneKey key{base->prec, base->filter, base->method, int(std::ceil(std::log2(double(count)))),
+                    log2_bin(nsum / count), log2_bin(nnzsum / nsum)};
+  *best = *base;
+  if (!force) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      it->second.apply(*best);
+      rep->cached = 1;
+      return SIGN_OK;
+    }
+  }
+  // best of reps full batch solves, host wall time (the solve waits for its stream)
+  auto timed = [&](const sign_opts &o, double &ms) -> sign_status {
+    ms = HUGE_VAL;
+    for (int r = 0; r < reps; ++r) {
+      const auto t0 = std::chrono::steady_clock::now();
+      const sign_status st = sign_solve_batch(hs, count, &o, nullptr);
+      if (st != SIGN_OK) return st;
+      const auto t1 = std::chrono::steady_clock::now();
+      ms = std::min(ms, std::chrono::duration<double, std::milli>(t1 - t0).count());
+      ++rep->timed;
+    }
+    return SIGN_OK;
+  };
+  double cur_ms = 0.0;
+  sign_status st = timed(*best, cur_ms);
+  if (st != SIGN_OK) return st;
+  rep->ms_base = cur_ms;
+  // one field at a time; a candidate replaces the current choice only when it
+  // is faster by more than 1% (the timing noise of a batch solve)
+  auto sweep = [&](auto set, std::initializer_list<double> values) -> sign_status {
+    for (double v : values) {
+      sign_opts c = *best;
+      set(c, v);
+      if (std::memcmp(&c, best, sizeof(c)) == 0) continue;
+      double ms = 0.0;
+      const sign_status s2 = timed(c, ms);
+      if (s2 != SIGN_OK) return s2;
+      if (ms < 0.99 * cur_ms) {
+        *best = c;
+        cur_ms = ms;
+      }
+    }
+    return SIGN_OK;
+  };
+  const bool fp32 = base->prec == SIGN_PREC_MIXED && base->method == SIGN_METHOD_NSF;
+  if (fp32 && base->fp32_band) {
+    st = sweep([](sign_opts &o, double v) { o.band_min_eff = v; }, {0.02, 0.04, 0.08, 0.16, 0.32});
+    if (st != SIGN_OK) return st;
+  }
+  st = sweep([](sign_opts &o, double v) { o.group_margin = v; }, {-1.0, 0.0, 0.05, 0.15});
+  if (st != SIGN_OK) return st;
+  if (fp32) {
+    st = sweep([](sign_opts &o, double v) { o.pair_rows = int(v); }, {0.0, 1.0});
+    if (st != SIGN_OK) return st;
+  }
+  rep->ms_best = cur_ms;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = TunedSchedule{best->band_min_eff, best->group_margin, best->pair_rows};
   return SIGN_OK;
 }
 

@@ -407,8 +407,11 @@ struct Solver {
     {
       ProfScope ps(KC_BOUNDS, s);
       if (band && mode == MODE_SQUARE) w.bandrow.ensure(size_t(N > 0 ? N : 1), s);
-      launch_bounds(N, A, B, st.d_seg.template as<int32_t>(), active, mode, sizeof(T) == 8 ? 1 : 2,
-                    band ? 1 : 0, dp && dp->any() ? w.dslot.as<int>() : nullptr,
+      // schedule: FP64 rows by lane use (or all on 32 lanes), FP32 rows in pairs (or one per warp)
+      const int groups = sizeof(T) == 8 ? (o.group_margin < 0.0 ? 0 : 1) : (o.pair_rows ? 2 : 0);
+      launch_bounds(N, A, B, st.d_seg.template as<int32_t>(), active, mode, groups,
+                    float(o.group_margin), band ? 1 : 0, float(o.band_min_eff),
+                    dp && dp->any() ? w.dslot.as<int>() : nullptr,
                     st.d_moff.template as<int64_t>(), w.lo.as<int32_t>(),
                     w.len.as<int32_t>(), w.ub.as<int64_t>(), w.wlist.as<int32_t>(),
                     w.counters.as<int>(), w.work.as<double>(), band_work_dev(),

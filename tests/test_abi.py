@@ -35,6 +35,7 @@ def test_binding_covers_header_and_loads():
     assert (o.tol, o.filter, o.c4, o.switch_resid, o.max_iter) == (1e-8, 1, 1e-4, 1e-6, 100)
     assert (o.prec, o.fp32_until, o.scale_1norm, o.dense_frac, o.dense64_min_n) == (0, 1e-4, 1, 0.25, 1024)
     assert (o.fp32_band, o.filter_t, o.budget_norm, o.method) == (1, 0, 0, 0)
+    assert (o.band_min_eff, o.group_margin, o.pair_rows) == (0.08, 0.05, 1)
     assert sg.last_error() == ""
 
 
