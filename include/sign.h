@@ -166,7 +166,11 @@ sign_status sign_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int
 
 /* sign_create for `count` matrices at once (arrays of their arguments):
  * the copies and checks of all of them are queued back to back on
- * cuda_stream, which is waited for once. On any error no handle is created,
+ * cuda_stream, which is waited for once. When every array is device memory
+ * (on_device = 1) or pinned, mapped host memory (cudaMallocHost,
+ * cudaHostAlloc, cudaHostRegister), one gather kernel reads them all; other
+ * host memory is copied with one cudaMemcpyAsync per array. The checks run
+ * as one kernel over all matrices. On any error no handle is created,
  * every out[i] is NULL, and sign_last_error names the first bad matrix. */
 sign_status sign_create_batch(int count, const int64_t *n, const int64_t *nnz,
                               const int64_t *const *rowptr, const int32_t *const *col,
@@ -216,7 +220,10 @@ sign_status sign_get_csr(sign_t h, int64_t *nnz_out, int64_t *row_ptr, int32_t *
 
 /* sign_get_csr for `count` handles at once (arrays of its arguments): the
  * copies are queued on each handle's stream, which is then waited for once
- * (so a batch solved together costs one wait instead of count). Every handle
+ * (so a batch solved together costs one wait instead of count). When the
+ * handles share one stream and every output array is device memory
+ * (on_device = 1) or pinned, mapped host memory, one gather kernel writes
+ * them all; otherwise one cudaMemcpyAsync per array. Every handle
  * must hold a result; row_ptr, col and val must all be given, each array with
  * its handle's n+1 and nnz elements. On an error no copy is queued unless the
  * status is SIGN_ECUDA; sign_last_error names the first bad handle. */

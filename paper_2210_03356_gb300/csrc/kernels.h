@@ -12,6 +12,28 @@ namespace sgn {
 // nnz, column out of range or not strictly ascending, value not finite).
 void launch_validate(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col,
                      const double *val, int *flag, cudaStream_t s);
+// launch_validate for `count` matrices in one launch: jobs[m] describes matrix
+// m (device pointers), row_off (count + 1, on the device) the exclusive prefix
+// of their row counts, total_rows = row_off[count]; flags[m] |= 1 if matrix m
+// is malformed.
+struct ValidateJob {
+  int64_t n, nnz;
+  const int64_t *rp;
+  const int32_t *col;
+  const double *val;
+};
+void launch_validate_batch(int count, const ValidateJob *jobs, const int64_t *row_off,
+                           int64_t total_rows, int *flags, cudaStream_t s);
+
+// Copies `count` chunks (src, dst: device-accessible pointers, e.g. device
+// memory or mapped pinned host memory; bytes a multiple of 4, the chunks not
+// overlapping) in one launch.
+struct CopyChunk {
+  const void *src;
+  void *dst;
+  int64_t bytes;
+};
+void launch_copy_chunks(int count, const CopyChunk *chunks, cudaStream_t s);
 
 // Matrix-wide statistics for the server's footprint model. Initialise
 // min_gap_bits to the bits of +inf and the rest to 0; then min_gap_bits holds

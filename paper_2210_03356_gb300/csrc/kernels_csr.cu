@@ -50,6 +50,63 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t *rp, const int3
   });
 }
 
+// The same checks for a batch of matrices in one launch: a warp per row of
+// all of them (row_off: exclusive prefix of the row counts), the matrix
+// found by binary search; thread m also checks matrix m's first and last
+// row pointer.
+__global__ void k_validate_batch(int count, const ValidateJob *jobs, const int64_t *row_off,
+                                 int *flags) {
+  const int lane = lane_id();
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (tid < count) {
+    const ValidateJob &j = jobs[tid];
+    if (j.rp[0] != 0 || j.rp[j.n] != j.nnz) atomicOr(flags + tid, 1);
+  }
+  for_each_row_warp(row_off[count], [&](int64_t g) {
+    int lo = 0, hi = count - 1;  // the last matrix whose first row is <= g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (row_off[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    const ValidateJob &j = jobs[lo];
+    const int64_t r = g - row_off[lo];
+    const int64_t b = j.rp[r], e = j.rp[r + 1];
+    if (e < b || b < 0 || e > j.nnz) {
+      if (lane == 0) atomicOr(flags + lo, 1);
+      return;
+    }
+    bool bad = false;
+    for (int64_t p = b + lane; p < e; p += 32) {
+      const int32_t c = j.col[p];
+      if (c < 0 || c >= j.n) bad = true;
+      if (p > b && j.col[p - 1] >= c) bad = true;
+      if (!isfinite(j.val[p])) bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags + lo, 1);
+  });
+}
+
+// ------------------------------------------------------------ gathered copies
+// One CTA per chunk (grid-stride): 16-byte words when both ends and the
+// length allow it, else 4-byte words (every chunk's length is a multiple of 4).
+__global__ void k_copy_chunks(int count, const CopyChunk *chunks) {
+  for (int c = blockIdx.x; c < count; c += gridDim.x) {
+    const CopyChunk ch = chunks[c];
+    const uintptr_t a = reinterpret_cast<uintptr_t>(ch.src), b = reinterpret_cast<uintptr_t>(ch.dst);
+    if (((a | b | uintptr_t(ch.bytes)) & 15u) == 0) {
+      const int4 *s4 = static_cast<const int4 *>(ch.src);
+      int4 *d4 = static_cast<int4 *>(ch.dst);
+      const int64_t n4 = ch.bytes >> 4;
+      for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = s4[i];
+    } else {
+      const uint32_t *s1 = static_cast<const uint32_t *>(ch.src);
+      uint32_t *d1 = static_cast<uint32_t *>(ch.dst);
+      const int64_t n1 = ch.bytes >> 2;
+      for (int64_t i = threadIdx.x; i < n1; i += blockDim.x) d1[i] = s1[i];
+    }
+  }
+}
+
 // ------------------------------------------------------------ footprint statistics
 // Per row: diagonal magnitude, off-diagonal sum and farthest column, folded
 // into the matrix-wide Gershgorin gap, row-sum bound and half-bandwidth.
@@ -422,6 +479,20 @@ void launch_gersh(int64_t n, const int64_t *rp, const int32_t *col, const double
 void launch_validate(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col,
                      const double *val, int *flag, cudaStream_t s) {
   k_validate<<<grid_for(n, 8), 256, 0, s>>>(n, nnz, rp, col, val, flag);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_validate_batch(int count, const ValidateJob *jobs, const int64_t *row_off,
+                           int64_t total_rows, int *flags, cudaStream_t s) {
+  if (count < 1) return;
+  const int64_t items = total_rows > count ? total_rows : count;
+  k_validate_batch<<<grid_for(items, 8), 256, 0, s>>>(count, jobs, row_off, flags);
+  SGN_LAUNCH_CHECK();
+}
+
+void launch_copy_chunks(int count, const CopyChunk *chunks, cudaStream_t s) {
+  if (count < 1) return;
+  k_copy_chunks<<<count < 152 * 8 ? count : 152 * 8, 256, 0, s>>>(count, chunks);
   SGN_LAUNCH_CHECK();
 }
 

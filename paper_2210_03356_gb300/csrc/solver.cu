@@ -68,6 +68,45 @@ std::map<TuneKey, TunedSchedule> g_tune;
 
 int log2_bin(double v) { return v > 0.0 ? int(std::floor(std::log2(v))) : -1; }
 
+// The device address of pinned, mapped host memory; nullptr for device,
+// managed or pageable memory.
+void *mapped_host(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // not an error of the solver: the pointer is just not CUDA's
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Copies between device memory and mapped pinned host memory queued as one
+// gather kernel (k_copy_chunks) instead of one cudaMemcpyAsync per array: a
+// batch of 512 results is 1536 arrays. The chunk list goes through a pinned
+// arena of the calling thread; every user of the arena synchronises its
+// stream before returning, so the arena is free at the next call.
+thread_local Staging g_xfer_stage;
+
+struct Gather {
+  std::vector<CopyChunk> chunks;
+  void add(const void *src, void *dst, int64_t bytes) {
+    const int64_t step = int64_t(1) << 20;
+    for (int64_t o = 0; o < bytes; o += step)
+      chunks.push_back(CopyChunk{static_cast<const char *>(src) + o, static_cast<char *>(dst) + o,
+                                 std::min(step, bytes - o)});
+  }
+  size_t staged_bytes() const { return sizeof(CopyChunk) * chunks.size() + 64; }
+  // queues the copies on s; the arena must have room for staged_bytes(); list
+  // is device scratch that must live until s is synchronised
+  void launch(DevBuf &list, cudaStream_t s) {
+    if (chunks.empty()) return;
+    const size_t bytes = sizeof(CopyChunk) * chunks.size();
+    list.ensure(bytes, s);
+    SGN_CUDA(cudaMemcpyAsync(list.p, g_xfer_stage.put(chunks.data(), bytes), bytes,
+                             cudaMemcpyHostToDevice, s));
+    launch_copy_chunks(int(chunks.size()), list.as<CopyChunk>(), s);
+  }
+};
+
 }  // namespace
 
 namespace sgn {
@@ -165,26 +204,59 @@ sign_status sign_create_batch(int count, const int64_t *n, const int64_t *nnz,
     hs.reserve(size_t(count));
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    DevBuf flags;
-    flags.ensure(sizeof(int) * size_t(count), s);
-    SGN_CUDA(cudaMemsetAsync(flags.p, 0, sizeof(int) * size_t(count), s));
-    for (int i = 0; i < count; ++i) {  // copies and checks queued back to back, one wait
+    // device arrays, or host arrays that are all pinned and mapped: one
+    // gather kernel reads them
+    Gather g;
+    std::vector<const void *> src(3 * size_t(count), nullptr);
+    bool gather = true;
+    for (int i = 0; i < count && gather; ++i) {
+      auto dev = [&](const void *p) -> const void * { return on_device ? p : mapped_host(p); };
+      src[3 * i] = dev(rowptr[i]);
+      src[3 * i + 1] = nnz[i] > 0 ? dev(col[i]) : nullptr;
+      src[3 * i + 2] = nnz[i] > 0 ? dev(val[i]) : nullptr;
+      gather = src[3 * i] && (nnz[i] == 0 || (src[3 * i + 1] && src[3 * i + 2]));
+    }
+    std::vector<ValidateJob> jobs(static_cast<size_t>(count));
+    std::vector<int64_t> row_off(size_t(count) + 1, 0);
+    for (int i = 0; i < count; ++i) {  // copies queued back to back, one check, one wait
       hs.emplace_back(new sign_ctx);
       sign_ctx *h = hs.back().get();
       h->n = n[i];
       h->nnz = nnz[i];
       h->stream = s;
       h->a.ensure(n[i], nnz[i], s);
-      SGN_CUDA(cudaMemcpyAsync(h->a.rp.p, rowptr[i], sizeof(int64_t) * size_t(n[i] + 1), kind, s));
-      if (nnz[i] > 0) {
-        SGN_CUDA(cudaMemcpyAsync(h->a.col.p, col[i], sizeof(int32_t) * size_t(nnz[i]), kind, s));
-        SGN_CUDA(cudaMemcpyAsync(h->a.val.p, val[i], sizeof(double) * size_t(nnz[i]), kind, s));
+      if (gather) {
+        g.add(src[3 * i], h->a.rp.p, int64_t(sizeof(int64_t)) * (n[i] + 1));
+        if (nnz[i] > 0) {
+          g.add(src[3 * i + 1], h->a.col.p, int64_t(sizeof(int32_t)) * nnz[i]);
+          g.add(src[3 * i + 2], h->a.val.p, int64_t(sizeof(double)) * nnz[i]);
+        }
+      } else {
+        SGN_CUDA(cudaMemcpyAsync(h->a.rp.p, rowptr[i], sizeof(int64_t) * size_t(n[i] + 1), kind, s));
+        if (nnz[i] > 0) {
+          SGN_CUDA(cudaMemcpyAsync(h->a.col.p, col[i], sizeof(int32_t) * size_t(nnz[i]), kind, s));
+          SGN_CUDA(cudaMemcpyAsync(h->a.val.p, val[i], sizeof(double) * size_t(nnz[i]), kind, s));
+        }
       }
-      launch_validate(n[i], nnz[i], h->a.d_rp(), h->a.d_col(), h->a.d_val(), flags.as<int>() + i,
-                      s);
+      jobs[size_t(i)] = ValidateJob{n[i], nnz[i], h->a.d_rp(), h->a.d_col(), h->a.d_val()};
+      row_off[size_t(i) + 1] = row_off[size_t(i)] + n[i];
     }
+    // jobs, row offsets and flags in one device buffer, staged through the arena
+    const size_t jb = sizeof(ValidateJob) * size_t(count), rb = sizeof(int64_t) * (size_t(count) + 1);
+    const size_t jb_al = (jb + 255) & ~size_t(255), rb_al = (rb + 255) & ~size_t(255);
+    DevBuf list, vbuf;
+    g_xfer_stage.reserve(g.staged_bytes() + jb + rb + 256);
+    g.launch(list, s);
+    char *vb = static_cast<char *>(vbuf.ensure(jb_al + rb_al + sizeof(int) * size_t(count), s));
+    SGN_CUDA(cudaMemcpyAsync(vb, g_xfer_stage.put(jobs.data(), jb), jb, cudaMemcpyHostToDevice, s));
+    SGN_CUDA(cudaMemcpyAsync(vb + jb_al, g_xfer_stage.put(row_off.data(), rb), rb,
+                             cudaMemcpyHostToDevice, s));
+    int *flags = reinterpret_cast<int *>(vb + jb_al + rb_al);
+    SGN_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * size_t(count), s));
+    launch_validate_batch(count, reinterpret_cast<const ValidateJob *>(vb),
+                          reinterpret_cast<const int64_t *>(vb + jb_al), row_off.back(), flags, s);
     std::vector<int> hf(size_t(count), 0);
-    SGN_CUDA(cudaMemcpyAsync(hf.data(), flags.p, sizeof(int) * size_t(count),
+    SGN_CUDA(cudaMemcpyAsync(hf.data(), flags, sizeof(int) * size_t(count),
                              cudaMemcpyDeviceToHost, s));
     SGN_CUDA(cudaStreamSynchronize(s));
     for (int i = 0; i < count; ++i)
@@ -274,6 +346,35 @@ sign_status sign_get_csr_batch(int count, const sign_t *hs, int64_t *const *row_
       return fail(SIGN_EINVAL, "handle " + std::to_string(i) + ": NULL output array");
   }
   try {
+    // device arrays, or host arrays that are all pinned and mapped, handles
+    // on one stream: one gather kernel writes every result into them
+    bool gather = true;
+    for (int i = 1; i < count && gather; ++i) gather = hs[i]->stream == hs[0]->stream;
+    if (gather) {
+      Gather g;
+      for (int i = 0; i < count && gather; ++i) {
+        const sign_ctx *h = hs[i];
+        auto dev = [&](void *p) -> void * { return on_device ? p : mapped_host(p); };
+        void *rp = dev(row_ptr[i]);
+        void *cl = h->result.nnz > 0 ? dev(col[i]) : nullptr;
+        void *vl = h->result.nnz > 0 ? dev(val[i]) : nullptr;
+        gather = rp && (h->result.nnz == 0 || (cl && vl));
+        if (!gather) break;
+        g.add(h->result.rp.p, rp, int64_t(sizeof(int64_t)) * (h->n + 1));
+        if (h->result.nnz > 0) {
+          g.add(h->result.col.p, cl, int64_t(sizeof(int32_t)) * h->result.nnz);
+          g.add(h->result.val.p, vl, int64_t(sizeof(double)) * h->result.nnz);
+        }
+      }
+      if (gather) {
+        cudaStream_t s = hs[0]->stream;
+        DevBuf list;
+        g_xfer_stage.reserve(g.staged_bytes());
+        g.launch(list, s);
+        SGN_CUDA(cudaStreamSynchronize(s));
+        return SIGN_OK;
+      }
+    }
     cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     std::vector<cudaStream_t> streams;
     for (int i = 0; i < count; ++i) {

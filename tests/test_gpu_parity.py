@@ -385,6 +385,59 @@ def test_create_batch_names_the_bad_matrix_and_reads_into_caller_buffers(sg):
         b.close()
 
 
+def test_batch_transfers_pinned_device_and_pageable(sg):
+    """sign_create_batch and sign_get_csr_batch take one gather kernel when
+    every array is pinned host or device memory, and one copy per array
+    otherwise: the handles and results must be the same either way, and a
+    malformed matrix read through the gather must still be named."""
+    import torch
+    from paper_2210_03356_gb300 import Batch, SignError
+    shapes = w.banded_batch_shapes(12, nmin=200, nmax=2500)
+    mats = [w.banded(n, b, s) for n, b, s in shapes] + [w.tridiagonal(777)]
+
+    def pinned(a):
+        t = [torch.from_numpy(x).pin_memory() for x in (a.rowptr, a.col, a.val)]
+        return type("P", (), {"n": a.n, "rowptr": t[0].numpy(), "col": t[1].numpy(),
+                              "val": t[2].numpy(), "_keep": t})
+
+    def on_dev(a):
+        return type("D", (), {"n": a.n, "rowptr": torch.from_numpy(a.rowptr).cuda(),
+                              "col": torch.from_numpy(a.col).cuda(),
+                              "val": torch.from_numpy(a.val).cuda()})
+
+    opts = sg.default_opts(tol=1e-8, filter="exact", prec="mixed", dense_frac=2.0)
+    ref = None
+    for make in (lambda a: a, pinned, on_dev,
+                 lambda a: pinned(a) if a.n % 2 else a):  # pinned and pageable mixed
+        b = Batch([make(a) for a in mats])
+        try:
+            b.solve(opts)
+            nnz = [h.result_nnz() for h in b.handles]
+            pin = [tuple(torch.empty(k, dtype=d, pin_memory=True).numpy()
+                         for k, d in ((h.n + 1, torch.int64), (z, torch.int32),
+                                      (z, torch.float64)))
+                   for h, z in zip(b.handles, nnz)]
+            page = [(np.empty(h.n + 1, np.int64), np.empty(z, np.int32), np.empty(z, np.float64))
+                    for h, z in zip(b.handles, nnz)]
+            got_pin = [tuple(x.copy() for x in r) for r in b.results(pin)]
+            got_page = b.results(page)
+            for (r1, c1, v1), (r2, c2, v2) in zip(got_pin, got_page):
+                assert np.array_equal(r1, r2) and np.array_equal(c1, c2)
+                assert np.array_equal(v1.view(np.uint64), v2.view(np.uint64))
+            if ref is None:
+                ref = got_pin
+            for (r1, c1, v1), (r2, c2, v2) in zip(got_pin, ref):
+                assert np.array_equal(r1, r2) and np.array_equal(c1, c2)
+                assert np.array_equal(v1.view(np.uint64), v2.view(np.uint64))
+        finally:
+            b.close()
+    bad = w.CSR(3, np.array([0, 1, 3, 4], np.int64), np.array([0, 2, 1, 2], np.int32),
+                np.array([1.0, 2.0, np.nan, 1.0]))
+    with pytest.raises(SignError) as e:
+        Batch([pinned(a) for a in mats[:3]] + [pinned(bad)])
+    assert e.value.status == sg.SIGN_EINVAL and "matrix 3" in str(e.value)
+
+
 def test_trim_memory_between_solves(sg):
     """Kept blocks and pool memory handed back; the next solve is unchanged."""
     mats = [w.banded(n, b, s) for n, b, s in w.banded_batch_shapes(6, nmin=200, nmax=900)]
