@@ -94,10 +94,20 @@ __global__ void k_copy_chunks(int count, const CopyChunk *chunks) {
     const CopyChunk ch = chunks[c];
     const uintptr_t a = reinterpret_cast<uintptr_t>(ch.src), b = reinterpret_cast<uintptr_t>(ch.dst);
     if (((a | b | uintptr_t(ch.bytes)) & 15u) == 0) {
+      // four 16-byte words per thread in flight (the far side may be host memory)
       const int4 *s4 = static_cast<const int4 *>(ch.src);
       int4 *d4 = static_cast<int4 *>(ch.dst);
       const int64_t n4 = ch.bytes >> 4;
-      for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = s4[i];
+      const int64_t T = blockDim.x;
+      int64_t i = threadIdx.x;
+      for (; i + 3 * T < n4; i += 4 * T) {
+        const int4 v0 = s4[i], v1 = s4[i + T], v2 = s4[i + 2 * T], v3 = s4[i + 3 * T];
+        d4[i] = v0;
+        d4[i + T] = v1;
+        d4[i + 2 * T] = v2;
+        d4[i + 3 * T] = v3;
+      }
+      for (; i < n4; i += T) d4[i] = s4[i];
     } else {
       const uint32_t *s1 = static_cast<const uint32_t *>(ch.src);
       uint32_t *d1 = static_cast<uint32_t *>(ch.dst);
