@@ -120,6 +120,57 @@ __global__ void k_row_info(int64_t n, const int64_t *rs, const int64_t *re, cons
   }
 }
 
+// Rows of A with more entries than this are walked by a whole warp in k_bounds.
+constexpr int64_t BOUNDS_LONG = 256;
+
+// The bounds and class of one row of sparse work, from its k hull [kf, kl],
+// its column hull [mn, mx] (mx < 0: no output) and its multiply-adds wk;
+// writes lo, len, ub, work of row r and, for band tiles, the row's statistics.
+__device__ __forceinline__ int bounds_row(int64_t r, int m, int64_t na, int32_t mn, int32_t mx,
+                                          int32_t kf, int32_t kl, int64_t wk, int mode,
+                                          int groups, float group_margin, int band, int32_t *lo,
+                                          int32_t *len, int64_t *ub, double *work, int *sseg,
+                                          int *slo, int *sL, int *skf, int *skl, int *sna,
+                                          float *swk) {
+  int cls = RC_NONE;
+  if (mx < 0) {
+    ub[r] = 0;
+    len[r] = 0;
+    lo[r] = 0;
+    work[r] = double(wk);
+  } else {
+    const int32_t L = mx - mn + 1;
+    const int64_t bound = wk + (mode == MODE_UPDATE ? na : 0);
+    if (L > WARP_W) {
+      cls = RC_CTA;
+    } else if (!groups) {
+      cls = RC_G32;
+    } else if (groups == GROUPS_PAIRS) {
+      cls = L <= WARP_W / 2 ? RC_G16 : RC_G32;
+    } else {
+      const float avg = float(wk) / float(na > 0 ? na : 1);
+      const float u32 = lane_use(avg, 32), u16 = lane_use(avg, 16), u8 = lane_use(avg, 8);
+      cls = RC_G32;
+      if (L <= WARP_W / 2 && u16 > u32 + group_margin) cls = RC_G16;
+      if (L <= WARP_W / 4 && u8 > (cls == RC_G16 ? u16 : u32) + group_margin) cls = RC_G8;
+    }
+    lo[r] = mn;
+    len[r] = L;
+    ub[r] = bound < L ? bound : L;
+    work[r] = double(wk);
+  }
+  if (band) {
+    *sseg = m;
+    *slo = mx < 0 ? 0 : mn;
+    *sL = mx < 0 ? 0 : mx - mn + 1;
+    *skf = kf;
+    *skl = kl;
+    *sna = int(na);
+    *swk = float(wk);
+  }
+  return cls;
+}
+
 // counters: [RC_*] list lengths, [RC_QUEUE + RC_*] work-queue heads of the numeric kernels.
 __global__ void __launch_bounds__(BOUNDS_TILE)
     k_bounds(int64_t n, const int64_t *ars, const int64_t *are, const int32_t *acol,
@@ -141,93 +192,96 @@ __global__ void __launch_bounds__(BOUNDS_TILE)
   const int64_t ntiles = (n + BOUNDS_TILE - 1) / BOUNDS_TILE;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t t0 = tile * BOUNDS_TILE;
-    for (int i = warp; i < BOUNDS_TILE; i += nw) {
-      int64_t r = t0 + i;
-      int cls = RC_NONE;
-      if (lane == 0) s_seg[i] = -1;  // not eligible for a band tile
-      if (r < n) {
-        const int m = seg[r];
-        if (!active[m] || (dslot && dslot[m] >= 0)) {
-          // inactive, or on the dense path: no sparse work; a dense row of an
-          // update gets a whole row of slots for 1.5 X - 0.5 X T
-          if (lane == 0) {
-            bool dense = active[m] && dslot && dslot[m] >= 0;
-            ub[r] = dense && mode == MODE_UPDATE ? moff[m + 1] - moff[m] : 0;
-            len[r] = 0;
-            lo[r] = 0;
-            work[r] = 0.0;
-          }
+    // One thread per row: its own pass over A_i (four B records in flight),
+    // with no reductions across lanes. Rows of more than BOUNDS_LONG entries
+    // are left to the whole warp afterwards.
+    const int i = threadIdx.x;
+    const int64_t r = t0 + i;
+    int cls = RC_NONE;
+    bool longrow = false;
+    s_seg[i] = -1;  // not eligible for a band tile
+    int m = 0;
+    int64_t a0 = 0, a1 = 0;
+    if (r < n) {
+      m = seg[r];
+      if (!active[m] || (dslot && dslot[m] >= 0)) {
+        // inactive, or on the dense path: no sparse work; a dense row of an
+        // update gets a whole row of slots for 1.5 X - 0.5 X T
+        const bool dense = active[m] && dslot && dslot[m] >= 0;
+        ub[r] = dense && mode == MODE_UPDATE ? moff[m + 1] - moff[m] : 0;
+        len[r] = 0;
+        lo[r] = 0;
+        work[r] = 0.0;
+      } else {
+        a0 = ars[r];
+        a1 = are[r];
+        if (a1 - a0 > BOUNDS_LONG) {
+          longrow = true;
         } else {
-          int32_t mn = INT_MAX, mx = -1, kf = INT_MAX, kl = -1;
+          int32_t mn = INT_MAX, mx = -1;
           int64_t wk = 0;
-          int64_t a0 = ars[r], a1 = are[r];
-          for (int64_t p = a0 + lane; p < a1; p += 32) {
-            int32_t k = acol[p];
-            kf = min(kf, k);
-            kl = max(kl, k);
-            const int4 bi = binfo[k];  // B_k: first column, last column, length
+          int64_t p = a0;
+          for (; p + 4 <= a1; p += 4) {
+            const int32_t k0 = acol[p], k1 = acol[p + 1], k2 = acol[p + 2], k3 = acol[p + 3];
+            const int4 b0 = binfo[k0], b1 = binfo[k1], b2 = binfo[k2], b3 = binfo[k3];
+            wk += int64_t(b0.z) + b1.z + b2.z + b3.z;
+            // an empty B row has first column 0 and last -1: no effect on either
+            mn = min(mn, min(min(b0.z ? b0.x : INT_MAX, b1.z ? b1.x : INT_MAX),
+                             min(b2.z ? b2.x : INT_MAX, b3.z ? b3.x : INT_MAX)));
+            mx = max(mx, max(max(b0.y, b1.y), max(b2.y, b3.y)));
+          }
+          for (; p < a1; ++p) {
+            const int4 bi = binfo[acol[p]];
             wk += bi.z;
-            if (bi.z > 0) {
-              mn = min(mn, bi.x);
-              mx = max(mx, bi.y);
-            }
-            if (mode == MODE_UPDATE) {
-              mn = min(mn, k);
-              mx = max(mx, k);
-            }
+            if (bi.z > 0) mn = min(mn, bi.x);
+            mx = max(mx, bi.y);
           }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            wk += __shfl_xor_sync(0xffffffffu, wk, o);
-            if (band) {
-              kf = min(kf, __shfl_xor_sync(0xffffffffu, kf, o));
-              kl = max(kl, __shfl_xor_sync(0xffffffffu, kl, o));
-            }
+          const int32_t kf = a1 > a0 ? acol[a0] : INT_MAX, kl = a1 > a0 ? acol[a1 - 1] : -1;
+          if (mode == MODE_UPDATE && a1 > a0) {  // the columns of X_i itself (ascending)
+            mn = min(mn, kf);
+            mx = max(mx, kl);
           }
-          if (mx < 0) {
-            if (lane == 0) {
-              ub[r] = 0;
-              len[r] = 0;
-              lo[r] = 0;
-              work[r] = double(wk);
-            }
-          } else {
-            int32_t L = mx - mn + 1;
-            int64_t bound = wk + (mode == MODE_UPDATE ? a1 - a0 : 0);
-            if (L > WARP_W) {
-              cls = RC_CTA;
-            } else if (!groups) {
-              cls = RC_G32;
-            } else if (groups == GROUPS_PAIRS) {
-              cls = L <= WARP_W / 2 ? RC_G16 : RC_G32;
-            } else {
-              float avg = float(wk) / float(a1 > a0 ? a1 - a0 : 1);
-              float u32 = lane_use(avg, 32), u16 = lane_use(avg, 16), u8 = lane_use(avg, 8);
-              cls = RC_G32;
-              if (L <= WARP_W / 2 && u16 > u32 + group_margin) cls = RC_G16;
-              if (L <= WARP_W / 4 && u8 > (cls == RC_G16 ? u16 : u32) + group_margin) cls = RC_G8;
-            }
-            if (lane == 0) {
-              lo[r] = mn;
-              len[r] = L;
-              ub[r] = bound < L ? bound : L;
-              work[r] = double(wk);
-            }
-          }
-          if (band && lane == 0) {
-            s_seg[i] = m;
-            s_lo[i] = mx < 0 ? 0 : mn;
-            s_L[i] = mx < 0 ? 0 : mx - mn + 1;
-            s_kf[i] = kf;
-            s_kl[i] = kl;
-            s_na[i] = int(a1 - a0);
-            s_wk[i] = float(wk);
-          }
+          cls = bounds_row(r, m, a1 - a0, mn, mx, kf, kl, wk, mode, groups, group_margin, band,
+                           lo, len, ub, work, s_seg + i, s_lo + i, s_L + i, s_kf + i, s_kl + i,
+                           s_na + i, s_wk + i);
         }
       }
-      if (lane == 0) s_cls[i] = (unsigned char)cls;
+    }
+    s_cls[i] = (unsigned char)cls;
+    // long rows: the warp walks each with its lanes striding over A_i
+    unsigned lm = __ballot_sync(0xffffffffu, longrow);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int li = warp * 32 + src;
+      const int64_t lr = t0 + li;
+      const int lmat = __shfl_sync(0xffffffffu, m, src);
+      const int64_t la0 = __shfl_sync(0xffffffffu, a0, src), la1 = __shfl_sync(0xffffffffu, a1, src);
+      int32_t mn = INT_MAX, mx = -1;
+      int64_t wk = 0;
+      for (int64_t p = la0 + lane; p < la1; p += 32) {
+        const int4 bi = binfo[acol[p]];
+        wk += bi.z;
+        if (bi.z > 0) mn = min(mn, bi.x);
+        mx = max(mx, bi.y);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        wk += __shfl_xor_sync(0xffffffffu, wk, o);
+      }
+      if (lane == src) {
+        const int32_t kf = acol[la0], kl = acol[la1 - 1];
+        if (mode == MODE_UPDATE) {
+          mn = min(mn, kf);
+          mx = max(mx, kl);
+        }
+        s_cls[li] = (unsigned char)bounds_row(lr, lmat, la1 - la0, mn, mx, kf, kl, wk, mode,
+                                              groups, group_margin, band, lo, len, ub, work,
+                                              s_seg + li, s_lo + li, s_L + li, s_kf + li,
+                                              s_kl + li, s_na + li, s_wk + li);
+      }
     }
     __syncthreads();
     // band tiles: aligned groups of 16 rows of one matrix, all with sparse
