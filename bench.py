@@ -890,8 +890,7 @@ def main():
         def e2e_step():
             b2 = sg.Batch(pinned)
             b2.solve(opts)
-            for i, hnd in enumerate(b2.handles):
-                nnz = hnd.result_nnz()
+            for i, (hnd, nnz) in enumerate(zip(b2.handles, b2.result_nnz())):
                 if i == len(outs) or outs[i][1].size < nnz:
                     buf = (torch.empty(hnd.n + 1, dtype=torch.int64, pin_memory=True),
                            torch.empty(max(nnz, 1), dtype=torch.int32, pin_memory=True),

@@ -233,6 +233,14 @@ sign_status sign_get_csr_batch(int count, const sign_t *hs, int64_t *const *row_
 /* Releases the handle and its device memory (NULL is ignored). */
 void sign_destroy(sign_t h);
 
+/* sign_destroy for `count` handles (NULL entries are skipped): each distinct
+ * stream is waited for once, then every handle is freed. */
+void sign_destroy_batch(const sign_t *hs, int count);
+
+/* nnz_out[i] = the stored entries of handle i's result (as sign_get_csr with
+ * no arrays). SIGN_ESTATE names the first handle without a result. */
+sign_status sign_result_nnz_batch(int count, const sign_t *hs, int64_t *nnz_out);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *sign_last_error(void);
 

@@ -373,8 +373,7 @@ class Batch:
         if len(outs) != len(self.handles):
             raise ValueError("one (rowptr, col, val) per handle")
         views = []
-        for h, (rp, col, val) in zip(self.handles, outs):
-            nnz = h.result_nnz()
+        for h, nnz, (rp, col, val) in zip(self.handles, self.result_nnz(), outs):
             if (rp.dtype != np.int64 or col.dtype != np.int32 or val.dtype != np.float64 or
                     rp.size < h.n + 1 or col.size < nnz or val.size < nnz or
                     not (rp.flags.c_contiguous and col.flags.c_contiguous and
@@ -391,13 +390,23 @@ class Batch:
             raise SignError(st, "sign_get_csr_batch")
         return views
 
-    def traces(self) -> list:
-        infos, iarr, _ = self.infos
-        return [i.trace(s) for i, s in zip(infos, iarr)]
+    def result_nnz(self) -> list:
+        """sign_result_nnz_batch: the stored entries of every result."""
+        k = len(self.handles)
+        out = (C.c_int64 * k)()
+        st = load().sign_result_nnz_batch(k, self.arr, out)
+        if st != SIGN_OK:
+            raise SignError(st, "sign_result_nnz_batch")
+        return list(out)
 
     def close(self):
-        for h in self.handles:
-            h.close()
+        """sign_destroy_batch: one wait per stream, then every handle freed."""
+        live = [h for h in self.handles if getattr(h, "h", None)]
+        if live:
+            arr = (N.sign_t * len(live))(*[h.h for h in live])
+            load().sign_destroy_batch(arr, len(live))
+            for h in live:
+                h.h = None
 
 
 class Server:

@@ -84,6 +84,8 @@ SIGNATURES = {
     "sign_solve": (C.c_int, [sign_t, C.POINTER(sign_opts), C.POINTER(sign_info)]),
     "sign_solve_batch": (C.c_int, [C.POINTER(sign_t), C.c_int, C.POINTER(sign_opts),
                                    C.POINTER(sign_info)]),
+    "sign_result_nnz_batch": (C.c_int, [C.c_int, C.POINTER(sign_t), C.POINTER(C.c_int64)]),
+    "sign_destroy_batch": (None, [C.POINTER(sign_t), C.c_int]),
     "sign_tune_batch": (C.c_int, [C.POINTER(sign_t), C.c_int, C.POINTER(sign_opts), C.c_int,
                                   C.c_int, C.POINTER(sign_opts), C.POINTER(sign_tune_report)]),
     "sign_get_csr": (C.c_int, [sign_t, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p,

@@ -481,6 +481,28 @@ sign_status sign_tune_batch(sign_t *hs, int count, const sign_opts *base, int re
   return SIGN_OK;
 }
 
+sign_status sign_result_nnz_batch(int count, const sign_t *hs, int64_t *nnz_out) {
+  g_err.clear();
+  if (count < 1 || !hs || !nnz_out) return fail(SIGN_EINVAL, "need count >= 1 and non-NULL arrays");
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return fail(SIGN_EINVAL, "handle " + std::to_string(i) + " is NULL");
+    if (!hs[i]->has_result)
+      return fail(SIGN_ESTATE, "handle " + std::to_string(i) + ": no result, call sign_solve first");
+    nnz_out[i] = hs[i]->result.nnz;
+  }
+  return SIGN_OK;
+}
+
+void sign_destroy_batch(const sign_t *hs, int count) {
+  if (!hs || count < 1) return;
+  std::vector<cudaStream_t> streams;
+  for (int i = 0; i < count; ++i)
+    if (hs[i] && std::find(streams.begin(), streams.end(), hs[i]->stream) == streams.end())
+      streams.push_back(hs[i]->stream);
+  for (cudaStream_t s : streams) cudaStreamSynchronize(s);
+  for (int i = 0; i < count; ++i) delete hs[i];
+}
+
 void sign_destroy(sign_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);

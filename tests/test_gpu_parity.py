@@ -413,6 +413,7 @@ def test_batch_transfers_pinned_device_and_pageable(sg):
         try:
             b.solve(opts)
             nnz = [h.result_nnz() for h in b.handles]
+            assert b.result_nnz() == nnz
             pin = [tuple(torch.empty(k, dtype=d, pin_memory=True).numpy()
                          for k, d in ((h.n + 1, torch.int64), (z, torch.int32),
                                       (z, torch.float64)))
