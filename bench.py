@@ -23,6 +23,7 @@ the same workload with the host's cores, as the reference arm.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -781,6 +782,10 @@ def main():
     for _ in range(args.warmup):
         out = batch.solve(opts)
     assert all(s == sg.SIGN_OK for s, _, _ in out), out[:4]
+    # the inputs and handles made so far live until the end: keep them out of
+    # the interpreter's full collections, which otherwise pause a step now and
+    # then (about 30 ms scanning them; the usual setting of a long-lived service)
+    gc.freeze()
 
     clocks = Clocks(local)
     clocks.start()
@@ -908,6 +913,7 @@ def main():
 
         for _ in range(args.warmup):  # untimed, as for the device-timed steps
             e2e_step()
+        gc.freeze()  # the pinned inputs and result buffers, as above
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
@@ -915,7 +921,8 @@ def main():
         barrier()
         e2e_s = time.perf_counter() - t0
         line["e2e"] = {"value": len(mats) * world * args.steps / e2e_s, "unit": UNIT,
-                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "python_gc": "objects made before the timed steps frozen (gc.freeze)"}
         # the results of the last end-to-end step: identical to the timed steps'
         # (every solve is deterministic); their errors, outside any timed region
         if rank == 0:
