@@ -378,25 +378,37 @@ __device__ __forceinline__ void accumulate_k(T a, int64_t q0, int64_t q1, const 
                                              const T *bval, int64_t c0, T *acc,
                                              unsigned char *f, int tid) {
   if constexpr (sizeof(T) == 8) {
-    // FP64 (DFMA-bound): 64-bit positions, ~1% faster here than offsets
+    // FP64 (DFMA-bound): passes of STRIDE entries taken four, then two, then
+    // one at a time, the same for every lane of the group, so that only the
+    // row's last pass is partly active. A DFMA costs the FP64 pipe the same
+    // whatever its active lanes, and lanes running different unrollings
+    // would issue the instructions of each. 64-bit positions (~1% faster
+    // here than offsets).
+    const int np = int((q1 - q0 + STRIDE - 1) / STRIDE);  // group-uniform
     int64_t q = q0 + tid;
-    for (; q + 3 * STRIDE < q1; q += 4 * STRIDE) {
-      int j0 = int(bcol[q] - c0), j1 = int(bcol[q + STRIDE] - c0);
-      int j2 = int(bcol[q + 2 * STRIDE] - c0), j3 = int(bcol[q + 3 * STRIDE] - c0);
-      T v0 = bval[q], v1 = bval[q + STRIDE], v2 = bval[q + 2 * STRIDE], v3 = bval[q + 3 * STRIDE];
+    int pass = 0;
+    for (; pass + 4 <= np; pass += 4, q += 4 * STRIDE) {
+      const bool ok3 = q + 3 * STRIDE < q1;  // only the last pass can be partial
+      const int j0 = int(bcol[q] - c0), j1 = int(bcol[q + STRIDE] - c0);
+      const int j2 = int(bcol[q + 2 * STRIDE] - c0);
+      const int j3 = ok3 ? int(bcol[q + 3 * STRIDE] - c0) : 0;
+      const T v0 = bval[q], v1 = bval[q + STRIDE], v2 = bval[q + 2 * STRIDE];
+      const T v3 = ok3 ? bval[q + 3 * STRIDE] : T(0);
       mac<T, MARK>(acc, f, j0, a, v0);
       mac<T, MARK>(acc, f, j1, a, v1);
       mac<T, MARK>(acc, f, j2, a, v2);
-      mac<T, MARK>(acc, f, j3, a, v3);
+      if (ok3) mac<T, MARK>(acc, f, j3, a, v3);
     }
-    if (q + STRIDE < q1) {
-      int j0 = int(bcol[q] - c0), j1 = int(bcol[q + STRIDE] - c0);
-      T v0 = bval[q], v1 = bval[q + STRIDE];
+    if (pass + 2 <= np) {
+      const bool ok1 = q + STRIDE < q1;
+      const int j0 = int(bcol[q] - c0), j1 = ok1 ? int(bcol[q + STRIDE] - c0) : 0;
+      const T v0 = bval[q], v1 = ok1 ? bval[q + STRIDE] : T(0);
       mac<T, MARK>(acc, f, j0, a, v0);
-      mac<T, MARK>(acc, f, j1, a, v1);
+      if (ok1) mac<T, MARK>(acc, f, j1, a, v1);
+      pass += 2;
       q += 2 * STRIDE;
     }
-    if (q < q1) mac<T, MARK>(acc, f, int(bcol[q] - c0), a, bval[q]);
+    if (pass < np && q < q1) mac<T, MARK>(acc, f, int(bcol[q] - c0), a, bval[q]);
   } else {
     // FP32 (issue-bound): 32-bit offsets from the start of B_k, one 64-bit
     // address per k (~4% faster)
