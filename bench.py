@@ -52,11 +52,12 @@ WORKLOAD = ("banded batch: 512 symmetric banded matrices, n log-uniform [200,800
 FP64_UNIT_GFLOPS = 152 * 2 * 2 * 2.07
 FP32_UNIT_GFLOPS = 152 * 128 * 2 * 2.07
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic
-# byte of each product class, from one ncu capture of the first 128 matrices
-# of the batch (profiles/dram_traffic_products_banded128.md). A full-size
-# launch is taken to move DRAM bytes in the same proportion to its
-# algorithmic bytes. Valid for the product kernels as that capture built them.
-DRAM_PER_ALG_BYTE = {"numeric_square_f64": 0.900, "numeric_update_f64": 0.563,
+# byte of each product class, from ncu captures of the first 128 matrices of
+# the batch: FP64 from profiles/k_num_group_f64_lanes_dram_banded128.md, FP32
+# (row-wise kernels) from profiles/dram_traffic_products_banded128.md. A
+# full-size launch is taken to move DRAM bytes in the same proportion to its
+# algorithmic bytes. Valid for the product kernels as those captures built them.
+DRAM_PER_ALG_BYTE = {"numeric_square_f64": 0.911, "numeric_update_f64": 0.563,
                      "numeric_square_f32": 0.851, "numeric_update_f32": 0.871}
 
 
