@@ -357,11 +357,13 @@ __global__ void __launch_bounds__(BT_WARPS * 32, BT_CTAS)
           __syncwarp();
           {  // the chunk's pattern: B words of the stored k of row hi (every other)
             const unsigned sh = unsigned(kb + ks) & 31u;
-            unsigned m = __funnelshift_r(sm.am[bf][hi][0], sm.am[bf][hi][1], sh);
-            m &= hh ? 0xaaaaaaaau : 0x55555555u;
-            while (m) {
-              patw |= sm.bm[bf][__ffs(m) - 1];
-              m &= m - 1;
+            const unsigned m = __funnelshift_r(sm.am[bf][hi][0], sm.am[bf][hi][1], sh);
+            // the 16 k of this lane's half, unrolled: independent loads, no chain
+#pragma unroll
+            for (int t = 0; t < 32; t += 2) {
+              const int tt = t + hh;
+              const unsigned bw = sm.bm[bf][tt];
+              patw |= ((m >> tt) & 1u) ? bw : 0u;
             }
           }
           for (int kk = 0; kk < nk4; kk += 4) {
