@@ -238,13 +238,13 @@ __device__ __forceinline__ int bucket0(unsigned long long key, unsigned long lon
   return t <= base ? 0 : int(t - base);
 }
 
+// The smallest of the lanes' 64-bit values: the high words' minimum, then the
+// minimum of the low words among the lanes holding it (two warp reductions).
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = w < v ? w : v;
-  }
-  return v;
+  const unsigned hi = unsigned(v >> 32);
+  const unsigned mh = __reduce_min_sync(0xffffffffu, hi);
+  const unsigned ml = __reduce_min_sync(0xffffffffu, hi == mh ? unsigned(v) : 0xffffffffu);
+  return ((unsigned long long)mh << 32) | ml;
 }
 
 // A chunk of consecutive rows, their extents and matrices staged in shared
