@@ -276,12 +276,17 @@ __device__ __forceinline__ int stage_rows(const SelRows &R, const int *active, i
   return t;
 }
 
-// Level-0 histogram. A CTA takes a chunk of consecutive rows, a warp one row
-// at a time, each lane a contiguous run of the row's entries. Neighbouring
-// entries of a row have similar magnitudes, so a lane sums its run per bucket
-// in registers and adds the run's total once when the bucket changes: into a
-// shared histogram for the chunk's first matrix (almost every row: matrices
-// span many chunks), else into the global one.
+constexpr int HIST_LPR = 8;  // lanes per row of the level-0 histogram
+
+// Level-0 histogram. A CTA takes a chunk of consecutive rows, a warp
+// 32 / HIST_LPR rows at a time with HIST_LPR lanes each (the per-row work is
+// then spread over more entries per lane), each lane a contiguous run of the
+// row's entries. Neighbouring entries of a row have similar magnitudes, so a
+// lane sums its run per bucket in registers and adds the run's total once
+// when the bucket changes: into a shared histogram for the chunk's first
+// matrix (almost every row: matrices span many chunks), else into the global
+// one.
+
 template <typename T>
 __global__ void __launch_bounds__(SEL_THREADS)
     k_sel_hist0(SelRows R, const int *active, const T *val, const MatScalars *ms, SelScratch sc) {
@@ -306,15 +311,19 @@ __global__ void __launch_bounds__(SEL_THREADS)
     }
     __syncthreads();
     const int m0 = cr.m[0];
-    for (int i = warp; i < r1 - r0; i += nw) {
-      const int64_t e0 = cr.b[i], e1 = cr.e[i];
-      if (e0 >= e1) continue;
-      const int m = cr.m[i];
-      const unsigned long long bkey = s_bkey[i], tiny = s_tiny[i];
-      const int eb = s_eb[i];
+    // HIST_LPR lanes per row, 32 / HIST_LPR rows of the chunk per warp at a time
+    const int g = lane / HIST_LPR, gl = lane % HIST_LPR;
+    const int nr = int(r1 - r0);
+    for (int i0 = warp * (32 / HIST_LPR); i0 < nr; i0 += nw * (32 / HIST_LPR)) {
+      const int i = i0 + g;
+      const bool has = i < nr;
+      const int64_t e0 = has ? cr.b[i] : 0, e1 = has ? cr.e[i] : 0;
+      const int m = has ? cr.m[i] : m0;
+      const unsigned long long bkey = has ? s_bkey[i] : 0ULL, tiny = has ? s_tiny[i] : ~0ULL;
+      const int eb = has ? s_eb[i] : 0;
       unsigned long long *hist = m == m0 ? s_h : sc.hist0 + size_t(m) * NB0 * 2;
-      int64_t per = (e1 - e0 + 31) / 32;
-      int64_t p0 = e0 + lane * per, p1 = min(p0 + per, e1);
+      const int64_t per = (e1 - e0 + HIST_LPR - 1) / HIST_LPR;
+      const int64_t p0 = e0 + gl * per, p1 = min(p0 + per, e1);
       int cur = -1;
       unsigned long long clo = 0, chi = 0, mymin = ~0ULL;
       // four independent loads in flight, then the entries in order
@@ -346,8 +355,12 @@ __global__ void __launch_bounds__(SEL_THREADS)
         }
       }
       if (cur >= 0) add128(hist + 2 * cur, clo, chi);
-      mymin = warp_min_u64(mymin);
-      if (lane == 0 && mymin != ~0ULL) {
+#pragma unroll
+      for (int o = HIST_LPR / 2; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, mymin, o, HIST_LPR);
+        mymin = w < mymin ? w : mymin;
+      }
+      if (gl == 0 && has && mymin != ~0ULL) {
         if (m == m0)
           atomicMin(&s_min, mymin);
         else
