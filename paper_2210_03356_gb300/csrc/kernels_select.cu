@@ -251,8 +251,8 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 // memory by one thread per row, so that a warp's loop over the chunk's rows
 // waits on the values only, not on the chain row -> matrix -> scalars.
 // Rows of inactive matrices are staged empty.
-constexpr int RPC = 64;  // rows per chunk (row lists); flat values: 8 rows of kFlatRow
-__device__ __forceinline__ int64_t chunk_rows(const SelRows &R) { return R.rs ? RPC : 8; }
+constexpr int RPC = 64;  // rows per chunk (row lists); flat values: 32 rows of kFlatRow
+__device__ __forceinline__ int64_t chunk_rows(const SelRows &R) { return R.rs ? RPC : 32; }
 
 struct ChunkRows {
   int64_t b[RPC], e[RPC];
@@ -458,28 +458,29 @@ struct DropSum {
   double d = 0.0;
   __device__ __forceinline__ void add(float x) { ff_add_sq48(x, hi, lo); }
   __device__ __forceinline__ void add(double x) { d = __fma_rn(x, x, d); }
-  // the warp's total, valid in every lane
-  template <typename T>
-  __device__ __forceinline__ double warp_total() {
+  // the total over each group of W lanes (W divides 32), valid in every lane
+  template <typename T, int W>
+  __device__ __forceinline__ double group_total() {
     if constexpr (sizeof(T) == 4) {
       if (!__any_sync(0xffffffffu, hi != 0.0f)) return 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+      for (int o = W / 2; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o, W);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o, W);
         ff_add(hi, lo, h2, l2);
       }
       return ldexp(double(hi) + double(lo), -96);
     } else {
       if (!__any_sync(0xffffffffu, d != 0.0)) return 0.0;  // FP64 adds only for rows that drop
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      for (int o = W / 2; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o, W);
       return d;
     }
   }
 };
 
-constexpr int EX_U = 4;  // 32-entry chunks of a row loaded at once
+constexpr int EX_U = 4;  // entries per lane of a row loaded at once
+constexpr int FLT_LPR = 8;  // lanes per row of the candidate pass and the filter write
 
 // Candidates: the entries of the crossing bucket (top 16 bits of the key equal
 // to the prefix, 0 < key <= b), appended with one atomic per warp.
@@ -516,19 +517,26 @@ __global__ void __launch_bounds__(SEL_THREADS)
       s_tkey[t] = above == ~0ULL ? INF_KEY : above;  // tau without a crossing
     }
     __syncthreads();
-    for (int i = warp; i < r1 - r0; i += nw) {
+    // FLT_LPR lanes per row, 32 / FLT_LPR rows of the chunk per warp at a time
+    const int g = lane / FLT_LPR, gl = lane % FLT_LPR;
+    const int nr = int(r1 - r0);
+    for (int i0 = warp * (32 / FLT_LPR); i0 < nr; i0 += nw * (32 / FLT_LPR)) {
+      const int i = i0 + g;
+      const bool has = i < nr && (cnt || s_found[i] != 0);
       const int64_t r = r0 + i;
-      const bool found = s_found[i] != 0;
-      if (!cnt && !found) continue;
-      const int64_t e0 = cr.b[i], e1 = cr.e[i];  // empty for inactive matrices: 0 and 0
-      const unsigned long long bkey = s_bkey[i], top = s_top[i], tkey = s_tkey[i];
+      const bool found = has && s_found[i] != 0;
+      // empty for inactive matrices: 0 and 0 written
+      const int64_t e0 = has ? cr.b[i] : 0, e1 = has ? cr.e[i] : 0;
+      const unsigned long long bkey = has ? s_bkey[i] : 0ULL, top = has ? s_top[i] : 0ULL;
+      const unsigned long long tkey = has ? s_tkey[i] : INF_KEY;
       int c = 0;
       DropSum ds;
-      for (int64_t p0 = e0; p0 < e1; p0 += 32 * EX_U) {
+      for (int64_t p0 = e0;; p0 += FLT_LPR * EX_U) {
+        if (!__any_sync(0xffffffffu, p0 < e1)) break;  // every row of the warp done
         T x[EX_U];
 #pragma unroll
         for (int u = 0; u < EX_U; ++u) {
-          const int64_t p = p0 + 32 * u + lane;
+          const int64_t p = p0 + FLT_LPR * u + gl;
           x[u] = p < e1 ? val[p] : T(0);  // a zero is neither counted nor dropped
         }
         bool take[EX_U];
@@ -551,7 +559,6 @@ __global__ void __launch_bounds__(SEL_THREADS)
           else
             ++c;
         }
-        if (!found) continue;
 #pragma unroll
         for (int u = 0; u < EX_U; ++u) {
           const unsigned mask = __ballot_sync(0xffffffffu, take[u]);
@@ -569,9 +576,10 @@ __global__ void __launch_bounds__(SEL_THREADS)
         }
       }
       if (!cnt) continue;
-      c = __reduce_add_sync(0xffffffffu, c);
-      const double d = ds.warp_total<T>();
-      if (lane == 0) {
+#pragma unroll
+      for (int o = FLT_LPR / 2; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o, FLT_LPR);
+      const double d = ds.group_total<T, FLT_LPR>();
+      if (gl == 0 && has) {
         cnt[r] = c;
         dropped[r] = d;
       }
@@ -736,31 +744,38 @@ __global__ void __launch_bounds__(SEL_THREADS)
       s_tkey[t] = (unsigned long long)__double_as_longlong(ms[mt].tau);
     }
     __syncthreads();
-    for (int i = warp; i < r1 - r0; i += nw) {
+    // FLT_LPR lanes per row, 32 / FLT_LPR rows of the chunk per warp at a time
+    const int g = lane / FLT_LPR, gl = lane % FLT_LPR;
+    const unsigned gbits = (1u << FLT_LPR) - 1u, glt = (1u << gl) - 1u;
+    const int nr = int(r1 - r0);
+    for (int i0 = warp * (32 / FLT_LPR); i0 < nr; i0 += nw * (32 / FLT_LPR)) {
+      const int i = i0 + g;
+      const bool has = i < nr;
       // the row's room from the counts; the same rule decides both, and the
       // bound keeps a write inside the row whatever the values are
-      const unsigned long long tkey = s_tkey[i];
-      int64_t out = s_out[i];
-      const int64_t oend = s_oend[i], b = cr.b[i], e = cr.e[i];
-      for (int64_t p0 = b; p0 < e; p0 += 32 * EX_U) {
+      const unsigned long long tkey = has ? s_tkey[i] : INF_KEY;
+      int64_t out = has ? s_out[i] : 0;
+      const int64_t oend = has ? s_oend[i] : 0, b = has ? cr.b[i] : 0, e = has ? cr.e[i] : 0;
+      for (int64_t p0 = b;; p0 += FLT_LPR * EX_U) {
+        if (!__any_sync(0xffffffffu, p0 < e)) break;  // every row of the warp done
         T x[EX_U];
         int32_t c[EX_U];
 #pragma unroll
         for (int u = 0; u < EX_U; ++u) {
-          const int64_t p = p0 + 32 * u + lane;
+          const int64_t p = p0 + FLT_LPR * u + gl;
           x[u] = p < e ? val[p] : T(0);  // a zero is never kept
           c[u] = p < e ? col[p] : 0;
         }
 #pragma unroll
         for (int u = 0; u < EX_U; ++u) {
           const bool keep = keep_key(key_t<T>(x[u]), tkey);
-          const unsigned m32 = __ballot_sync(0xffffffffu, keep);
-          const int64_t pos = out + __popc(m32 & lt);
+          const unsigned gm = (__ballot_sync(0xffffffffu, keep) >> (g * FLT_LPR)) & gbits;
+          const int64_t pos = out + __popc(gm & glt);
           if (keep && pos < oend) {
             ocol[pos] = c[u];
             oval[pos] = x[u];
           }
-          out += __popc(m32);
+          out += __popc(gm);
         }
       }
     }
@@ -810,7 +825,7 @@ void launch_select_exact(int nb, const SelRows &R, int64_t cand_cap, const int *
   SGN_CUDA(cudaMemsetAsync(sc.minabove, 0xff, size_t(nb) * 8, s));
   k_sel_prepare<<<(nb + 127) / 128, 128, 0, s>>>(nb, ms);
   SGN_LAUNCH_CHECK();
-  const int64_t rpc = R.rs ? RPC : 8;
+  const int64_t rpc = R.rs ? RPC : 32;
   {
     ProfScope ps(KC_SEL_HIST, s, 0.0, 0.0);
     if (R.nrows > 0) {
