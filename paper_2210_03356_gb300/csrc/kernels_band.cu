@@ -111,42 +111,53 @@ __global__ void k_band_spans_range(int64_t n, const int32_t *lo, const int32_t *
   }
 }
 
-// One warp per row (rows with skip[r] set are left alone): the row's band
-// and pattern words are cleared, then its values scattered and its pattern
-// bits OR-ed in (one atomic per run of a word's columns).
+constexpr int FILL_LPR = 8;  // lanes per row of the band layout
+
+// FILL_LPR lanes per row (rows with skip[r] set are left alone): the row's
+// band and pattern words are cleared, then its values scattered and its
+// pattern bits OR-ed in (one atomic per run of a word's columns).
+
 __global__ void k_band_fill(int64_t n, const int64_t *rs, const int64_t *re, const int32_t *col,
                             const float *val, const int64_t *pos, const int32_t *fc,
                             const int32_t *nf, const unsigned char *skip, float *bval,
                             unsigned *bmask) {
-  const int lane = threadIdx.x & 31;
+  // FILL_LPR lanes per row, 32 / FILL_LPR rows per warp at a time
+  constexpr int L = FILL_LPR;
+  const int lane = threadIdx.x & 31, g = lane / L, gl = lane % L;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < n; r += nwarps) {
-    const int32_t w = nf[r];
-    if (w == 0 || (skip && skip[r])) continue;
-    const int64_t a = rs[r], b = re[r];
-    const int64_t p0 = pos[r];
-    const int32_t f = fc[r];
-    float4 *z = reinterpret_cast<float4 *>(bval + p0);
-    for (int t = lane; t < w / 4; t += 32) z[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-    unsigned *dm = bmask + p0 / 2 - (f >> 5);
-    for (int x = (f >> 5) + lane; x <= (f + w - 1) >> 5; x += 32) dm[x] = 0u;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t r0 = warp * (32 / L); r0 < n; r0 += nwarps * (32 / L)) {
+    const int64_t r = r0 + g;
+    const int32_t w = r < n ? nf[r] : 0;
+    const bool has = w > 0 && !(skip && skip[r]);
+    const int64_t a = has ? rs[r] : 0, b = has ? re[r] : 0;
+    const int64_t p0 = has ? pos[r] : 0;
+    const int32_t f = has ? fc[r] : 0;
+    if (has) {
+      float4 *z = reinterpret_cast<float4 *>(bval + p0);
+      for (int t = gl; t < w / 4; t += L) z[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      unsigned *dz = bmask + p0 / 2 - (f >> 5);
+      for (int x = (f >> 5) + gl; x <= (f + w - 1) >> 5; x += L) dz[x] = 0u;
+    }
     __syncwarp();
+    unsigned *dm = bmask + p0 / 2 - (f >> 5);
     float *dv = bval + p0 - f;
-    for (int64_t p = a; p < b; p += 32) {
-      const bool ok = p + lane < b;
-      int32_t c = ok ? col[p + lane] : INT_MAX;
-      if (ok) dv[c] = val[p + lane];
+    for (int64_t p = a;; p += L) {
+      if (!__any_sync(0xffffffffu, p < b)) break;  // every row of the warp done
+      const bool ok = p + gl < b;
+      int32_t c = ok ? col[p + gl] : INT_MAX;
+      if (ok) dv[c] = val[p + gl];
       int wd = ok ? (c >> 5) : INT_MAX;
       unsigned bits = ok ? (1u << (c & 31)) : 0u;
-      // suffix OR over the lanes holding the same word (columns ascend)
+      // suffix OR over the group's lanes holding the same word (columns ascend)
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        unsigned ob = __shfl_down_sync(0xffffffffu, bits, d);
-        int ow = __shfl_down_sync(0xffffffffu, wd, d);
-        if (lane + d < 32 && ow == wd) bits |= ob;
+      for (int d = 1; d < L; d <<= 1) {
+        unsigned ob = __shfl_down_sync(0xffffffffu, bits, d, L);
+        int ow = __shfl_down_sync(0xffffffffu, wd, d, L);
+        if (gl + d < L && ow == wd) bits |= ob;
       }
-      int pw = __shfl_up_sync(0xffffffffu, wd, 1);
-      if (ok && (lane == 0 || pw != wd)) atomicOr(dm + wd, bits);
+      int pw = __shfl_up_sync(0xffffffffu, wd, 1, L);
+      if (ok && (gl == 0 || pw != wd)) atomicOr(dm + wd, bits);
     }
   }
 }
@@ -518,7 +529,7 @@ void launch_band_fill(int64_t n, const Rows &R, const float *val, const int64_t 
                       const int32_t *fc, const int32_t *nf, const unsigned char *skip, float *bval,
                       unsigned *bmask, cudaStream_t s) {
   if (n == 0) return;
-  int64_t g = (n + 7) / 8;
+  int64_t g = (n + 8 * (32 / FILL_LPR) - 1) / (8 * (32 / FILL_LPR));  // 8 warps per CTA
   if (g > int64_t(sm_count_band()) * 16) g = int64_t(sm_count_band()) * 16;
   k_band_fill<<<unsigned(g), 256, 0, s>>>(n, R.rs, R.re, R.col, val, pos, fc, nf, skip, bval,
                                           bmask);
