@@ -258,22 +258,35 @@ __global__ void k_asm_lens(int nblocks, const AsmBlock *blocks, const int64_t *b
 
 __global__ void k_asm_vals(int nblocks, const AsmBlock *blocks, const int64_t *boff, int64_t n,
                            const int64_t *drp, int32_t *dcol, void *dval, int dst_f32) {
-  int lane = lane_id();
-  for_each_row_warp(n, [&](int64_t r) {
+  // 8 lanes per row, four rows per warp at a time (rows are short)
+  constexpr int L = 8;
+  const int lane = lane_id(), gl = lane % L;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = warp * (32 / L) + lane / L; r < n; r += nwarps * (32 / L)) {
     int b = find_block(boff, nblocks, r);
     const AsmBlock B = blocks[b];
     int64_t sr = B.row0 + (r - boff[b]);
-    int64_t sb = B.rp[sr], se = B.rp[sr + 1], d = drp[r];
-    for (int64_t p = sb + lane; p < se; p += 32) {
-      dcol[d + (p - sb)] = int32_t(B.col[p] + B.col_shift);
-      double v = B.val_f32 ? double(static_cast<const float *>(B.val)[p])
-                           : static_cast<const double *>(B.val)[p];
-      if (dst_f32)
-        static_cast<float *>(dval)[d + (p - sb)] = __double2float_rn(v);
-      else
-        static_cast<double *>(dval)[d + (p - sb)] = v;
+    int64_t sb = B.rp[sr], se = B.rp[sr + 1], d = drp[r] - sb;
+    if (B.val_f32 && dst_f32) {  // FP32 to FP32: the values as they are
+      const float *sv = static_cast<const float *>(B.val);
+      float *dv = static_cast<float *>(dval);
+      for (int64_t p = sb + gl; p < se; p += L) {
+        dcol[d + p] = int32_t(B.col[p] + B.col_shift);
+        dv[d + p] = sv[p];
+      }
+    } else {
+      for (int64_t p = sb + gl; p < se; p += L) {
+        dcol[d + p] = int32_t(B.col[p] + B.col_shift);
+        double v = B.val_f32 ? double(static_cast<const float *>(B.val)[p])
+                             : static_cast<const double *>(B.val)[p];
+        if (dst_f32)
+          static_cast<float *>(dval)[d + p] = __double2float_rn(v);
+        else
+          static_cast<double *>(dval)[d + p] = v;
+      }
     }
-  });
+  }
 }
 
 __global__ void k_fill_seg(int nb, const int64_t *moff, int64_t n, int32_t *seg) {
@@ -535,8 +548,8 @@ void launch_assemble_vals(int nblocks, const AsmBlock *blocks, const int64_t *bo
                           const int64_t *dst_rp, int32_t *dst_col, void *dst_val, int dst_f32,
                           cudaStream_t s) {
   if (n_dst == 0) return;
-  k_asm_vals<<<grid_for(n_dst, 8), 256, 0, s>>>(nblocks, blocks, boff, n_dst, dst_rp, dst_col,
-                                                 dst_val, dst_f32);
+  k_asm_vals<<<grid_for(n_dst, 32), 256, 0, s>>>(nblocks, blocks, boff, n_dst, dst_rp, dst_col,
+                                                  dst_val, dst_f32);
   SGN_LAUNCH_CHECK();
 }
 
