@@ -469,7 +469,7 @@ struct DropSum {
         const float l2 = __shfl_xor_sync(0xffffffffu, lo, o, W);
         ff_add(hi, lo, h2, l2);
       }
-      return ldexp(double(hi) + double(lo), -96);
+      return (double(hi) + double(lo)) * 0x1p-96;  // exact scaling, one rounding as ldexp
     } else {
       if (!__any_sync(0xffffffffu, d != 0.0)) return 0.0;  // FP64 adds only for rows that drop
 #pragma unroll
@@ -695,7 +695,7 @@ __global__ void k_filter_count(int64_t n, const int32_t *seg, const int *active,
           const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
           ff_add(hi, lo, h2, l2);
         }
-        if (lane == 0) d2 = ldexp(double(hi) + double(lo), -96);
+        if (lane == 0) d2 = (double(hi) + double(lo)) * 0x1p-96;  // exact scaling, one rounding as ldexp
       }
     } else if (active[m]) {
       const double *v = static_cast<const double *>(val);

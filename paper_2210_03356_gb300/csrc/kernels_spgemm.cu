@@ -865,24 +865,34 @@ template <typename T>
 __global__ void k_rows_empty(int64_t n, const int64_t *ars, const int64_t *are, const T *aval,
                              const int32_t *len, const int64_t *cs, int64_t *ce, double *part) {
   int lane = lane_id();
+  const int g = lane >> 3, gl = lane & 7;  // four groups of 8 lanes
   int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  // a lane per row finds the empty ones, 32 at a time; the warp serves each
+  // a lane per row finds the empty ones, 32 at a time; the warp's four groups
+  // of 8 lanes serve them four at a time
   for (int64_t r0 = warp * 32; r0 < n; r0 += nwarps * 32) {
     unsigned empty = __ballot_sync(0xffffffffu, r0 + lane < n && len[r0 + lane] == 0);
     while (empty) {
-      const int64_t r = r0 + (__ffs(empty) - 1);
-      empty &= empty - 1;
-      if (lane == 0) ce[r] = cs[r];
+      int my = -1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!empty) break;
+        if (k == g) my = __ffs(empty) - 1;
+        empty &= empty - 1;
+      }
+      const bool has = my >= 0;
+      const int64_t r = r0 + (has ? my : 0);
+      if (has && gl == 0) ce[r] = cs[r];
       if (!part) continue;
       double xs = 0.0;
-      for (int64_t p = ars[r] + lane; p < are[r]; p += 32) {
-        double x = double(aval[p]);
-        xs += x * x;
-      }
+      if (has)
+        for (int64_t p = ars[r] + gl; p < are[r]; p += 8) {
+          double x = double(aval[p]);
+          xs += x * x;
+        }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, o);
-      if (lane == 0) {
+      for (int o = 4; o > 0; o >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, o, 8);
+      if (has && gl == 0) {
         part[2 * r] = 1.0;
         part[2 * r + 1] = xs;
       }
