@@ -19,6 +19,20 @@ __device__ __forceinline__ void for_each_row_warp(int64_t n, F f) {
   for (int64_t r = warp; r < n; r += nwarps) f(r);
 }
 
+// Rows taken by groups of 8 lanes, four rows per warp at a time: for short
+// rows (an input A has a few to a few tens of entries per row). f(r, has, gl)
+// is called by every lane of the warp, has = false for a group without a row.
+template <typename F>
+__device__ __forceinline__ void for_each_row_group8(int64_t n, F f) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r0 = warp * 4; r0 < n; r0 += nwarps * 4) {
+    const int64_t r = r0 + (lane >> 3);
+    f(r < n ? r : r0, r < n, lane & 7);
+  }
+}
+
 int grid_for(int64_t items, int per_block, int cap = 152 * 16) {
   int64_t g = (items + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -310,13 +324,13 @@ __device__ __forceinline__ void add128(unsigned long long *lohi, unsigned long l
 
 __global__ void k_absmax(int64_t n, const int32_t *seg, const int64_t *rp, const double *val,
                          unsigned long long *mmax) {
-  int lane = lane_id();
-  for_each_row_warp(n, [&](int64_t r) {
+  for_each_row_group8(n, [&](int64_t r, bool has, int gl) {
     double m = 0.0;
-    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) m = fmax(m, fabs(val[p]));
+    if (has)
+      for (int64_t p = rp[r] + gl; p < rp[r + 1]; p += 8) m = fmax(m, fabs(val[p]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0 && m > 0.0)
+    for (int o = 4; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o, 8));
+    if (has && gl == 0 && m > 0.0)
       atomicMax(&mmax[seg[r]], (unsigned long long)__double_as_longlong(m));
   });
 }
@@ -324,13 +338,13 @@ __global__ void k_absmax(int64_t n, const int32_t *seg, const int64_t *rp, const
 __global__ void k_colsum(int64_t n, const int32_t *seg, const int64_t *rp, const int32_t *col,
                          const double *val, const unsigned long long *mmax,
                          unsigned long long *colsum) {
-  int lane = lane_id();
-  for_each_row_warp(n, [&](int64_t r) {
+  for_each_row_group8(n, [&](int64_t r, bool has, int gl) {
+    if (!has) return;
     double M = __longlong_as_double((long long)mmax[seg[r]]);
     if (M == 0.0) return;
     int e;
     frexp(M, &e);
-    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) {
+    for (int64_t p = rp[r] + gl; p < rp[r + 1]; p += 8) {
       unsigned long long q = __double2ull_rn(ldexp(fabs(val[p]), 62 - e));
       if (q) add128(&colsum[2 * int64_t(col[p])], q);
     }
@@ -370,10 +384,10 @@ __global__ void k_norm_final(int nb, const unsigned long long *mmax,
 
 __global__ void k_scale(int64_t n, const int32_t *seg, const int64_t *rp, double *val,
                         const double *norm) {
-  int lane = lane_id();
-  for_each_row_warp(n, [&](int64_t r) {
+  for_each_row_group8(n, [&](int64_t r, bool has, int gl) {
+    if (!has) return;
     double s = norm[seg[r]];
-    for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) val[p] = __ddiv_rn(val[p], s);
+    for (int64_t p = rp[r] + gl; p < rp[r + 1]; p += 8) val[p] = __ddiv_rn(val[p], s);
   });
 }
 
@@ -568,9 +582,9 @@ void launch_onenorm(int nb, const int64_t *moff, const int32_t *seg, int64_t n, 
   unsigned long long *maxhi = mmax + nb;        // nb
   unsigned long long *maxlo = maxhi + nb;       // nb
   SGN_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned long long) * size_t(2 * n + 3 * nb), s));
-  k_absmax<<<grid_for(n, 8), 256, 0, s>>>(n, seg, rp, val, mmax);
+  k_absmax<<<grid_for(n, 32), 256, 0, s>>>(n, seg, rp, val, mmax);
   SGN_LAUNCH_CHECK();
-  k_colsum<<<grid_for(n, 8), 256, 0, s>>>(n, seg, rp, col, val, mmax, colsum);
+  k_colsum<<<grid_for(n, 32), 256, 0, s>>>(n, seg, rp, col, val, mmax, colsum);
   SGN_LAUNCH_CHECK();
   k_colmax_hi<<<grid_for(n, 256), 256, 0, s>>>(n, seg, colsum, maxhi);
   SGN_LAUNCH_CHECK();
@@ -582,7 +596,7 @@ void launch_onenorm(int nb, const int64_t *moff, const int32_t *seg, int64_t n, 
 
 void launch_scale(int64_t n, const int32_t *seg, const int64_t *rp, double *val,
                   const double *norm, cudaStream_t s) {
-  k_scale<<<grid_for(n, 8), 256, 0, s>>>(n, seg, rp, val, norm);
+  k_scale<<<grid_for(n, 32), 256, 0, s>>>(n, seg, rp, val, norm);
   SGN_LAUNCH_CHECK();
 }
 
