@@ -64,19 +64,19 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t *rp, const int3
   });
 }
 
-// The same checks for a batch of matrices in one launch: a warp per row of
+// The same checks for a batch of matrices in one launch: 8 lanes per row of
 // all of them (row_off: exclusive prefix of the row counts), the matrix
 // found by binary search; thread m also checks matrix m's first and last
 // row pointer.
 __global__ void k_validate_batch(int count, const ValidateJob *jobs, const int64_t *row_off,
                                  int *flags) {
-  const int lane = lane_id();
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (tid < count) {
     const ValidateJob &j = jobs[tid];
     if (j.rp[0] != 0 || j.rp[j.n] != j.nnz) atomicOr(flags + tid, 1);
   }
-  for_each_row_warp(row_off[count], [&](int64_t g) {
+  for_each_row_group8(row_off[count], [&](int64_t g, bool has, int gl) {
+    if (!has) return;
     int lo = 0, hi = count - 1;  // the last matrix whose first row is <= g
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -86,17 +86,17 @@ __global__ void k_validate_batch(int count, const ValidateJob *jobs, const int64
     const int64_t r = g - row_off[lo];
     const int64_t b = j.rp[r], e = j.rp[r + 1];
     if (e < b || b < 0 || e > j.nnz) {
-      if (lane == 0) atomicOr(flags + lo, 1);
+      if (gl == 0) atomicOr(flags + lo, 1);
       return;
     }
     bool bad = false;
-    for (int64_t p = b + lane; p < e; p += 32) {
+    for (int64_t p = b + gl; p < e; p += 8) {
       const int32_t c = j.col[p];
       if (c < 0 || c >= j.n) bad = true;
       if (p > b && j.col[p - 1] >= c) bad = true;
       if (!isfinite(j.val[p])) bad = true;
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags + lo, 1);
+    if (bad) atomicOr(flags + lo, 1);
   });
 }
 
@@ -523,7 +523,7 @@ void launch_validate_batch(int count, const ValidateJob *jobs, const int64_t *ro
                            int64_t total_rows, int *flags, cudaStream_t s) {
   if (count < 1) return;
   const int64_t items = total_rows > count ? total_rows : count;
-  k_validate_batch<<<grid_for(items, 8), 256, 0, s>>>(count, jobs, row_off, flags);
+  k_validate_batch<<<grid_for(items, 32), 256, 0, s>>>(count, jobs, row_off, flags);
   SGN_LAUNCH_CHECK();
 }
 
