@@ -269,9 +269,11 @@ sign_status sign_threshold_exact(const double *val, int64_t nnz, double b, int o
  * Scratch lives in one file-scope device array (about 12 MiB per GPU that
  * loads the library, held until exit). The first call on each device, made
  * with that device current, looks up the array's address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array: calls that overlap on the GPU race, so the
- * caller must serialize them. Returns after cuda_stream has finished. */
+ * (cudaGetSymbolAddress). No call can be captured into a CUDA graph: each
+ * copies its small inputs and the threshold through host memory and waits
+ * for cuda_stream. All calls share the array: calls that overlap on the GPU
+ * race, so the caller must serialize them. Returns after cuda_stream has
+ * finished. */
 #define SIGN_NOALLOC_MAX_NNZ ((int64_t)1 << 20)
 sign_status sign_threshold_exact_noalloc(const double *val, int64_t nnz, double b,
                                          void *cuda_stream, double *tau_out);

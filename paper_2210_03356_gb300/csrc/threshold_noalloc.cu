@@ -12,10 +12,11 @@
 // The array (about 12 MiB) exists on every GPU that loads this library until
 // the process exits. Its host-side name is only a stand-in: the device
 // address is looked up once per device with cudaGetSymbolAddress, with that
-// device current, on the first call made while it is current; that first
-// call should therefore come before any stream capture. Every call reuses the
-// same array, so calls that overlap on the GPU (other streams, other host
-// threads on the same device) race and must be serialized by the caller.
+// device current, on the first call made while it is current. No call can
+// be captured into a CUDA graph: each copies its small inputs and the result
+// through host memory and waits for the stream. Every call reuses the same
+// array, so calls that overlap on the GPU (other streams, other host threads
+// on the same device) race and must be serialized by the caller.
 #include <cmath>
 #include <cstring>
 #include <mutex>
