@@ -45,6 +45,14 @@ def _ptr(x):
     return x.ctypes.data_as(C.c_void_p)
 
 
+def _addr(x) -> int:
+    """The address of a torch tensor's or numpy array's data, as an int (for
+    filling pointer arrays of a batch without one ctypes object per array)."""
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.__array_interface__["data"][0]
+
+
 def current_stream():
     """The torch current CUDA stream handle, or None (legacy default stream)."""
     try:
@@ -320,9 +328,9 @@ class Batch:
         k = len(mats)
         ns = (C.c_int64 * k)(*[int(a.n) for a in mats])
         nnzs = (C.c_int64 * k)(*[int(rp[-1]) for rp, _, _ in keep])
-        rps = (C.c_void_p * k)(*[_ptr(t[0]) for t in keep])
-        cols = (C.c_void_p * k)(*[_ptr(t[1]) for t in keep])
-        vals = (C.c_void_p * k)(*[_ptr(t[2]) for t in keep])
+        rps = (C.c_void_p * k)(*[_addr(t[0]) for t in keep])
+        cols = (C.c_void_p * k)(*[_addr(t[1]) for t in keep])
+        vals = (C.c_void_p * k)(*[_addr(t[2]) for t in keep])
         out = (N.sign_t * k)()
         st = L.sign_create_batch(k, ns, nnzs, rps, cols, vals, int(on_dev[0]), stream, out)
         if st != SIGN_OK:
@@ -382,9 +390,9 @@ class Batch:
                                  "float64[nnz]")
             views.append((rp[:h.n + 1], col[:nnz], val[:nnz]))
         k = len(outs)
-        rps = (C.c_void_p * k)(*[_ptr(o[0]) for o in outs])
-        cols = (C.c_void_p * k)(*[_ptr(o[1]) for o in outs])
-        vals = (C.c_void_p * k)(*[_ptr(o[2]) for o in outs])
+        rps = (C.c_void_p * k)(*[_addr(o[0]) for o in outs])
+        cols = (C.c_void_p * k)(*[_addr(o[1]) for o in outs])
+        vals = (C.c_void_p * k)(*[_addr(o[2]) for o in outs])
         st = load().sign_get_csr_batch(k, self.arr, rps, cols, vals, 0)
         if st != SIGN_OK:
             raise SignError(st, "sign_get_csr_batch")
