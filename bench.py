@@ -246,9 +246,10 @@ def serve_pool(seed: int = w.BASE_SEED + 4000, size: int = 160):
     return pool, weights / weights.sum()
 
 
-def serve_leg(sg, rates, seconds: float, seed: int = 7):
+def serve_leg(sg, rates, seconds: float, seed: int = 7, max_wait_s: float = 0.0):
     """Open-loop Poisson stream per rate through a fresh server; latency is
-    completion minus scheduled arrival (both CLOCK_MONOTONIC)."""
+    completion minus scheduled arrival (both CLOCK_MONOTONIC). max_wait_s > 0:
+    the server refuses (SIGN_EAGAIN) submissions predicted to wait longer."""
     pool, p = serve_pool()
     rng = np.random.default_rng(seed)
     opts = sg.default_opts(tol=TOL, filter="exact", prec="mixed")
@@ -261,8 +262,8 @@ def serve_leg(sg, rates, seconds: float, seed: int = 7):
         k = max(1, int(rng.poisson(rate * seconds)))
         arrivals = np.cumsum(rng.exponential(1.0 / rate, k))
         picks = rng.choice(len(pool), size=k, p=p)
-        tickets, refused, t_arr = [], 0, []
-        with sg.Server(opts) as srv:
+        tickets, refused, late, t_arr = [], 0, 0, []
+        with sg.Server(opts, max_wait_s=max_wait_s) as srv:
             t0 = time.monotonic() + 0.05
             for at, i in zip(arrivals, picks):
                 wait = t0 + at - time.monotonic()
@@ -272,7 +273,9 @@ def serve_leg(sg, rates, seconds: float, seed: int = 7):
                     tickets.append(srv.submit(pool[i]))
                     t_arr.append(t0 + at)
                 except sg.SignError as e:
-                    if e.status != sg.SIGN_ENOMEM:
+                    if e.status == sg.SIGN_EAGAIN:
+                        late += 1
+                    elif e.status != sg.SIGN_ENOMEM:
                         raise
                     refused += 1
             lat, done, lanes, bad = [], [], [], 0
@@ -295,6 +298,7 @@ def serve_leg(sg, rates, seconds: float, seed: int = 7):
                     "p99_ms": float(np.percentile(x, 99)), "mean_ms": float(x.mean())}
 
         row = {"rate_req_per_s": rate, "requests": k, "refused": refused,
+               "refused_for_wait": late,
                "completed": len(tickets), "not_converged": int(bad),
                "solves_per_s": len(tickets) / span if done else 0.0,
                "max_active_seen": st["max_active_seen"], "rounds": st["rounds"]}
@@ -305,7 +309,7 @@ def serve_leg(sg, rates, seconds: float, seed: int = 7):
     return {"mix": SERVE_MIX, "seconds_per_rate": seconds, "mem_budget_bytes": 120e9,
             "lanes": "2: requests predicted to fill in (no Gershgorin gap) on a lane of their own",
             "latency": "completion minus scheduled arrival, both on CLOCK_MONOTONIC",
-            "rates": out}
+            "max_wait_s": max_wait_s, "rates": out}
 
 
 # ---------------------------------------------------------------------- fill tracking
@@ -977,6 +981,9 @@ def main():
     if args.legs == "all" and args.serve_seconds > 0 and rank == 0:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
         line["serving"] = serve_leg(sg, rates, args.serve_seconds)
+        # past capacity with a latency target: refusals instead of a growing queue
+        line["serving_latency_target"] = serve_leg(sg, [rates[-1]], args.serve_seconds,
+                                                   max_wait_s=0.25)
     if args.fill_iters > 0 and rank == 0:
         line["laplacian2d_fill"] = fill_leg(sg, args.fill_iters)
     if args.laplacian2d and rank == 0:

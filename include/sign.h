@@ -55,7 +55,8 @@ typedef enum {
   SIGN_ECUDA = 5,     /* a CUDA runtime call failed                          */
   SIGN_ETIMEOUT = 6,  /* a bounded wait of a tensor-core kernel gave up     */
   SIGN_ESTATE = 7,    /* call out of order (e.g. sign_get_csr before solve)  */
-  SIGN_EAGAIN = 8     /* server: the request has not finished yet            */
+  SIGN_EAGAIN = 8     /* server: the request has not finished yet, or a
+                         submission was refused for its predicted wait        */
 } sign_status;
 
 typedef enum {
@@ -347,6 +348,12 @@ typedef struct {
                         Gershgorin gap, or w >= n/4 in the model above) a
                         worker, solver and stream of their own, the other
                         lane's stream having the higher priority (2)      */
+  double max_wait_s; /* latency target: a submission whose predicted wait
+                        for admission exceeds this many seconds is refused
+                        with SIGN_EAGAIN. The prediction is the requests
+                        queued ahead on its lane divided by that lane's
+                        completion rate over its last 64 completions (no
+                        prediction before 8); 0 = no target (0)          */
 } sign_server_opts;
 
 typedef struct {
@@ -378,8 +385,9 @@ sign_status sign_server_create(const sign_server_opts *o, sign_server_t *out);
 /* Copies a CSR matrix (the arguments of sign_create) and queues it. Returns
  * after the copy: the caller may reuse its arrays at once. *ticket names the
  * request. SIGN_EINVAL for malformed input, SIGN_ENOMEM when the predicted
- * footprint exceeds mem_budget or max_queue requests are waiting (the
- * request is then refused and has no ticket). */
+ * footprint exceeds mem_budget or max_queue requests are waiting, SIGN_EAGAIN
+ * when its predicted wait exceeds max_wait_s (the request is then refused
+ * and has no ticket). */
 sign_status sign_server_submit(sign_server_t srv, int64_t n, int64_t nnz, const int64_t *rowptr,
                                const int32_t *col, const double *val, int on_device,
                                uint64_t *ticket);

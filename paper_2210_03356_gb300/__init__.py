@@ -427,7 +427,7 @@ class Server:
     """
 
     def __init__(self, opts=None, mem_budget: float = 120e9, max_active: int = 1024,
-                 max_queue: int = 65536, lanes: int = 2, **kw):
+                 max_queue: int = 65536, lanes: int = 2, max_wait_s: float = 0.0, **kw):
         L = load()
         so = N.sign_server_opts()
         L.sign_server_default_opts(C.byref(so))
@@ -441,6 +441,7 @@ class Server:
                                         for k, v in kw.items()})
         so.mem_budget, so.max_active, so.max_queue = float(mem_budget), int(max_active), int(max_queue)
         so.lanes = int(lanes)
+        so.max_wait_s = float(max_wait_s)
         self.opts = so
         self.h = C.c_void_p()
         st = L.sign_server_create(C.byref(so), C.byref(self.h))
@@ -449,7 +450,8 @@ class Server:
         self._n = {}
 
     def submit(self, a) -> int:
-        """Queues matrix a (host numpy or CUDA torch CSR); raises SignError if refused."""
+        """Queues matrix a (host numpy or CUDA torch CSR); raises SignError if refused
+        (status SIGN_EAGAIN when its predicted wait exceeds max_wait_s)."""
         on_dev = _is_torch_cuda(a.val)
         if on_dev:
             keep = (a.rowptr.contiguous(), a.col.contiguous(), a.val.contiguous())

@@ -47,7 +47,7 @@ class sign_info(C.Structure):
 
 class sign_server_opts(C.Structure):
     _fields_ = [("solve", sign_opts), ("mem_budget", C.c_double), ("max_active", C.c_int),
-                ("max_queue", C.c_int), ("lanes", C.c_int)]
+                ("max_queue", C.c_int), ("lanes", C.c_int), ("max_wait_s", C.c_double)]
 
 
 class sign_request_times(C.Structure):

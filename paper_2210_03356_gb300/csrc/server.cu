@@ -47,6 +47,15 @@ struct Lane {
   std::deque<Request *> queue;
   std::unordered_map<int, Request *> by_mat;  // solver id -> request on the GPU
   int64_t active = 0;
+  std::deque<double> done_t;  // times of the last 64 completions (the rate estimate)
+  // Predicted wait for admission of a request queued now: the requests
+  // ahead of it over the lane's recent completion rate; -1 before 8 completions.
+  double predicted_wait() const {
+    if (done_t.size() < 8) return -1.0;
+    const double span = done_t.back() - done_t.front();
+    if (!(span > 0.0)) return 0.0;
+    return double(queue.size()) * span / double(done_t.size() - 1);
+  }
 };
 
 double now_s() {
@@ -93,6 +102,8 @@ void sign_server_s::finish(Lane &L, Request *r, const MatState *ms, int status) 
   }
   r->info.nnz_final = r->h->has_result ? r->h->result.nnz : 0;
   r->t.t_done = now_s();
+  L.done_t.push_back(r->t.t_done);
+  if (L.done_t.size() > 64) L.done_t.pop_front();
   r->state = RQ_DONE;
   L.active--;
   st.active--;
@@ -217,6 +228,7 @@ void sign_server_default_opts(sign_server_opts *o) {
   o->max_active = 1024;
   o->max_queue = 65536;
   o->lanes = 2;
+  o->max_wait_s = 0.0;
 }
 
 static sign_status server_create(const sign_server_opts *o, sign_server_t *out);
@@ -255,8 +267,9 @@ static sign_status server_create(const sign_server_opts *o, sign_server_t *out) 
   if (!o) return set_last_error("opts is NULL"), SIGN_EINVAL;
   if (!check_opts(&o->solve, why)) return set_last_error(why), SIGN_EINVAL;
   if (!(o->mem_budget > 0.0) || o->max_active < 1 || o->max_queue < 1 || o->lanes < 1 ||
-      o->lanes > 2)
-    return set_last_error("need mem_budget > 0, max_active >= 1, max_queue >= 1, lanes 1 or 2"),
+      o->lanes > 2 || !(o->max_wait_s >= 0.0))
+    return set_last_error("need mem_budget > 0, max_active >= 1, max_queue >= 1, lanes 1 or 2, "
+                          "max_wait_s >= 0"),
            SIGN_EINVAL;
   auto S = std::make_unique<sign_server_s>();
   S->o = *o;
@@ -337,17 +350,23 @@ static sign_status server_submit(sign_server_t S, int64_t n, int64_t nnz, const 
   {
     std::lock_guard<std::mutex> lk(S->mu);
     S->st.submitted++;
-    if (S->stop || fp > S->o.mem_budget || S->queued() >= S->o.max_queue) {
+    const double wait = S->o.max_wait_s > 0.0 ? S->lanes[lane]->predicted_wait() : -1.0;
+    const bool full = fp > S->o.mem_budget || S->queued() >= S->o.max_queue;
+    const bool late = S->o.max_wait_s > 0.0 && wait > S->o.max_wait_s;
+    if (S->stop || full || late) {
       S->st.refused++;
       if (S->stop)
         std::snprintf(msg, sizeof msg, "server is stopping");
       else if (fp > S->o.mem_budget)
         std::snprintf(msg, sizeof msg, "predicted footprint %.3g bytes exceeds mem_budget %.3g",
                       fp, S->o.mem_budget);
-      else
+      else if (full)
         std::snprintf(msg, sizeof msg, "%d requests already waiting (max_queue)",
                       S->o.max_queue);
-      refused = S->stop ? SIGN_ESTATE : SIGN_ENOMEM;
+      else
+        std::snprintf(msg, sizeof msg, "predicted wait %.3g s exceeds max_wait_s %.3g", wait,
+                      S->o.max_wait_s);
+      refused = S->stop ? SIGN_ESTATE : full ? SIGN_ENOMEM : SIGN_EAGAIN;
     } else {
       r->h = h;
       r->t.t_submit = now_s();

@@ -135,6 +135,33 @@ def test_refusals_and_invalid_requests(sg):
     assert st["submitted"] == 3 and st["refused"] == 1 and st["completed"] == 2
 
 
+def test_latency_target_refuses_with_eagain(sg):
+    """max_wait_s: once a lane has a completion rate (8 completions), a
+    submission whose predicted wait (queued ahead / rate) exceeds the target
+    is refused with SIGN_EAGAIN; what is admitted still solves as alone."""
+    with pytest.raises(sg.SignError):
+        sg.Server(max_wait_s=-1.0)
+    mats = [w.banded(int(n), 4, 50 + i) for i, n in enumerate(np.linspace(600, 1400, 24))]
+    with sg.Server(tol=1e-8, filter="exact", prec="mixed", lanes=1, max_active=4,
+                   max_wait_s=1e-4) as srv:
+        first = [srv.submit(a) for a in mats[:10]]  # no rate yet: never refused
+        for t in first:
+            assert srv.poll(t, wait_ms=60000)["status"] == sg.SIGN_OK
+        taken, refused = [], 0
+        for a in mats * 8:  # a burst: at most 4 on the GPU, the rest queues
+            try:
+                taken.append((srv.submit(a), a))
+            except sg.SignError as e:
+                assert e.status == sg.SIGN_EAGAIN and "max_wait_s" in str(e)
+                refused += 1
+        assert refused > 0 and taken
+        for t, a in taken[:6]:
+            assert srv.poll(t, wait_ms=60000)["status"] == sg.SIGN_OK
+            _same(sg.solve(a, tol=1e-8, filter="exact", prec=1), *srv.take(t))
+        st = srv.stats()
+    assert st["refused"] == refused
+
+
 def test_trim_after_a_destroyed_server(sg):
     """Blocks freed on this thread for a server's upload stream outlive the
     stream; trimming afterwards must not use it, and solving still works."""
