@@ -81,7 +81,7 @@ struct SelScratch {
 static_assert(sizeof(SelState) <= kSelStateBytes, "select state outgrew its scratch slot");
 static_assert(NB0 == 1024 && NDIG == 256, "scratch layout in kernels.h assumes these sizes");
 
-__host__ __device__ inline size_t align_up(size_t x) { return sel_align(x); }
+inline size_t align_up(size_t x) { return sel_align(x); }
 
 SelScratch carve(void *base, int nb, int64_t cap) {
   char *p = static_cast<char *>(base);
@@ -154,11 +154,6 @@ template <>
 __device__ __forceinline__ unsigned long long key_t<float>(float x) { return key_f32(x); }
 template <>
 __device__ __forceinline__ unsigned long long key_t<double>(double x) { return key_f64(x); }
-
-__device__ __forceinline__ unsigned long long key_of(const void *val, int f32, int64_t p) {
-  return f32 ? key_f32(static_cast<const float *>(val)[p])
-             : key_f64(static_cast<const double *>(val)[p]);
-}
 
 // (hi, lo) += x^2 for FP32 x, exactly: the square's rounding error comes from
 // an FMA and the sum's from TwoSum; all in FP32, which this GPU runs at 64x
@@ -236,15 +231,6 @@ __device__ __forceinline__ int bucket0(unsigned long long key, unsigned long lon
   long long t = (long long)(key >> 48);
   if (base < 0) base = 0;
   return t <= base ? 0 : int(t - base);
-}
-
-// The smallest of the lanes' 64-bit values: the high words' minimum, then the
-// minimum of the low words among the lanes holding it (two warp reductions).
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
-  const unsigned hi = unsigned(v >> 32);
-  const unsigned mh = __reduce_min_sync(0xffffffffu, hi);
-  const unsigned ml = __reduce_min_sync(0xffffffffu, hi == mh ? unsigned(v) : 0xffffffffu);
-  return ((unsigned long long)mh << 32) | ml;
 }
 
 // A chunk of consecutive rows, their extents and matrices staged in shared
@@ -730,7 +716,6 @@ __global__ void __launch_bounds__(SEL_THREADS)
   __shared__ int64_t s_out[RPC], s_oend[RPC];
   __shared__ unsigned long long s_tkey[RPC];
   const int lane = lane_id(), warp = threadIdx.x >> 5, nw = SEL_THREADS / 32;
-  const unsigned lt = (1u << lane) - 1u;
   const SelRows R{n, seg, rs, re, 0};
   const int64_t nchunks = (n + RPC - 1) / RPC;
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
